@@ -1,0 +1,168 @@
+"""Seeded synthetic post-bounce profiles for the MGFLD transport step.
+
+This module only manufactures inputs (numpy arrays); it contains none of the
+transport arithmetic.  Both the CUDA path and the CPU oracle consume the arrays
+it returns.
+
+Profile family (one radial ray; r in cm, rho in g/cm^3, T = kT in MeV):
+  * N_r + 1 radial edges log-spaced from 10 km to 1e4 km;
+  * rho = 3e14 (r/10 km)^-3 (1 + d_rho) floored at 1e6,
+    T = 30 (r/10 km)^-1 (1 + d_T) floored at 0.1,
+    Ye rising from 0.1 to 0.5 linearly in log r; sampled at zone midpoints;
+  * d_rho, d_T: per-ray angular perturbations 0.05 * sum_{l=1..8} sum_m c_lm Y_lm
+    normalised to a maximum of 0.05, with c_lm ~ N(0,1) (axisymmetric m = 0 for
+    2D ray sets on theta_j = (j + 1/2) pi / N_ray; real Y_lm for 3D sets on a
+    theta x phi grid of cell centres);
+  * N_E + 1 energy edges log-spaced from 2 to 250 MeV (energies at infinity);
+  * kappa_abs = kappa_scat = 1e-40 rho e_g^2 /cm with iid lognormal(0, 0.2)
+    noise per (ray, zone, group) shared by the four species, where e_g is the
+    geometric mean of the group's edges;
+  * NES kernel scale 1e-41 rho (cm^3/s), the synthetic neutrino-electron
+    scattering strength;
+  * initial occupation psi0 = 1/(1 + exp(e_g/T)) (Fermi-Dirac, zero chemical
+    potential) for all species.
+Seeds are 1809_05608 + 1000 * config + field, so every ray subset of a
+configuration sees exactly the values of the full configuration.
+"""
+from __future__ import annotations
+
+import dataclasses
+
+import numpy as np
+
+KM = 1.0e5
+BASE_SEED = 180905608
+N_SPECIES = 4
+
+FIELD_RHO, FIELD_T, FIELD_KAPPA = 1, 2, 3
+
+
+@dataclasses.dataclass(frozen=True)
+class ConfigSpec:
+    name: str
+    n_ray: int
+    n_r: int
+    n_e: int
+    steps: int
+    geometry: str            # '1d', '2d' or '3d'
+    precision: str           # 'fp64' or 'mixed'
+    tol: float
+    n_theta: int = 0         # 3D only
+    n_phi: int = 0
+
+
+CONFIGS = {
+    1: ConfigSpec('single-ray 64x12 fp64', 1, 64, 12, 1, '1d', 'fp64', 1e-13),
+    2: ConfigSpec('2d 256 rays 512x20 fp64', 256, 512, 20, 10, '2d', 'fp64', 1e-13),
+    3: ConfigSpec('2d 1024 rays 512x20 mixed', 1024, 512, 20, 20, '2d', 'mixed', 1e-10),
+    4: ConfigSpec('3d 64x64 rays 540x20 mixed', 4096, 540, 20, 10, '3d', 'mixed', 1e-10, 64, 64),
+    5: ConfigSpec('adjoint 512 rays 512x20', 512, 512, 20, 20, '2d', 'mixed', 1e-10),
+}
+
+
+def _seed(config: int, field: int) -> int:
+    return BASE_SEED + 1000 * config + field
+
+
+def _legendre_p(l, m, x):
+    """Associated Legendre P_l^m(x) by the standard upward recurrence (unnormalised)."""
+    pmm = np.ones_like(x)
+    if m > 0:
+        somx2 = np.sqrt((1.0 - x) * (1.0 + x))
+        fact = 1.0
+        for _ in range(m):
+            pmm = -pmm * fact * somx2
+            fact += 2.0
+    if l == m:
+        return pmm
+    pmmp1 = x * (2 * m + 1) * pmm
+    if l == m + 1:
+        return pmmp1
+    pll = pmmp1
+    for ll in range(m + 2, l + 1):
+        pll = (x * (2 * ll - 1) * pmmp1 - (ll + m - 1) * pmm) / (ll - m)
+        pmm, pmmp1 = pmmp1, pll
+    return pll
+
+
+def angular_perturbation(spec: ConfigSpec, config: int, field: int) -> np.ndarray:
+    """Per-ray relative perturbation in [-0.05, 0.05] (l = 1..8 harmonics)."""
+    if spec.geometry == '1d':
+        return np.zeros(spec.n_ray)
+    rng = np.random.default_rng(_seed(config, field))
+    if spec.geometry == '2d':
+        theta = (np.arange(spec.n_ray) + 0.5) * np.pi / spec.n_ray
+        x = np.cos(theta)
+        d = np.zeros(spec.n_ray)
+        for l in range(1, 9):
+            d += rng.standard_normal() * _legendre_p(l, 0, x)
+    else:
+        th = (np.arange(spec.n_theta) + 0.5) * np.pi / spec.n_theta
+        ph = (np.arange(spec.n_phi) + 0.5) * 2.0 * np.pi / spec.n_phi
+        TH, PH = np.meshgrid(th, ph, indexing='ij')
+        x = np.cos(TH)
+        d = np.zeros_like(TH)
+        for l in range(1, 9):
+            for m in range(-l, l + 1):
+                c = rng.standard_normal()
+                p = _legendre_p(l, abs(m), x)
+                d += c * p * (np.cos(m * PH) if m >= 0 else np.sin(-m * PH))
+        d = d.reshape(-1)
+    return 0.05 * d / np.max(np.abs(d))
+
+
+def make_problem(config: int, rays=None, n_ray=None, n_r=None, n_e=None):
+    """Inputs of configuration `config` (1-5), optionally for a ray subset.
+
+    `rays` (index array or slice) selects rays of the full configuration; n_ray,
+    n_r, n_e override the sizes (a resized problem is its own workload with the
+    same recipe).  Returns dict(problem=..., psi0, ye0, T0, spec)."""
+    spec = CONFIGS[config]
+    if n_ray is not None or n_r is not None or n_e is not None:
+        nr_new = n_ray or spec.n_ray
+        geometry = spec.geometry
+        if geometry == '3d' and nr_new != spec.n_theta * spec.n_phi:
+            geometry = '2d'
+        if nr_new == 1:
+            geometry = '1d'
+        spec = dataclasses.replace(spec, n_ray=nr_new, n_r=n_r or spec.n_r,
+                                   n_e=n_e or spec.n_e, geometry=geometry)
+    NR, NE, NRAY = spec.n_r, spec.n_e, spec.n_ray
+    r_edge1 = np.logspace(np.log10(10 * KM), np.log10(1e4 * KM), NR + 1)
+    r_mid = 0.5 * (r_edge1[1:] + r_edge1[:-1])
+    x = r_mid / (10 * KM)
+    d_rho = angular_perturbation(spec, config, FIELD_RHO)
+    d_T = angular_perturbation(spec, config, FIELD_T)
+    rho = np.maximum(3e14 * x[None, :] ** -3 * (1.0 + d_rho[:, None]), 1e6)
+    T = np.maximum(30.0 * x[None, :] ** -1 * (1.0 + d_T[:, None]), 0.1)
+    ye = np.broadcast_to(0.1 + 0.4 * np.log(x) / np.log(1e3), (NRAY, NR)).copy()
+    e_edge = np.logspace(np.log10(2.0), np.log10(250.0), NE + 1)
+    e_g = np.sqrt(e_edge[1:] * e_edge[:-1])
+    rng = np.random.default_rng(_seed(config, FIELD_KAPPA))
+    noise = rng.lognormal(0.0, 0.2, size=(NRAY, NR, NE))
+    kappa = 1e-40 * rho[:, :, None] * e_g[None, None, :] ** 2 * noise
+    kappa4 = np.ascontiguousarray(np.broadcast_to(kappa[:, None], (NRAY, N_SPECIES, NR, NE)))
+    xg = np.exp(-e_g[None, None, None, :] / T[:, None, :, None])
+    psi0 = xg / (1.0 + xg)
+    psi0 = np.ascontiguousarray(np.broadcast_to(psi0, (NRAY, N_SPECIES, NR, NE)))
+    r_edge = np.ascontiguousarray(np.broadcast_to(r_edge1, (NRAY, NR + 1)))
+    prob = dict(r_edge=r_edge, lapse=None, e_edge=e_edge, rho=rho,
+                kappa_abs=kappa4, kappa_scat=kappa4.copy(), nes_coef=1e-41 * rho,
+                dt=1e-6, outer_bc=0, scale=None)
+    out = dict(problem=prob, psi0=psi0, ye0=ye, T0=T, spec=spec)
+    if rays is not None:
+        out = subset_rays(out, rays)
+    return out
+
+
+def subset_rays(inp, rays):
+    """Restrict every per-ray array of an input dict to the selected rays."""
+    prob = dict(inp['problem'])
+    for key in ('r_edge', 'lapse', 'rho', 'kappa_abs', 'kappa_scat', 'nes_coef'):
+        if prob.get(key) is not None:
+            prob[key] = np.ascontiguousarray(prob[key][rays])
+    out = dict(inp)
+    out['problem'] = prob
+    for key in ('psi0', 'ye0', 'T0'):
+        out[key] = np.ascontiguousarray(inp[key][rays])
+    return out
