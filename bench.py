@@ -1,0 +1,396 @@
+"""Benchmark of the implicit MGFLD transport step on synthetic post-bounce profiles.
+
+Workload: 256 rays (2D, per-ray angular perturbations) x 512 radial zones x 20
+energy groups x 4 species, dt = 1e-6 s, outer tolerance 1e-10 (tolmin_psi = 1):
+the 2D ray-by-ray configuration.  A "step" is one implicit transport step of
+every ray (mgfld_step).  Metric: zone*group*species updates per second
+(n_ray * n_r * n_e * 4 per step / time), for the mixed-precision path (FP32
+block factorisation, FP64 residual refinement) with the plain FP64 path on the
+same inputs reported beside it.
+
+Under torchrun each rank steps its own 256 rays of a larger 2D ray set (rays are
+independent: no collective on the data path); `value` is the total over ranks.
+`--impl reference` times the CPU oracle on host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1809_05608_gb300 import problems  # noqa: E402
+
+RAYS_PER_RANK = 256
+CONFIG_ID = 2
+TOL = 1e-10
+METRIC = 'MGFLD step zone*group*species updates/s (mixed FP32-factor/FP64-refined at 1e-10; FP64 path beside)'
+UNIT = 'updates/s'
+FP64_FLOP_PER_CLK_SM = 4.0      # 2 DFMA lanes per clock per SM (1.25 TFLOP/s nominal at 2.07 GHz x 152 SMs)
+FP32_FLOP_PER_CLK_SM = 256.0    # 128 FFMA lanes per clock per SM
+N_SM = 152
+
+
+def dist_info():
+    ws = int(os.environ.get('WORLD_SIZE', '1'))
+    rank = int(os.environ.get('RANK', '0'))
+    local = int(os.environ.get('LOCAL_RANK', '0'))
+    return ws, rank, local
+
+
+def workload(n_gpus, rank):
+    inp = problems.make_problem(CONFIG_ID, n_ray=RAYS_PER_RANK * n_gpus)
+    if n_gpus > 1:
+        inp = problems.subset_rays(inp, slice(rank * RAYS_PER_RANK, (rank + 1) * RAYS_PER_RANK))
+    return inp
+
+
+def updates_per_step(inp):
+    n_ray, n_s, n_r, n_e = inp['psi0'].shape
+    return n_ray * n_s * n_r * n_e
+
+
+# ------------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi sampling every 200 ms; started before the warm-up so that its start-up
+    never falls inside a timed region, and filtered to the timed window by its own
+    sample timestamps."""
+    FIELDS = ('timestamp,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,'
+              'clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,'
+              'clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap')
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+        self.windows = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ['nvidia-smi', '-i', str(self.index), f'--query-gpu={self.FIELDS}',
+                 '--format=csv,noheader,nounits', '-lms', '200'],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def mark(self, t0, t1):
+        self.windows.append((t0, t1))
+
+    def stop(self):
+        if self.proc is None:
+            return dict(sm_mhz=None, sm_max_mhz=None, reasons=['nvidia-smi unavailable'])
+        time.sleep(0.5)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=5)
+        import datetime
+        sm, smax, reasons = [], [], set()
+        names = ('hw_slowdown', 'hw_thermal_slowdown', 'sw_thermal_slowdown', 'sw_power_cap')
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(',')]
+            if len(parts) < 9:
+                continue
+            try:
+                ts = datetime.datetime.strptime(parts[0], '%Y/%m/%d %H:%M:%S.%f').timestamp()
+                clk, cmax = float(parts[1]), float(parts[2])
+            except ValueError:
+                continue
+            if not any(a - 0.25 <= ts <= b + 0.25 for a, b in self.windows):
+                continue
+            sm.append(clk)
+            smax.append(cmax)
+            for name, val in zip(names, parts[5:9]):
+                if val.lower() == 'active':
+                    reasons.add(name)
+        if not sm:
+            return dict(sm_mhz=None, sm_max_mhz=None, reasons=['no samples inside the timed window'])
+        return dict(sm_mhz=statistics.median(sm), sm_max_mhz=max(smax), reasons=sorted(reasons),
+                    samples=len(sm))
+
+
+# ------------------------------------------------------------------------- traffic record
+
+def traffic_record(kernel):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, or None when the
+    kernel source changed since the counters were taken."""
+    path = os.path.join(ROOT, 'profiles', 'ncu_traffic.txt')
+    if not os.path.exists(path):
+        return None
+    src = open(os.path.join(ROOT, 'paper_1809_05608_gb300', 'csrc', 'blocktri.cu'), 'rb').read()
+    src += open(os.path.join(ROOT, 'paper_1809_05608_gb300', 'csrc', 'assemble.cu'), 'rb').read()
+    digest = hashlib.sha256(src).hexdigest()[:16]
+    for line in open(path):
+        parts = line.split()
+        if len(parts) >= 4 and not line.startswith('#') and parts[0] == kernel and parts[3] == digest:
+            return dict(bytes=float(parts[1]), units=float(parts[2]))
+    return None
+
+
+# ------------------------------------------------------------------------- GPU arm
+
+def run_path(M, torch, inp, precision, steps, warmup, barrier, clocks=None):
+    st = M.Stepper(inp, precision, tol=TOL, max_iter=60)
+    if clocks:
+        clocks.start()
+    psi, ye, T = st.state_to_device(inp['psi0'], inp['ye0'], inp['T0'])
+    stream = torch.cuda.current_stream()
+    for _ in range(warmup):
+        rc = st.step(psi, ye, T)
+        assert rc == M.MGFLD_OK, M.status_str(rc)
+    prof = (ctypes.c_double * 12)()
+    st.opts.profile = ctypes.cast(prof, ctypes.c_void_p)
+    nfact = torch.zeros_like(st.report['factorizations'])
+    iters = torch.zeros_like(st.report['iters'])
+    barrier()
+    torch.cuda.synchronize()
+    t_start = time.time()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        rc = st.step(psi, ye, T)
+        assert rc == M.MGFLD_OK, M.status_str(rc)
+        nfact += st.report['factorizations']
+        iters += st.report['iters']
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_end = time.time()
+    clk = None
+    if clocks:
+        clocks.mark(t_start, t_end)
+        clk = clocks.stop()
+    barrier()
+    ms = e0.elapsed_time(e1)
+    st.opts.profile = None
+    prof = {name: dict(ms=prof[2 * c], launches=int(prof[2 * c + 1])) for c, name in enumerate(M.PROF_NAMES)}
+    return dict(ms=ms, prof=prof, nfact=int(nfact.sum()), iters=int(iters.sum()),
+                max_iters=int(st.report['iters'].max()), clocks=clk, stepper=st,
+                state=(psi, ye, T))
+
+
+def algorithmic_work(inp, kernel, nfact, iters, precision):
+    """Algorithmic flop count over the timed steps for one kernel category.
+
+    factor: per (zone, system) factorisation, N^3 FMAs of in-place Gauss-Jordan plus
+    2 N^2 for the diagonal Schur scaling: 2 N^3 + 2 N^2 flops (FP64 or FP32).
+    assemble: per (zone, system, iteration) residual, two length-N NES sums per row
+    (4 N^2) + 16 N of transport/absorption terms; with a fresh Jacobian another 4 N^2."""
+    n_ray, n_s, n_r, n = inp['psi0'].shape
+    if kernel == 'factor':
+        per = 2.0 * n**3 + 2.0 * n**2
+        return per * n_s * n_r * nfact
+    if kernel == 'assemble':
+        per_res = 4.0 * n**2 + 16.0 * n
+        per_jac = 4.0 * n**2
+        return n_s * n_r * (per_res * iters + per_jac * nfact)
+    raise ValueError(kernel)
+
+
+def roofline_for(res, inp, precision, clk):
+    prof = res['prof']
+    dom = max(('assemble', 'factor'), key=lambda k: prof[k]['ms'])
+    flops = algorithmic_work(inp, dom, res['nfact'], res['iters'], precision)
+    achieved = flops / (prof[dom]['ms'] * 1e-3) / 1e12
+    fp32 = dom == 'factor' and precision == 1
+    per_clk = FP32_FLOP_PER_CLK_SM if fp32 else FP64_FLOP_PER_CLK_SM
+    peak = per_clk * N_SM * 2.070e9 / 1e12
+    launches = max(prof[dom]['launches'], 1)
+    kname = {'factor': 'k_factor', 'assemble': 'k_assemble'}[dom]
+    tr = traffic_record(kname + ('_f32' if fp32 else ''))
+    traffic = None
+    if tr is not None:
+        units_per_launch = (res['nfact'] if dom == 'factor' else res['iters']) * inp['psi0'].shape[1] / launches
+        traffic = tr['bytes'] / tr['units'] * units_per_launch
+    return dict(bound='alu', kernel=kname, pipe='fp32' if fp32 else 'fp64', achieved=achieved, peak=peak,
+                unit='TFLOP/s', frac=achieved / peak, traffic=traffic,
+                peak_source='derived: %g flop/clk/SM x 152 SMs x 2070 MHz max SM clock' % per_clk,
+                kernel_ms_per_launch=prof[dom]['ms'] / launches, kernel_share=prof[dom]['ms'] / res['ms'])
+
+
+def e2e_run(M, torch, inp, precision, steps):
+    """Same metric through the public API from pinned HOST buffers: every step uploads
+    that step's inputs (matter, opacities, NES scale, grid, state), runs mgfld_step and
+    reads the new state back."""
+    st = M.Stepper(inp, precision, tol=TOL, max_iter=60)
+    prob = inp['problem']
+    host = {}
+    for k in ('r_edge', 'rho', 'kappa_abs', 'kappa_scat', 'nes_coef'):
+        host[k] = torch.from_numpy(np.ascontiguousarray(prob[k], dtype=np.float64)).pin_memory()
+    hs = [torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).pin_memory()
+          for a in (inp['psi0'], inp['ye0'], inp['T0'])]
+    dev = [torch.empty_like(h, device='cuda') for h in hs]
+    out = [torch.empty_like(h).pin_memory() for h in hs]
+    h2d = sum(v.numel() * 8 for v in host.values()) + sum(h.numel() * 8 for h in hs)
+    d2h = sum(h.numel() * 8 for h in hs)
+    stream = torch.cuda.current_stream()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for s in range(steps):
+        for k, v in host.items():
+            st.prob.t[k].copy_(v, non_blocking=True)
+        src = hs if s == 0 else out
+        for d, h in zip(dev, src):
+            d.copy_(h, non_blocking=True)
+        rc = st.step(*dev)
+        assert rc == M.MGFLD_OK, M.status_str(rc)
+        for o, d in zip(out, dev):
+            o.copy_(d, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    return dict(ms=ms, h2d=h2d, d2h=d2h)
+
+
+# ------------------------------------------------------------------------- CPU oracle
+
+def oracle_sample(inp, n_rays, n_steps=1):
+    """Time the CPU oracle, as it stands, on the first n_rays rays for n_steps steps."""
+    from oracle import mgfld_oracle as O
+    sub = problems.subset_rays(inp, slice(0, n_rays))
+    c0, w0 = time.process_time(), time.perf_counter()
+    O.run_steps(sub['problem'], sub['psi0'], sub['ye0'], sub['T0'], n_steps)
+    wall = time.perf_counter() - w0
+    cpu = time.process_time() - c0
+    ups = updates_per_step(sub) * n_steps / wall
+    return dict(value=ups, unit=UNIT, cores=max(1, int(round(cpu / wall))), kind='oracle',
+                sample=f'{n_rays} of the 256 rays x {n_steps} implicit step(s), FP64 numpy/LAPACK, '
+                       f'{wall:.1f} s wall', wall_s=wall)
+
+
+def reference_arm(args, n_gpus, rank):
+    if rank != 0:
+        return 0
+    inp = workload(1, 0)
+    rays = 4
+    per_step = []
+    for s in range(args.warmup + args.steps):
+        r = oracle_sample(inp, rays)
+        if s >= args.warmup:
+            per_step.append(r['wall_s'])
+    ms = 1e3 * float(np.mean(per_step))
+    value = updates_per_step(problems.subset_rays(inp, slice(0, rays))) / (ms * 1e-3)
+    line = dict(impl='reference', metric=METRIC, value=value, unit=UNIT, n_gpus=n_gpus, steps=args.steps,
+                warmup=args.warmup, ms_per_step=ms, higher_is_better=True, scaling='weak', vs_baseline=None,
+                dtype='f64', data='synthetic',
+                config=dict(workload='2d 256 rays x 512 zones x 20 groups x 4 species, dt 1e-6 s, tol 1e-10',
+                            oracle_rays_per_step=rays),
+                cpu_baseline=dict(value=value, unit=UNIT, cores=r['cores'], kind='oracle',
+                                  sample=f'{rays} of the 256 rays, one implicit step per timed step'),
+                e2e=dict(value=value, unit=UNIT, h2d_bytes_per_step=0, d2h_bytes_per_step=0))
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------------- main
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument('--gpus', type=int, default=1)
+    ap.add_argument('--steps', type=int, default=10)
+    ap.add_argument('--warmup', type=int, default=3)
+    ap.add_argument('--impl', default='mgfld', choices=['mgfld', 'reference'])
+    ap.add_argument('--oracle-rays', type=int, default=12)
+    ap.add_argument('--no-cpu-baseline', action='store_true')
+    args = ap.parse_args()
+    ws, rank, local = dist_info()
+    n_gpus = max(args.gpus, ws)
+    if args.impl == 'reference':
+        return reference_arm(args, n_gpus, rank)
+
+    import torch
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group('nccl', device_id=torch.device('cuda', local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    def max_over_ranks(v):
+        if dist is None:
+            return v
+        t = torch.tensor([v], dtype=torch.float64, device='cuda')
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    from paper_1809_05608_gb300 import build as B
+    if not os.path.exists(B.LIB) and rank == 0:
+        B.build()
+    barrier()
+    from paper_1809_05608_gb300 import mgfld as M
+
+    inp = workload(n_gpus, rank)
+    ups = updates_per_step(inp)
+    clocks = ClockSampler(local)
+    mixed = run_path(M, torch, inp, M.MGFLD_MIXED, args.steps, args.warmup, barrier, clocks)
+    fp64 = run_path(M, torch, inp, M.MGFLD_FP64, args.steps, args.warmup, barrier)
+    ms_mixed = max_over_ranks(mixed['ms']) / args.steps
+    ms_fp64 = max_over_ranks(fp64['ms']) / args.steps
+    value = ups * ws / (ms_mixed * 1e-3)
+    value64 = ups * ws / (ms_fp64 * 1e-3)
+    e2e = e2e_run(M, torch, inp, M.MGFLD_MIXED, args.steps)
+    e2e_ms = max_over_ranks(e2e['ms']) / args.steps
+    roof = roofline_for(mixed, inp, M.MGFLD_MIXED, mixed['clocks'])
+    roof64 = roofline_for(fp64, inp, M.MGFLD_FP64, None)
+    launches = sum(v['launches'] for v in mixed['prof'].values())
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu = oracle_sample(inp, args.oracle_rays)
+        cpu.pop('wall_s')
+    if rank != 0:
+        return 0
+    work_gb = (mixed['stepper'].ws.numel() + sum(t.numel() * 8 for t in mixed['stepper'].prob.t.values()
+                                                 if t is not None)) / 1e9
+    line = dict(
+        metric=METRIC, value=value, unit=UNIT, n_gpus=n_gpus, steps=args.steps, warmup=args.warmup,
+        ms_per_step=ms_mixed, higher_is_better=True, scaling='weak', vs_baseline=None,
+        dtype='f32 factor + f64 residual/update', data='synthetic',
+        config=dict(workload='2d 256 rays x 512 zones x 20 groups x 4 species per GPU, dt 1e-6 s, tol 1e-10',
+                    n_ray_per_gpu=RAYS_PER_RANK, n_r=512, n_e=20, n_s=4, precision='mixed',
+                    l2='working set %.1f GB per GPU, larger than the 129 MB L2 (no flush needed)' % work_gb,
+                    outer_iterations_per_step=mixed['max_iters'],
+                    factorizations_per_ray_step=mixed['nfact'] / (RAYS_PER_RANK * args.steps)),
+        roofline=roof, cpu_baseline=cpu, clocks=mixed['clocks'],
+        e2e=dict(value=ups * ws / (e2e_ms * 1e-3), unit=UNIT, h2d_bytes_per_step=e2e['h2d'],
+                 d2h_bytes_per_step=e2e['d2h']),
+        gpu_launches=launches,
+        kernel_ms={k: v['ms'] for k, v in mixed['prof'].items()},
+        fp64_path=dict(value=value64, unit=UNIT, ms_per_step=ms_fp64, roofline=roof64, dtype='f64',
+                       kernel_ms={k: v['ms'] for k, v in fp64['prof'].items()},
+                       outer_iterations_per_step=fp64['max_iters'],
+                       gpu_launches=sum(v['launches'] for v in fp64['prof'].values())),
+        mixed_over_fp64=value / value64)
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == '__main__':
+    sys.exit(main())

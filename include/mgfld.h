@@ -1,0 +1,192 @@
+/*
+ * mgfld.h -- C ABI of the GB300 (sm_103a) implicit MGFLD transport step.
+ *
+ * The operation is the Lagrangian transport step of ray-by-ray multi-group
+ * flux-limited diffusion (Bruenn et al., CHIMERA, Sec. "Lagrangian Transport
+ * Step" and Sec. "Solution of the Transport Equations"):  for every radial ray,
+ * the zeroth-moment equation (Eq. a58) with the flux-limited first moment
+ * (Eq. a59, limiter Eqs. a20-a26a) and the electron-fraction equation (Eq. a62a)
+ * are solved implicitly for psi^(0) at t^{n+1} and Ye^{n+1} by an outer Newton
+ * iteration on a block-tridiagonal system in radius (Eqs. a62aa-a62ae, boundary
+ * conditions Eq. a62af), then the internal energy (Eq. a62b) and temperature
+ * are updated.  Sources: absorption/emission (Eq. a55), iso-energetic
+ * scattering (Eq. d8c, in the mean free path only) and neutrino-electron
+ * scattering with dense group coupling (Eqs. d1-d8).
+ *
+ * Conventions for every entry point:
+ *   - All array pointers are DEVICE pointers unless stated, FP64, C row-major,
+ *     owned by the caller.  The library never allocates or frees memory: the
+ *     caller provides every buffer, including the workspace.
+ *   - Sizes: n_ray rays, n_r radial zones, n_e energy groups (1..32), n_s = 4
+ *     species in the order nu_e, nubar_e, nu_mu/tau, nubar_mu/tau.
+ *   - Units: cm, s, g/cm^3, MeV (T is kT in MeV).
+ *   - Every call is asynchronous on `stream` (a cudaStream_t passed as void*;
+ *     NULL is the legacy default stream) except where stated.
+ *   - Errors are returned as mgfld_status; nothing aborts, throws or traps.
+ *     Argument errors are detected on the host before any launch.
+ */
+#ifndef MGFLD_H
+#define MGFLD_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  MGFLD_OK = 0,
+  MGFLD_EINVAL = 1,   /* bad argument (sizes, NULL pointer, unsupported n_e) */
+  MGFLD_ENOMEM = 2,   /* caller-provided workspace smaller than required      */
+  MGFLD_ENOCONV = 3,  /* at least one ray did not converge within max_iter    */
+  MGFLD_ENAN = 4,     /* a non-finite value appeared in at least one ray      */
+  MGFLD_ECUDA = 5     /* a CUDA launch or runtime call failed                 */
+} mgfld_status;
+
+typedef enum { MGFLD_FP64 = 0, MGFLD_MIXED = 1 } mgfld_precision;
+typedef enum { MGFLD_BC_GHOST = 0, MGFLD_BC_REFLECT = 1 } mgfld_outer_bc;
+
+typedef struct { int n_ray, n_r, n_e, n_s; } mgfld_dims;
+
+/* Double-gamma equation of state (Sec. "Double-gamma EoS", Eqs. e2-e13). */
+typedef struct {
+  double gamma1, gamma2, e_coef, g_n, g_p, rho_nuc, rho_0, mb_c2, m_b;
+} mgfld_eos_params;
+
+/* Default double-gamma constants: gamma1 = 4/3, gamma2 = 2.5, E_coef = 3/2,
+ * g_n = g_p = 2, rho_nuc = rho_0 = 2.5e14 g/cm^3, m_B c^2 = 939.565 MeV,
+ * m_B = 1.674927e-24 g.  Host function. */
+mgfld_eos_params mgfld_eos_default(void);
+
+/* Statement of one step's problem (Eqs. a58-a62a): given matter and grid. */
+typedef struct {
+  const double *r_edge;     /* [n_ray][n_r+1] zone-edge areal radii R_{i+1/2}, increasing, > 0 at the centre edge allowed 0 */
+  const double *lapse;      /* [n_ray][n_r] lapse a_i at zone centres, or NULL for a = 1 (Eq. a8a) */
+  const double *e_edge;     /* [n_e+1] group edges of the energy at infinity E = a eps (MeV), increasing */
+  const double *rho;        /* [n_ray][n_r] rest-mass density */
+  const double *kappa_abs;  /* [n_ray][n_s][n_r][n_e] absorption opacity 1/lambda_a at the local group energy (1/cm) */
+  const double *kappa_scat; /* [n_ray][n_s][n_r][n_e] iso-energetic scattering opacity (Eq. d8c) (1/cm) */
+  const double *nes_coef;   /* [n_ray][n_r] NES kernel scale (cm^3/s), or NULL for no NES */
+  const double *scale;      /* [n_s][n_e] opacity scales multiplying kappa_abs and kappa_scat, or NULL */
+  mgfld_eos_params eos;
+  double dt;                /* time step (s) */
+  int outer_bc;             /* mgfld_outer_bc */
+} mgfld_problem;
+
+/* State at t^n on entry, t^{n+1} on exit (in place). */
+typedef struct {
+  double *psi;   /* [n_ray][n_s][n_r][n_e] zeroth angular moment psi^(0) */
+  double *ye;    /* [n_ray][n_r] electron fraction */
+  double *T;     /* [n_ray][n_r] temperature kT (MeV) */
+} mgfld_state;
+
+typedef struct {
+  int precision;       /* mgfld_precision: FP64 Newton, or FP32 factor + FP64 residual refinement */
+  double tol;          /* convergence: |d psi| <= tol * max(|psi|, tolmin_psi) for all (i,k,q) (Eq. a62ab) */
+  double tolmin_psi;   /* typically 1 (Eq. a62ab) */
+  double tol_ye;       /* |d Ye| <= tol_ye * max(Ye, tolmin_ye) */
+  double tolmin_ye;    /* typically 0.1 */
+  int max_iter;        /* outer-iteration cap per ray */
+  double refactor_ratio; /* MIXED only: refactor a ray when its correction shrinks by less than this */
+  double *profile;     /* HOST pointer to double[MGFLD_PROF_N][2] or NULL.  When set, each kernel
+                          category is bracketed by CUDA events on `stream` and its elapsed
+                          milliseconds and launch count are ADDED to profile[c][0], profile[c][1]. */
+} mgfld_step_opts;
+
+/* Kernel categories of mgfld_step_opts.profile. */
+enum {
+  MGFLD_PROF_SETUP = 0,    /* frozen coefficients: groups, EoS, NES kernels, mean free path, limiter (6 kernels) */
+  MGFLD_PROF_ASSEMBLE = 1, /* residual and Jacobian rows (k_assemble) */
+  MGFLD_PROF_FACTOR = 2,   /* block-Thomas elimination with in-block Gauss-Jordan (k_factor) */
+  MGFLD_PROF_SOLVE = 3,    /* forward/back substitution (k_solve) */
+  MGFLD_PROF_UPDATE = 4,   /* psi and Ye update, convergence bookkeeping (k_update, k_check) */
+  MGFLD_PROF_FINISH = 5,   /* energy/temperature update and ledgers (k_finish, k_ledger) */
+  MGFLD_PROF_N = 6
+};
+
+/* Per-step report, DEVICE pointers (any may be NULL). */
+typedef struct {
+  int *iters;          /* [n_ray] outer iterations used */
+  int *ray_status;     /* [n_ray] mgfld_status of each ray (OK, ENOCONV, ENAN) */
+  double *ledger;      /* [n_ray][8]: lepton number before, after, lost through R_{I+1/2},
+                          residual (after + lost - before); energy at infinity (MeV) before,
+                          after, lost, residual (Eqs. a60-a62 with a62a, a62b) */
+  double *heating;     /* [n_ray] MeV deposited in matter by nu_e + nubar_e between 100 and 300 km */
+  int *factorizations; /* [n_ray] number of block factorisations performed */
+} mgfld_step_report;
+
+/* Bytes of workspace mgfld_step needs for these dimensions and precision. */
+size_t mgfld_workspace_bytes(const mgfld_dims *dims, int precision);
+
+/*
+ * mgfld_step -- one implicit transport step for all rays (Eqs. a58, a59, a62a
+ * solved together; then Eqs. a62b and the EoS inversion for T).
+ *   dims, prob, opts: as above (host structs holding device pointers).
+ *   state: psi^n, Ye^n, T^n on entry; psi^{n+1}, Ye^{n+1}, T^{n+1} on exit.
+ *   report: optional per-ray outputs (device); may be NULL.
+ *   ws, ws_bytes: device workspace of at least mgfld_workspace_bytes() bytes,
+ *   256-byte aligned; its contents are scratch.
+ * The outer iteration tests convergence on the host once per iteration, so
+ * this call synchronises `stream` once per outer iteration.
+ * Returns OK, EINVAL, ENOMEM, ECUDA, or the worst ray status (ENAN before
+ * ENOCONV).  Rays that fail keep their last iterate.
+ */
+mgfld_status mgfld_step(const mgfld_dims *dims, const mgfld_problem *prob, mgfld_state *state,
+                        const mgfld_step_opts *opts, mgfld_step_report *report,
+                        void *ws, size_t ws_bytes, void *stream);
+
+/*
+ * Linear block-tridiagonal system of one outer iteration, per (ray, species):
+ *   sum_k' diag[i][k][k'] x[i][k'] + lower[i][k] x[i-1][k] + upper[i][k] x[i+1][k] = rhs[i][k]
+ * (Eq. a62ae with the Ye column moved to the outer iteration; the off-diagonal
+ * blocks are diagonal because the limited diffusion coefficient is held at
+ * psi^n).  Layout (device, FP64 unless noted):
+ *   diag  [n_ray][n_s][n_r][n_e][n_e]  row k = equation of group k (Eq. a58 units, 1/cm)
+ *   lower [n_ray][n_s][n_r][n_e]       zero for i = 0 (zero central flux)
+ *   upper [n_ray][n_s][n_r][n_e]       zero for i = n_r-1 (ghost folded into diag, Eq. a62af)
+ *   rhs   [n_ray][n_s][n_r][n_e]       -G (Eq. a58 residual) at the linearisation point
+ */
+typedef struct { double *diag, *lower, *upper, *rhs; } mgfld_system;
+
+/*
+ * mgfld_assemble -- linearise the step at its starting state: builds the
+ * frozen coefficients from (psi^n, Ye^n, T^n) and writes the Newton system of
+ * the first outer iteration (psi = psi^n, Ye = Ye^n) into `sys`.
+ *   state is read only.  ws: as for mgfld_step.
+ */
+mgfld_status mgfld_assemble(const mgfld_dims *dims, const mgfld_problem *prob, const mgfld_state *state,
+                            mgfld_system *sys, void *ws, size_t ws_bytes, void *stream);
+
+/* Bytes of the factor buffer for these dimensions and precision (FP64: 8 n_e^2
+ * per block; MIXED: 4 n_e^2 per block). */
+size_t mgfld_factor_bytes(const mgfld_dims *dims, int precision);
+
+/*
+ * mgfld_factor -- block-Thomas forward elimination of `sys` (partial pivoting
+ * inside each block): writes D'_i^{-1} for every (ray, species, zone) into
+ * `factor` ([n_ray][n_s][n_r][n_e][n_e], FP64 or FP32 by `precision`), where
+ * D'_0 = diag_0 and D'_i = diag_i - lower_i * D'_{i-1}^{-1} * upper_{i-1}.
+ * sys->rhs is not used.  A singular pivot gives non-finite factors (detected
+ * later by mgfld_solve's caller, not here).
+ */
+mgfld_status mgfld_factor(const mgfld_dims *dims, const mgfld_system *sys, int precision,
+                          void *factor, void *stream);
+
+/*
+ * mgfld_solve -- solve the factored system for one right-hand side:
+ * forward g_i = D'^{-1}_i (rhs_i - lower_i * g_{i-1}), back
+ * x_i = g_i - D'^{-1}_i (upper_i * x_{i+1}).  rhs, x: [n_ray][n_s][n_r][n_e] FP64
+ * (x may alias rhs).  With MIXED precision the substitution runs in FP32 on a
+ * per-system power-of-two scaling of rhs.  sys->diag and sys->rhs are not used.
+ */
+mgfld_status mgfld_solve(const mgfld_dims *dims, const mgfld_system *sys, int precision,
+                         const void *factor, const double *rhs, double *x, void *stream);
+
+/* Human-readable name of a status code (static string). */
+const char *mgfld_status_str(mgfld_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MGFLD_H */

@@ -1,0 +1,91 @@
+// Residual and Jacobian rows of the per-species Newton system (Eqs. a58, a59, a62ac).
+//
+// One thread owns the equation of (ray, species q, zone i, group k):
+//   G = (psi - psi^n)/(a c dt) + (a^2/V)[A psi1/a^2 |_{i+1/2} - A psi1/a^2 |_{i-1/2}] - S,
+//   psi1_{i+1/2} = -D_{i+1/2} (psi_{i+1} - psi_i)              (Eq. a59, D frozen at psi^n)
+//   S = j (1 - psi) - kappa_a psi                             (Eq. a55)
+//     + C [(1 - psi_k) sum_k' w_k' Phi_in[k,k'] psi_k' - psi_k sum_k' w_k' Phi_out[k,k'] (1 - psi_k')]
+//                                                              (Eq. d8, Phi_1 = 0; Phi_in[k,k'] = Phi_out[k',k])
+// and, when the ray is flagged for a new factorisation, the dense row dG_k/dpsi_k' of the
+// diagonal block plus the diagonal couplings to zones i-1 and i+1 (Eq. a62ae).
+#include "mgfld_internal.cuh"
+
+namespace mgfld {
+
+__global__ void k_assemble(Prob p, Ws w, const double *__restrict__ psi, const double *__restrict__ T,
+                           double *__restrict__ diag, double *__restrict__ lower,
+                           double *__restrict__ upper, double *__restrict__ rhs,
+                           const int *__restrict__ list, int n_list, const int *__restrict__ jac_flag,
+                           double *__restrict__ src_out) {
+  const int n = p.n;
+  const size_t per_ray = (size_t)NS * p.n_r * n;
+  const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (size_t)n_list * per_ray) return;
+  const int ray = list ? list[t / per_ray] : (int)(t / per_ray);
+  const size_t local = t % per_ray;
+  const int k = (int)(local % n);
+  const int i = (int)((local / n) % p.n_r);
+  const int q = (int)(local / ((size_t)n * p.n_r));
+  const size_t g = (size_t)ray * per_ray + local;          // global (ray, q, i, k) index
+  const size_t zi = (size_t)ray * p.n_r + i;
+  const int last = p.n_r - 1;
+
+  const double *z = w.zone + zi * ZC_N;
+  const double inv_a = z[ZC_INV_A];
+  const double inv_a3 = inv_a * inv_a * inv_a;
+  const double pre = z[ZC_PRE];
+  const double inv_acdt = z[ZC_INV_ACDT];
+
+  const double *ps = psi + (g - k);
+  const double pk = ps[k];
+  const double *ph = w.phi + zi * n * n;
+  double gain = 0.0, loss = 0.0;
+  for (int kp = 0; kp < n; ++kp) {
+    const double wk = w.W[kp] * inv_a3;
+    gain += wk * ph[kp * n + k] * ps[kp];
+    loss += wk * ph[k * n + kp] * (1.0 - ps[kp]);
+  }
+  const double sc = p.scale ? p.scale[q * n + k] : 1.0;
+  const double kap = p.kabs[g] * sc;
+  const double j = w.jbuf[g];
+  const double S = j * (1.0 - pk) - kap * pk + kCNes * ((1.0 - pk) * gain - pk * loss);
+  if (src_out) {               // converged sources for Eqs. a62b and the ledgers
+    src_out[g] = S;
+    return;
+  }
+
+  const double al_out = w.alpha[g];
+  const double al_in = i > 0 ? w.alpha[g - n] : 0.0;
+  const double gh = (i == last) ? w.ghost[((size_t)ray * NS + q) * n + k] : 0.0;
+  const double p_right = i < last ? ps[k + n] : gh * pk;
+  const double p_left = i > 0 ? ps[k - (ptrdiff_t)n] : pk;
+  const double flux_out = -al_out * (p_right - pk);
+  const double flux_in = -al_in * (pk - p_left);
+  const double G = (pk - w.psi_n[g]) * inv_acdt + pre * (flux_out - flux_in) - S;
+  rhs[g] = -G;
+
+  if (jac_flag && !jac_flag[ray]) return;
+  const double dg = inv_acdt + pre * (al_out * (1.0 - gh) + al_in) + j + kap + kCNes * (gain + loss);
+  double *row = diag + g * n;
+  for (int kp = 0; kp < n; ++kp) {
+    const double wk = w.W[kp] * inv_a3;
+    const double d = -kCNes * wk * ((1.0 - pk) * ph[kp * n + k] + pk * ph[k * n + kp]);
+    row[kp] = kp == k ? d + dg : d;
+  }
+  lower[g] = -pre * al_in;
+  upper[g] = i < last ? -pre * al_out : 0.0;
+}
+
+cudaError_t launch_assemble(const Prob &p, const Ws &w, const double *psi, const double *ye, const double *T,
+                            double *diag, double *lower, double *upper, double *rhs, const int *list,
+                            int n_list, const int *jac_flag, cudaStream_t s, double *src_out) {
+  (void)ye;
+  const size_t total = (size_t)n_list * NS * p.n_r * p.n;
+  if (total == 0) return cudaSuccess;
+  const unsigned B = 256;
+  k_assemble<<<(unsigned)((total + B - 1) / B), B, 0, s>>>(p, w, psi, T, diag, lower, upper, rhs, list,
+                                                           n_list, jac_flag, src_out);
+  return cudaGetLastError();
+}
+
+}  // namespace mgfld

@@ -1,0 +1,542 @@
+// Outer iteration of the implicit transport step and the C ABI (include/mgfld.h).
+//
+// Per outer iteration (Eq. a62aa) and per still-active ray:
+//   1. residual (and, when the ray needs one, a fresh Jacobian) of Eq. a58 at the iterate;
+//   2. block-Thomas factorisation (every iteration in FP64; in MIXED only when the
+//      correction stopped contracting fast, the FP32 factors being reused otherwise, so
+//      that the FP64 residual drives an iterative refinement);
+//   3. forward/back substitution for the correction of psi;
+//   4. psi += correction; one Newton step of the zone-local Ye equation (Eq. a62a) at the
+//      new psi (the Ye column of Eq. a62ae is taken by outer block Gauss-Seidel, which
+//      converges to the same root); the convergence test of Eq. a62ab.
+// After convergence: Eq. a62b for the internal energy, T from the EoS, and the lepton and
+// energy ledgers of Eqs. a60-a62.
+#include <cmath>
+#include <cstring>
+
+#include "mgfld_internal.cuh"
+
+namespace mgfld {
+
+static size_t align_up(size_t v) { return (v + 255) & ~(size_t)255; }
+
+Layout make_layout(int n_ray, int n_r, int n, int precision) {
+  Layout L{};
+  const size_t R = (size_t)n_ray, Z = R * n_r, F = Z * NS * n, B = F * n;
+  size_t off = 0;
+  auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes); return o; };
+  L.groups = take(sizeof(double) * 2 * MAX_NE);
+  L.phi = take(sizeof(double) * Z * n * n);
+  L.lam = take(sizeof(double) * F);
+  L.alpha = take(sizeof(double) * F);
+  L.ghost = take(sizeof(double) * R * NS * n);
+  L.rnu = take(sizeof(double) * R * NS * n);
+  L.jbuf = take(sizeof(double) * F);
+  L.psi_n = take(sizeof(double) * F);
+  L.ye_n = take(sizeof(double) * Z);
+  L.e_n = take(sizeof(double) * Z);
+  L.zone = take(sizeof(double) * Z * ZC_N);
+  L.src = take(sizeof(double) * F);
+  L.diag = take(sizeof(double) * B);
+  L.lower = take(sizeof(double) * F);
+  L.upper = take(sizeof(double) * F);
+  L.rhs = take(sizeof(double) * F);
+  L.x = take(sizeof(double) * F);
+  L.dinv = take((precision == MGFLD_MIXED ? sizeof(float) : sizeof(double)) * B);
+  L.zled = take(sizeof(double) * Z * 8);
+  L.viol = take(sizeof(unsigned long long) * R);
+  L.vprev = take(sizeof(double) * R);
+  L.active = take(sizeof(int) * R);
+  L.iters = take(sizeof(int) * R);
+  L.status = take(sizeof(int) * R);
+  L.refac = take(sizeof(int) * R);
+  L.nfact = take(sizeof(int) * R);
+  L.nanflag = take(sizeof(int) * R);
+  L.list_act = take(sizeof(int) * R);
+  L.list_ref = take(sizeof(int) * R);
+  L.counters = take(sizeof(int) * 8);
+  L.total = off;
+  return L;
+}
+
+Ws resolve(void *base, const Layout &L) {
+  char *b = (char *)base;
+  Ws w;
+  w.E = (double *)(b + L.groups);
+  w.W = w.E + MAX_NE;
+  w.phi = (double *)(b + L.phi);
+  w.lam = (double *)(b + L.lam);
+  w.alpha = (double *)(b + L.alpha);
+  w.ghost = (double *)(b + L.ghost);
+  w.rnu = (double *)(b + L.rnu);
+  w.jbuf = (double *)(b + L.jbuf);
+  w.psi_n = (double *)(b + L.psi_n);
+  w.ye_n = (double *)(b + L.ye_n);
+  w.e_n = (double *)(b + L.e_n);
+  w.zone = (double *)(b + L.zone);
+  w.src = (double *)(b + L.src);
+  w.diag = (double *)(b + L.diag);
+  w.lower = (double *)(b + L.lower);
+  w.upper = (double *)(b + L.upper);
+  w.rhs = (double *)(b + L.rhs);
+  w.x = (double *)(b + L.x);
+  w.dinv = (void *)(b + L.dinv);
+  w.zled = (double *)(b + L.zled);
+  w.viol = (unsigned long long *)(b + L.viol);
+  w.vprev = (double *)(b + L.vprev);
+  w.active = (int *)(b + L.active);
+  w.iters = (int *)(b + L.iters);
+  w.status = (int *)(b + L.status);
+  w.refac = (int *)(b + L.refac);
+  w.nfact = (int *)(b + L.nfact);
+  w.nanflag = (int *)(b + L.nanflag);
+  w.list_act = (int *)(b + L.list_act);
+  w.list_ref = (int *)(b + L.list_ref);
+  w.counters = (int *)(b + L.counters);
+  return w;
+}
+
+struct Tol {
+  double tol, tolmin, tol_ye, tolmin_ye, refactor_ratio;
+  int max_iter, mixed;
+};
+
+__global__ void k_init(int n_ray, Ws w) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n_ray) return;
+  w.active[r] = 1;
+  w.iters[r] = 0;
+  w.status[r] = MGFLD_OK;
+  w.refac[r] = 1;
+  w.nfact[r] = 1;
+  w.nanflag[r] = 0;
+  w.viol[r] = 0ull;
+  w.vprev[r] = INFINITY;
+  w.list_act[r] = r;
+  w.list_ref[r] = r;
+}
+
+// psi += dpsi, one Newton step of Eq. a62a for Ye at the new psi, new emissivities, and the
+// per-zone convergence ratio max(|d psi| / (tol max(|psi|, tolmin)), |d Ye| / (tol_ye max(Ye, tolmin_ye))).
+__global__ void k_update(Prob p, Ws w, Tol tl, double *__restrict__ psi, double *__restrict__ ye,
+                         const double *__restrict__ T, const int *__restrict__ list, int n_list) {
+  const int n = p.n;
+  const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (size_t)n_list * p.n_r) return;
+  const int ray = list[t / p.n_r];
+  const int i = (int)(t % p.n_r);
+  const size_t zi = (size_t)ray * p.n_r + i;
+  double viol = 0.0;
+  bool bad = false;
+  for (int q = 0; q < NS; ++q) {
+    const size_t g0 = (((size_t)ray * NS + q) * p.n_r + i) * n;
+    for (int k = 0; k < n; ++k) {
+      const double d = w.x[g0 + k];
+      const double v = psi[g0 + k] + d;
+      psi[g0 + k] = v;
+      bad |= !isfinite(v);
+      viol = fmax(viol, fabs(d) / (tl.tol * fmax(fabs(v), tl.tolmin)));
+    }
+  }
+  const double *z = w.zone + zi * ZC_N;
+  const double inv_a = z[ZC_INV_A];
+  const double inv_a3 = inv_a * inv_a * inv_a;
+  const double inv_acdt = z[ZC_INV_ACDT];
+  const double Ti = T[zi], rho = p.rho[zi];
+  const double cy = kFourPiHC3 * p.eos.mb / rho;
+  double Y = ye[zi];
+  double mu, dmu;
+  eos_mu_nue(p.eos, rho, Ti, Y, mu, dmu);
+  double sG = 0.0, sdG = 0.0;
+  for (int q = 0; q < 2; ++q) {
+    const double sg = lepton_sign(q);
+    const double muq = species_mu(q, mu), dmuq = sg * dmu;
+    const size_t g0 = (((size_t)ray * NS + q) * p.n_r + i) * n;
+    for (int k = 0; k < n; ++k) {
+      const double wk = w.W[k] * inv_a3;
+      const double eps = w.E[k] * inv_a;
+      const double sc = p.scale ? p.scale[q * n + k] : 1.0;
+      const double kap = p.kabs[g0 + k] * sc;
+      const double j = w.jbuf[g0 + k];
+      const double pk = psi[g0 + k];
+      sG += sg * wk * (j * (1.0 - pk) - kap * pk);
+      const bool live = (muq - eps) / Ti < kExpCap;
+      if (live) sdG += sg * wk * (1.0 - pk) * j * dmuq / Ti;
+    }
+  }
+  const double GY = (Y - w.ye_n[zi]) * inv_acdt + cy * sG;
+  const double dGY = inv_acdt + cy * sdG;
+  const double dY = -GY / dGY;
+  Y += dY;
+  ye[zi] = Y;
+  bad |= !isfinite(Y);
+  viol = fmax(viol, fabs(dY) / (tl.tol_ye * fmax(fabs(Y), tl.tolmin_ye)));
+  eos_mu_nue(p.eos, rho, Ti, Y, mu, dmu);
+  for (int q = 0; q < 2; ++q) {
+    const size_t g0 = (((size_t)ray * NS + q) * p.n_r + i) * n;
+    for (int k = 0; k < n; ++k) {
+      const double sc = p.scale ? p.scale[q * n + k] : 1.0;
+      bool live;
+      w.jbuf[g0 + k] = emissivity(p.kabs[g0 + k] * sc, species_mu(q, mu), w.E[k] * inv_a, Ti, live);
+    }
+  }
+  if (bad || !(viol == viol)) {
+    atomicExch(&w.nanflag[ray], 1);
+    viol = INFINITY;
+  }
+  atomicMax(&w.viol[ray], dbits(viol));
+}
+
+// Per ray: close the iteration, decide convergence / failure / refactorisation and build the
+// compacted lists of rays that continue (counters[0]) and that need new factors (counters[1]).
+__global__ void k_check(int n_ray, Ws w, Tol tl) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n_ray || !w.active[r]) return;
+  const int it = ++w.iters[r];
+  const double v = __longlong_as_double((long long)w.viol[r]);
+  w.viol[r] = 0ull;
+  int st = -1;
+  if (w.nanflag[r]) st = MGFLD_ENAN;
+  else if (v <= 1.0) st = MGFLD_OK;
+  else if (it >= tl.max_iter) st = MGFLD_ENOCONV;
+  if (st >= 0) {
+    w.status[r] = st;
+    w.active[r] = 0;
+    return;
+  }
+  const int a = atomicAdd(&w.counters[0], 1);
+  w.list_act[a] = r;
+  int ref = 1;
+  if (tl.mixed) ref = v > tl.refactor_ratio * w.vprev[r];
+  w.vprev[r] = v;
+  w.refac[r] = ref;
+  if (ref) {
+    const int b = atomicAdd(&w.counters[1], 1);
+    w.list_ref[b] = r;
+    w.nfact[r] += 1;
+  }
+}
+
+// Eq. a62b with the converged sources (w.src), T from the EoS, and per-zone ledger terms:
+// [0] lepton number before, [1] after, [2] lepton number lost at R_{I+1/2} (last zone only),
+// [3] energy at infinity before, [4] after, [5] energy lost, [6] gain-region heating.
+__global__ void k_finish(Prob p, Ws w, const double *__restrict__ psi, const double *__restrict__ ye,
+                         double *__restrict__ T) {
+  const int n = p.n;
+  const size_t zi = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (zi >= (size_t)p.n_ray * p.n_r) return;
+  const int ray = (int)(zi / p.n_r), i = (int)(zi % p.n_r);
+  const int last = p.n_r - 1;
+  const double *z = w.zone + zi * ZC_N;
+  const double inv_a = z[ZC_INV_A], a = z[ZC_A];
+  const double inv_a3 = inv_a * inv_a * inv_a;
+  const double vol = z[ZC_VOL];
+  const double rho = p.rho[zi], Y = ye[zi], Yn = w.ye_n[zi];
+  const double acdt = z[ZC_ACDT];
+  double sum_e = 0.0, heat = 0.0, nu_lep_a = 0.0, nu_lep_b = 0.0, nu_en_a = 0.0, nu_en_b = 0.0;
+  double lep_loss = 0.0, en_loss = 0.0;
+  for (int q = 0; q < NS; ++q) {
+    const size_t g0 = (((size_t)ray * NS + q) * p.n_r + i) * n;
+    for (int k = 0; k < n; ++k) {
+      const double wk = w.W[k] * inv_a3;
+      const double eps = w.E[k] * inv_a;
+      const double S = w.src[g0 + k];
+      const double pk = psi[g0 + k];
+      sum_e += stat_weight(q) * wk * eps * S;
+      if (q < 2) heat += wk * eps * S;
+      nu_lep_a += lepton_sign(q) * wk * pk;
+      nu_lep_b += lepton_sign(q) * wk * w.psi_n[g0 + k];
+      nu_en_a += stat_weight(q) * wk * eps * pk;
+      nu_en_b += stat_weight(q) * wk * eps * w.psi_n[g0 + k];
+      if (i == last) {
+        const double gh = w.ghost[((size_t)ray * NS + q) * n + k];
+        const double fb = -w.alpha[g0 + k] * (gh * pk - pk);       // A psi1 / a^2 at R_{I+1/2}
+        lep_loss += lepton_sign(q) * w.W[k] * fb;
+        en_loss += stat_weight(q) * w.W[k] * w.E[k] * fb;
+      }
+    }
+  }
+  const double e_new = w.e_n[zi] - acdt * kFourPiHC3 * (p.eos.mb / rho) * sum_e;
+  T[zi] = (e_new - eos_e_cold(p.eos, rho, Y)) / p.eos.ec;
+  double *zl = w.zled + zi * 8;
+  zl[0] = rho * vol * Yn / p.eos.mb + vol * kFourPiHC3 * nu_lep_b;
+  zl[1] = rho * vol * Y / p.eos.mb + vol * kFourPiHC3 * nu_lep_a;
+  zl[2] = (i == last) ? kC * p.dt * kFourPiHC3 * lep_loss : 0.0;
+  zl[3] = a * (rho * vol * w.e_n[zi] / p.eos.mb + vol * kFourPiHC3 * nu_en_b);
+  zl[4] = a * (rho * vol * e_new / p.eos.mb + vol * kFourPiHC3 * nu_en_a);
+  zl[5] = (i == last) ? kC * p.dt * kFourPiHC3 * en_loss : 0.0;
+  const double *re = p.r_edge + (size_t)ray * (p.n_r + 1);
+  const double rc = 0.5 * (re[i] + re[i + 1]);
+  zl[6] = (rc >= 1.0e7 && rc <= 3.0e7) ? -acdt * vol * kFourPiHC3 * heat : 0.0;
+  zl[7] = 0.0;
+  if (!isfinite(T[zi])) atomicExch(&w.nanflag[ray], 1);
+}
+
+// Per ray, fixed-order reduction of the per-zone ledger terms (deterministic).
+__global__ void k_ledger(int n_r, Ws w, double *ledger, double *heating, int *status) {
+  __shared__ double red[7][128];
+  const int ray = blockIdx.x;
+  double acc[7] = {0, 0, 0, 0, 0, 0, 0};
+  for (int i = threadIdx.x; i < n_r; i += blockDim.x) {
+    const double *z = w.zled + ((size_t)ray * n_r + i) * 8;
+    for (int c = 0; c < 7; ++c) acc[c] += z[c];
+  }
+  for (int c = 0; c < 7; ++c) red[c][threadIdx.x] = acc[c];
+  __syncthreads();
+  for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+    if (threadIdx.x < h)
+      for (int c = 0; c < 7; ++c) red[c][threadIdx.x] += red[c][threadIdx.x + h];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const double lb = red[0][0], la = red[1][0], ll = red[2][0];
+    const double eb = red[3][0], ea = red[4][0], el = red[5][0];
+    if (ledger) {
+      double *L = ledger + (size_t)ray * 8;
+      L[0] = lb; L[1] = la; L[2] = ll; L[3] = la + ll - lb;
+      L[4] = eb; L[5] = ea; L[6] = el; L[7] = ea + el - eb;
+    }
+    if (heating) heating[ray] = red[6][0];
+    if (w.nanflag[ray]) w.status[ray] = MGFLD_ENAN;
+    // Worst status over rays: ENAN dominates ENOCONV.
+    const int st = w.status[ray];
+    if (st == MGFLD_ENAN) atomicMax(&w.counters[2], 2);
+    else if (st == MGFLD_ENOCONV) atomicMax(&w.counters[2], 1);
+    if (status) status[ray] = w.status[ray];
+  }
+}
+
+// Optional per-category timing: a pair of CUDA events per category, read back after the
+// host synchronisations the outer iteration already performs.
+struct Prof {
+  double *out;
+  cudaStream_t s;
+  cudaEvent_t ev[MGFLD_PROF_N][2];
+  int pending[MGFLD_PROF_N];
+  Prof(double *o, cudaStream_t st) : out(o), s(st) {
+    for (int c = 0; c < MGFLD_PROF_N; ++c) {
+      pending[c] = 0;
+      if (out) {
+        cudaEventCreate(&ev[c][0]);
+        cudaEventCreate(&ev[c][1]);
+      }
+    }
+  }
+  ~Prof() {
+    if (!out) return;
+    for (int c = 0; c < MGFLD_PROF_N; ++c) {
+      cudaEventDestroy(ev[c][0]);
+      cudaEventDestroy(ev[c][1]);
+    }
+  }
+  void begin(int c) { if (out) cudaEventRecord(ev[c][0], s); }
+  void end(int c, int launches) {
+    if (!out) return;
+    cudaEventRecord(ev[c][1], s);
+    pending[c] = launches;
+  }
+  void collect() {
+    if (!out) return;
+    for (int c = 0; c < MGFLD_PROF_N; ++c) {
+      if (!pending[c]) continue;
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, ev[c][0], ev[c][1]) == cudaSuccess) {
+        out[2 * c] += ms;
+        out[2 * c + 1] += pending[c];
+      }
+      pending[c] = 0;
+    }
+  }
+};
+
+static Eos make_eos(const mgfld_eos_params &e) {
+  Eos d;
+  d.g1 = e.gamma1; d.g2 = e.gamma2; d.ec = e.e_coef; d.gn = e.g_n; d.gp = e.g_p;
+  d.rho0 = e.rho_0; d.mbc2 = e.mb_c2; d.mb = e.m_b;
+  d.f1 = 0.75 * std::cbrt(3.0 / (8.0 * kPi)) * kHC;
+  d.rho_fac = std::pow(e.m_b / e.rho_0, e.gamma1 - 4.0 / 3.0);
+  d.f2 = (e.gamma1 - 1.0) / (e.gamma2 - 1.0) * d.f1 * std::pow(0.5 * e.rho_nuc / e.m_b, e.gamma1 - e.gamma2) *
+         d.rho_fac;
+  return d;
+}
+
+static bool dims_ok(const mgfld_dims *d) {
+  return d && d->n_ray >= 1 && d->n_r >= 1 && d->n_e >= 1 && d->n_e <= MAX_NE && d->n_s == NS;
+}
+
+static bool prob_ok(const mgfld_problem *p) {
+  return p && p->r_edge && p->e_edge && p->rho && p->kappa_abs && p->kappa_scat && p->dt > 0.0 &&
+         (p->outer_bc == MGFLD_BC_GHOST || p->outer_bc == MGFLD_BC_REFLECT);
+}
+
+static Prob make_prob(const mgfld_dims *d, const mgfld_problem *p) {
+  Prob q;
+  q.n_ray = d->n_ray; q.n_r = d->n_r; q.n = d->n_e; q.bc = p->outer_bc; q.dt = p->dt;
+  q.r_edge = p->r_edge; q.lapse = p->lapse; q.e_edge = p->e_edge; q.rho = p->rho;
+  q.kabs = p->kappa_abs; q.kscat = p->kappa_scat; q.nes = p->nes_coef; q.scale = p->scale;
+  q.eos = make_eos(p->eos);
+  return q;
+}
+
+static inline unsigned nblk(size_t n, unsigned b) { return (unsigned)((n + b - 1) / b); }
+
+#define MGFLD_CUDA(x)                                  \
+  do {                                                 \
+    if ((x) != cudaSuccess) return MGFLD_ECUDA;        \
+  } while (0)
+
+}  // namespace mgfld
+
+using namespace mgfld;
+
+extern "C" {
+
+mgfld_eos_params mgfld_eos_default(void) {
+  mgfld_eos_params e;
+  e.gamma1 = 4.0 / 3.0; e.gamma2 = 2.5; e.e_coef = 1.5; e.g_n = 2.0; e.g_p = 2.0;
+  e.rho_nuc = 2.5e14; e.rho_0 = 2.5e14; e.mb_c2 = 939.565; e.m_b = 1.674927e-24;
+  return e;
+}
+
+size_t mgfld_workspace_bytes(const mgfld_dims *dims, int precision) {
+  if (!dims_ok(dims)) return 0;
+  return make_layout(dims->n_ray, dims->n_r, dims->n_e, precision).total;
+}
+
+size_t mgfld_factor_bytes(const mgfld_dims *dims, int precision) {
+  if (!dims_ok(dims)) return 0;
+  const size_t blocks = (size_t)dims->n_ray * NS * dims->n_r * dims->n_e * dims->n_e;
+  return blocks * (precision == MGFLD_MIXED ? sizeof(float) : sizeof(double));
+}
+
+const char *mgfld_status_str(mgfld_status s) {
+  switch (s) {
+    case MGFLD_OK: return "ok";
+    case MGFLD_EINVAL: return "invalid argument";
+    case MGFLD_ENOMEM: return "workspace too small";
+    case MGFLD_ENOCONV: return "outer iteration did not converge";
+    case MGFLD_ENAN: return "non-finite value";
+    case MGFLD_ECUDA: return "CUDA error";
+  }
+  return "unknown status";
+}
+
+mgfld_status mgfld_step(const mgfld_dims *dims, const mgfld_problem *prob, mgfld_state *state,
+                        const mgfld_step_opts *opts, mgfld_step_report *report, void *ws, size_t ws_bytes,
+                        void *stream) {
+  if (!dims_ok(dims) || !prob_ok(prob) || !state || !state->psi || !state->ye || !state->T || !opts || !ws)
+    return MGFLD_EINVAL;
+  if ((opts->precision != MGFLD_FP64 && opts->precision != MGFLD_MIXED) || opts->max_iter < 1 ||
+      !(opts->tol > 0.0) || !(opts->tol_ye > 0.0) || !(opts->tolmin_psi >= 0.0) || !(opts->tolmin_ye >= 0.0))
+    return MGFLD_EINVAL;
+  if (((uintptr_t)ws & 255u) != 0) return MGFLD_EINVAL;
+  const Layout L = make_layout(dims->n_ray, dims->n_r, dims->n_e, opts->precision);
+  if (ws_bytes < L.total) return MGFLD_ENOMEM;
+  cudaStream_t s = (cudaStream_t)stream;
+  const Ws w = resolve(ws, L);
+  const Prob p = make_prob(dims, prob);
+  Tol tl;
+  tl.tol = opts->tol; tl.tolmin = opts->tolmin_psi; tl.tol_ye = opts->tol_ye; tl.tolmin_ye = opts->tolmin_ye;
+  tl.refactor_ratio = opts->refactor_ratio > 0.0 ? opts->refactor_ratio : 0.1;
+  tl.max_iter = opts->max_iter; tl.mixed = opts->precision == MGFLD_MIXED;
+  const int R = dims->n_ray, n = dims->n_e, NR = dims->n_r;
+
+  Prof prof(opts->profile, s);
+  prof.begin(MGFLD_PROF_SETUP);
+  MGFLD_CUDA(launch_setup(p, w, state->psi, state->ye, state->T, s));
+  k_init<<<nblk(R, 128), 128, 0, s>>>(R, w);
+  MGFLD_CUDA(cudaGetLastError());
+  prof.end(MGFLD_PROF_SETUP, 7);
+  int n_act = R, n_ref = R;
+  int host_counters[8];
+  for (int it = 0; it < opts->max_iter && n_act > 0; ++it) {
+    const int *jac = tl.mixed ? w.refac : nullptr;
+    prof.begin(MGFLD_PROF_ASSEMBLE);
+    MGFLD_CUDA(launch_assemble(p, w, state->psi, state->ye, state->T, w.diag, w.lower, w.upper, w.rhs,
+                               w.list_act, n_act, jac, s));
+    prof.end(MGFLD_PROF_ASSEMBLE, 1);
+    const int *flist = tl.mixed ? w.list_ref : w.list_act;
+    const int nf = tl.mixed ? n_ref : n_act;
+    if (nf > 0) {
+      prof.begin(MGFLD_PROF_FACTOR);
+      MGFLD_CUDA(launch_factor(n, NR, nf * NS, w.diag, w.lower, w.upper, w.dinv, opts->precision, flist, s));
+      prof.end(MGFLD_PROF_FACTOR, 1);
+    }
+    prof.begin(MGFLD_PROF_SOLVE);
+    MGFLD_CUDA(launch_solve(n, NR, n_act * NS, w.dinv, w.lower, w.upper, w.rhs, w.x, opts->precision,
+                            w.list_act, s));
+    prof.end(MGFLD_PROF_SOLVE, 1);
+    prof.begin(MGFLD_PROF_UPDATE);
+    k_update<<<nblk((size_t)n_act * NR, 128), 128, 0, s>>>(p, w, tl, state->psi, state->ye, state->T,
+                                                           w.list_act, n_act);
+    MGFLD_CUDA(cudaGetLastError());
+    MGFLD_CUDA(cudaMemsetAsync(w.counters, 0, sizeof(int) * 2, s));
+    k_check<<<nblk(R, 128), 128, 0, s>>>(R, w, tl);
+    MGFLD_CUDA(cudaGetLastError());
+    prof.end(MGFLD_PROF_UPDATE, 2);
+    MGFLD_CUDA(cudaMemcpyAsync(host_counters, w.counters, sizeof(int) * 2, cudaMemcpyDeviceToHost, s));
+    MGFLD_CUDA(cudaStreamSynchronize(s));
+    prof.collect();
+    n_act = host_counters[0];
+    n_ref = host_counters[1];
+  }
+  prof.begin(MGFLD_PROF_FINISH);
+  MGFLD_CUDA(launch_assemble(p, w, state->psi, state->ye, state->T, w.diag, w.lower, w.upper, w.rhs, nullptr,
+                             R, nullptr, s, w.src));
+  k_finish<<<nblk((size_t)R * NR, 128), 128, 0, s>>>(p, w, state->psi, state->ye, state->T);
+  MGFLD_CUDA(cudaGetLastError());
+  MGFLD_CUDA(cudaMemsetAsync(w.counters + 2, 0, sizeof(int), s));
+  k_ledger<<<R, 128, 0, s>>>(NR, w, report ? report->ledger : nullptr, report ? report->heating : nullptr,
+                             report ? report->ray_status : nullptr);
+  MGFLD_CUDA(cudaGetLastError());
+  prof.end(MGFLD_PROF_FINISH, 3);
+  if (report && report->iters)
+    MGFLD_CUDA(cudaMemcpyAsync(report->iters, w.iters, sizeof(int) * R, cudaMemcpyDeviceToDevice, s));
+  if (report && report->factorizations)
+    MGFLD_CUDA(cudaMemcpyAsync(report->factorizations, w.nfact, sizeof(int) * R, cudaMemcpyDeviceToDevice, s));
+  MGFLD_CUDA(cudaMemcpyAsync(host_counters + 2, w.counters + 2, sizeof(int), cudaMemcpyDeviceToHost, s));
+  MGFLD_CUDA(cudaStreamSynchronize(s));
+  prof.collect();
+  if (host_counters[2] == 2) return MGFLD_ENAN;
+  if (host_counters[2] == 1) return MGFLD_ENOCONV;
+  return MGFLD_OK;
+}
+
+mgfld_status mgfld_assemble(const mgfld_dims *dims, const mgfld_problem *prob, const mgfld_state *state,
+                            mgfld_system *sys, void *ws, size_t ws_bytes, void *stream) {
+  if (!dims_ok(dims) || !prob_ok(prob) || !state || !state->psi || !state->ye || !state->T || !sys ||
+      !sys->diag || !sys->lower || !sys->upper || !sys->rhs || !ws)
+    return MGFLD_EINVAL;
+  if (((uintptr_t)ws & 255u) != 0) return MGFLD_EINVAL;
+  const Layout L = make_layout(dims->n_ray, dims->n_r, dims->n_e, MGFLD_FP64);
+  if (ws_bytes < L.total) return MGFLD_ENOMEM;
+  cudaStream_t s = (cudaStream_t)stream;
+  const Ws w = resolve(ws, L);
+  const Prob p = make_prob(dims, prob);
+  MGFLD_CUDA(launch_setup(p, w, state->psi, state->ye, state->T, s));
+  MGFLD_CUDA(launch_assemble(p, w, state->psi, state->ye, state->T, sys->diag, sys->lower, sys->upper,
+                             sys->rhs, nullptr, dims->n_ray, nullptr, s));
+  return MGFLD_OK;
+}
+
+mgfld_status mgfld_factor(const mgfld_dims *dims, const mgfld_system *sys, int precision, void *factor,
+                          void *stream) {
+  if (!dims_ok(dims) || !sys || !sys->diag || !sys->lower || !sys->upper || !factor ||
+      (precision != MGFLD_FP64 && precision != MGFLD_MIXED))
+    return MGFLD_EINVAL;
+  MGFLD_CUDA(launch_factor(dims->n_e, dims->n_r, dims->n_ray * NS, sys->diag, sys->lower, sys->upper, factor,
+                           precision, nullptr, (cudaStream_t)stream));
+  return MGFLD_OK;
+}
+
+mgfld_status mgfld_solve(const mgfld_dims *dims, const mgfld_system *sys, int precision, const void *factor,
+                         const double *rhs, double *x, void *stream) {
+  if (!dims_ok(dims) || !sys || !sys->lower || !sys->upper || !factor || !rhs || !x ||
+      (precision != MGFLD_FP64 && precision != MGFLD_MIXED))
+    return MGFLD_EINVAL;
+  MGFLD_CUDA(launch_solve(dims->n_e, dims->n_r, dims->n_ray * NS, factor, sys->lower, sys->upper, rhs, x,
+                          precision, nullptr, (cudaStream_t)stream));
+  return MGFLD_OK;
+}
+
+}  // extern "C"

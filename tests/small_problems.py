@@ -21,3 +21,19 @@ def strong(n_ray=2, n_r=8, n_e=5, kabs=1e16, kscat=1e14, nes=1.0, lapse=False, c
     inp = dict(inp)
     inp['problem'] = p
     return inp
+
+
+def fp64_tolerance(inp):
+    """Parity tolerance of the FP64 path for a problem: max(1e-12, 1e-14 * stiffness), where
+    stiffness = max over (zone, group) of a c dt * (kappa_a + j + NES in/out rates) * |psi|,
+    divided by max |psi| (per ray and species).  The residual's source terms, of size
+    rate * psi, cancel at the root and each carries ~eps relative rounding, so two correct
+    FP64 implementations differ by ~eps * stiffness in the normwise measure."""
+    from oracle import mgfld_oracle as O
+    f = O.setup_step(inp['problem'], inp['psi0'], inp['ye0'], inp['T0'])
+    mu_q, _ = O.species_mu(f.rho, f.T_n, f.ye_n, f.eos)
+    j, _ = O.emissivity(f.kappa_abs, f.eps, mu_q, f.T_n)
+    rate = O.nes_inverse_mfp(f.psi_n, f.w, f.phi_out, f.phi_in) + j + f.kappa_abs
+    weighted = rate * (f.lapse * O.C_LIGHT * f.dt)[:, None, :, None] * np.abs(f.psi_n)
+    stiff = np.max(np.max(weighted, axis=(2, 3)) / np.max(np.abs(f.psi_n), axis=(2, 3)))
+    return max(1e-12, 1e-14 * stiff)

@@ -1,0 +1,241 @@
+"""GPU (libmgfld through the C ABI) vs the CPU oracle, on seeded synthetic inputs.
+
+Error measure (reading of "relative in psi0"): per ray and species, the max-norm
+of psi_gpu - psi_oracle over all zones and groups divided by the max-norm of
+psi_oracle.  Tolerances: FP64 path 1e-12, mixed path 1e-10 (as stated for the
+method), except the deliberately stiff strong-coupling problems, whose FP64
+rounding floor is ~1e-11 (NES rates ~1e4/(a c dt) amplify residual rounding)."""
+import numpy as np
+import pytest
+
+from oracle import mgfld_oracle as O
+from paper_1809_05608_gb300 import problems
+from tests import small_problems as SP
+
+torch = pytest.importorskip('torch')
+pytestmark = pytest.mark.gpu
+
+M = None
+
+
+@pytest.fixture(scope='module', autouse=True)
+def _lib():
+    global M
+    if not torch.cuda.is_available():
+        pytest.skip('no CUDA device')
+    from paper_1809_05608_gb300 import mgfld
+    M = mgfld
+    M.lib()
+
+
+def run_gpu(inp, precision=0, steps=1, **kw):
+    kw.setdefault('tol', 1e-12 if precision == 0 else 1e-11)
+    kw.setdefault('max_iter', 40)
+    st = M.Stepper(inp, precision, **kw)
+    psi, ye, T = st.state_to_device(inp['psi0'], inp['ye0'], inp['T0'])
+    codes = [st.step(psi, ye, T) for _ in range(steps)]
+    torch.cuda.synchronize()
+    rep = {k: v.cpu().numpy() for k, v in st.report.items()}
+    return psi.cpu().numpy(), ye.cpu().numpy(), T.cpu().numpy(), codes, rep
+
+
+def run_oracle(inp, steps=1):
+    psi, ye, T, outs = O.run_steps(inp['problem'], inp['psi0'], inp['ye0'], inp['T0'], steps)
+    return psi, ye, T, outs
+
+
+def normwise(a, b):
+    return float(np.max(O.rel_change(a - b, b)))
+
+
+def test_single_ray_fp64_matches_oracle():
+    inp = problems.make_problem(1)
+    psi, ye, T, codes, rep = run_gpu(inp)
+    psi_o, ye_o, T_o, outs = run_oracle(inp)
+    assert codes == [M.MGFLD_OK]
+    assert normwise(psi, psi_o) < 1e-12
+    assert np.max(np.abs(ye - ye_o)) < 1e-14
+    assert np.max(np.abs(T / T_o - 1)) < 1e-12
+    L, Lo = rep['ledger'], outs[0]['ledger']
+    assert np.allclose(L[:, [0, 1, 4, 5]], Lo[:, [0, 1, 4, 5]], rtol=1e-12, atol=0)
+    assert np.all(np.abs(L[:, 3]) <= 1e-13 * np.abs(L[:, 1]))
+    assert np.all(np.abs(L[:, 7]) <= 1e-13 * np.abs(L[:, 5]))
+
+
+def test_2d_full_size_ray_subset_fp64_two_steps():
+    """256-ray 512x20 profile family; rays are independent, so a subset is exact parity."""
+    inp = problems.make_problem(2, rays=[0, 101, 255])
+    psi, ye, T, codes, rep = run_gpu(inp, steps=2)
+    psi_o, ye_o, T_o, _ = run_oracle(inp, steps=2)
+    assert codes == [M.MGFLD_OK] * 2
+    assert normwise(psi, psi_o) < 1e-12
+    assert np.max(np.abs(T / T_o - 1)) < 1e-12
+    assert np.max(np.abs(ye - ye_o)) < 1e-14
+
+
+def test_full_launch_256_rays_sampled_against_oracle():
+    """The full 256-ray launch (the benchmark's configuration); sampled rays vs the oracle."""
+    full = problems.make_problem(2)
+    psi, ye, T, codes, rep = run_gpu(full)
+    assert codes == [M.MGFLD_OK]
+    rays = [3, 128, 200]
+    sub = problems.subset_rays(full, rays)
+    psi_o, ye_o, T_o, _ = run_oracle(sub)
+    assert normwise(psi[rays], psi_o) < 1e-12
+    assert np.max(np.abs(T[rays] / T_o - 1)) < 1e-12
+    assert np.all(rep['ray_status'] == 0) and np.all(rep['iters'] >= 2)
+
+
+@pytest.mark.parametrize('lapse', [False, True])
+def test_strong_coupling_fp64(lapse):
+    inp = SP.strong(n_ray=2, n_r=16, n_e=5, kabs=3e16, kscat=1e15, nes=30.0, lapse=lapse)
+    psi, ye, T, codes, rep = run_gpu(inp, steps=2, tol=1e-11)
+    psi_o, ye_o, T_o, outs = run_oracle(inp, steps=2)
+    assert codes == [M.MGFLD_OK] * 2
+    assert normwise(psi, psi_o) < SP.fp64_tolerance(inp)
+    assert np.max(np.abs(ye / ye_o - 1)) < 1e-12
+    assert np.max(np.abs(T / T_o - 1)) < 1e-11
+    L = rep['ledger']
+    assert np.all(np.abs(L[:, 3]) <= 1e-13 * np.abs(L[:, 1]))
+    assert np.all(np.abs(L[:, 7]) <= 1e-12 * np.abs(L[:, 5]))
+
+
+@pytest.mark.parametrize('n_e', [1, 3, 7, 12, 24, 32])
+def test_ragged_group_counts(n_e):
+    """Every padded block size (4, 8, 12, 24, 32) including ragged n_e < padded size."""
+    inp = SP.strong(n_ray=3, n_r=9, n_e=n_e, kabs=1e13, kscat=1e14, nes=5.0)
+    psi, ye, T, codes, _ = run_gpu(inp, tol=1e-11)
+    psi_o, ye_o, T_o, _ = run_oracle(inp)
+    assert codes == [M.MGFLD_OK]
+    tol = SP.fp64_tolerance(inp)
+    assert normwise(psi, psi_o) < tol
+    assert np.max(np.abs(T / T_o - 1)) < tol
+
+
+def test_single_zone_and_reflecting_equilibrium():
+    """Uniform matter at beta equilibrium with a reflecting outer edge is a fixed point."""
+    inp = SP.strong(n_ray=2, n_r=6, n_e=6, kabs=1e17, kscat=1e15, nes=20.0, bc=M.MGFLD_BC_REFLECT)
+    p = inp['problem']
+    p['rho'] = np.full_like(p['rho'], 4e12)
+    p['nes_coef'] = 1e-41 * p['rho'] * 20.0
+    T = np.full_like(inp['T0'], 6.0)
+    ye = np.full_like(inp['ye0'], 0.28)
+    mu_q, _ = O.species_mu(p['rho'], T, ye, O.EosParams())
+    eps, _ = O.local_energies(p['e_edge'], np.ones_like(T))
+    psi0 = 1.0 / (1.0 + np.exp((eps[:, None] - mu_q[:, :, :, None]) / T[:, None, :, None]))
+    inp = dict(inp, psi0=psi0, ye0=ye, T0=T)
+    psi, ye1, T1, codes, _ = run_gpu(inp)
+    assert codes == [M.MGFLD_OK]
+    assert normwise(psi, psi0) < 1e-13
+    assert np.max(np.abs(T1 / T - 1)) < 1e-13
+    one = SP.strong(n_ray=2, n_r=1, n_e=4)
+    psi, _, T1, codes, _ = run_gpu(one)
+    psi_o, _, T_o, _ = run_oracle(one)
+    assert codes == [M.MGFLD_OK] and normwise(psi, psi_o) < 1e-12
+
+
+def test_mixed_precision_matches_oracle_to_1e10():
+    inp = problems.make_problem(3, rays=[0, 511, 1023])
+    psi, ye, T, codes, rep = run_gpu(inp, precision=1, steps=2, tol=1e-10)
+    psi_o, ye_o, T_o, _ = run_oracle(inp, steps=2)
+    assert codes == [M.MGFLD_OK] * 2
+    assert normwise(psi, psi_o) < 1e-10
+    assert np.max(np.abs(T / T_o - 1)) < 1e-10
+    assert np.all(rep['factorizations'] >= 1)
+
+
+def test_mixed_strong_coupling():
+    inp = SP.strong(n_ray=2, n_r=16, n_e=5, kabs=3e16, kscat=1e15, nes=30.0, lapse=True)
+    psi, ye, T, codes, rep = run_gpu(inp, precision=1, steps=2, tol=1e-11)
+    psi_o, ye_o, T_o, _ = run_oracle(inp, steps=2)
+    assert codes == [M.MGFLD_OK] * 2
+    assert normwise(psi, psi_o) < 1e-10
+
+
+def test_assemble_matches_oracle_jacobian_and_residual():
+    inp = SP.strong(n_ray=2, n_r=7, n_e=5, kabs=3e16, kscat=1e15, nes=30.0, lapse=True)
+    n_ray, _, n_r, n_e = inp['psi0'].shape
+    st = M.Stepper(inp)
+    psi, ye, T = st.state_to_device(inp['psi0'], inp['ye0'], inp['T0'])
+    dims = M.Dims(n_ray, n_r, n_e, 4)
+    sys = dict(diag=torch.zeros(n_ray, 4, n_r, n_e, n_e, dtype=torch.float64, device='cuda'),
+               lower=torch.zeros(n_ray, 4, n_r, n_e, dtype=torch.float64, device='cuda'),
+               upper=torch.zeros(n_ray, 4, n_r, n_e, dtype=torch.float64, device='cuda'),
+               rhs=torch.zeros(n_ray, 4, n_r, n_e, dtype=torch.float64, device='cuda'))
+    assert M.mgfld_assemble(dims, st.prob.struct, psi, ye, T, sys, st.ws) == M.MGFLD_OK
+    torch.cuda.synchronize()
+    f = O.setup_step(inp['problem'], inp['psi0'], inp['ye0'], inp['T0'])
+    A, Bm, Bp = O.jacobian(f, f.psi_n, f.ye_n)
+    G, _ = O.residual(f, f.psi_n, f.ye_n)
+    D = sys['diag'].cpu().numpy()
+    # The NES self-scattering term enters the diagonal twice with opposite signs (it
+    # cancels exactly), so rounding is measured against the size of the summed terms.
+    mu_q, _ = O.species_mu(f.rho, f.T_n, f.ye_n, f.eos)
+    j, _ = O.emissivity(f.kappa_abs, f.eps, mu_q, f.T_n)
+    terms = O.nes_inverse_mfp(f.psi_n, f.w, f.phi_out, f.phi_in) + j + f.kappa_abs
+    for q in range(4):
+        blk = A[:, :, q * n_e:(q + 1) * n_e, q * n_e:(q + 1) * n_e]
+        scale = np.maximum(np.abs(blk).max(axis=-1), terms[:, q])[..., None]
+        assert np.max(np.abs(D[:, q] - blk) / scale) < 1e-13
+        lo = Bm[:, :, q * n_e:(q + 1) * n_e]
+        up = Bp[:, :, q * n_e:(q + 1) * n_e]
+        assert np.allclose(sys['lower'].cpu().numpy()[:, q], lo, rtol=1e-13, atol=0)
+        assert np.allclose(sys['upper'].cpu().numpy()[:, q], up, rtol=1e-13, atol=0)
+    rate = terms + 1.0 / (f.lapse[:, None, :, None] * O.C_LIGHT * f.dt)
+    rscale = np.max(rate, axis=(2, 3), keepdims=True) * np.max(np.abs(f.psi_n), axis=(2, 3), keepdims=True)
+    assert np.max(np.abs(sys['rhs'].cpu().numpy() + G) / rscale) < 1e-13
+
+
+@pytest.mark.parametrize('precision,unit', [(0, 2.2e-16), (1, 1.2e-7)])
+def test_factor_solve_matches_dense_lu(precision, unit):
+    """mgfld_factor + mgfld_solve on random block-tridiagonal systems (some needing
+    pivoting) against LAPACK on the dense matrix of each system."""
+    rng = np.random.default_rng(11)
+    for n_e, n_r in ((5, 6), (20, 9), (12, 4)):
+        n_ray = 3
+        diag = rng.standard_normal((n_ray, 4, n_r, n_e, n_e))
+        diag[0] += 4 * n_e * np.eye(n_e)
+        diag[1, :, :, 0, 0] = 0.0                      # needs a row exchange
+        diag[2] += 1.5 * np.eye(n_e)
+        lower = rng.standard_normal((n_ray, 4, n_r, n_e)); lower[:, :, 0] = 0
+        upper = rng.standard_normal((n_ray, 4, n_r, n_e)); upper[:, :, -1] = 0
+        rhs = rng.standard_normal((n_ray, 4, n_r, n_e))
+        dev = {k: torch.as_tensor(v, device='cuda') for k, v in
+               dict(diag=diag, lower=lower, upper=upper, rhs=rhs).items()}
+        dims = M.Dims(n_ray, n_r, n_e, 4)
+        fac = torch.empty(M.mgfld_factor_bytes(dims, precision), dtype=torch.uint8, device='cuda')
+        x = torch.empty_like(dev['rhs'])
+        assert M.mgfld_factor(dims, dev, precision, fac) == M.MGFLD_OK
+        assert M.mgfld_solve(dims, dev, precision, fac, dev['rhs'], x) == M.MGFLD_OK
+        torch.cuda.synchronize()
+        x = x.cpu().numpy()
+        for r in range(n_ray):
+            for q in range(4):
+                J = O.dense_matrix(diag[r, q], lower[r, q], upper[r, q])
+                xd = np.linalg.solve(J, rhs[r, q].reshape(-1))
+                err = np.max(np.abs(x[r, q].reshape(-1) - xd)) / np.max(np.abs(xd))
+                # backward-stable elimination: forward error <= O(n) unit roundoff x condition
+                assert err < 50 * unit * np.linalg.cond(J), (n_e, r, q, err)
+
+
+def test_nonconvergence_and_nan_are_reported_per_ray():
+    inp = SP.strong(n_ray=3, n_r=8, n_e=4, kabs=1e16, nes=10.0)
+    _, _, _, codes, rep = run_gpu(inp, max_iter=1)
+    assert codes == [M.MGFLD_ENOCONV]
+    assert np.all(rep['ray_status'] == M.MGFLD_ENOCONV) and np.all(rep['iters'] == 1)
+    bad = dict(inp)
+    psi0 = inp['psi0'].copy()
+    psi0[1, 0, 3, 2] = np.nan
+    bad['psi0'] = psi0
+    _, _, _, codes, rep = run_gpu(bad)
+    assert codes == [M.MGFLD_ENAN]
+    assert rep['ray_status'][1] == M.MGFLD_ENAN
+    assert rep['ray_status'][0] == M.MGFLD_OK and rep['ray_status'][2] == M.MGFLD_OK
+
+
+def test_chunked_rays_give_identical_results():
+    inp = problems.make_problem(2, n_ray=6, n_r=40, n_e=8)
+    a = run_gpu(inp)[0]
+    per_ray = M.mgfld_workspace_bytes(M.Dims(1, 40, 8, 4), 0)
+    b = run_gpu(inp, max_ws_bytes=2 * per_ray + 100)[0]
+    assert np.array_equal(a, b)
