@@ -87,6 +87,13 @@ class ClockSampler:
             self.thread.start()
         except OSError:
             self.proc = None
+            return
+        # nvidia-smi's start-up (NVML initialisation) perturbs the GPU for a moment: wait for
+        # its first sample before anything is timed.
+        t0 = time.time()
+        while not self.lines and time.time() - t0 < 15.0 and self.proc.poll() is None:
+            time.sleep(0.05)
+        time.sleep(0.5)
 
     def _read(self):
         for line in self.proc.stdout:
