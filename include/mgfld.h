@@ -182,6 +182,35 @@ mgfld_status mgfld_factor(const mgfld_dims *dims, const mgfld_system *sys, int p
 mgfld_status mgfld_solve(const mgfld_dims *dims, const mgfld_system *sys, int precision,
                          const void *factor, const double *rhs, double *x, void *stream);
 
+/* Capacity of the device scratch array used by mgfld_step_noalloc: 64 MiB per GPU. */
+#define MGFLD_NOALLOC_SCRATCH_BYTES ((size_t)64 << 20)
+
+/*
+ * mgfld_step_noalloc -- mgfld_step without a caller workspace.  (The paper has no
+ * counterpart; this is a packaging choice of this library.)
+ *
+ * For callers that cannot allocate device memory for the library: a host code that
+ * links this solver as a black box and has no GPU allocator of its own, a process
+ * whose device memory is reserved in full by another framework's pool, or a loop
+ * that cannot afford the device synchronisation of cudaMalloc/cudaFree.  The step's
+ * scratch is a fixed array of MGFLD_NOALLOC_SCRATCH_BYTES in the library's device
+ * image, kept by every GPU that loads the library until the process exits; nothing is
+ * allocated or freed by this call.  Inputs and outputs are the caller's, as for
+ * mgfld_step.
+ *   - Returns MGFLD_ENOMEM, before touching the GPU, when mgfld_workspace_bytes(dims,
+ *     opts->precision) exceeds MGFLD_NOALLOC_SCRATCH_BYTES (e.g. 3 rays of 512 zones x
+ *     20 groups in FP64); split the rays into several calls.
+ *   - Returns MGFLD_EINVAL if opts->profile is set (timing would create CUDA events).
+ *   - The first call on each device looks up the array's device address with that
+ *     device current; make that first call before any stream capture begins.
+ *   - All calls on a device share the one array: calls that may overlap on the GPU
+ *     (other streams, other host threads) race and must be serialised by the caller.
+ *     Each call rewrites every part of the scratch it reads, so the contents left by
+ *     a previous call never leak into a result.
+ */
+mgfld_status mgfld_step_noalloc(const mgfld_dims *dims, const mgfld_problem *prob, mgfld_state *state,
+                                const mgfld_step_opts *opts, mgfld_step_report *report, void *stream);
+
 /* Human-readable name of a status code (static string). */
 const char *mgfld_status_str(mgfld_status s);
 

@@ -21,7 +21,8 @@ MGFLD_BC_GHOST, MGFLD_BC_REFLECT = 0, 1
 N_SPECIES = 4
 
 EXPORTED = ('mgfld_eos_default', 'mgfld_workspace_bytes', 'mgfld_step', 'mgfld_assemble',
-            'mgfld_factor_bytes', 'mgfld_factor', 'mgfld_solve', 'mgfld_status_str')
+            'mgfld_factor_bytes', 'mgfld_factor', 'mgfld_solve', 'mgfld_status_str', 'mgfld_step_noalloc')
+NOALLOC_SCRATCH_BYTES = 64 << 20
 
 
 class Dims(ctypes.Structure):
@@ -90,6 +91,8 @@ def lib():
     L.mgfld_solve.restype = ctypes.c_int
     L.mgfld_solve.argtypes = [P(Dims), P(System), ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
                               ctypes.c_void_p, ctypes.c_void_p]
+    L.mgfld_step_noalloc.restype = ctypes.c_int
+    L.mgfld_step_noalloc.argtypes = [P(Dims), P(Problem), P(State), P(StepOpts), P(StepReport), ctypes.c_void_p]
     L.mgfld_status_str.restype = ctypes.c_char_p
     L.mgfld_status_str.argtypes = [ctypes.c_int]
     _lib = L
@@ -186,6 +189,20 @@ def mgfld_step(dims, problem_struct, psi, ye, T, opts, ws, report=None, stream=N
     return lib().mgfld_step(ctypes.byref(dims), ctypes.byref(problem_struct), ctypes.byref(st),
                             ctypes.byref(opts), ctypes.byref(rep) if rep is not None else None,
                             _ptr(ws), ws.numel() * ws.element_size(), _stream(stream))
+
+
+def mgfld_step_noalloc(dims, problem_struct, psi, ye, T, opts, report=None, stream=None):
+    """mgfld_step with the library's own fixed device scratch (no workspace argument) for
+    callers that cannot allocate device memory; at most NOALLOC_SCRATCH_BYTES of workspace."""
+    rep = None
+    if report is not None:
+        rep = StepReport(_ptr(report.get('iters')), _ptr(report.get('ray_status')),
+                         _ptr(report.get('ledger')), _ptr(report.get('heating')),
+                         _ptr(report.get('factorizations')))
+    st = State(_ptr(psi), _ptr(ye), _ptr(T))
+    return lib().mgfld_step_noalloc(ctypes.byref(dims), ctypes.byref(problem_struct), ctypes.byref(st),
+                                    ctypes.byref(opts), ctypes.byref(rep) if rep is not None else None,
+                                    _stream(stream))
 
 
 def mgfld_assemble(dims, problem_struct, psi, ye, T, sys, ws, stream=None):
