@@ -99,7 +99,7 @@ enum {
   MGFLD_PROF_ASSEMBLE = 1, /* residual and Jacobian rows (k_assemble) */
   MGFLD_PROF_FACTOR = 2,   /* block-Thomas elimination with in-block Gauss-Jordan (k_factor) */
   MGFLD_PROF_SOLVE = 3,    /* forward/back substitution (k_solve) */
-  MGFLD_PROF_UPDATE = 4,   /* psi and Ye update, convergence bookkeeping (k_update, k_check) */
+  MGFLD_PROF_UPDATE = 4,   /* psi and Ye update, convergence bookkeeping (k_update_psi, k_update_ye, k_check) */
   MGFLD_PROF_FINISH = 5,   /* energy/temperature update and ledgers (k_finish, k_ledger) */
   MGFLD_PROF_N = 6
 };

@@ -12,9 +12,9 @@
 
 namespace mgfld {
 
-__global__ void k_assemble(Prob p, Ws w, const double *__restrict__ psi, const double *__restrict__ T,
-                           double *__restrict__ diag, double *__restrict__ lower,
-                           double *__restrict__ upper, double *__restrict__ rhs,
+template <typename TD>
+__global__ void k_assemble(Prob p, Ws w, const double *__restrict__ psi, TD *__restrict__ diag,
+                           double *__restrict__ lower, double *__restrict__ upper, double *__restrict__ rhs,
                            const int *__restrict__ list, int n_list, const int *__restrict__ jac_flag,
                            double *__restrict__ src_out) {
   const int n = p.n;
@@ -22,34 +22,36 @@ __global__ void k_assemble(Prob p, Ws w, const double *__restrict__ psi, const d
   const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (size_t)n_list * per_ray) return;
   const int ray = list ? list[t / per_ray] : (int)(t / per_ray);
+  // Thread order (zone, species, group) inside a ray: the four species of a zone share the
+  // zone's NES kernel rows through L1.
   const size_t local = t % per_ray;
   const int k = (int)(local % n);
-  const int i = (int)((local / n) % p.n_r);
-  const int q = (int)(local / ((size_t)n * p.n_r));
-  const size_t g = (size_t)ray * per_ray + local;          // global (ray, q, i, k) index
+  const int q = (int)((local / n) % NS);
+  const int i = (int)(local / ((size_t)n * NS));
+  const size_t g = (((size_t)ray * NS + q) * p.n_r + i) * n + k;   // (ray, q, i, k) storage index
   const size_t zi = (size_t)ray * p.n_r + i;
   const int last = p.n_r - 1;
 
   const double *z = w.zone + zi * ZC_N;
-  const double inv_a = z[ZC_INV_A];
-  const double inv_a3 = inv_a * inv_a * inv_a;
   const double pre = z[ZC_PRE];
   const double inv_acdt = z[ZC_INV_ACDT];
 
   const double *ps = psi + (g - k);
   const double pk = ps[k];
-  const double *ph = w.phi + zi * n * n;
-  double gain = 0.0, loss = 0.0;
+  const double *fin = w.phin + (zi * n + k) * n;
+  const double *fout = w.phout + (zi * n + k) * n;
+  double gain = 0.0, lp = 0.0;
   for (int kp = 0; kp < n; ++kp) {
-    const double wk = w.W[kp] * inv_a3;
-    gain += wk * ph[kp * n + k] * ps[kp];
-    loss += wk * ph[k * n + kp] * (1.0 - ps[kp]);
+    const double pv = ps[kp];
+    gain += fin[kp] * pv;
+    lp += fout[kp] * pv;
   }
+  const double loss = w.rsum[zi * n + k] - lp;          // sum_k' phout (1 - psi_k')
   const double sc = p.scale ? p.scale[q * n + k] : 1.0;
   const double kap = p.kabs[g] * sc;
   const double j = w.jbuf[g];
-  const double S = j * (1.0 - pk) - kap * pk + kCNes * ((1.0 - pk) * gain - pk * loss);
-  if (src_out) {               // converged sources for Eqs. a62b and the ledgers
+  const double S = j * (1.0 - pk) - kap * pk + ((1.0 - pk) * gain - pk * loss);
+  if (src_out) {               // converged sources for Eq. a62b and the ledgers
     src_out[g] = S;
     return;
   }
@@ -65,26 +67,39 @@ __global__ void k_assemble(Prob p, Ws w, const double *__restrict__ psi, const d
   rhs[g] = -G;
 
   if (jac_flag && !jac_flag[ray]) return;
-  const double dg = inv_acdt + pre * (al_out * (1.0 - gh) + al_in) + j + kap + kCNes * (gain + loss);
-  double *row = diag + g * n;
-  for (int kp = 0; kp < n; ++kp) {
-    const double wk = w.W[kp] * inv_a3;
-    const double d = -kCNes * wk * ((1.0 - pk) * ph[kp * n + k] + pk * ph[k * n + kp]);
-    row[kp] = kp == k ? d + dg : d;
+  const double dg = inv_acdt + pre * (al_out * (1.0 - gh) + al_in) + j + kap + (gain + loss);
+  TD *row = diag + g * n;
+  // dS_k/dpsi_k' = (1 - psi_k) phin + psi_k phout = phin - psi_k phd, entered with a minus.
+  if (sizeof(TD) == 4 && w.phin32) {
+    const float *fi = w.phin32 + (zi * n + k) * n, *fd = w.phd32 + (zi * n + k) * n;
+    const float pf = (float)pk;
+    for (int kp = 0; kp < n; ++kp) row[kp] = TD(fmaf(pf, fd[kp], -fi[kp]));
+  } else {
+    const double *fd = w.phd + (zi * n + k) * n;
+    for (int kp = 0; kp < n; ++kp) row[kp] = TD(fma(pk, fd[kp], -fin[kp]));
   }
+  row[k] = TD(double(row[k]) + dg);
   lower[g] = -pre * al_in;
   upper[g] = i < last ? -pre * al_out : 0.0;
+  if (w.lower32) {
+    w.lower32[g] = (float)lower[g];
+    w.upper32[g] = (float)upper[g];
+  }
 }
 
-cudaError_t launch_assemble(const Prob &p, const Ws &w, const double *psi, const double *ye, const double *T,
-                            double *diag, double *lower, double *upper, double *rhs, const int *list,
-                            int n_list, const int *jac_flag, cudaStream_t s, double *src_out) {
-  (void)ye;
+cudaError_t launch_assemble(const Prob &p, const Ws &w, const double *psi, void *diag, int diag_fp32,
+                            double *lower, double *upper, double *rhs, const int *list, int n_list,
+                            const int *jac_flag, cudaStream_t s, double *src_out) {
   const size_t total = (size_t)n_list * NS * p.n_r * p.n;
   if (total == 0) return cudaSuccess;
   const unsigned B = 256;
-  k_assemble<<<(unsigned)((total + B - 1) / B), B, 0, s>>>(p, w, psi, T, diag, lower, upper, rhs, list,
-                                                           n_list, jac_flag, src_out);
+  const unsigned grid = (unsigned)((total + B - 1) / B);
+  if (diag_fp32)
+    k_assemble<float><<<grid, B, 0, s>>>(p, w, psi, (float *)diag, lower, upper, rhs, list, n_list, jac_flag,
+                                         src_out);
+  else
+    k_assemble<double><<<grid, B, 0, s>>>(p, w, psi, (double *)diag, lower, upper, rhs, list, n_list,
+                                          jac_flag, src_out);
   return cudaGetLastError();
 }
 

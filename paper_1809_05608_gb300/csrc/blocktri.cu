@@ -22,37 +22,42 @@ struct Pack {
   static constexpr int THREADS = SPC * NP;
 };
 
-// 1/x for x of either precision.  FP64: FP32 seed refined by two Newton-Raphson steps
-// x_{m+1} = x_m (2 - d x_m) (quadratic convergence: 24 -> 48 -> full bits), which keeps
-// the FP64 pipe to four fused multiply-adds; outside the FP32 range a plain division.
+// Approximate 1/x for the pivot of a Gauss-Jordan step.  FP64: an FP32 seed refined by one
+// Newton-Raphson step x1 = x0 + x0 (1 - d x0) (quadratic convergence: ~2^-23 -> ~2^-46
+// relative), two fused multiply-adds on the scarce FP64 pipe; outside the FP32 range a
+// plain division.  The factors only steer the outer iteration, whose fixed point is set by
+// the FP64 residual, so a ~1e-14 relative error in the inverse costs nothing in the result.
 __device__ inline double recip(double d) {
   const double ad = fabs(d);
   if (!(ad > 1e-30 && ad < 1e30)) return 1.0 / d;
-  double x = (double)__frcp_rn((float)d);
-  double e = fma(-d, x, 1.0);
-  x = fma(x, e, x);
-  e = fma(-d, x, 1.0);
-  return fma(x, e, x);
+  const double x = (double)__frcp_rn((float)d);
+  return fma(x, fma(-d, x, 1.0), x);
 }
 __device__ inline float recip(float d) { return __frcp_rn(d); }
+
+// Pivot-search key: |x| as an integer (non-negative IEEE values order like their bit
+// patterns), so the comparisons run on the integer pipe instead of the FP64 pipe.
+__device__ inline long long pivot_key(double x) { return __double_as_longlong(fabs(x)); }
+__device__ inline long long pivot_key(float x) { return (long long)__float_as_int(fabsf(x)); }
 
 template <typename T> __device__ inline T to_t(double v);
 template <> __device__ inline double to_t<double>(double v) { return v; }
 template <> __device__ inline float to_t<float>(double v) { return (float)v; }
+template <typename T> __device__ inline T to_t(float v) { return (T)v; }
 
 // Map the j-th system of the launch to a global (ray, species) system index.
 __device__ inline long system_of(long j, const int *ray_list) {
   return ray_list ? (long)ray_list[j / NS] * NS + (j % NS) : j;
 }
 
-template <int NP, typename T>
+template <int NP, typename T, typename TIn>
 __global__ void __launch_bounds__(Pack<NP>::THREADS)
-k_factor(int n, int n_r, int n_sys, const double *__restrict__ diag, const double *__restrict__ lower,
+k_factor(int n, int n_r, int n_sys, const TIn *__restrict__ diag, const double *__restrict__ lower,
          const double *__restrict__ upper, T *__restrict__ dinv, const int *__restrict__ ray_list) {
   constexpr int SPC = Pack<NP>::SPC;
   __shared__ T tile[SPC][NP][NP + 1];   // natural-order inverse of the previous zone
   __shared__ T prow[SPC][NP];           // pivot row of the current step
-  __shared__ T cand[SPC][NP];           // pivot candidates (|a|, -1 once used)
+  __shared__ long long cand[SPC][NP];   // pivot candidates (key of |a|, -1 once used)
   __shared__ T ushr[SPC][NP];           // upper_{i-1}, the column scaling of the Schur update
   __shared__ int pivrow[SPC][NP];       // row chosen at each step
 
@@ -92,13 +97,13 @@ k_factor(int n, int n_r, int n_sys, const double *__restrict__ diag, const doubl
     int my_step = 0;
 #pragma unroll
     for (int pstep = 0; pstep < NP; ++pstep) {
-      cand[s][r] = used ? T(-1) : fabs(a[pstep]);
+      cand[s][r] = used ? -1LL : pivot_key(a[pstep]);
       __syncthreads();
       int best = 0;
-      T bv = cand[s][0];
+      long long bv = cand[s][0];
 #pragma unroll
       for (int c = 1; c < NP; ++c) {
-        const T v = cand[s][c];
+        const long long v = cand[s][c];
         if (v > bv) { bv = v; best = c; }
       }
       const bool me = (r == best);
@@ -226,12 +231,393 @@ k_solve(int n, int n_r, int n_sys, const T *__restrict__ dinv, const double *__r
   }
 }
 
+// ---------------------------------------------------------------------------------------
+// Warp-synchronous FP32 variants (MIXED precision): one warp per (ray, species) system, lane r
+// owns block row r (NP <= 32), no CTA-wide barriers.  The pivot is found with a warp max
+// reduction on integer keys, the pivot row is broadcast with shuffles, and the per-zone
+// natural-order inverse goes through a per-warp shared-memory tile.  FP32 arithmetic is 63x
+// cheaper than FP64 on this GPU, so these kernels are bound by the dependency chain along
+// the zones, which the warp form shortens.
+constexpr int kWarpsPerCta = 4;
+
+template <int NP, typename TIn, typename TC>
+__global__ void __launch_bounds__(kWarpsPerCta * 32)
+k_factor_w32(int n, int n_r, int n_sys, const TIn *__restrict__ diag, const TC *__restrict__ lower,
+             const TC *__restrict__ upper, float *__restrict__ dinv, const int *__restrict__ ray_list) {
+  __shared__ float tile[kWarpsPerCta][NP][NP + 1];
+  __shared__ float ushr[kWarpsPerCta][NP];
+  const unsigned full = 0xffffffffu;
+  const int wid = threadIdx.x >> 5, r = threadIdx.x & 31;
+  const long jsys = (long)blockIdx.x * kWarpsPerCta + wid;
+  if (jsys >= n_sys) return;                        // whole warp leaves; no CTA barrier below
+  const long sys = system_of(jsys, ray_list);
+  const bool real = r < n;
+  const bool row = r < NP;
+  float nxt[NP];
+  float nl = 0.f;
+  auto load_row = [&](int i) {
+    const size_t zr = ((size_t)sys * n_r + i) * n + r;
+#pragma unroll
+    for (int c = 0; c < NP; ++c) {
+      if (real && c < n) nxt[c] = (float)diag[zr * n + c];
+      else nxt[c] = (c == r) ? 1.f : 0.f;
+    }
+    nl = (real && i > 0) ? (float)lower[zr] : 0.f;
+  };
+  load_row(0);
+  for (int i = 0; i < n_r; ++i) {
+    const size_t zrow = ((size_t)sys * n_r + i) * n + r;
+    float a[NP];
+#pragma unroll
+    for (int c = 0; c < NP; ++c) a[c] = nxt[c];
+    const float lr = nl;
+    if (i + 1 < n_r) load_row(i + 1);
+    if (i > 0 && row) {
+#pragma unroll
+      for (int c = 0; c < NP; ++c) a[c] = a[c] - (lr * tile[wid][r][c]) * ushr[wid][c];
+    }
+    bool used = !row;
+    int my_step = 0;
+    int piv[NP];
+#pragma unroll
+    for (int pstep = 0; pstep < NP; ++pstep) {
+      const int key = used ? -1 : __float_as_int(fabsf(a[pstep]));
+      const int kmax = __reduce_max_sync(full, key);
+      const int best = __ffs(__ballot_sync(full, key == kmax)) - 1;
+      piv[pstep] = best;
+      float prow[NP];
+#pragma unroll
+      for (int c = 0; c < NP; ++c) prow[c] = __shfl_sync(full, a[c], best);
+      const bool me = (r == best);
+      const float inv = __frcp_rn(prow[pstep]);
+      const float f = me ? (1.f - inv) : a[pstep] * inv;
+#pragma unroll
+      for (int c = 0; c < NP; ++c) a[c] = a[c] - f * prow[c];
+      a[pstep] = me ? inv : -f;
+      if (me) { used = true; my_step = pstep; }
+    }
+    __syncwarp();
+    if (row) {
+#pragma unroll
+      for (int c = 0; c < NP; ++c) tile[wid][my_step][piv[c]] = a[c];
+      ushr[wid][r] = real ? (float)upper[zrow] : 0.f;
+    }
+    __syncwarp();
+    if (real) {
+      float *out = dinv + zrow * n;
+#pragma unroll
+      for (int c = 0; c < NP; ++c)
+        if (c < n) out[c] = tile[wid][r][c];
+    }
+  }
+}
+
+template <int NP>
+__global__ void __launch_bounds__(kWarpsPerCta * 32)
+k_solve_w32(int n, int n_r, int n_sys, const float *__restrict__ dinv, const double *__restrict__ lower,
+            const double *__restrict__ upper, const double *__restrict__ rhs, double *__restrict__ x,
+            const int *__restrict__ ray_list) {
+  const unsigned full = 0xffffffffu;
+  const int wid = threadIdx.x >> 5, r = threadIdx.x & 31;
+  const long jsys = (long)blockIdx.x * kWarpsPerCta + wid;
+  if (jsys >= n_sys) return;
+  const long sys = system_of(jsys, ray_list);
+  const bool real = r < n;
+  const size_t base = (size_t)sys * n_r * n;
+  // Power-of-two scaling of the right-hand side (FP32 range), as in the CTA kernel.
+  double m = 0.0;
+  if (real)
+    for (int i = 0; i < n_r; ++i) m = fmax(m, fabs(rhs[base + (size_t)i * n + r]));
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) m = fmax(m, __shfl_xor_sync(full, m, off));
+  double scale = 1.0;
+  if (m > 0.0 && isfinite(m)) {
+    int e;
+    frexp(m, &e);
+    scale = ldexp(1.0, -e);
+  }
+  float nrow[NP], rowv[NP];
+#pragma unroll
+  for (int c = 0; c < NP; ++c) nrow[c] = 0.f;
+  double nb = 0.0, nc = 0.0;
+  auto load = [&](int i, bool fwd) {
+    const size_t zr = base + (size_t)i * n + r;
+    const float *src = dinv + zr * n;
+#pragma unroll
+    for (int c = 0; c < NP; ++c) nrow[c] = (c < n) ? src[c] : 0.f;
+    nb = fwd ? rhs[zr] : x[zr];
+    nc = fwd ? (i > 0 ? lower[zr] : 0.0) : (i < n_r - 1 ? upper[zr] : 0.0);
+  };
+  if (real) load(0, true);
+  float g_prev = 0.f;
+  for (int i = 0; i < n_r; ++i) {
+#pragma unroll
+    for (int c = 0; c < NP; ++c) rowv[c] = nrow[c];
+    const double b = nb, l = nc;
+    if (real && i + 1 < n_r) load(i + 1, true);
+    const float v = real ? (float)(b * scale) - (float)l * g_prev : 0.f;
+    float acc0 = 0.f, acc1 = 0.f;
+#pragma unroll
+    for (int c = 0; c < NP; c += 2) {
+      acc0 = fmaf(rowv[c], __shfl_sync(full, v, c), acc0);
+      if (c + 1 < NP) acc1 = fmaf(rowv[c + 1], __shfl_sync(full, v, c + 1), acc1);
+    }
+    const float g = acc0 + acc1;
+    if (real) x[base + (size_t)i * n + r] = (double)g;
+    g_prev = g;
+  }
+  if (real) load(n_r - 1, false);
+  float x_next = 0.f;
+  for (int i = n_r - 1; i >= 0; --i) {
+#pragma unroll
+    for (int c = 0; c < NP; ++c) rowv[c] = nrow[c];
+    const double gz = nb, u = nc;
+    if (real && i > 0) load(i - 1, false);
+    const float v = real ? (float)u * x_next : 0.f;
+    float acc0 = 0.f, acc1 = 0.f;
+#pragma unroll
+    for (int c = 0; c < NP; c += 2) {
+      acc0 = fmaf(rowv[c], __shfl_sync(full, v, c), acc0);
+      if (c + 1 < NP) acc1 = fmaf(rowv[c + 1], __shfl_sync(full, v, c + 1), acc1);
+    }
+    const float xi = gz - (acc0 + acc1);
+    if (real) x[base + (size_t)i * n + r] = (double)xi / scale;
+    x_next = xi;
+  }
+}
+
+#define MGFLD_DISPATCH_NP(n, ...)                          \
+  if (n <= 4) { constexpr int NP = 4; __VA_ARGS__; }         \
+  else if (n <= 8) { constexpr int NP = 8; __VA_ARGS__; }    \
+  else if (n <= 12) { constexpr int NP = 12; __VA_ARGS__; }  \
+  else if (n <= 16) { constexpr int NP = 16; __VA_ARGS__; }  \
+  else if (n <= 20) { constexpr int NP = 20; __VA_ARGS__; }  \
+  else if (n <= 24) { constexpr int NP = 24; __VA_ARGS__; }  \
+  else { constexpr int NP = 32; __VA_ARGS__; }
+
+// ---------------------------------------------------------------------------------------
+// TMA-fed warp solve (MIXED, even n): each warp streams its system's per-zone inverse block and
+// the zone's right-hand side / coupling vectors into a ring of shared-memory slots with bulk
+// asynchronous copies (cp.async.bulk, completion counted on an mbarrier per slot), issued
+// STAGES-1 zones ahead by lane 0, so the recurrence never waits on a global-memory round trip.
+// Every wait is bounded: on timeout the warp flags `err`, waits (bounded) for its copies in
+// flight and returns.
+template <int NP>
+struct SolveRing {
+  static constexpr int STAGES = NP <= 24 ? 6 : 4;
+  static constexpr int WPC = 2;                              // warps (systems) per CTA
+  static constexpr int SLOT = NP * NP * 4;                   // bytes: one inverse block
+};
+
+__device__ inline unsigned smem_addr(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ inline void mbar_init(unsigned long long *bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ inline void mbar_fence_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ inline void mbar_expect_tx(unsigned long long *bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ inline void bulk_g2s(void *dst, const void *src, unsigned bytes, unsigned long long *bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+                   "r"(smem_addr(dst)), "l"(src), "r"(bytes), "r"(smem_addr(bar))
+               : "memory");
+}
+__device__ inline bool mbar_try_wait(unsigned long long *bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+constexpr int kWaitLimit = 1 << 22;
+__device__ inline bool mbar_wait_bounded(unsigned long long *bar, unsigned parity) {
+  for (int it = 0; it < kWaitLimit; ++it)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+
+// Per-system max |rhs| (for the power-of-two scaling of the FP32 solve), one CTA per system,
+// coalesced over the system's contiguous n_r x n right-hand side.
+__global__ void k_sysmax(int n, int n_r, const double *__restrict__ rhs, const int *__restrict__ ray_list,
+                         int *__restrict__ sys_exp) {
+  __shared__ double red[256];
+  const long sys = system_of(blockIdx.x, ray_list);
+  const size_t base = (size_t)sys * n_r * n, cnt = (size_t)n_r * n;
+  double m = 0.0;
+  for (size_t e = threadIdx.x; e < cnt; e += blockDim.x) m = fmax(m, fabs(rhs[base + e]));
+  red[threadIdx.x] = m;
+  __syncthreads();
+  for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+    if (threadIdx.x < h) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + h]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    // k with max |rhs| 2^k in [0.5, 1): the exponent field read off the bit pattern.
+    m = red[0];
+    const long long b = __double_as_longlong(m);
+    const int e = (int)((b >> 52) & 0x7ff);
+    sys_exp[blockIdx.x] = (m > 0.0 && e < 0x7ff) ? 1022 - e : 0;
+  }
+}
+
+template <int NP>
+__global__ void __launch_bounds__(SolveRing<NP>::WPC * 32)
+k_solve_tma(int n, int n_r, int n_sys, const float *__restrict__ dinv, const float *__restrict__ lower,
+            const float *__restrict__ upper, const double *__restrict__ rhs, double *__restrict__ x,
+            float *__restrict__ g32, const int *__restrict__ ray_list, const int *__restrict__ sys_exp, int *err) {
+  using R = SolveRing<NP>;
+  constexpr int S = R::STAGES;
+  constexpr int D = 8;                                      // depth of the per-lane vector queue
+  __shared__ __align__(128) unsigned char ring[R::WPC][S][NP * NP * 4];
+  __shared__ __align__(8) unsigned long long bar[R::WPC][S];
+  const unsigned full = 0xffffffffu;
+  const int wid = threadIdx.x >> 5, r = threadIdx.x & 31;
+  const long jsys = (long)blockIdx.x * R::WPC + wid;
+  if (jsys >= n_sys) return;
+  const long sys = system_of(jsys, ray_list);
+  const bool real = r < n;
+  const size_t base = (size_t)sys * n_r * n;
+  const unsigned blk = (unsigned)(n * n * 4);
+  const int kexp = sys_exp[jsys];             // rhs is scaled by 2^kexp before rounding to FP32
+  if (r == 0) {
+    for (int k = 0; k < S; ++k) mbar_init(&bar[wid][k], 1);
+    mbar_fence_init();
+  }
+  __syncwarp();
+
+  // Use u < n_r is forward zone u, u >= n_r backward zone 2 n_r - 1 - u; one bulk copy (the
+  // zone's inverse block) per use.
+  auto zone_of = [&](int u) { return u < n_r ? u : 2 * n_r - 1 - u; };
+  auto issue = [&](int u) {
+    unsigned long long *b = &bar[wid][u % S];
+    mbar_expect_tx(b, blk);
+    bulk_g2s(ring[wid][u % S], dinv + (base + (size_t)zone_of(u) * n) * n, blk, b);
+  };
+  auto wait = [&](int u, int issued_to) -> bool {
+    bool ok = mbar_wait_bounded(&bar[wid][u % S], (unsigned)((u / S) & 1));
+    ok = __all_sync(full, ok);
+    if (!ok) {                                    // give up: flag, drain own copies, return
+      if (r == 0) {
+        atomicExch(err, 1);
+        for (int v = u + 1; v <= issued_to; ++v) mbar_wait_bounded(&bar[wid][v % S], (unsigned)((v / S) & 1));
+      }
+      __syncwarp();
+    }
+    return ok;
+  };
+  // Per-lane queue of the zone vectors (own row), D zones ahead, all in FP32 (no FP64-pipe
+  // conversion on the recurrence: the rhs is rescaled by exponent arithmetic).
+  float qa[D], qb[D];
+  auto fetch = [&](int u, float &va, float &vb) {
+    va = 0.f;
+    vb = 0.f;
+    if (!real || u >= 2 * n_r) return;
+    const int i = zone_of(u);
+    const size_t zr = base + (size_t)i * n + r;
+    if (u < n_r) {
+      va = d2f_exp2(rhs[zr], kexp);
+      vb = i > 0 ? lower[zr] : 0.f;
+    } else {
+      va = g32[zr];                                 // forward result written by this lane
+      vb = i < n_r - 1 ? upper[zr] : 0.f;
+    }
+  };
+
+  int issued = -1;
+  if (r == 0)
+    for (int u = 0; u < S - 1 && u < n_r; ++u) issue(u);
+  issued = (S - 1 < n_r ? S - 1 : n_r) - 1;
+#pragma unroll
+  for (int d = 0; d < D; ++d) fetch(d < n_r ? d : 2 * n_r, qa[d], qb[d]);
+  float g_prev = 0.f;
+  for (int i = 0; i < n_r; ++i) {
+    const float b = qa[0], l = qb[0];
+#pragma unroll
+    for (int d = 0; d < D - 1; ++d) { qa[d] = qa[d + 1]; qb[d] = qb[d + 1]; }
+    fetch(i + D < n_r ? i + D : 2 * n_r, qa[D - 1], qb[D - 1]);
+    if (!wait(i, issued)) return;
+    const float *row = (const float *)ring[wid][i % S] + (size_t)r * n;
+    const float v = real ? b - l * g_prev : 0.f;
+    float acc0 = 0.f, acc1 = 0.f;
+#pragma unroll
+    for (int c = 0; c < NP; c += 2) {
+      const float v0 = __shfl_sync(full, v, c), v1 = __shfl_sync(full, v, c + 1);
+      if (real && c < n) acc0 = fmaf(row[c], v0, acc0);
+      if (real && c + 1 < n) acc1 = fmaf(row[c + 1], v1, acc1);
+    }
+    const float g = acc0 + acc1;
+    if (real) g32[base + (size_t)i * n + r] = g;
+    g_prev = g;
+    __syncwarp();
+    const int nu = i + S - 1;
+    if (nu < n_r) {
+      if (r == 0) issue(nu);
+      issued = nu;
+    }
+  }
+  if (r == 0)
+    for (int u = n_r; u < n_r + S - 1 && u < 2 * n_r; ++u) issue(u);
+  issued = (n_r + S - 1 < 2 * n_r ? n_r + S - 1 : 2 * n_r) - 1;
+#pragma unroll
+  for (int d = 0; d < D; ++d) fetch(n_r + d, qa[d], qb[d]);
+  float x_next = 0.f;
+  for (int k = 0; k < n_r; ++k) {
+    const int u = n_r + k, i = n_r - 1 - k;
+    const float gz = qa[0], uu = qb[0];
+#pragma unroll
+    for (int d = 0; d < D - 1; ++d) { qa[d] = qa[d + 1]; qb[d] = qb[d + 1]; }
+    fetch(u + D, qa[D - 1], qb[D - 1]);
+    if (!wait(u, issued)) return;
+    const float *row = (const float *)ring[wid][u % S] + (size_t)r * n;
+    const float v = real ? uu * x_next : 0.f;
+    float acc0 = 0.f, acc1 = 0.f;
+#pragma unroll
+    for (int c = 0; c < NP; c += 2) {
+      const float v0 = __shfl_sync(full, v, c), v1 = __shfl_sync(full, v, c + 1);
+      if (real && c < n) acc0 = fmaf(row[c], v0, acc0);
+      if (real && c + 1 < n) acc1 = fmaf(row[c + 1], v1, acc1);
+    }
+    const float xi = gz - (acc0 + acc1);
+    if (real) x[base + (size_t)i * n + r] = f2d_exp2(xi, -kexp);
+    x_next = xi;
+    __syncwarp();
+    const int nu = u + S - 1;
+    if (nu < 2 * n_r) {
+      if (r == 0) issue(nu);
+      issued = nu;
+    }
+  }
+}
+
+cudaError_t launch_solve_tma(int n, int n_r, int n_sys, const void *dinv, const float *lower32,
+                             const float *upper32, const double *rhs, double *x, float *g32,
+                             const int *ray_list, int *sys_exp, int *err, cudaStream_t s) {
+  if (n_sys == 0) return cudaSuccess;
+  k_sysmax<<<n_sys, 256, 0, s>>>(n, n_r, rhs, ray_list, sys_exp);
+  MGFLD_DISPATCH_NP(n, {
+    using R = SolveRing<NP>;
+    const unsigned grid = (unsigned)((n_sys + R::WPC - 1) / R::WPC);
+    k_solve_tma<NP><<<grid, R::WPC * 32, 0, s>>>(n, n_r, n_sys, (const float *)dinv, lower32, upper32, rhs, x,
+                                                 g32, ray_list, sys_exp, err);
+    return cudaGetLastError();
+  })
+}
+
 template <int NP, typename T>
-static cudaError_t run_factor(int n, int n_r, int n_sys, const double *diag, const double *lower,
+static cudaError_t run_factor(int n, int n_r, int n_sys, const void *diag, int diag_fp32, const double *lower,
                               const double *upper, void *dinv, const int *ray_list, cudaStream_t s) {
   constexpr int SPC = Pack<NP>::SPC;
   const unsigned grid = (unsigned)((n_sys + SPC - 1) / SPC);
-  k_factor<NP, T><<<grid, Pack<NP>::THREADS, 0, s>>>(n, n_r, n_sys, diag, lower, upper, (T *)dinv, ray_list);
+  if (diag_fp32)
+    k_factor<NP, T, float><<<grid, Pack<NP>::THREADS, 0, s>>>(n, n_r, n_sys, (const float *)diag, lower, upper,
+                                                              (T *)dinv, ray_list);
+  else
+    k_factor<NP, T, double><<<grid, Pack<NP>::THREADS, 0, s>>>(n, n_r, n_sys, (const double *)diag, lower,
+                                                               upper, (T *)dinv, ray_list);
   return cudaGetLastError();
 }
 
@@ -246,24 +632,34 @@ static cudaError_t run_solve(int n, int n_r, int n_sys, const void *dinv, const 
   return cudaGetLastError();
 }
 
-#define MGFLD_DISPATCH_NP(n, CALL)            \
-  if (n <= 4) { constexpr int NP = 4; CALL; }      \
-  else if (n <= 8) { constexpr int NP = 8; CALL; } \
-  else if (n <= 12) { constexpr int NP = 12; CALL; } \
-  else if (n <= 16) { constexpr int NP = 16; CALL; } \
-  else if (n <= 20) { constexpr int NP = 20; CALL; } \
-  else if (n <= 24) { constexpr int NP = 24; CALL; } \
-  else { constexpr int NP = 32; CALL; }
-
-cudaError_t launch_factor(int n, int n_r, int n_sys, const double *diag, const double *lower,
+cudaError_t launch_factor(int n, int n_r, int n_sys, const void *diag, int diag_fp32, const double *lower,
                           const double *upper, void *dinv, int precision, const int *ray_list,
                           cudaStream_t s) {
   if (n_sys == 0) return cudaSuccess;
   if (precision == MGFLD_MIXED) {
-    MGFLD_DISPATCH_NP(n, return (run_factor<NP, float>(n, n_r, n_sys, diag, lower, upper, dinv, ray_list, s)))
+    const unsigned grid = (unsigned)((n_sys + kWarpsPerCta - 1) / kWarpsPerCta);
+    if (diag_fp32) {
+      MGFLD_DISPATCH_NP(n, k_factor_w32<NP, float, double><<<grid, kWarpsPerCta * 32, 0, s>>>(
+                               n, n_r, n_sys, (const float *)diag, lower, upper, (float *)dinv, ray_list);
+                           return cudaGetLastError())
+    } else {
+      MGFLD_DISPATCH_NP(n, k_factor_w32<NP, double, double><<<grid, kWarpsPerCta * 32, 0, s>>>(
+                               n, n_r, n_sys, (const double *)diag, lower, upper, (float *)dinv, ray_list);
+                           return cudaGetLastError())
+    }
   } else {
-    MGFLD_DISPATCH_NP(n, return (run_factor<NP, double>(n, n_r, n_sys, diag, lower, upper, dinv, ray_list, s)))
+    MGFLD_DISPATCH_NP(n, return (run_factor<NP, double>(n, n_r, n_sys, diag, diag_fp32, lower, upper, dinv,
+                                                        ray_list, s)))
   }
+}
+
+cudaError_t launch_factor_f32(int n, int n_r, int n_sys, const float *diag, const float *lower32,
+                              const float *upper32, float *dinv, const int *ray_list, cudaStream_t s) {
+  if (n_sys == 0) return cudaSuccess;
+  const unsigned grid = (unsigned)((n_sys + kWarpsPerCta - 1) / kWarpsPerCta);
+  MGFLD_DISPATCH_NP(n, k_factor_w32<NP, float, float><<<grid, kWarpsPerCta * 32, 0, s>>>(
+                           n, n_r, n_sys, diag, lower32, upper32, dinv, ray_list);
+                       return cudaGetLastError())
 }
 
 cudaError_t launch_solve(int n, int n_r, int n_sys, const void *dinv, const double *lower,
@@ -271,7 +667,10 @@ cudaError_t launch_solve(int n, int n_r, int n_sys, const void *dinv, const doub
                          const int *ray_list, cudaStream_t s) {
   if (n_sys == 0) return cudaSuccess;
   if (precision == MGFLD_MIXED) {
-    MGFLD_DISPATCH_NP(n, return (run_solve<NP, float>(n, n_r, n_sys, dinv, lower, upper, rhs, x, ray_list, s)))
+    const unsigned grid = (unsigned)((n_sys + kWarpsPerCta - 1) / kWarpsPerCta);
+    MGFLD_DISPATCH_NP(n, k_solve_w32<NP><<<grid, kWarpsPerCta * 32, 0, s>>>(n, n_r, n_sys, (const float *)dinv,
+                                                                          lower, upper, rhs, x, ray_list);
+                         return cudaGetLastError())
   } else {
     MGFLD_DISPATCH_NP(n, return (run_solve<NP, double>(n, n_r, n_sys, dinv, lower, upper, rhs, x, ray_list, s)))
   }

@@ -31,6 +31,8 @@ __host__ __device__ inline double lepton_sign(int q) { return q == 0 ? 1.0 : (q 
 // Double-gamma EoS constants with F1, F2 pre-evaluated on the host (Eqs. e4, e7).
 struct Eos {
   double g1, g2, ec, gn, gp, rho0, mbc2, mb, f1, f2, rho_fac;  // rho_fac = (m_B/rho_0)^(g1-4/3)
+  double log_gn_gp;         // ln(g_n / g_p)
+  int g1_is_4_3, g2_is_5_2; // the default exponents, evaluated with cbrt / sqrt instead of pow
 };
 
 // Device view of one problem (pointers into caller memory and the workspace).
@@ -43,8 +45,9 @@ struct Prob {
 
 // Workspace regions (byte offsets from the workspace base).
 struct Layout {
-  size_t groups, phi, lam, alpha, ghost, rnu, jbuf, psi_n, ye_n, e_n, zone, src;
-  size_t diag, lower, upper, rhs, x, dinv, zled;
+  int mixed;
+  size_t groups, phout, phin, phd, rsum, phin32, phd32, lam, alpha, ghost, rnu, jbuf, psi_n, ye_n, e_n, zone, src;
+  size_t diag, lower, upper, rhs, x, dinv, zled, sscale, kinv, lower32, upper32, g32;
   size_t viol, vprev, active, iters, status, refac, nfact, nanflag, list_act, list_ref, counters;
   size_t total;
 };
@@ -53,17 +56,34 @@ Layout make_layout(int n_ray, int n_r, int n, int precision);
 
 // Per-zone constants evaluated once per step: a^2/V (flux divergence prefactor of Eq. a58),
 // 1/(a c dt), 1/a, V, mu_nue at (rho, T^n, Ye^n), a and a c dt.
-enum { ZC_PRE = 0, ZC_INV_ACDT = 1, ZC_INV_A = 2, ZC_VOL = 3, ZC_MU = 4, ZC_A = 5, ZC_ACDT = 6, ZC_N = 8 };
+// ZC_MUA, ZC_MUB: the Ye-independent factors of mu_e and of the nuclear part of mu_n, so that
+// mu_nue(Ye) = A Ye^(g1-1) - B (1-Ye)^(g2-1) + T ln(Ye/(1-Ye)) + T ln(g_n/g_p) (Eqs. e11-e13; the
+// thermal de Broglie terms of mu_p and mu_n cancel in mu_e + mu_p - mu_n).
+// ZC_E*: constants of the outer edge i+1/2 of zone i (for the last zone, the edge to the
+// ghost): 1/(3 (R_{i+1} - R_i)), 4 pi R_{i+1/2}^2 / a_{i+1/2}^2 and 1/R_{i+1/2}^2 (Eq. a59).
+enum { ZC_PRE = 0, ZC_INV_ACDT = 1, ZC_INV_A = 2, ZC_VOL = 3, ZC_MU = 4, ZC_A = 5, ZC_ACDT = 6,
+       ZC_MUA = 7, ZC_MUB = 8, ZC_EI3DR = 9, ZC_EGEO = 10, ZC_EIR2 = 11, ZC_N = 12 };
 
 // Pointers resolved from a layout.
 struct Ws {
   double *E, *W;            // group centre energy at infinity E_k and E_k^2 dE_k (Eq. a01b)
-  double *phi, *lam, *alpha, *ghost, *rnu, *jbuf, *psi_n, *ye_n, *e_n;
+  // Weighted NES kernels of each zone, [ray][zone][k][k'] (row k contiguous), with the moment
+  // constant C = 2 pi / (c (hc)^3) and the group weight w_k' = eps_k'^2 d eps_k' folded in:
+  //   phout[k][k'] = C w_k' Phi_out(eps_k, eps_k'),  phin[k][k'] = C w_k' Phi_in(eps_k, eps_k').
+  double *phout, *phin;
+  double *phd;              // phin - phout: the NES Jacobian row is -phin + psi_k phd (one FMA)
+  double *rsum;             // [ray][zone][k] row sums of phout: sum_k' phout (1 - psi_k') = rsum - phout.psi
+  float *phin32, *phd32;    // FP32 copies for the Jacobian of the mixed path
+  double *lam, *alpha, *ghost, *rnu, *jbuf, *psi_n, *ye_n, *e_n;
   double *zone;             // per zone [n_ray][n_r][ZC_N]: see ZC_* below
   double *src;              // per (ray, q, i, k): total source S at the converged state
   double *diag, *lower, *upper, *rhs, *x;
   void *dinv;
   double *zled;             // per-zone ledger terms [n_ray][n_r][8]
+  int *sscale;              // per listed system: exponent k of the 2^k scaling of the FP32 solve
+  float *lower32, *upper32; // FP32 copies of the (step-constant) coupling coefficients, MIXED only
+  float *g32;               // forward-substitution results of the FP32 solve
+  double *kinv;             // per (ray, q, i, k): 1/lambda^(t) at psi^n (transport opacity)
   unsigned long long *viol; // per-ray max violation ratio (double bits, non-negative)
   double *vprev;
   int *active, *iters, *status, *refac, *nfact, *nanflag, *list_act, *list_ref, *counters;
@@ -89,6 +109,32 @@ __device__ inline void eos_mu_nue(const Eos &e, double rho, double T, double ye,
   const double mu_p = T * log(n_e * lam3 / e.gp);
   mu = mu_e + mu_p - mu_n;
   dmu = (e.g1 - 1.0) * mu_e / ye + T / ye + (e.g2 - 1.0) * mu_nn / (1.0 - ye) + T / (1.0 - ye);
+}
+
+// The same chemical potential from the per-zone factors A, B (see ZC_MUA) at temperature T.
+__device__ inline void mu_nue_zone(const Eos &e, double A, double B, double T, double ye, double &mu, double &dmu) {
+  const double yn = 1.0 - ye;
+  const double mu_e = A * (e.g1_is_4_3 ? cbrt(ye) : pow(ye, e.g1 - 1.0));
+  const double mu_nn = B * (e.g2_is_5_2 ? yn * sqrt(yn) : pow(yn, e.g2 - 1.0));
+  mu = mu_e - mu_nn + T * (log(ye / yn) + e.log_gn_gp);
+  dmu = ((e.g1 - 1.0) * mu_e + T) / ye + ((e.g2 - 1.0) * mu_nn + T) / yn;
+}
+
+// a / (tol b) for a, b >= 0 as a float, without an FP64 division: exponents by integer
+// arithmetic, mantissas (the leading 23 bits) divided in FP32.  tol = tolm * 2^tole.
+// Enough for convergence tests (ratio <= 1) and contraction ratios; +inf for non-finite a.
+__device__ inline float tol_ratio(double a, double b, float tolm, int tole) {
+  const long long ba = __double_as_longlong(a), bb = __double_as_longlong(b);
+  if (ba == 0) return 0.f;
+  if (bb == 0) return INFINITY;
+  const int ea = (int)(ba >> 52), eb = (int)(bb >> 52);
+  if (ea >= 2047) return INFINITY;
+  const float ma = __int_as_float(0x3f800000 | (int)((ba >> 29) & 0x7fffff));
+  const float mb = __int_as_float(0x3f800000 | (int)((bb >> 29) & 0x7fffff));
+  const int e = ea - eb - tole;
+  if (e > 120) return INFINITY;
+  if (e < -120) return 0.f;
+  return ldexpf(ma / (tolm * mb), e);
 }
 
 // Internal energy per baryon without its thermal part (Eq. e10 / N_B at T = 0).
@@ -117,12 +163,47 @@ __device__ inline unsigned long long dbits(double v) { return (unsigned long lon
 cudaError_t launch_groups(const Prob &p, const Ws &w, cudaStream_t s);
 cudaError_t launch_setup(const Prob &p, const Ws &w, const double *psi, const double *ye, const double *T,
                          cudaStream_t s);
-cudaError_t launch_assemble(const Prob &p, const Ws &w, const double *psi, const double *ye, const double *T,
-                            double *diag, double *lower, double *upper, double *rhs, const int *list,
-                            int n_list, const int *jac_flag, cudaStream_t s, double *src_out = nullptr);
-cudaError_t launch_factor(int n, int n_r, int n_sys, const double *diag, const double *lower,
+// diag is double (FP64 path, C ABI) or float (MIXED: the Jacobian feeds the FP32 factor only).
+cudaError_t launch_assemble(const Prob &p, const Ws &w, const double *psi, void *diag, int diag_fp32,
+                            double *lower, double *upper, double *rhs, const int *list, int n_list,
+                            const int *jac_flag, cudaStream_t s, double *src_out = nullptr);
+cudaError_t launch_factor(int n, int n_r, int n_sys, const void *diag, int diag_fp32, const double *lower,
                           const double *upper, void *dinv, int precision, const int *ray_list,
                           cudaStream_t s);
+// MIXED-precision solve fed by bulk asynchronous copies; requires even n, 16-byte aligned
+// arrays and rhs != x.  Sets *err on a bounded-wait timeout.
+cudaError_t launch_solve_tma(int n, int n_r, int n_sys, const void *dinv, const float *lower32,
+                             const float *upper32, const double *rhs, double *x, float *g32,
+                             const int *ray_list, int *sys_exp, int *err, cudaStream_t s);
+
+// Exact power-of-two rescaling between FP64 and FP32 by exponent arithmetic on the bit
+// patterns (integer pipe only; mantissa truncated to 24 bits; results below the FP32 normal
+// range flush to zero, above it become infinite).
+__device__ inline float d2f_exp2(double v, int k) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+  const int e = (int)((b >> 52) & 0x7ff);
+  if (e == 0) return 0.f;
+  const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
+  const int ef = e == 0x7ff ? 255 : e - 1023 + k + 127;
+  if (ef <= 0) return __uint_as_float(sign);
+  if (ef >= 255) return __uint_as_float(sign | 0x7f800000u | (e == 0x7ff ? (unsigned)((b >> 29) & 0x7fffff) : 0u));
+  return __uint_as_float(sign | ((unsigned)ef << 23) | (unsigned)((b >> 29) & 0x7fffff));
+}
+__device__ inline double f2d_exp2(float v, int k) {
+  const unsigned b = __float_as_uint(v);
+  const int e = (int)((b >> 23) & 0xff);
+  if (e == 0) return 0.0;
+  const unsigned long long sign = (unsigned long long)(b & 0x80000000u) << 32;
+  const unsigned long long man = (unsigned long long)(b & 0x7fffffu) << 29;
+  if (e == 255) return __longlong_as_double((long long)(sign | (0x7ffull << 52) | man));
+  const long long ed = (long long)e - 127 + 1023 + k;
+  if (ed <= 0) return __longlong_as_double((long long)sign);
+  if (ed >= 0x7ff) return __longlong_as_double((long long)(sign | (0x7ffull << 52)));
+  return __longlong_as_double((long long)(sign | ((unsigned long long)ed << 52) | man));
+}
+// MIXED-precision factor with FP32 diagonal blocks and FP32 coupling coefficients.
+cudaError_t launch_factor_f32(int n, int n_r, int n_sys, const float *diag, const float *lower32,
+                              const float *upper32, float *dinv, const int *ray_list, cudaStream_t s);
 cudaError_t launch_solve(int n, int n_r, int n_sys, const void *dinv, const double *lower,
                          const double *upper, const double *rhs, double *x, int precision,
                          const int *ray_list, cudaStream_t s);

@@ -28,8 +28,11 @@ __global__ void k_zone(Prob p, Ws w, const double *__restrict__ ye, const double
   const double rho = p.rho[t];
   w.ye_n[t] = ye[t];
   w.e_n[t] = eos_e_cold(p.eos, rho, ye[t]) + p.eos.ec * T[t];
+  const Eos &e = p.eos;
+  const double muA = e.g1 * e.f1 * pow(rho / e.mb, e.g1 - 1.0) * e.rho_fac;
+  const double muB = e.g2 * e.f2 * pow(rho / e.mb, e.g2 - 1.0);
   double mu, dmu;
-  eos_mu_nue(p.eos, rho, T[t], ye[t], mu, dmu);
+  mu_nue_zone(e, muA, muB, T[t], ye[t], mu, dmu);
   const double a = lapse_at(p, ray, i);
   const double *re = p.r_edge + (size_t)ray * (p.n_r + 1);
   const double rm = re[i], rp = re[i + 1];
@@ -42,63 +45,132 @@ __global__ void k_zone(Prob p, Ws w, const double *__restrict__ ye, const double
   z[ZC_MU] = mu;
   z[ZC_A] = a;
   z[ZC_ACDT] = a * kC * p.dt;
+  z[ZC_MUA] = muA;
+  z[ZC_MUB] = muB;
+  const int last = p.n_r - 1;
+  const double r_i = 0.5 * (rm + rp);
+  const double r_r = i < last ? 0.5 * (re[i + 1] + re[i + 2]) : 2.0 * rp - r_i;
+  const double a_r = i < last ? lapse_at(p, ray, i + 1) : a;
+  const double a_e = 0.5 * (a + a_r);
+  z[ZC_EI3DR] = 1.0 / (3.0 * (r_r - r_i));
+  z[ZC_EGEO] = 4.0 * kPi * rp * rp / (a_e * a_e);
+  z[ZC_EIR2] = 1.0 / (rp * rp);
 }
 
-// Row k of the NES out-kernel of zone (ray, i): down/iso-scattering coef e^{-(eps_k - eps_k')/T}
-// computed directly, up-scattering from detailed balance (Eq. d7up) as coef e^{-2(eps_k' - eps_k)/T}.
-__global__ void k_phi(Prob p, Ws w, const double *__restrict__ T) {
+// Weighted NES kernels of zone (ray, i), one thread per row k (Eqs. d7down, d7up):
+// down/iso-scattering Phi_out(eps_k, eps_k'<=k) = coef e^{-(eps_k - eps_k')/T} is built from the
+// N-1 ratios g_m = e^{-(eps_m - eps_{m-1})/T} of consecutive groups (one exponential each, shared
+// by the zone through shared memory) as a running product; up-scattering is its square
+// (coef e^{-2(eps_k' - eps_k)/T}) and Phi_in(eps_k, eps_k') = Phi_out(eps_k', eps_k).
+// Zones per block of k_phi: the staged rows (2 n^2 doubles per zone) stay under 40 KB.
+static inline int phi_zones_per_block(int n) {
+  const int z = 40960 / (16 * n * n + 8 * n);
+  return z < 1 ? 1 : (z > 8 ? 8 : z);
+}
+
+__global__ void k_phi(Prob p, Ws w, const double *__restrict__ T, int zpb) {
+  extern __shared__ double smem[];
+  const int n = p.n;
+  double *gapm = smem;                       // [zpb][n]
+  double *sout = smem + (size_t)zpb * n;      // [zpb][n][n]
+  double *sin_ = sout + (size_t)zpb * n * n;  // [zpb][n][n]
+  const int zl = threadIdx.x / n, k = threadIdx.x % n;
+  const size_t nz = (size_t)p.n_ray * p.n_r;
+  const size_t z0 = (size_t)blockIdx.x * zpb;
+  const size_t zi = z0 + zl;
+  const bool live = zl < zpb && zi < nz;
+  const int ray = live ? (int)(zi / p.n_r) : 0, i = live ? (int)(zi % p.n_r) : 0;
+  const double inv_a = live ? 1.0 / lapse_at(p, ray, i) : 1.0;
+  const double Ti = live ? T[zi] : 1.0;
+  double *gap = gapm + (size_t)(live ? zl : 0) * n;
+  if (live && k > 0) gap[k] = exp(-(w.E[k] - w.E[k - 1]) * inv_a / Ti);
+  __syncthreads();
+  if (live) {
+    double *out = sout + (zl * n + k) * n;
+    double *in = sin_ + (zl * n + k) * n;
+    const double coef = p.nes ? p.nes[zi] : 0.0;
+    const double cc = kCNes * inv_a * inv_a * inv_a * coef;   // C w_k' = C W_k' / a^3
+    out[k] = cc * w.W[k];
+    in[k] = out[k];
+    double P = 1.0;
+    for (int kp = k - 1; kp >= 0; --kp) {
+      P *= gap[kp + 1];                         // e^{-(eps_k - eps_kp)/T}
+      out[kp] = cc * w.W[kp] * P;               // down-scattering k -> kp
+      in[kp] = cc * w.W[kp] * (P * P);          // up-scattering kp -> k
+    }
+    double Q = 1.0;
+    for (int kp = k + 1; kp < n; ++kp) {
+      Q *= gap[kp];                             // e^{-(eps_kp - eps_k)/T}
+      out[kp] = cc * w.W[kp] * (Q * Q);         // up-scattering k -> kp
+      in[kp] = cc * w.W[kp] * Q;                // down-scattering kp -> k
+    }
+    double rs = 0.0;
+    for (int kp = 0; kp < n; ++kp) rs += out[kp];
+    w.rsum[zi * n + k] = rs;
+  }
+  __syncthreads();
+  // Coalesced copy of the block's zones (contiguous in [ray][zone][k][k'] order).
+  const size_t nzb = (z0 + zpb <= nz) ? (size_t)zpb : nz - z0;
+  const size_t cnt = nzb * n * n;
+  const size_t base = z0 * n * n;
+  for (size_t e = threadIdx.x; e < cnt; e += blockDim.x) {
+    const double o = sout[e], v = sin_[e];
+    w.phout[base + e] = o;
+    w.phin[base + e] = v;
+    if (w.phin32) {
+      w.phin32[base + e] = (float)v;
+      w.phd32[base + e] = (float)(v - o);
+    } else {
+      w.phd[base + e] = v - o;
+    }
+  }
+}
+
+// Emissivity at Ye^n and the transport mean free path at psi^n, one thread per (ray, zone,
+// group) for the four species (which share the zone's NES rows and, for nu_mu/tau and their
+// antiparticles with mu = 0, the exponential):
+// 1/lambda = kappa_a + j + kappa_s + sum_k' [phin psi_k' + phout (1 - psi_k')].
+__global__ void k_jlam(Prob p, Ws w, const double *__restrict__ psi, const double *__restrict__ T) {
   const int n = p.n;
   const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (size_t)p.n_ray * p.n_r * n) return;
   const int k = (int)(t % n);
-  const size_t zi = t / n;                       // ray * n_r + i
+  const size_t zi = t / n;
   const int ray = (int)(zi / p.n_r), i = (int)(zi % p.n_r);
-  double *row = w.phi + t * n;
-  if (!p.nes) {
-    for (int kp = 0; kp < n; ++kp) row[kp] = 0.0;
-    return;
-  }
-  const double inv_a = 1.0 / lapse_at(p, ray, i);
-  const double Ti = T[zi], coef = p.nes[zi];
-  const double ek = w.E[k] * inv_a;
-  for (int kp = 0; kp < n; ++kp) {
-    const double d = ek - w.E[kp] * inv_a;
-    row[kp] = coef * (kp <= k ? exp(-d / Ti) : exp(2.0 * d / Ti));
-  }
-}
-
-// Emissivity at Ye^n and the transport mean free path at psi^n:
-// 1/lambda = kappa_a + j + kappa_s + C sum_k' w_k' [Phi_in psi + Phi_out (1 - psi)].
-__global__ void k_jlam(Prob p, Ws w, const double *__restrict__ psi, const double *__restrict__ ye,
-                       const double *__restrict__ T) {
-  const int n = p.n;
-  const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= (size_t)p.n_ray * NS * p.n_r * n) return;
-  const int k = (int)(t % n);
-  size_t u = t / n;
-  const int i = (int)(u % p.n_r);
-  u /= p.n_r;
-  const int q = (int)(u % NS);
-  const int ray = (int)(u / NS);
-  const size_t zi = (size_t)ray * p.n_r + i;
   const double *z = w.zone + zi * ZC_N;
   const double inv_a = z[ZC_INV_A];
   const double Ti = T[zi];
-  const double sc = p.scale ? p.scale[q * n + k] : 1.0;
-  const double kap = p.kabs[t] * sc, ksc = p.kscat[t] * sc;
-  bool live;
-  const double j = emissivity(kap, species_mu(q, z[ZC_MU]), w.E[k] * inv_a, Ti, live);
-  w.jbuf[t] = j;
-  const double *ps = psi + (t - k);             // psi[ray][q][i][0]
-  const double *ph = w.phi + zi * n * n;
-  const double inv_a3 = inv_a * inv_a * inv_a;
-  double nes = 0.0;
-  for (int kp = 0; kp < n; ++kp) {
-    const double wk = w.W[kp] * inv_a3;
-    nes += wk * (ph[kp * n + k] * ps[kp] + ph[k * n + kp] * (1.0 - ps[kp]));
+  const double eps = w.E[k] * inv_a;
+  const double mu = z[ZC_MU];
+  const double *fin = w.phin + (zi * n + k) * n;
+  const double *fout = w.phout + (zi * n + k) * n;
+  const double rs = w.rsum[zi * n + k];
+  double e_mu0 = 0.0;
+  for (int q = 0; q < NS; ++q) {
+    const size_t g = (((size_t)ray * NS + q) * p.n_r + i) * n + k;
+    const double sc = p.scale ? p.scale[q * n + k] : 1.0;
+    const double kap = p.kabs[g] * sc, ksc = p.kscat[g] * sc;
+    double j;
+    if (q == 3) {
+      j = kap * e_mu0;                     // same exponent as q = 2 (mu = 0)
+    } else {
+      bool live;
+      j = emissivity(1.0, species_mu(q, mu), eps, Ti, live);
+      if (q == 2) e_mu0 = j;
+      j *= kap;
+    }
+    w.jbuf[g] = j;
+    const double *ps = psi + (g - k);
+    double gain = 0.0, lp = 0.0;
+    for (int kp = 0; kp < n; ++kp) {
+      gain += fin[kp] * ps[kp];
+      lp += fout[kp] * ps[kp];
+    }
+    const double kt = kap + j + ksc + gain + (rs - lp);
+    w.kinv[g] = kt;
+    w.lam[g] = 1.0 / kt;
+    w.psi_n[g] = psi[g];
   }
-  w.lam[t] = 1.0 / (kap + j + ksc + kCNes * nes);
-  w.psi_n[t] = psi[t];
 }
 
 // Neutrinosphere radius per (ray, q, k): where the optical depth integrated inward from
@@ -110,14 +182,14 @@ __global__ void k_nusphere(Prob p, Ws w) {
   if (t >= p.n_ray * NS * n) return;
   const int k = t % n, q = (t / n) % NS, ray = t / (n * NS);
   const double *re = p.r_edge + (size_t)ray * (p.n_r + 1);
-  const double *lam = w.lam + ((size_t)ray * NS + q) * p.n_r * n + k;
+  const size_t off = ((size_t)ray * NS + q) * p.n_r * n + k;
+  const double *kt = w.kinv + off;                 // 1/lambda, so the scan needs no division
   double tau_out = 0.0;
   double rnu = re[0];
   for (int i = p.n_r - 1; i >= 0; --i) {
-    const double li = lam[(size_t)i * n];
-    const double dtau = (re[i + 1] - re[i]) / li;
+    const double dtau = (re[i + 1] - re[i]) * kt[(size_t)i * n];
     if (tau_out + dtau >= kTauNu) {
-      rnu = re[i + 1] - (kTauNu - tau_out) * li;
+      rnu = re[i + 1] - (kTauNu - tau_out) * w.lam[off + (size_t)i * n];
       break;
     }
     tau_out += dtau;
@@ -150,43 +222,38 @@ __global__ void k_edges(Prob p, Ws w) {
   const int gq = (ray * NS + q) * n + k;
   const double psi_i = w.psi_n[t];
   const double lam_i = w.lam[t];
-  const double r_i = 0.5 * (re[i] + re[i + 1]);
-  const double a_i = lapse_at(p, ray, i);
-  double psi_r, lam_r, r_r, a_r;
+  double psi_r, lam_r;
   if (i < last) {
     psi_r = w.psi_n[t + n];
     lam_r = w.lam[t + n];
-    r_r = 0.5 * (re[i + 1] + re[i + 2]);
-    a_r = lapse_at(p, ray, i + 1);
   } else {
     psi_r = w.ghost[gq] * psi_i;
     lam_r = lam_i;
-    r_r = 2.0 * re[p.n_r] - r_i;
-    a_r = a_i;
   }
   const double lam_e = sqrt(lam_i * lam_r);
   const double dpsi = psi_r - psi_i;
-  const double dR = r_r - r_i;
   const double psi_e = 0.5 * (psi_i + psi_r);
-  const double r_e = re[i + 1];
+  const double *z = w.zone + ((size_t)ray * p.n_r + i) * ZC_N;
   double F;
   if (psi_e <= 1e-300) {
     F = 0.0;
   } else if (dpsi == 0.0) {
     F = 1.0;
   } else {
-    const double x = lam_e * fabs(dpsi / dR) / 3.0;
-    F = 1.0 / (1.0 + x / psi_e);
+    const double x = lam_e * fabs(dpsi) * z[ZC_EI3DR];       // lambda |d psi/dR| / 3
+    // F = min(F_intrp, F_geom) with F_intrp = psi_e/(psi_e + x) and, outside the
+    // neutrinosphere, F_geom = h psi_e / x, h = (1 + mu_nu)/2; F_geom is the smaller one
+    // exactly when h psi_e < (1 - h) x, so only the chosen quotient is evaluated.
     const double rnu = w.rnu[gq];
-    if (r_e > rnu) {
-      const double s = rnu / r_e;
-      const double mu = sqrt(fmax(1.0 - s * s, 0.0));
-      F = fmin(F, 0.5 * (1.0 + mu) * psi_e / x);
+    bool geom = false;
+    double h = 1.0;
+    if (re[i + 1] > rnu) {
+      h = 0.5 * (1.0 + sqrt(fmax(1.0 - rnu * rnu * z[ZC_EIR2], 0.0)));
+      geom = h * psi_e < (1.0 - h) * x;
     }
+    F = geom ? h * psi_e / x : psi_e / (psi_e + x);
   }
-  const double D = lam_e * F / (3.0 * dR);
-  const double a_e = 0.5 * (a_i + a_r);
-  w.alpha[t] = 4.0 * kPi * r_e * r_e * D / (a_e * a_e);
+  w.alpha[t] = lam_e * F * z[ZC_EI3DR] * z[ZC_EGEO];
 }
 
 static inline unsigned nblk(size_t n, unsigned b) { return (unsigned)((n + b - 1) / b); }
@@ -204,8 +271,12 @@ cudaError_t launch_setup(const Prob &p, const Ws &w, const double *psi, const do
   const size_t nall = nzk * NS;
   k_groups<<<1, MAX_NE, 0, s>>>(p.n, p.e_edge, w.E, w.W);
   k_zone<<<nblk(nz, B), B, 0, s>>>(p, w, ye, T);
-  k_phi<<<nblk(nzk, B), B, 0, s>>>(p, w, T);
-  k_jlam<<<nblk(nall, B), B, 0, s>>>(p, w, psi, ye, T);
+  {
+    const int zpb = phi_zones_per_block(p.n);
+    const size_t sm = sizeof(double) * ((size_t)zpb * p.n + 2 * (size_t)zpb * p.n * p.n);
+    k_phi<<<nblk(nz, zpb), zpb * p.n, sm, s>>>(p, w, T, zpb);
+  }
+  k_jlam<<<nblk(nzk, B), B, 0, s>>>(p, w, psi, T);
   k_nusphere<<<nblk((size_t)p.n_ray * NS * p.n, B), B, 0, s>>>(p, w);
   k_edges<<<nblk(nall, B), B, 0, s>>>(p, w);
   return cudaGetLastError();

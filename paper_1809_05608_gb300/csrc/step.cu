@@ -13,6 +13,7 @@
 // energy ledgers of Eqs. a60-a62.
 #include <cmath>
 #include <cstring>
+#include <mutex>
 
 #include "mgfld_internal.cuh"
 
@@ -22,11 +23,17 @@ static size_t align_up(size_t v) { return (v + 255) & ~(size_t)255; }
 
 Layout make_layout(int n_ray, int n_r, int n, int precision) {
   Layout L{};
+  L.mixed = precision == MGFLD_MIXED;
   const size_t R = (size_t)n_ray, Z = R * n_r, F = Z * NS * n, B = F * n;
   size_t off = 0;
   auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes); return o; };
   L.groups = take(sizeof(double) * 2 * MAX_NE);
-  L.phi = take(sizeof(double) * Z * n * n);
+  L.phout = take(sizeof(double) * Z * n * n);
+  L.phin = take(sizeof(double) * Z * n * n);
+  L.phd = take(sizeof(double) * Z * n * n);
+  L.rsum = take(sizeof(double) * Z * n);
+  L.phin32 = take(precision == MGFLD_MIXED ? sizeof(float) * Z * n * n : 0);
+  L.phd32 = take(precision == MGFLD_MIXED ? sizeof(float) * Z * n * n : 0);
   L.lam = take(sizeof(double) * F);
   L.alpha = take(sizeof(double) * F);
   L.ghost = take(sizeof(double) * R * NS * n);
@@ -37,13 +44,18 @@ Layout make_layout(int n_ray, int n_r, int n, int precision) {
   L.e_n = take(sizeof(double) * Z);
   L.zone = take(sizeof(double) * Z * ZC_N);
   L.src = take(sizeof(double) * F);
-  L.diag = take(sizeof(double) * B);
+  L.diag = take((precision == MGFLD_MIXED ? sizeof(float) : sizeof(double)) * B);
   L.lower = take(sizeof(double) * F);
   L.upper = take(sizeof(double) * F);
   L.rhs = take(sizeof(double) * F);
   L.x = take(sizeof(double) * F);
   L.dinv = take((precision == MGFLD_MIXED ? sizeof(float) : sizeof(double)) * B);
   L.zled = take(sizeof(double) * Z * 8);
+  L.sscale = take(sizeof(int) * R * NS);
+  L.lower32 = take(precision == MGFLD_MIXED ? sizeof(float) * F : 0);
+  L.upper32 = take(precision == MGFLD_MIXED ? sizeof(float) * F : 0);
+  L.g32 = take(precision == MGFLD_MIXED ? sizeof(float) * F : 0);
+  L.kinv = take(sizeof(double) * F);
   L.viol = take(sizeof(unsigned long long) * R);
   L.vprev = take(sizeof(double) * R);
   L.active = take(sizeof(int) * R);
@@ -64,7 +76,12 @@ Ws resolve(void *base, const Layout &L) {
   Ws w;
   w.E = (double *)(b + L.groups);
   w.W = w.E + MAX_NE;
-  w.phi = (double *)(b + L.phi);
+  w.phout = (double *)(b + L.phout);
+  w.phin = (double *)(b + L.phin);
+  w.phd = (double *)(b + L.phd);
+  w.rsum = (double *)(b + L.rsum);
+  w.phin32 = L.mixed ? (float *)(b + L.phin32) : nullptr;
+  w.phd32 = L.mixed ? (float *)(b + L.phd32) : nullptr;
   w.lam = (double *)(b + L.lam);
   w.alpha = (double *)(b + L.alpha);
   w.ghost = (double *)(b + L.ghost);
@@ -82,6 +99,11 @@ Ws resolve(void *base, const Layout &L) {
   w.x = (double *)(b + L.x);
   w.dinv = (void *)(b + L.dinv);
   w.zled = (double *)(b + L.zled);
+  w.sscale = (int *)(b + L.sscale);
+  w.lower32 = L.mixed ? (float *)(b + L.lower32) : nullptr;
+  w.upper32 = L.mixed ? (float *)(b + L.upper32) : nullptr;
+  w.g32 = L.mixed ? (float *)(b + L.g32) : nullptr;
+  w.kinv = (double *)(b + L.kinv);
   w.viol = (unsigned long long *)(b + L.viol);
   w.vprev = (double *)(b + L.vprev);
   w.active = (int *)(b + L.active);
@@ -99,6 +121,8 @@ Ws resolve(void *base, const Layout &L) {
 struct Tol {
   double tol, tolmin, tol_ye, tolmin_ye, refactor_ratio;
   int max_iter, mixed;
+  float tolm, tolm_ye;      // tol = tolm 2^tole (for tol_ratio)
+  int tole, tole_ye;
 };
 
 __global__ void k_init(int n_ray, Ws w) {
@@ -116,75 +140,115 @@ __global__ void k_init(int n_ray, Ws w) {
   w.list_ref[r] = r;
 }
 
-// psi += dpsi, one Newton step of Eq. a62a for Ye at the new psi, new emissivities, and the
-// per-zone convergence ratio max(|d psi| / (tol max(|psi|, tolmin)), |d Ye| / (tol_ye max(Ye, tolmin_ye))).
-__global__ void k_update(Prob p, Ws w, Tol tl, double *__restrict__ psi, double *__restrict__ ye,
-                         const double *__restrict__ T, const int *__restrict__ list, int n_list) {
+// Largest violation ratio of a warp's lanes reported once per ray (lanes of one warp may
+// belong to two rays at a boundary, then each lane reports for itself).  Ratios are
+// non-negative floats, so their bit patterns order like their values.
+__device__ inline void report_violation(Ws &w, int ray, float viol) {
+  const unsigned full = 0xffffffffu;
+  const int ray0 = __shfl_sync(full, ray, 0);
+  if (__all_sync(full, ray == ray0)) {
+    for (int off = 16; off > 0; off >>= 1) viol = fmaxf(viol, __shfl_down_sync(full, viol, off));
+    if ((threadIdx.x & 31) == 0) atomicMax(&w.viol[ray], (unsigned long long)__float_as_uint(viol));
+  } else {
+    atomicMax(&w.viol[ray], (unsigned long long)__float_as_uint(viol));
+  }
+}
+
+// psi += dpsi (Eq. a62aa) and the per-element convergence ratio |d psi| / (tol max(|psi|, tolmin))
+// of Eq. a62ab, one thread per (ray, q, i, k) of the active rays.  All 32 lanes of a warp reach
+// the reduction (out-of-range lanes carry ratio 0).
+__global__ void k_update_psi(Prob p, Ws w, Tol tl, double *__restrict__ psi, const int *__restrict__ list,
+                             int n_list) {
+  const size_t per_ray = (size_t)NS * p.n_r * p.n;
+  const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool in = t < (size_t)n_list * per_ray;
+  const int ray = in ? list[t / per_ray] : list[0];
+  float viol = 0.f;
+  if (in) {
+    const size_t g = (size_t)ray * per_ray + t % per_ray;
+    const double d = w.x[g];
+    const double v = psi[g] + d;
+    psi[g] = v;
+    viol = tol_ratio(fabs(d), fmax(fabs(v), tl.tolmin), tl.tolm, tl.tole);
+    if (!isfinite(v)) {
+      atomicExch(&w.nanflag[ray], 1);
+      viol = INFINITY;
+    }
+  }
+  report_violation(w, ray, viol);
+}
+
+// One Newton step of the zone-local Ye equation (Eq. a62a) at the updated psi, with T held at
+// T^n (Sec. "Lagrangian Transport Step"), then the nu_e / nubar_e emissivities at the new Ye.
+// A change dmu of the chemical potential rescales j = kappa_a e^{(mu - eps)/T} by e^{dmu/T},
+// one exponential per species (direct evaluation where the exponent cap is involved).
+__global__ void k_update_ye(Prob p, Ws w, Tol tl, const double *__restrict__ psi, double *__restrict__ ye,
+                            const double *__restrict__ T, const int *__restrict__ list, int n_list) {
   const int n = p.n;
   const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= (size_t)n_list * p.n_r) return;
-  const int ray = list[t / p.n_r];
-  const int i = (int)(t % p.n_r);
-  const size_t zi = (size_t)ray * p.n_r + i;
-  double viol = 0.0;
-  bool bad = false;
-  for (int q = 0; q < NS; ++q) {
-    const size_t g0 = (((size_t)ray * NS + q) * p.n_r + i) * n;
-    for (int k = 0; k < n; ++k) {
-      const double d = w.x[g0 + k];
-      const double v = psi[g0 + k] + d;
-      psi[g0 + k] = v;
-      bad |= !isfinite(v);
-      viol = fmax(viol, fabs(d) / (tl.tol * fmax(fabs(v), tl.tolmin)));
+  const bool in = t < (size_t)n_list * p.n_r;
+  const int ray = in ? list[t / p.n_r] : list[0];
+  float viol = 0.f;
+  if (in) {
+    const int i = (int)(t % p.n_r);
+    const size_t zi = (size_t)ray * p.n_r + i;
+    const double *z = w.zone + zi * ZC_N;
+    const double inv_a = z[ZC_INV_A];
+    const double inv_a3 = inv_a * inv_a * inv_a;
+    const double inv_acdt = z[ZC_INV_ACDT];
+    const double Ti = T[zi], rho = p.rho[zi];
+    const double cy = kFourPiHC3 * p.eos.mb / rho;
+    const double capT = kExpCap * Ti;
+    double Y = ye[zi];
+    double mu, dmu;
+    mu_nue_zone(p.eos, z[ZC_MUA], z[ZC_MUB], Ti, Y, mu, dmu);
+    double sG = 0.0, sdG = 0.0;
+    for (int q = 0; q < 2; ++q) {
+      const double sg = lepton_sign(q);
+      const double muq = species_mu(q, mu), dmuq_T = sg * dmu / Ti;
+      const size_t g0 = (((size_t)ray * NS + q) * p.n_r + i) * n;
+      double a0 = 0.0, a1 = 0.0;
+      for (int k = 0; k < n; ++k) {
+        const double wk = w.W[k];
+        const double sc = p.scale ? p.scale[q * n + k] : 1.0;
+        const double kap = p.kabs[g0 + k] * sc;
+        const double j = w.jbuf[g0 + k];
+        const double pk = psi[g0 + k];
+        a0 += wk * (j * (1.0 - pk) - kap * pk);
+        if (muq - w.E[k] * inv_a < capT) a1 += wk * (1.0 - pk) * j;
+      }
+      sG += sg * a0 * inv_a3;
+      sdG += sg * a1 * inv_a3 * dmuq_T;
+    }
+    const double GY = (Y - w.ye_n[zi]) * inv_acdt + cy * sG;
+    const double dGY = inv_acdt + cy * sdG;
+    const double dY = -GY / dGY;
+    Y += dY;
+    ye[zi] = Y;
+    viol = tol_ratio(fabs(dY), fmax(fabs(Y), tl.tolmin_ye), tl.tolm_ye, tl.tole_ye);
+    double mu1, dmu1;
+    mu_nue_zone(p.eos, z[ZC_MUA], z[ZC_MUB], Ti, Y, mu1, dmu1);
+    for (int q = 0; q < 2; ++q) {
+      const double m0 = species_mu(q, mu), m1 = species_mu(q, mu1);
+      const double ratio = exp((m1 - m0) / Ti);
+      const size_t g0 = (((size_t)ray * NS + q) * p.n_r + i) * n;
+      for (int k = 0; k < n; ++k) {
+        const double eps = w.E[k] * inv_a;
+        if (m0 - eps < capT && m1 - eps < capT) {
+          w.jbuf[g0 + k] *= ratio;
+        } else {
+          const double sc = p.scale ? p.scale[q * n + k] : 1.0;
+          bool live;
+          w.jbuf[g0 + k] = emissivity(p.kabs[g0 + k] * sc, m1, eps, Ti, live);
+        }
+      }
+    }
+    if (!isfinite(Y)) {
+      atomicExch(&w.nanflag[ray], 1);
+      viol = INFINITY;
     }
   }
-  const double *z = w.zone + zi * ZC_N;
-  const double inv_a = z[ZC_INV_A];
-  const double inv_a3 = inv_a * inv_a * inv_a;
-  const double inv_acdt = z[ZC_INV_ACDT];
-  const double Ti = T[zi], rho = p.rho[zi];
-  const double cy = kFourPiHC3 * p.eos.mb / rho;
-  double Y = ye[zi];
-  double mu, dmu;
-  eos_mu_nue(p.eos, rho, Ti, Y, mu, dmu);
-  double sG = 0.0, sdG = 0.0;
-  for (int q = 0; q < 2; ++q) {
-    const double sg = lepton_sign(q);
-    const double muq = species_mu(q, mu), dmuq = sg * dmu;
-    const size_t g0 = (((size_t)ray * NS + q) * p.n_r + i) * n;
-    for (int k = 0; k < n; ++k) {
-      const double wk = w.W[k] * inv_a3;
-      const double eps = w.E[k] * inv_a;
-      const double sc = p.scale ? p.scale[q * n + k] : 1.0;
-      const double kap = p.kabs[g0 + k] * sc;
-      const double j = w.jbuf[g0 + k];
-      const double pk = psi[g0 + k];
-      sG += sg * wk * (j * (1.0 - pk) - kap * pk);
-      const bool live = (muq - eps) / Ti < kExpCap;
-      if (live) sdG += sg * wk * (1.0 - pk) * j * dmuq / Ti;
-    }
-  }
-  const double GY = (Y - w.ye_n[zi]) * inv_acdt + cy * sG;
-  const double dGY = inv_acdt + cy * sdG;
-  const double dY = -GY / dGY;
-  Y += dY;
-  ye[zi] = Y;
-  bad |= !isfinite(Y);
-  viol = fmax(viol, fabs(dY) / (tl.tol_ye * fmax(fabs(Y), tl.tolmin_ye)));
-  eos_mu_nue(p.eos, rho, Ti, Y, mu, dmu);
-  for (int q = 0; q < 2; ++q) {
-    const size_t g0 = (((size_t)ray * NS + q) * p.n_r + i) * n;
-    for (int k = 0; k < n; ++k) {
-      const double sc = p.scale ? p.scale[q * n + k] : 1.0;
-      bool live;
-      w.jbuf[g0 + k] = emissivity(p.kabs[g0 + k] * sc, species_mu(q, mu), w.E[k] * inv_a, Ti, live);
-    }
-  }
-  if (bad || !(viol == viol)) {
-    atomicExch(&w.nanflag[ray], 1);
-    viol = INFINITY;
-  }
-  atomicMax(&w.viol[ray], dbits(viol));
+  report_violation(w, ray, viol);
 }
 
 // Per ray: close the iteration, decide convergence / failure / refactorisation and build the
@@ -193,7 +257,7 @@ __global__ void k_check(int n_ray, Ws w, Tol tl) {
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= n_ray || !w.active[r]) return;
   const int it = ++w.iters[r];
-  const double v = __longlong_as_double((long long)w.viol[r]);
+  const double v = (double)__uint_as_float((unsigned)w.viol[r]);
   w.viol[r] = 0ull;
   int st = -1;
   if (w.nanflag[r]) st = MGFLD_ENAN;
@@ -306,28 +370,35 @@ __global__ void k_ledger(int n_r, Ws w, double *ledger, double *heating, int *st
   }
 }
 
-// Optional per-category timing: a pair of CUDA events per category, read back after the
-// host synchronisations the outer iteration already performs.
+// Optional per-category timing: a pair of CUDA events per category, read back after the host
+// synchronisations the outer iteration already performs.  The events are created on the
+// first profiled call on each device and kept for the life of the process (creating and
+// destroying events on every call perturbed the host-synchronised loop).
 struct Prof {
   double *out;
   cudaStream_t s;
-  cudaEvent_t ev[MGFLD_PROF_N][2];
+  cudaEvent_t (*ev)[2];
   int pending[MGFLD_PROF_N];
-  Prof(double *o, cudaStream_t st) : out(o), s(st) {
-    for (int c = 0; c < MGFLD_PROF_N; ++c) {
-      pending[c] = 0;
-      if (out) {
-        cudaEventCreate(&ev[c][0]);
-        cudaEventCreate(&ev[c][1]);
-      }
-    }
-  }
-  ~Prof() {
+  Prof(double *o, cudaStream_t st) : out(o), s(st), ev(nullptr) {
+    for (int c = 0; c < MGFLD_PROF_N; ++c) pending[c] = 0;
     if (!out) return;
-    for (int c = 0; c < MGFLD_PROF_N; ++c) {
-      cudaEventDestroy(ev[c][0]);
-      cudaEventDestroy(ev[c][1]);
+    static std::mutex lock;
+    static cudaEvent_t cache[64][MGFLD_PROF_N][2];
+    static bool made[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+      out = nullptr;
+      return;
     }
+    std::lock_guard<std::mutex> g(lock);
+    if (!made[dev]) {
+      for (int c = 0; c < MGFLD_PROF_N; ++c) {
+        cudaEventCreate(&cache[dev][c][0]);
+        cudaEventCreate(&cache[dev][c][1]);
+      }
+      made[dev] = true;
+    }
+    ev = cache[dev];
   }
   void begin(int c) { if (out) cudaEventRecord(ev[c][0], s); }
   void end(int c, int launches) {
@@ -357,6 +428,9 @@ static Eos make_eos(const mgfld_eos_params &e) {
   d.rho_fac = std::pow(e.m_b / e.rho_0, e.gamma1 - 4.0 / 3.0);
   d.f2 = (e.gamma1 - 1.0) / (e.gamma2 - 1.0) * d.f1 * std::pow(0.5 * e.rho_nuc / e.m_b, e.gamma1 - e.gamma2) *
          d.rho_fac;
+  d.log_gn_gp = std::log(e.g_n / e.g_p);
+  d.g1_is_4_3 = e.gamma1 == 4.0 / 3.0;
+  d.g2_is_5_2 = e.gamma2 == 2.5;
   return d;
 }
 
@@ -439,6 +513,8 @@ mgfld_status mgfld_step(const mgfld_dims *dims, const mgfld_problem *prob, mgfld
   tl.tol = opts->tol; tl.tolmin = opts->tolmin_psi; tl.tol_ye = opts->tol_ye; tl.tolmin_ye = opts->tolmin_ye;
   tl.refactor_ratio = opts->refactor_ratio > 0.0 ? opts->refactor_ratio : 0.1;
   tl.max_iter = opts->max_iter; tl.mixed = opts->precision == MGFLD_MIXED;
+  tl.tolm = (float)std::frexp(opts->tol, &tl.tole);
+  tl.tolm_ye = (float)std::frexp(opts->tol_ye, &tl.tole_ye);
   const int R = dims->n_ray, n = dims->n_e, NR = dims->n_r;
 
   Prof prof(opts->profile, s);
@@ -446,43 +522,55 @@ mgfld_status mgfld_step(const mgfld_dims *dims, const mgfld_problem *prob, mgfld
   MGFLD_CUDA(launch_setup(p, w, state->psi, state->ye, state->T, s));
   k_init<<<nblk(R, 128), 128, 0, s>>>(R, w);
   MGFLD_CUDA(cudaGetLastError());
+  MGFLD_CUDA(cudaMemsetAsync(w.counters, 0, sizeof(int) * 8, s));
   prof.end(MGFLD_PROF_SETUP, 7);
   int n_act = R, n_ref = R;
   int host_counters[8];
   for (int it = 0; it < opts->max_iter && n_act > 0; ++it) {
     const int *jac = tl.mixed ? w.refac : nullptr;
     prof.begin(MGFLD_PROF_ASSEMBLE);
-    MGFLD_CUDA(launch_assemble(p, w, state->psi, state->ye, state->T, w.diag, w.lower, w.upper, w.rhs,
-                               w.list_act, n_act, jac, s));
+    MGFLD_CUDA(launch_assemble(p, w, state->psi, w.diag, tl.mixed, w.lower, w.upper, w.rhs, w.list_act, n_act,
+                               jac, s));
     prof.end(MGFLD_PROF_ASSEMBLE, 1);
     const int *flist = tl.mixed ? w.list_ref : w.list_act;
     const int nf = tl.mixed ? n_ref : n_act;
     if (nf > 0) {
       prof.begin(MGFLD_PROF_FACTOR);
-      MGFLD_CUDA(launch_factor(n, NR, nf * NS, w.diag, w.lower, w.upper, w.dinv, opts->precision, flist, s));
+      if (tl.mixed)
+        MGFLD_CUDA(launch_factor_f32(n, NR, nf * NS, (const float *)w.diag, w.lower32, w.upper32, (float *)w.dinv,
+                                     flist, s));
+      else
+        MGFLD_CUDA(launch_factor(n, NR, nf * NS, w.diag, 0, w.lower, w.upper, w.dinv, opts->precision, flist, s));
       prof.end(MGFLD_PROF_FACTOR, 1);
     }
     prof.begin(MGFLD_PROF_SOLVE);
-    MGFLD_CUDA(launch_solve(n, NR, n_act * NS, w.dinv, w.lower, w.upper, w.rhs, w.x, opts->precision,
-                            w.list_act, s));
+    if (tl.mixed && n % 2 == 0)
+      MGFLD_CUDA(launch_solve_tma(n, NR, n_act * NS, w.dinv, w.lower32, w.upper32, w.rhs, w.x, w.g32,
+                                  w.list_act, w.sscale, w.counters + 3, s));
+    else
+      MGFLD_CUDA(launch_solve(n, NR, n_act * NS, w.dinv, w.lower, w.upper, w.rhs, w.x, opts->precision,
+                              w.list_act, s));
     prof.end(MGFLD_PROF_SOLVE, 1);
     prof.begin(MGFLD_PROF_UPDATE);
-    k_update<<<nblk((size_t)n_act * NR, 128), 128, 0, s>>>(p, w, tl, state->psi, state->ye, state->T,
-                                                           w.list_act, n_act);
+    k_update_psi<<<nblk((size_t)n_act * NS * NR * n, 256), 256, 0, s>>>(p, w, tl, state->psi, w.list_act, n_act);
+    MGFLD_CUDA(cudaGetLastError());
+    k_update_ye<<<nblk((size_t)n_act * NR, 128), 128, 0, s>>>(p, w, tl, state->psi, state->ye, state->T,
+                                                              w.list_act, n_act);
     MGFLD_CUDA(cudaGetLastError());
     MGFLD_CUDA(cudaMemsetAsync(w.counters, 0, sizeof(int) * 2, s));
     k_check<<<nblk(R, 128), 128, 0, s>>>(R, w, tl);
     MGFLD_CUDA(cudaGetLastError());
-    prof.end(MGFLD_PROF_UPDATE, 2);
-    MGFLD_CUDA(cudaMemcpyAsync(host_counters, w.counters, sizeof(int) * 2, cudaMemcpyDeviceToHost, s));
+    prof.end(MGFLD_PROF_UPDATE, 3);
+    MGFLD_CUDA(cudaMemcpyAsync(host_counters, w.counters, sizeof(int) * 4, cudaMemcpyDeviceToHost, s));
     MGFLD_CUDA(cudaStreamSynchronize(s));
     prof.collect();
+    if (host_counters[3] != 0) return MGFLD_ECUDA;      // a bounded wait in the solve gave up
     n_act = host_counters[0];
     n_ref = host_counters[1];
   }
   prof.begin(MGFLD_PROF_FINISH);
-  MGFLD_CUDA(launch_assemble(p, w, state->psi, state->ye, state->T, w.diag, w.lower, w.upper, w.rhs, nullptr,
-                             R, nullptr, s, w.src));
+  MGFLD_CUDA(launch_assemble(p, w, state->psi, w.diag, tl.mixed, w.lower, w.upper, w.rhs, nullptr, R, nullptr,
+                             s, w.src));
   k_finish<<<nblk((size_t)R * NR, 128), 128, 0, s>>>(p, w, state->psi, state->ye, state->T);
   MGFLD_CUDA(cudaGetLastError());
   MGFLD_CUDA(cudaMemsetAsync(w.counters + 2, 0, sizeof(int), s));
@@ -514,8 +602,8 @@ mgfld_status mgfld_assemble(const mgfld_dims *dims, const mgfld_problem *prob, c
   const Ws w = resolve(ws, L);
   const Prob p = make_prob(dims, prob);
   MGFLD_CUDA(launch_setup(p, w, state->psi, state->ye, state->T, s));
-  MGFLD_CUDA(launch_assemble(p, w, state->psi, state->ye, state->T, sys->diag, sys->lower, sys->upper,
-                             sys->rhs, nullptr, dims->n_ray, nullptr, s));
+  MGFLD_CUDA(launch_assemble(p, w, state->psi, sys->diag, 0, sys->lower, sys->upper, sys->rhs, nullptr,
+                             dims->n_ray, nullptr, s));
   return MGFLD_OK;
 }
 
@@ -524,8 +612,8 @@ mgfld_status mgfld_factor(const mgfld_dims *dims, const mgfld_system *sys, int p
   if (!dims_ok(dims) || !sys || !sys->diag || !sys->lower || !sys->upper || !factor ||
       (precision != MGFLD_FP64 && precision != MGFLD_MIXED))
     return MGFLD_EINVAL;
-  MGFLD_CUDA(launch_factor(dims->n_e, dims->n_r, dims->n_ray * NS, sys->diag, sys->lower, sys->upper, factor,
-                           precision, nullptr, (cudaStream_t)stream));
+  MGFLD_CUDA(launch_factor(dims->n_e, dims->n_r, dims->n_ray * NS, sys->diag, 0, sys->lower, sys->upper,
+                           factor, precision, nullptr, (cudaStream_t)stream));
   return MGFLD_OK;
 }
 
