@@ -49,11 +49,22 @@ def dist_info():
     return ws, rank, local
 
 
-def workload(n_gpus, rank):
-    inp = problems.make_problem(CONFIG_ID, n_ray=RAYS_PER_RANK * n_gpus)
+def shard(n_gpus, rank, rays_per_rank=RAYS_PER_RANK):
+    """Rays of rank `rank`: a contiguous block of a 2D ray set of rays_per_rank * n_gpus rays
+    (rays are independent within a step, so ranks exchange nothing on the data path)."""
+    return slice(rank * rays_per_rank, (rank + 1) * rays_per_rank)
+
+
+def workload(n_gpus, rank, rays_per_rank=RAYS_PER_RANK):
+    inp = problems.make_problem(CONFIG_ID, n_ray=rays_per_rank * n_gpus)
     if n_gpus > 1:
-        inp = problems.subset_rays(inp, slice(rank * RAYS_PER_RANK, (rank + 1) * RAYS_PER_RANK))
+        inp = problems.subset_rays(inp, shard(n_gpus, rank, rays_per_rank))
     return inp
+
+
+def job_throughput(updates_per_rank_step, world, ms_per_step_max):
+    """Whole-job updates/s: every rank's rays over the slowest rank's time per step."""
+    return updates_per_rank_step * world / (ms_per_step_max * 1e-3)
 
 
 def updates_per_step(inp):
@@ -369,8 +380,8 @@ def main():
     fp64 = run_path(M, torch, inp, M.MGFLD_FP64, args.steps, args.warmup, barrier)
     ms_mixed = max_over_ranks(mixed['ms']) / args.steps
     ms_fp64 = max_over_ranks(fp64['ms']) / args.steps
-    value = ups * ws / (ms_mixed * 1e-3)
-    value64 = ups * ws / (ms_fp64 * 1e-3)
+    value = job_throughput(ups, ws, ms_mixed)
+    value64 = job_throughput(ups, ws, ms_fp64)
     e2e = e2e_run(M, torch, inp, M.MGFLD_MIXED, args.steps)
     e2e_ms = max_over_ranks(e2e['ms']) / args.steps
     roof = roofline_for(mixed, inp, M.MGFLD_MIXED, mixed['clocks'])
@@ -394,7 +405,7 @@ def main():
                     outer_iterations_per_step=mixed['max_iters'],
                     factorizations_per_ray_step=mixed['nfact'] / (RAYS_PER_RANK * args.steps)),
         roofline=roof, cpu_baseline=cpu, clocks=mixed['clocks'],
-        e2e=dict(value=ups * ws / (e2e_ms * 1e-3), unit=UNIT, h2d_bytes_per_step=e2e['h2d'],
+        e2e=dict(value=job_throughput(ups, ws, e2e_ms), unit=UNIT, h2d_bytes_per_step=e2e['h2d'],
                  d2h_bytes_per_step=e2e['d2h']),
         gpu_launches=launches,
         kernel_ms={k: v['ms'] for k, v in mixed['prof'].items()},
