@@ -211,6 +211,53 @@ mgfld_status mgfld_solve(const mgfld_dims *dims, const mgfld_system *sys, int pr
 mgfld_status mgfld_step_noalloc(const mgfld_dims *dims, const mgfld_problem *prob, mgfld_state *state,
                                 const mgfld_step_opts *opts, mgfld_step_report *report, void *stream);
 
+/*
+ * Discrete adjoint of one step (FP64).  The paper has no adjoint; it is the exact
+ * derivative of the discrete step defined by Eqs. a58, a59, a62a, a62b with the
+ * coefficients frozen at the start of the step (Eqs. a17, a20-a26a, a55, a62af, d7, d8).
+ *
+ * For a step p = (psi^n, Ye^n, T^n, scale) -> (psi^{n+1}, Ye^{n+1}, T^{n+1}, H), where
+ * H[ray] is the heating of mgfld_step_report, and a scalar loss
+ *   L = <psi_bar, psi^{n+1}> + <ye_bar, Ye^{n+1}> + <T_bar, T^{n+1}> + heat_weight sum(H),
+ * mgfld_adjoint writes dL/dpsi^n, dL/dYe^n, dL/dT^n and adds dL/dscale.  The root
+ * (psi^{n+1}, Ye^{n+1}) is the caller's (normally mgfld_step's output); the
+ * implicit-function theorem turns the root condition G(x; p) = 0 into one
+ * transposed solve J^T mu = dL/dx, J = dG/dx at the root, done by block
+ * Gauss-Seidel between psi (block-Thomas on the transposed per-species system) and
+ * Ye (zone-local), then p_bar = dL/dp - mu^T dG/dp.  T^{n+1} enters L through
+ * Eq. a62b and the EoS inversion.  All pointers are DEVICE pointers; inputs (the
+ * *_bar arrays) may be NULL for zero.  Shapes as the state arrays; scale_bar is
+ * [n_s][n_e] and may be NULL (no scale gradient).
+ */
+typedef struct {
+  const double *psi_bar, *ye_bar, *T_bar; /* dL/d(psi, Ye, T)^{n+1}, or NULL */
+  double heat_weight;                     /* weight of sum(H) in L */
+  double *psi_bar_out, *ye_bar_out, *T_bar_out; /* dL/d(psi, Ye, T)^n (overwritten; required) */
+  double *scale_bar;                      /* dL/dscale is ADDED here, or NULL */
+  int max_sweeps;                         /* Gauss-Seidel sweeps at most (0: 30) */
+  double sweep_tol;                       /* stop when max|d mu_Ye| <= sweep_tol max|mu_Ye| (0: 1e-15) */
+  int sweeps_used;                        /* out (host): sweeps performed */
+  double sweep_change;                    /* out (host): relative mu_Ye change of the last sweep */
+} mgfld_adjoint_io;
+
+/* Bytes of workspace mgfld_adjoint needs (0 for invalid dims). */
+size_t mgfld_adjoint_workspace_bytes(const mgfld_dims *dims);
+
+/*
+ * mgfld_adjoint -- reverse of one mgfld_step.
+ *   prob: the step's problem (prob->scale as used in the step, or NULL for ones).
+ *   state_n: (psi^n, Ye^n, T^n), the step's input.  state_np1: psi^{n+1}, Ye^{n+1}
+ *   (T is not read).  ws: device workspace, 256-byte aligned, of at least
+ *   mgfld_adjoint_workspace_bytes(); scratch.
+ * Synchronises `stream` once per Gauss-Seidel sweep (the stopping test).
+ * Returns OK, EINVAL (bad argument, psi_bar_out/ye_bar_out/T_bar_out missing),
+ * ENOMEM (workspace too small), ENOCONV (the sweeps did not reach sweep_tol; the
+ * outputs hold the last sweep's gradients), ENAN (a non-finite sweep change) or ECUDA.
+ */
+mgfld_status mgfld_adjoint(const mgfld_dims *dims, const mgfld_problem *prob, const mgfld_state *state_n,
+                           const mgfld_state *state_np1, mgfld_adjoint_io *io, void *ws, size_t ws_bytes,
+                           void *stream);
+
 /* Human-readable name of a status code (static string). */
 const char *mgfld_status_str(mgfld_status s);
 

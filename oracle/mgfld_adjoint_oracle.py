@@ -150,13 +150,17 @@ class Step:
         x = lam_e * torch.abs(dpsi / dR) / 3.0
         r_e = self.r_edge[:, 1:][:, None, :, None]
         r_nu = self.r_nu[:, :, None, :]
-        safe_x = torch.where(x > 0, x, torch.ones_like(x))
         safe_pe = torch.where(psi_e > 1e-300, psi_e, torch.ones_like(psi_e))
         f_int = safe_pe / (safe_pe + x)
         outside = r_e > r_nu
         mu = torch.sqrt(torch.where(outside, 1.0 - (r_nu / r_e) ** 2, torch.ones_like(r_nu / r_e)))
-        f_geo = torch.where(outside, 0.5 * (1.0 + mu) * safe_pe / safe_x, torch.full_like(x, np.inf))
-        F = torch.minimum(f_int, f_geo)
+        h = 0.5 * (1.0 + mu)
+        # min(F_intrp, F_geom) taken as the branch it selects (F_geom < F_intrp exactly when
+        # h psi_e < (1 - h) x): the same value, and the unselected quotient, whose denominator
+        # may be tiny, stays out of the derivative.
+        use_geo = (outside & (h * safe_pe < (1.0 - h) * x)).detach()
+        safe_x = torch.where(use_geo, x, torch.ones_like(x))
+        F = torch.where(use_geo, h * safe_pe / safe_x, f_int)
         F = torch.where(dpsi == 0.0, torch.ones_like(F), F)
         F = torch.where(psi_e <= 1e-300, torch.zeros_like(F), F)
         D = lam_e * F / (3.0 * dR)

@@ -54,6 +54,11 @@ struct Layout {
 
 Layout make_layout(int n_ray, int n_r, int n, int precision);
 
+// Argument checks and the device view of a caller's problem (shared by the C entry points).
+bool dims_ok(const mgfld_dims *d);
+bool prob_ok(const mgfld_problem *p);
+Prob make_prob(const mgfld_dims *d, const mgfld_problem *p);
+
 // Per-zone constants evaluated once per step: a^2/V (flux divergence prefactor of Eq. a58),
 // 1/(a c dt), 1/a, V, mu_nue at (rho, T^n, Ye^n), a and a c dt.
 // ZC_MUA, ZC_MUB: the Ye-independent factors of mu_e and of the nuclear part of mu_n, so that

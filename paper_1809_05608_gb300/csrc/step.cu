@@ -434,16 +434,16 @@ static Eos make_eos(const mgfld_eos_params &e) {
   return d;
 }
 
-static bool dims_ok(const mgfld_dims *d) {
+bool dims_ok(const mgfld_dims *d) {
   return d && d->n_ray >= 1 && d->n_r >= 1 && d->n_e >= 1 && d->n_e <= MAX_NE && d->n_s == NS;
 }
 
-static bool prob_ok(const mgfld_problem *p) {
+bool prob_ok(const mgfld_problem *p) {
   return p && p->r_edge && p->e_edge && p->rho && p->kappa_abs && p->kappa_scat && p->dt > 0.0 &&
          (p->outer_bc == MGFLD_BC_GHOST || p->outer_bc == MGFLD_BC_REFLECT);
 }
 
-static Prob make_prob(const mgfld_dims *d, const mgfld_problem *p) {
+Prob make_prob(const mgfld_dims *d, const mgfld_problem *p) {
   Prob q;
   q.n_ray = d->n_ray; q.n_r = d->n_r; q.n = d->n_e; q.bc = p->outer_bc; q.dt = p->dt;
   q.r_edge = p->r_edge; q.lapse = p->lapse; q.e_edge = p->e_edge; q.rho = p->rho;

@@ -21,7 +21,8 @@ MGFLD_BC_GHOST, MGFLD_BC_REFLECT = 0, 1
 N_SPECIES = 4
 
 EXPORTED = ('mgfld_eos_default', 'mgfld_workspace_bytes', 'mgfld_step', 'mgfld_assemble',
-            'mgfld_factor_bytes', 'mgfld_factor', 'mgfld_solve', 'mgfld_status_str', 'mgfld_step_noalloc')
+            'mgfld_factor_bytes', 'mgfld_factor', 'mgfld_solve', 'mgfld_status_str', 'mgfld_step_noalloc',
+            'mgfld_adjoint_workspace_bytes', 'mgfld_adjoint')
 NOALLOC_SCRATCH_BYTES = 64 << 20
 
 
@@ -61,6 +62,14 @@ class System(ctypes.Structure):
                 ('rhs', ctypes.c_void_p)]
 
 
+class AdjointIO(ctypes.Structure):
+    _fields_ = [('psi_bar', ctypes.c_void_p), ('ye_bar', ctypes.c_void_p), ('T_bar', ctypes.c_void_p),
+                ('heat_weight', ctypes.c_double), ('psi_bar_out', ctypes.c_void_p),
+                ('ye_bar_out', ctypes.c_void_p), ('T_bar_out', ctypes.c_void_p), ('scale_bar', ctypes.c_void_p),
+                ('max_sweeps', ctypes.c_int), ('sweep_tol', ctypes.c_double), ('sweeps_used', ctypes.c_int),
+                ('sweep_change', ctypes.c_double)]
+
+
 _lib = None
 
 
@@ -93,6 +102,11 @@ def lib():
                               ctypes.c_void_p, ctypes.c_void_p]
     L.mgfld_step_noalloc.restype = ctypes.c_int
     L.mgfld_step_noalloc.argtypes = [P(Dims), P(Problem), P(State), P(StepOpts), P(StepReport), ctypes.c_void_p]
+    L.mgfld_adjoint_workspace_bytes.restype = ctypes.c_size_t
+    L.mgfld_adjoint_workspace_bytes.argtypes = [P(Dims)]
+    L.mgfld_adjoint.restype = ctypes.c_int
+    L.mgfld_adjoint.argtypes = [P(Dims), P(Problem), P(State), P(State), P(AdjointIO), ctypes.c_void_p,
+                                ctypes.c_size_t, ctypes.c_void_p]
     L.mgfld_status_str.restype = ctypes.c_char_p
     L.mgfld_status_str.argtypes = [ctypes.c_int]
     _lib = L
@@ -223,6 +237,25 @@ def mgfld_solve(dims, sys, precision, factor, rhs, x, stream=None):
     s = System(_ptr(sys.get('diag')), _ptr(sys['lower']), _ptr(sys['upper']), _ptr(sys.get('rhs')))
     return lib().mgfld_solve(ctypes.byref(dims), ctypes.byref(s), int(precision), _ptr(factor), _ptr(rhs),
                              _ptr(x), _stream(stream))
+
+
+def mgfld_adjoint_workspace_bytes(dims: Dims) -> int:
+    return int(lib().mgfld_adjoint_workspace_bytes(ctypes.byref(dims)))
+
+
+def mgfld_adjoint(dims, problem_struct, state_n, state_np1, bars, out, ws, heat_weight=1.0, scale_bar=None,
+                  max_sweeps=0, sweep_tol=0.0, stream=None):
+    """Reverse of one step.  state_n = (psi, ye, T) at the step's start, state_np1 = (psi, ye)
+    at its root; bars = (psi_bar, ye_bar, T_bar) of the step's outputs (entries may be None);
+    out = (psi_bar_out, ye_bar_out, T_bar_out) tensors to overwrite; scale_bar [4, n_e] is
+    accumulated into.  Returns (status, sweeps used, last relative mu_Ye change)."""
+    s0 = State(_ptr(state_n[0]), _ptr(state_n[1]), _ptr(state_n[2]))
+    s1 = State(_ptr(state_np1[0]), _ptr(state_np1[1]), None)
+    io = AdjointIO(_ptr(bars[0]), _ptr(bars[1]), _ptr(bars[2]), float(heat_weight), _ptr(out[0]), _ptr(out[1]),
+                   _ptr(out[2]), _ptr(scale_bar), int(max_sweeps), float(sweep_tol), 0, 0.0)
+    rc = lib().mgfld_adjoint(ctypes.byref(dims), ctypes.byref(problem_struct), ctypes.byref(s0), ctypes.byref(s1),
+                             ctypes.byref(io), _ptr(ws), ws.numel() * ws.element_size(), _stream(stream))
+    return rc, io.sweeps_used, io.sweep_change
 
 
 # ---------------------------------------------------------------------------- convenience
