@@ -168,8 +168,8 @@ def traffic_record(kernel):
 
 # ------------------------------------------------------------------------- GPU arm
 
-def run_path(M, torch, inp, precision, steps, warmup, barrier, clocks=None):
-    st = M.Stepper(inp, precision, tol=TOL, max_iter=60)
+def run_path(M, torch, inp, precision, steps, warmup, barrier, clocks=None, refactor_ratio=None):
+    st = M.Stepper(inp, precision, tol=TOL, max_iter=60, refactor_ratio=refactor_ratio)
     if clocks:
         clocks.start()
     psi, ye, T = st.state_to_device(inp['psi0'], inp['ye0'], inp['T0'])
@@ -223,15 +223,16 @@ def algorithmic_work(inp, kernel, nfact, iters, precision):
 
     factor: per (zone, system) factorisation, N^3 FMAs of in-place Gauss-Jordan plus
     2 N^2 for the diagonal Schur scaling: 2 N^3 + 2 N^2 flops (FP64 or FP32).
-    assemble: per (zone, system, iteration) residual, two length-N NES sums per row
-    (4 N^2) + 16 N of transport/absorption terms; with a fresh Jacobian another 4 N^2."""
+    assemble (FP64 pipe only): per (zone, system, iteration) residual, two length-N NES sums
+    per row (4 N^2) + 16 N of transport/absorption terms; with a fresh FP64 Jacobian one FMA
+    per entry (2 N^2).  The mixed path's Jacobian rows are FP32 and are not counted."""
     n_ray, n_s, n_r, n = inp['psi0'].shape
     if kernel == 'factor':
         per = 2.0 * n**3 + 2.0 * n**2
         return per * n_s * n_r * nfact
     if kernel == 'assemble':
         per_res = 4.0 * n**2 + 16.0 * n
-        per_jac = 4.0 * n**2
+        per_jac = 2.0 * n**2 if precision == 0 else 0.0
         return n_s * n_r * (per_res * iters + per_jac * nfact)
     raise ValueError(kernel)
 
@@ -377,15 +378,20 @@ def main():
     ups = updates_per_step(inp)
     clocks = ClockSampler(local)
     mixed = run_path(M, torch, inp, M.MGFLD_MIXED, args.steps, args.warmup, barrier, clocks)
-    fp64 = run_path(M, torch, inp, M.MGFLD_FP64, args.steps, args.warmup, barrier)
+    # FP64 beside it: the same modified-Newton policy with FP64 factors (the like-for-like
+    # baseline), and Newton with a new FP64 factorisation every iteration.
+    fp64 = run_path(M, torch, inp, M.MGFLD_FP64, args.steps, args.warmup, barrier, refactor_ratio=0.1)
+    newton = run_path(M, torch, inp, M.MGFLD_FP64, args.steps, args.warmup, barrier, refactor_ratio=0.0)
     ms_mixed = max_over_ranks(mixed['ms']) / args.steps
     ms_fp64 = max_over_ranks(fp64['ms']) / args.steps
+    ms_newton = max_over_ranks(newton['ms']) / args.steps
     value = job_throughput(ups, ws, ms_mixed)
     value64 = job_throughput(ups, ws, ms_fp64)
     e2e = e2e_run(M, torch, inp, M.MGFLD_MIXED, args.steps)
     e2e_ms = max_over_ranks(e2e['ms']) / args.steps
     roof = roofline_for(mixed, inp, M.MGFLD_MIXED, mixed['clocks'])
     roof64 = roofline_for(fp64, inp, M.MGFLD_FP64, None)
+    roof_newton = roofline_for(newton, inp, M.MGFLD_FP64, None)
     launches = sum(v['launches'] for v in mixed['prof'].values())
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -410,9 +416,16 @@ def main():
         gpu_launches=launches,
         kernel_ms={k: v['ms'] for k, v in mixed['prof'].items()},
         fp64_path=dict(value=value64, unit=UNIT, ms_per_step=ms_fp64, roofline=roof64, dtype='f64',
+                       iteration='modified Newton, refactor when a correction shrinks by less than 10x',
                        kernel_ms={k: v['ms'] for k, v in fp64['prof'].items()},
                        outer_iterations_per_step=fp64['max_iters'],
+                       factorizations_per_ray_step=fp64['nfact'] / (RAYS_PER_RANK * args.steps),
                        gpu_launches=sum(v['launches'] for v in fp64['prof'].values())),
+        fp64_newton_path=dict(value=job_throughput(ups, ws, ms_newton), unit=UNIT, ms_per_step=ms_newton,
+                              roofline=roof_newton, dtype='f64', iteration='Newton, new factors every iteration',
+                              kernel_ms={k: v['ms'] for k, v in newton['prof'].items()},
+                              outer_iterations_per_step=newton['max_iters'],
+                              factorizations_per_ray_step=newton['nfact'] / (RAYS_PER_RANK * args.steps)),
         mixed_over_fp64=value / value64)
     print(json.dumps(line), flush=True)
     if dist is not None:

@@ -87,7 +87,10 @@ typedef struct {
   double tol_ye;       /* |d Ye| <= tol_ye * max(Ye, tolmin_ye) */
   double tolmin_ye;    /* typically 0.1 */
   int max_iter;        /* outer-iteration cap per ray */
-  double refactor_ratio; /* MIXED only: refactor a ray when its correction shrinks by less than this */
+  double refactor_ratio; /* modified Newton: a ray keeps its factors while each correction is at most
+                            this fraction of the previous one, and is refactored otherwise.  MIXED
+                            always iterates this way (0 selects 0.1); FP64 does when > 0, and with 0
+                            refactors every iteration (Newton, Eq. a62aa) */
   double *profile;     /* HOST pointer to double[MGFLD_PROF_N][2] or NULL.  When set, each kernel
                           category is bracketed by CUDA events on `stream` and its elapsed
                           milliseconds and launch count are ADDED to profile[c][0], profile[c][1]. */

@@ -120,7 +120,7 @@ Ws resolve(void *base, const Layout &L) {
 
 struct Tol {
   double tol, tolmin, tol_ye, tolmin_ye, refactor_ratio;
-  int max_iter, mixed;
+  int max_iter, mixed, chord;   // chord: reuse factors while the iteration contracts fast enough
   float tolm, tolm_ye;      // tol = tolm 2^tole (for tol_ratio)
   int tole, tole_ye;
 };
@@ -271,7 +271,7 @@ __global__ void k_check(int n_ray, Ws w, Tol tl) {
   const int a = atomicAdd(&w.counters[0], 1);
   w.list_act[a] = r;
   int ref = 1;
-  if (tl.mixed) ref = v > tl.refactor_ratio * w.vprev[r];
+  if (tl.chord) ref = v > tl.refactor_ratio * w.vprev[r];
   w.vprev[r] = v;
   w.refac[r] = ref;
   if (ref) {
@@ -513,6 +513,7 @@ mgfld_status mgfld_step(const mgfld_dims *dims, const mgfld_problem *prob, mgfld
   tl.tol = opts->tol; tl.tolmin = opts->tolmin_psi; tl.tol_ye = opts->tol_ye; tl.tolmin_ye = opts->tolmin_ye;
   tl.refactor_ratio = opts->refactor_ratio > 0.0 ? opts->refactor_ratio : 0.1;
   tl.max_iter = opts->max_iter; tl.mixed = opts->precision == MGFLD_MIXED;
+  tl.chord = tl.mixed || opts->refactor_ratio > 0.0;
   tl.tolm = (float)std::frexp(opts->tol, &tl.tole);
   tl.tolm_ye = (float)std::frexp(opts->tol_ye, &tl.tole_ye);
   const int R = dims->n_ray, n = dims->n_e, NR = dims->n_r;
@@ -527,13 +528,13 @@ mgfld_status mgfld_step(const mgfld_dims *dims, const mgfld_problem *prob, mgfld
   int n_act = R, n_ref = R;
   int host_counters[8];
   for (int it = 0; it < opts->max_iter && n_act > 0; ++it) {
-    const int *jac = tl.mixed ? w.refac : nullptr;
+    const int *jac = tl.chord ? w.refac : nullptr;
     prof.begin(MGFLD_PROF_ASSEMBLE);
     MGFLD_CUDA(launch_assemble(p, w, state->psi, w.diag, tl.mixed, w.lower, w.upper, w.rhs, w.list_act, n_act,
                                jac, s));
     prof.end(MGFLD_PROF_ASSEMBLE, 1);
-    const int *flist = tl.mixed ? w.list_ref : w.list_act;
-    const int nf = tl.mixed ? n_ref : n_act;
+    const int *flist = tl.chord ? w.list_ref : w.list_act;
+    const int nf = tl.chord ? n_ref : n_act;
     if (nf > 0) {
       prof.begin(MGFLD_PROF_FACTOR);
       if (tl.mixed)

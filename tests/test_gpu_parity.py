@@ -123,6 +123,27 @@ def test_full_launch_256_rays_sampled_against_oracle():
     assert np.all(rep['ray_status'] == 0) and np.all(rep['iters'] >= 2)
 
 
+@pytest.mark.parametrize('kind', ['2d', 'strong'])
+def test_fp64_modified_newton_matches_oracle(kind):
+    """FP64 factors reused while the iteration contracts (refactor_ratio 0.1): the same root as
+    the oracle's Newton, with fewer factorisations than iterations."""
+    if kind == '2d':
+        inp = problems.make_problem(2, rays=[0, 101, 255])
+        tol = 1e-12
+    else:
+        inp = SP.strong(n_ray=2, n_r=16, n_e=5, kabs=3e16, kscat=1e15, nes=30.0, lapse=True)
+        tol = 1e-11
+    psi, ye, T, codes, rep = run_gpu(inp, steps=2, tol=tol, refactor_ratio=0.1)
+    psi_o, ye_o, T_o, _ = run_oracle(inp, steps=2)
+    assert codes == [M.MGFLD_OK] * 2
+    fwd = normwise(psi, psi_o)
+    print(f'fp64 modified Newton ({kind}): forward {fwd:.2e} (gate {fp64_gate(inp):.1e}); '
+          f'iterations {rep["iters"].tolist()}, factorisations {rep["factorizations"].tolist()}')
+    assert fwd < fp64_gate(inp)
+    assert np.max(np.abs(T / T_o - 1)) < fp64_gate(inp)
+    assert np.all(rep['factorizations'] < rep['iters'])
+
+
 @pytest.mark.parametrize('lapse', [False, True])
 def test_strong_coupling_fp64(lapse):
     inp = SP.strong(n_ray=2, n_r=16, n_e=5, kabs=3e16, kscat=1e15, nes=30.0, lapse=lapse)
