@@ -22,44 +22,78 @@ struct Pack {
   static constexpr int THREADS = SPC * NP;
 };
 
-// Approximate 1/x for the pivot of a Gauss-Jordan step.  FP64: an FP32 seed refined by one
-// Newton-Raphson step x1 = x0 + x0 (1 - d x0) (quadratic convergence: ~2^-23 -> ~2^-46
-// relative), two fused multiply-adds on the scarce FP64 pipe; outside the FP32 range a
-// plain division.  The factors only steer the outer iteration, whose fixed point is set by
-// the FP64 residual, so a ~1e-14 relative error in the inverse costs nothing in the result.
+// 1/d for the pivot of a Gauss-Jordan step without FP64-pipe conversions or compares: the
+// mantissa of d, rounded to 24 bits, becomes an FP32 value m in [1, 2] by bit manipulation
+// (integer pipe), its reciprocal is taken in FP32, the exponent of 1/d is rebuilt from the two
+// exponents, and one Newton-Raphson step x1 = x0 + x0 (1 - d x0) (two FMAs on the FP64 pipe)
+// takes the ~2^-23 seed to ~2^-46 relative.  Zero, subnormal, non-finite and extreme-exponent
+// pivots take a plain division (rare; a zero pivot means a singular block).  The factors only
+// steer the outer iteration, whose fixed point is set by the FP64 residual.
 __device__ inline double recip(double d) {
-  const double ad = fabs(d);
-  if (!(ad > 1e-30 && ad < 1e30)) return 1.0 / d;
-  const double x = (double)__frcp_rn((float)d);
+  const unsigned long long b = (unsigned long long)__double_as_longlong(d);
+  const int e = (int)((b >> 52) & 0x7ff);
+  const unsigned m23 = (unsigned)((b >> 29) & 0x7fffff);
+  const float up = ((b >> 28) & 1ull) ? 1.1920928955078125e-7f : 0.f;     // round the dropped bits
+  const float m = __uint_as_float(0x3f800000u | m23) + up;                 // exact; may be 2.0
+  const unsigned rb = __float_as_uint(__frcp_rn(m));                      // 1/m in (0.5, 1]
+  const int ed = (int)(rb >> 23) - 127 + 2046 - e;                         // biased exponent of 1/|d|
+  if (e == 0 || e == 0x7ff || ed <= 0 || ed >= 0x7ff) return 1.0 / d;
+  const double x = __longlong_as_double((long long)((b & 0x8000000000000000ull) |
+                                                    ((unsigned long long)ed << 52) |
+                                                    ((unsigned long long)(rb & 0x7fffff) << 29)));
   return fma(x, fma(-d, x, 1.0), x);
 }
-__device__ inline float recip(float d) { return __frcp_rn(d); }
 
-// Pivot-search key: |x| as an integer (non-negative IEEE values order like their bit
-// patterns), so the comparisons run on the integer pipe instead of the FP64 pipe.
-__device__ inline long long pivot_key(double x) { return __double_as_longlong(fabs(x)); }
-__device__ inline long long pivot_key(float x) { return (long long)__float_as_int(fabsf(x)); }
+// 32-bit pivot-search key of row r: the upper word of |x| (sign cleared; non-negative IEEE
+// values order like their bit patterns) with its 5 lowest bits replaced by 31 - r.  One integer
+// max over the keys then finds the largest |x| to 15 mantissa bits, ties going to the lowest
+// row, and the winner's row is 31 - (key & 31).  Rows already used as pivots carry -1.
+__device__ inline int pivot_key(double x, int r) {
+  const unsigned hi = (unsigned)((unsigned long long)__double_as_longlong(x) >> 32) & 0x7fffffffu;
+  return (int)((hi & ~31u) | (unsigned)(31 - r));
+}
 
-template <typename T> __device__ inline T to_t(double v);
-template <> __device__ inline double to_t<double>(double v) { return v; }
-template <> __device__ inline float to_t<float>(double v) { return (float)v; }
-template <typename T> __device__ inline T to_t(float v) { return (T)v; }
+template <int NP>
+__device__ inline int max_key(const int *__restrict__ c) {
+  static_assert(NP % 4 == 0, "padded block sizes are multiples of 4");
+  int m[NP / 4];
+#pragma unroll
+  for (int j = 0; j < NP / 4; ++j) {
+    const int4 v = reinterpret_cast<const int4 *>(c)[j];
+    m[j] = max(max(v.x, v.y), max(v.z, v.w));
+  }
+#pragma unroll
+  for (int w = 1; w < NP / 4; w *= 2)
+#pragma unroll
+    for (int j = 0; j + w < NP / 4; j += 2 * w) m[j] = max(m[j], m[j + w]);
+  return m[0];
+}
 
 // Map the j-th system of the launch to a global (ray, species) system index.
 __device__ inline long system_of(long j, const int *ray_list) {
   return ray_list ? (long)ray_list[j / NS] * NS + (j % NS) : j;
 }
 
-template <int NP, typename T, typename TIn>
+template <typename T> __device__ inline T to_t(double v);
+template <> __device__ inline double to_t<double>(double v) { return v; }
+template <> __device__ inline float to_t<float>(double v) { return (float)v; }
+
+// FP64 block-Thomas elimination (one thread per block row, SPC systems per CTA).  Per pivot
+// step: barrier; every row reads the NP candidate keys of its system (NP/4 vector loads, a
+// depth-log2 max tree); the pivot row publishes itself; barrier; every row forms its multiplier
+// with one FMA and updates its NP entries.  The entry of the next pivot column is updated
+// first and its key published at once, so that the next search only waits for that one FMA
+// while the other NP - 1 drain through the FP64 pipe.
+template <int NP, typename TIn>
 __global__ void __launch_bounds__(Pack<NP>::THREADS)
 k_factor(int n, int n_r, int n_sys, const TIn *__restrict__ diag, const double *__restrict__ lower,
-         const double *__restrict__ upper, T *__restrict__ dinv, const int *__restrict__ ray_list) {
+         const double *__restrict__ upper, double *__restrict__ dinv, const int *__restrict__ ray_list) {
   constexpr int SPC = Pack<NP>::SPC;
-  __shared__ T tile[SPC][NP][NP + 1];   // natural-order inverse of the previous zone
-  __shared__ T prow[SPC][NP];           // pivot row of the current step
-  __shared__ long long cand[SPC][NP];   // pivot candidates (key of |a|, -1 once used)
-  __shared__ T ushr[SPC][NP];           // upper_{i-1}, the column scaling of the Schur update
-  __shared__ int pivrow[SPC][NP];       // row chosen at each step
+  __shared__ double tile[SPC][NP][NP + 1];           // natural-order inverse of the previous zone
+  __shared__ __align__(16) double prow[SPC][NP];     // pivot row of the current step
+  __shared__ __align__(16) int cand[SPC][NP];        // pivot-search keys
+  __shared__ double ushr[SPC][NP];                   // upper_{i-1}, the column scaling of the Schur update
+  __shared__ int pivrow[SPC][NP];                    // row chosen at each step
 
   const int s = threadIdx.x / NP, r = threadIdx.x % NP;
   const long jsys = (long)blockIdx.x * SPC + s;
@@ -68,69 +102,76 @@ k_factor(int n, int n_r, int n_sys, const TIn *__restrict__ diag, const double *
   const bool real = valid && r < n;
 
   // Rows of the next zone are fetched one zone ahead (registers) to hide memory latency.
-  T nxt[NP];
+  double nxt[NP];
   double nl = 0.0;
   auto load_row = [&](int i) {
     const size_t zr = ((size_t)sys * n_r + i) * n + r;
 #pragma unroll
     for (int c = 0; c < NP; ++c) {
-      if (real && c < n) nxt[c] = to_t<T>(diag[zr * n + c]);
-      else nxt[c] = (c == r) ? T(1) : T(0);
+      if (real && c < n) nxt[c] = (double)diag[zr * n + c];
+      else nxt[c] = (c == r) ? 1.0 : 0.0;
     }
     nl = (real && i > 0) ? lower[zr] : 0.0;
   };
   load_row(0);
   for (int i = 0; i < n_r; ++i) {
     const size_t zrow = ((size_t)sys * n_r + i) * n + r;   // (sys, i, r)
-    T a[NP];
+    double a[NP];
 #pragma unroll
     for (int c = 0; c < NP; ++c) a[c] = nxt[c];
-    const T lr = to_t<T>(nl);
+    const double lr = nl;
     if (i + 1 < n_r) load_row(i + 1);
     if (i > 0) {
 #pragma unroll
-      for (int c = 0; c < NP; ++c) a[c] = a[c] - (lr * tile[s][r][c]) * ushr[s][c];
+      for (int c = 0; c < NP; ++c) a[c] = fma(-(lr * tile[s][r][c]), ushr[s][c], a[c]);
     }
 
     // Gauss-Jordan inversion in place with partial pivoting (implicit row exchanges).
     bool used = false;
     int my_step = 0;
+    cand[s][r] = pivot_key(a[0], r);
 #pragma unroll
     for (int pstep = 0; pstep < NP; ++pstep) {
-      cand[s][r] = used ? -1LL : pivot_key(a[pstep]);
       __syncthreads();
-      int best = 0;
-      long long bv = cand[s][0];
-#pragma unroll
-      for (int c = 1; c < NP; ++c) {
-        const long long v = cand[s][c];
-        if (v > bv) { bv = v; best = c; }
-      }
+      const int best = 31 - (max_key<NP>(cand[s]) & 31);
       const bool me = (r == best);
       if (me) {
 #pragma unroll
-        for (int c = 0; c < NP; ++c) prow[s][c] = a[c];
+        for (int c = 0; c < NP; c += 2)
+          *reinterpret_cast<double2 *>(&prow[s][c]) = make_double2(a[c], a[c + 1]);
         pivrow[s][pstep] = r;
         used = true;
         my_step = pstep;
       }
       __syncthreads();
-      const T inv = recip(prow[s][pstep]);
-      // Uniform update for every row: a -= f * pivot_row, with f chosen so that the
-      // pivot row itself becomes pivot_row / pivot (f = 1 - 1/pivot).
-      const T f = me ? (T(1) - inv) : a[pstep] * inv;
+      double pr[NP];
 #pragma unroll
-      for (int c = 0; c < NP; ++c) a[c] = a[c] - f * prow[s][c];
+      for (int c = 0; c < NP; c += 2) {
+        const double2 v = *reinterpret_cast<const double2 *>(&prow[s][c]);
+        pr[c] = v.x;
+        pr[c + 1] = v.y;
+      }
+      const double inv = recip(pr[pstep]);
+      // Uniform update for every row: a -= f * pivot_row, with f chosen so that the pivot row
+      // itself becomes pivot_row / pivot (f = 1 - 1/pivot): one FMA either way.
+      const double f = fma(me ? -1.0 : a[pstep], inv, me ? 1.0 : 0.0);
+      if (pstep + 1 < NP) {
+        a[pstep + 1] = fma(-f, pr[pstep + 1], a[pstep + 1]);
+        cand[s][r] = used ? -1 : pivot_key(a[pstep + 1], r);
+      }
+#pragma unroll
+      for (int c = 0; c < NP; ++c)
+        if (c != pstep + 1) a[c] = fma(-f, pr[c], a[c]);
       a[pstep] = me ? inv : -f;
     }
     // Row r now holds row my_step of the inverse, with column c belonging to input row pivrow[c].
     __syncthreads();
 #pragma unroll
     for (int c = 0; c < NP; ++c) tile[s][my_step][pivrow[s][c]] = a[c];
-    ushr[s][r] = real ? to_t<T>(upper[zrow]) : T(0);
+    ushr[s][r] = real ? upper[zrow] : 0.0;
     __syncthreads();
     if (real) {
-      T *out = dinv + zrow * n;
+      double *out = dinv + zrow * n;
 #pragma unroll
       for (int c = 0; c < NP; ++c)
         if (c < n) out[c] = tile[s][r][c];
@@ -607,17 +648,17 @@ cudaError_t launch_solve_tma(int n, int n_r, int n_sys, const void *dinv, const 
   })
 }
 
-template <int NP, typename T>
+template <int NP>
 static cudaError_t run_factor(int n, int n_r, int n_sys, const void *diag, int diag_fp32, const double *lower,
                               const double *upper, void *dinv, const int *ray_list, cudaStream_t s) {
   constexpr int SPC = Pack<NP>::SPC;
   const unsigned grid = (unsigned)((n_sys + SPC - 1) / SPC);
   if (diag_fp32)
-    k_factor<NP, T, float><<<grid, Pack<NP>::THREADS, 0, s>>>(n, n_r, n_sys, (const float *)diag, lower, upper,
-                                                              (T *)dinv, ray_list);
+    k_factor<NP, float><<<grid, Pack<NP>::THREADS, 0, s>>>(n, n_r, n_sys, (const float *)diag, lower, upper,
+                                                           (double *)dinv, ray_list);
   else
-    k_factor<NP, T, double><<<grid, Pack<NP>::THREADS, 0, s>>>(n, n_r, n_sys, (const double *)diag, lower,
-                                                               upper, (T *)dinv, ray_list);
+    k_factor<NP, double><<<grid, Pack<NP>::THREADS, 0, s>>>(n, n_r, n_sys, (const double *)diag, lower, upper,
+                                                            (double *)dinv, ray_list);
   return cudaGetLastError();
 }
 
@@ -648,7 +689,7 @@ cudaError_t launch_factor(int n, int n_r, int n_sys, const void *diag, int diag_
                            return cudaGetLastError())
     }
   } else {
-    MGFLD_DISPATCH_NP(n, return (run_factor<NP, double>(n, n_r, n_sys, diag, diag_fp32, lower, upper, dinv,
+    MGFLD_DISPATCH_NP(n, return (run_factor<NP>(n, n_r, n_sys, diag, diag_fp32, lower, upper, dinv,
                                                         ray_list, s)))
   }
 }
