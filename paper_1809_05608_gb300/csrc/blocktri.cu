@@ -94,6 +94,7 @@ k_factor(int n, int n_r, int n_sys, const TIn *__restrict__ diag, const double *
   __shared__ __align__(16) int cand[SPC][NP];        // pivot-search keys
   __shared__ double ushr[SPC][NP];                   // upper_{i-1}, the column scaling of the Schur update
   __shared__ int pivrow[SPC][NP];                    // row chosen at each step
+  __shared__ double pinv[SPC];                       // 1 / pivot of the current step
 
   const int s = threadIdx.x / NP, r = threadIdx.x % NP;
   const long jsys = (long)blockIdx.x * SPC + s;
@@ -136,6 +137,9 @@ k_factor(int n, int n_r, int n_sys, const TIn *__restrict__ diag, const double *
       const int best = 31 - (max_key<NP>(cand[s]) & 31);
       const bool me = (r == best);
       if (me) {
+        // The pivot entry was updated first in the previous step, so its reciprocal is
+        // formed while the rest of this row is still in the FP64 pipe.
+        pinv[s] = recip(a[pstep]);
 #pragma unroll
         for (int c = 0; c < NP; c += 2)
           *reinterpret_cast<double2 *>(&prow[s][c]) = make_double2(a[c], a[c + 1]);
@@ -151,9 +155,10 @@ k_factor(int n, int n_r, int n_sys, const TIn *__restrict__ diag, const double *
         pr[c] = v.x;
         pr[c + 1] = v.y;
       }
-      const double inv = recip(pr[pstep]);
+      const double inv = pinv[s];
       // Uniform update for every row: a -= f * pivot_row, with f chosen so that the pivot row
-      // itself becomes pivot_row / pivot (f = 1 - 1/pivot): one FMA either way.
+      // itself becomes pivot_row / pivot (f = 1 - 1/pivot): one FMA either way.  The pivot
+      // column itself is overwritten below, so its update is skipped.
       const double f = fma(me ? -1.0 : a[pstep], inv, me ? 1.0 : 0.0);
       if (pstep + 1 < NP) {
         a[pstep + 1] = fma(-f, pr[pstep + 1], a[pstep + 1]);
@@ -161,7 +166,7 @@ k_factor(int n, int n_r, int n_sys, const TIn *__restrict__ diag, const double *
       }
 #pragma unroll
       for (int c = 0; c < NP; ++c)
-        if (c != pstep + 1) a[c] = fma(-f, pr[c], a[c]);
+        if (c != pstep + 1 && c != pstep) a[c] = fma(-f, pr[c], a[c]);
       a[pstep] = me ? inv : -f;
     }
     // Row r now holds row my_step of the inverse, with column c belonging to input row pivrow[c].
