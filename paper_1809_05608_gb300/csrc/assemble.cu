@@ -16,7 +16,7 @@ template <typename TD>
 __global__ void k_assemble(Prob p, Ws w, const double *__restrict__ psi, TD *__restrict__ diag,
                            double *__restrict__ lower, double *__restrict__ upper, double *__restrict__ rhs,
                            const int *__restrict__ list, int n_list, const int *__restrict__ jac_flag,
-                           double *__restrict__ src_out) {
+                           double *__restrict__ src_out, int first) {
   const int n = p.n;
   const size_t per_ray = (size_t)NS * p.n_r * n;
   const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -41,10 +41,15 @@ __global__ void k_assemble(Prob p, Ws w, const double *__restrict__ psi, TD *__r
   const double *fin = w.phin + (zi * n + k) * n;
   const double *fout = w.phout + (zi * n + k) * n;
   double gain = 0.0, lp = 0.0;
-  for (int kp = 0; kp < n; ++kp) {
-    const double pv = ps[kp];
-    gain += fin[kp] * pv;
-    lp += fout[kp] * pv;
+  if (first) {                 // psi = psi^n: the setup already formed these sums
+    gain = w.g0[g];
+    lp = w.l0[g];
+  } else {
+    for (int kp = 0; kp < n; ++kp) {
+      const double pv = ps[kp];
+      gain += fin[kp] * pv;
+      lp += fout[kp] * pv;
+    }
   }
   const double loss = w.rsum[zi * n + k] - lp;          // sum_k' phout (1 - psi_k')
   const double sc = p.scale ? p.scale[q * n + k] : 1.0;
@@ -89,17 +94,17 @@ __global__ void k_assemble(Prob p, Ws w, const double *__restrict__ psi, TD *__r
 
 cudaError_t launch_assemble(const Prob &p, const Ws &w, const double *psi, void *diag, int diag_fp32,
                             double *lower, double *upper, double *rhs, const int *list, int n_list,
-                            const int *jac_flag, cudaStream_t s, double *src_out) {
+                            const int *jac_flag, cudaStream_t s, double *src_out, int first) {
   const size_t total = (size_t)n_list * NS * p.n_r * p.n;
   if (total == 0) return cudaSuccess;
   const unsigned B = 256;
   const unsigned grid = (unsigned)((total + B - 1) / B);
   if (diag_fp32)
     k_assemble<float><<<grid, B, 0, s>>>(p, w, psi, (float *)diag, lower, upper, rhs, list, n_list, jac_flag,
-                                         src_out);
+                                         src_out, first);
   else
     k_assemble<double><<<grid, B, 0, s>>>(p, w, psi, (double *)diag, lower, upper, rhs, list, n_list,
-                                          jac_flag, src_out);
+                                          jac_flag, src_out, first);
   return cudaGetLastError();
 }
 

@@ -46,7 +46,8 @@ struct Prob {
 // Workspace regions (byte offsets from the workspace base).
 struct Layout {
   int mixed;
-  size_t groups, phout, phin, phd, rsum, phin32, phd32, lam, alpha, ghost, rnu, jbuf, psi_n, ye_n, e_n, zone, src;
+  size_t groups, phout, phin, phd, rsum, phin32, phd32, lam, slam, g0, l0, alpha, ghost, rnu, jbuf, psi_n, ye_n, e_n,
+      zone, src;
   size_t diag, lower, upper, rhs, x, dinv, zled, sscale, kinv, lower32, upper32, g32;
   size_t viol, vprev, active, iters, status, refac, nfact, nanflag, list_act, list_ref, counters;
   size_t total;
@@ -80,6 +81,8 @@ struct Ws {
   double *rsum;             // [ray][zone][k] row sums of phout: sum_k' phout (1 - psi_k') = rsum - phout.psi
   float *phin32, *phd32;    // FP32 copies for the Jacobian of the mixed path
   double *lam, *alpha, *ghost, *rnu, *jbuf, *psi_n, *ye_n, *e_n;
+  double *slam;             // per (ray, q, i, k): sqrt(lambda^(t)) at psi^n (edge mean free path = product)
+  double *g0, *l0;          // per (ray, q, i, k): the NES sums phin.psi^n and phout.psi^n (first iteration)
   double *zone;             // per zone [n_ray][n_r][ZC_N]: see ZC_* below
   double *src;              // per (ray, q, i, k): total source S at the converged state
   double *diag, *lower, *upper, *rhs, *x;
@@ -169,9 +172,10 @@ cudaError_t launch_groups(const Prob &p, const Ws &w, cudaStream_t s);
 cudaError_t launch_setup(const Prob &p, const Ws &w, const double *psi, const double *ye, const double *T,
                          cudaStream_t s);
 // diag is double (FP64 path, C ABI) or float (MIXED: the Jacobian feeds the FP32 factor only).
+// first: psi is still psi^n (first outer iteration), so the NES sums come from the setup (g0, l0).
 cudaError_t launch_assemble(const Prob &p, const Ws &w, const double *psi, void *diag, int diag_fp32,
                             double *lower, double *upper, double *rhs, const int *list, int n_list,
-                            const int *jac_flag, cudaStream_t s, double *src_out = nullptr);
+                            const int *jac_flag, cudaStream_t s, double *src_out = nullptr, int first = 0);
 cudaError_t launch_factor(int n, int n_r, int n_sys, const void *diag, int diag_fp32, const double *lower,
                           const double *upper, void *dinv, int precision, const int *ray_list,
                           cudaStream_t s);

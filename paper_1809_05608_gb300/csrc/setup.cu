@@ -57,24 +57,36 @@ __global__ void k_zone(Prob p, Ws w, const double *__restrict__ ye, const double
   z[ZC_EIR2] = 1.0 / (rp * rp);
 }
 
-// Weighted NES kernels of zone (ray, i), one thread per row k (Eqs. d7down, d7up):
-// down/iso-scattering Phi_out(eps_k, eps_k'<=k) = coef e^{-(eps_k - eps_k')/T} is built from the
-// N-1 ratios g_m = e^{-(eps_m - eps_{m-1})/T} of consecutive groups (one exponential each, shared
-// by the zone through shared memory) as a running product; up-scattering is its square
+// Weighted NES kernels of zone (ray, i) (Eqs. d7down, d7up): down/iso-scattering
+// Phi_out(eps_k, eps_k'<=k) = coef e^{-(eps_k - eps_k')/T} is built from the N-1 ratios
+// g_m = e^{-(eps_m - eps_{m-1})/T} of consecutive groups (one exponential each, shared by the
+// zone through shared memory) as a running product along the row; up-scattering is its square
 // (coef e^{-2(eps_k' - eps_k)/T}) and Phi_in(eps_k, eps_k') = Phi_out(eps_k', eps_k).
-// Zones per block of k_phi: the staged rows (2 n^2 doubles per zone) stay under 40 KB.
+// Rows k and n-1-k share a thread, so that every thread runs the same n-1 steps of the
+// down-scattering chains and n-1 of the up-scattering chains (no divergent loop lengths).
+// Rows are staged in shared memory with a padded stride (n + 1) and copied out coalesced.
+static inline int phi_threads_per_zone(int n) { return (n + 1) / 2; }
+static inline size_t phi_zone_bytes(int n) { return sizeof(double) * (2 * (size_t)n * (n + 1) + 2 * (size_t)n); }
+// Zones per block: zones * threads per zone a multiple of 32 where the staging fits in 113 KB
+// (two blocks per SM), else as many zones as fit.
 static inline int phi_zones_per_block(int n) {
-  const int z = 40960 / (16 * n * n + 8 * n);
-  return z < 1 ? 1 : (z > 8 ? 8 : z);
+  const int h = phi_threads_per_zone(n);
+  int g = h, b = 32;
+  while (b) { const int t = g % b; g = b; b = t; }
+  const int full = 32 / g;
+  const int fit = (int)((size_t)113 * 1024 / phi_zone_bytes(n));
+  return full <= fit ? full : (fit < 1 ? 1 : fit);
 }
+static inline size_t phi_smem_bytes(int n) { return (size_t)phi_zones_per_block(n) * phi_zone_bytes(n); }
 
 __global__ void k_phi(Prob p, Ws w, const double *__restrict__ T, int zpb) {
   extern __shared__ double smem[];
-  const int n = p.n;
-  double *gapm = smem;                       // [zpb][n]
-  double *sout = smem + (size_t)zpb * n;      // [zpb][n][n]
-  double *sin_ = sout + (size_t)zpb * n * n;  // [zpb][n][n]
-  const int zl = threadIdx.x / n, k = threadIdx.x % n;
+  const int n = p.n, H = (n + 1) / 2, ld = n + 1;
+  double *gapm = smem;                                   // [zpb][n]  e^{-(eps_m - eps_{m-1})/T}
+  double *cwm = gapm + (size_t)zpb * n;                   // [zpb][n]  C w_m = C W_m / a^3
+  double *sout = cwm + (size_t)zpb * n;                   // [zpb][n][n + 1]
+  double *sin_ = sout + (size_t)zpb * n * ld;             // [zpb][n][n + 1]
+  const int zl = threadIdx.x / H, t = threadIdx.x % H;
   const size_t nz = (size_t)p.n_ray * p.n_r;
   const size_t z0 = (size_t)blockIdx.x * zpb;
   const size_t zi = z0 + zl;
@@ -83,43 +95,71 @@ __global__ void k_phi(Prob p, Ws w, const double *__restrict__ T, int zpb) {
   const double inv_a = live ? 1.0 / lapse_at(p, ray, i) : 1.0;
   const double Ti = live ? T[zi] : 1.0;
   double *gap = gapm + (size_t)(live ? zl : 0) * n;
-  if (live && k > 0) gap[k] = exp(-(w.E[k] - w.E[k - 1]) * inv_a / Ti);
-  __syncthreads();
+  double *cw = cwm + (size_t)(live ? zl : 0) * n;
   if (live) {
-    double *out = sout + (zl * n + k) * n;
-    double *in = sin_ + (zl * n + k) * n;
-    const double coef = p.nes ? p.nes[zi] : 0.0;
-    const double cc = kCNes * inv_a * inv_a * inv_a * coef;   // C w_k' = C W_k' / a^3
-    out[k] = cc * w.W[k];
-    in[k] = out[k];
-    double P = 1.0;
-    for (int kp = k - 1; kp >= 0; --kp) {
-      P *= gap[kp + 1];                         // e^{-(eps_k - eps_kp)/T}
-      out[kp] = cc * w.W[kp] * P;               // down-scattering k -> kp
-      in[kp] = cc * w.W[kp] * (P * P);          // up-scattering kp -> k
+    const double cc = kCNes * inv_a * inv_a * inv_a * (p.nes ? p.nes[zi] : 0.0);
+    for (int k = t; k < n; k += H) {
+      if (k > 0) gap[k] = exp(-(w.E[k] - w.E[k - 1]) * inv_a / Ti);
+      cw[k] = cc * w.W[k];
     }
-    double Q = 1.0;
-    for (int kp = k + 1; kp < n; ++kp) {
-      Q *= gap[kp];                             // e^{-(eps_kp - eps_k)/T}
-      out[kp] = cc * w.W[kp] * (Q * Q);         // up-scattering k -> kp
-      in[kp] = cc * w.W[kp] * Q;                // down-scattering kp -> k
-    }
-    double rs = 0.0;
-    for (int kp = 0; kp < n; ++kp) rs += out[kp];
-    w.rsum[zi * n + k] = rs;
   }
   __syncthreads();
-  // Coalesced copy of the block's zones (contiguous in [ray][zone][k][k'] order).
+  if (live) {
+    const int ka = t, kb = n - 1 - t;                   // ka <= kb; equal for the middle row of odd n
+    double *oa = sout + ((size_t)zl * n + ka) * ld, *ia = sin_ + ((size_t)zl * n + ka) * ld;
+    double *ob = sout + ((size_t)zl * n + kb) * ld, *ib = sin_ + ((size_t)zl * n + kb) * ld;
+    double rsa = cw[ka], rsb = (ka == kb) ? 0.0 : cw[kb];
+    oa[ka] = cw[ka];
+    ia[ka] = cw[ka];
+    ob[kb] = cw[kb];
+    ib[kb] = cw[kb];
+    // Down-scattering (k' < k): row ka's ka entries, then row kb's kb entries (n - 1 steps).
+    double P = 1.0;
+    for (int j = 0; j < n - 1; ++j) {
+      const bool first = j < ka;
+      if (!first && ka == kb) break;                    // middle row: its chain is already done
+      const int kp = first ? ka - 1 - j : kb - 1 - (j - ka);
+      if (j == ka) P = 1.0;
+      P *= gap[kp + 1];                                 // e^{-(eps_k - eps_kp)/T}
+      const double o = cw[kp] * P;                      // down-scattering k -> kp
+      const double v = cw[kp] * (P * P);                // up-scattering kp -> k
+      if (first) { oa[kp] = o; ia[kp] = v; rsa += o; } else { ob[kp] = o; ib[kp] = v; rsb += o; }
+    }
+    // Up-scattering (k' > k): row kb's n-1-kb entries, then row ka's n-1-ka entries.
+    const int nb = n - 1 - kb;
+    double Q = 1.0;
+    for (int j = 0; j < n - 1; ++j) {
+      const bool first = j < nb;
+      if (!first && ka == kb) break;
+      const int kp = first ? kb + 1 + j : ka + 1 + (j - nb);
+      if (j == nb) Q = 1.0;
+      Q *= gap[kp];                                     // e^{-(eps_kp - eps_k)/T}
+      const double o = cw[kp] * (Q * Q);                // up-scattering k -> kp
+      const double v = cw[kp] * Q;                      // down-scattering kp -> k
+      if (first) { ob[kp] = o; ib[kp] = v; rsb += o; } else { oa[kp] = o; ia[kp] = v; rsa += o; }
+    }
+    if (kb != ka) {
+      w.rsum[zi * n + ka] = rsa;
+      w.rsum[zi * n + kb] = rsb;
+    } else {
+      w.rsum[zi * n + ka] = rsa + rsb;                  // middle row of odd n: both chains are its own
+    }
+  }
+  __syncthreads();
+  // Coalesced copy of the block's zones (contiguous in [ray][zone][k][k'] order).  The FP32
+  // copies of the mixed path are made by exponent/mantissa bit arithmetic (integer pipe,
+  // truncating): only the difference in - out uses the FP64 pipe.
   const size_t nzb = (z0 + zpb <= nz) ? (size_t)zpb : nz - z0;
   const size_t cnt = nzb * n * n;
   const size_t base = z0 * n * n;
   for (size_t e = threadIdx.x; e < cnt; e += blockDim.x) {
-    const double o = sout[e], v = sin_[e];
+    const size_t row = e / n, col = e - row * n;
+    const double o = sout[row * ld + col], v = sin_[row * ld + col];
     w.phout[base + e] = o;
     w.phin[base + e] = v;
     if (w.phin32) {
-      w.phin32[base + e] = (float)v;
-      w.phd32[base + e] = (float)(v - o);
+      w.phin32[base + e] = d2f_exp2(v, 0);
+      w.phd32[base + e] = d2f_exp2(v - o, 0);
     } else {
       w.phd[base + e] = v - o;
     }
@@ -167,8 +207,12 @@ __global__ void k_jlam(Prob p, Ws w, const double *__restrict__ psi, const doubl
       lp += fout[kp] * ps[kp];
     }
     const double kt = kap + j + ksc + gain + (rs - lp);
+    const double y = rsqrt(kt);            // sqrt(lambda): the edge mean free path is a product
     w.kinv[g] = kt;
-    w.lam[g] = 1.0 / kt;
+    w.slam[g] = y;
+    w.lam[g] = y * y;
+    w.g0[g] = gain;                        // reused by the first outer iteration's residual
+    w.l0[g] = lp;
     w.psi_n[g] = psi[g];
   }
 }
@@ -202,7 +246,8 @@ __global__ void k_nusphere(Prob p, Ws w) {
 }
 
 // alpha_{i+1/2} = A_{i+1/2} D_{i+1/2} / a_{i+1/2}^2 with D = lambda_e F / (3 (R_{i+1} - R_i)),
-// lambda_e = sqrt(lambda_i lambda_{i+1}), F = min(F_intrp, F_geom) at psi^n.
+// lambda_e = sqrt(lambda_i lambda_{i+1}) (the product of the stored square roots),
+// F = min(F_intrp, F_geom) at psi^n.
 __global__ void k_edges(Prob p, Ws w) {
   const int n = p.n;
   const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -221,16 +266,16 @@ __global__ void k_edges(Prob p, Ws w) {
   const double *re = p.r_edge + (size_t)ray * (p.n_r + 1);
   const int gq = (ray * NS + q) * n + k;
   const double psi_i = w.psi_n[t];
-  const double lam_i = w.lam[t];
-  double psi_r, lam_r;
+  const double sl_i = w.slam[t];
+  double psi_r, sl_r;
   if (i < last) {
     psi_r = w.psi_n[t + n];
-    lam_r = w.lam[t + n];
+    sl_r = w.slam[t + n];
   } else {
     psi_r = w.ghost[gq] * psi_i;
-    lam_r = lam_i;
+    sl_r = sl_i;
   }
-  const double lam_e = sqrt(lam_i * lam_r);
+  const double lam_e = sl_i * sl_r;
   const double dpsi = psi_r - psi_i;
   const double psi_e = 0.5 * (psi_i + psi_r);
   const double *z = w.zone + ((size_t)ray * p.n_r + i) * ZC_N;
@@ -242,16 +287,19 @@ __global__ void k_edges(Prob p, Ws w) {
   } else {
     const double x = lam_e * fabs(dpsi) * z[ZC_EI3DR];       // lambda |d psi/dR| / 3
     // F = min(F_intrp, F_geom) with F_intrp = psi_e/(psi_e + x) and, outside the
-    // neutrinosphere, F_geom = h psi_e / x, h = (1 + mu_nu)/2; F_geom is the smaller one
-    // exactly when h psi_e < (1 - h) x, so only the chosen quotient is evaluated.
+    // neutrinosphere, F_geom = h psi_e / x, h = (1 + mu_nu)/2, mu_nu = sqrt(1 - rho^2),
+    // rho = R_nu / R_{i+1/2}.  F_geom is the smaller one exactly when h psi_e < (1 - h) x, i.e.
+    // mu_nu (psi_e + x) < x - psi_e, tested without the square root as
+    // x > psi_e and (1 - rho^2)(psi_e + x)^2 < (x - psi_e)^2; only the chosen quotient is formed.
     const double rnu = w.rnu[gq];
     bool geom = false;
-    double h = 1.0;
-    if (re[i + 1] > rnu) {
-      h = 0.5 * (1.0 + sqrt(fmax(1.0 - rnu * rnu * z[ZC_EIR2], 0.0)));
-      geom = h * psi_e < (1.0 - h) * x;
+    double m2 = 1.0;
+    if (re[i + 1] > rnu && x > psi_e) {
+      m2 = fmax(1.0 - rnu * rnu * z[ZC_EIR2], 0.0);
+      const double sp = psi_e + x, df = x - psi_e;
+      geom = m2 * (sp * sp) < df * df;
     }
-    F = geom ? h * psi_e / x : psi_e / (psi_e + x);
+    F = geom ? 0.5 * (1.0 + sqrt(m2)) * psi_e / x : psi_e / (psi_e + x);
   }
   w.alpha[t] = lam_e * F * z[ZC_EI3DR] * z[ZC_EGEO];
 }
@@ -273,8 +321,12 @@ cudaError_t launch_setup(const Prob &p, const Ws &w, const double *psi, const do
   k_zone<<<nblk(nz, B), B, 0, s>>>(p, w, ye, T);
   {
     const int zpb = phi_zones_per_block(p.n);
-    const size_t sm = sizeof(double) * ((size_t)zpb * p.n + 2 * (size_t)zpb * p.n * p.n);
-    k_phi<<<nblk(nz, zpb), zpb * p.n, sm, s>>>(p, w, T, zpb);
+    const size_t sm = phi_smem_bytes(p.n);
+    if (sm > 48 * 1024) {
+      const cudaError_t e = cudaFuncSetAttribute(k_phi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      if (e != cudaSuccess) return e;
+    }
+    k_phi<<<nblk(nz, zpb), zpb * phi_threads_per_zone(p.n), sm, s>>>(p, w, T, zpb);
   }
   k_jlam<<<nblk(nzk, B), B, 0, s>>>(p, w, psi, T);
   k_nusphere<<<nblk((size_t)p.n_ray * NS * p.n, B), B, 0, s>>>(p, w);

@@ -30,7 +30,7 @@ Layout make_layout(int n_ray, int n_r, int n, int precision) {
   L.groups = take(sizeof(double) * 2 * MAX_NE);
   L.phout = take(sizeof(double) * Z * n * n);
   L.phin = take(sizeof(double) * Z * n * n);
-  L.phd = take(sizeof(double) * Z * n * n);
+  L.phd = take(precision == MGFLD_MIXED ? 0 : sizeof(double) * Z * n * n);
   L.rsum = take(sizeof(double) * Z * n);
   L.phin32 = take(precision == MGFLD_MIXED ? sizeof(float) * Z * n * n : 0);
   L.phd32 = take(precision == MGFLD_MIXED ? sizeof(float) * Z * n * n : 0);
@@ -67,6 +67,12 @@ Layout make_layout(int n_ray, int n_r, int n, int precision) {
   L.list_act = take(sizeof(int) * R);
   L.list_ref = take(sizeof(int) * R);
   L.counters = take(sizeof(int) * 8);
+  // Setup-only arrays share storage with buffers that are first written after the setup has
+  // consumed them: sqrt(lambda) (read by the limiter kernel) lives in rhs, and the NES sums at
+  // psi^n (read by the first residual, before the first solve or the final sources) in x and src.
+  L.slam = L.rhs;
+  L.g0 = L.src;
+  L.l0 = L.x;
   L.total = off;
   return L;
 }
@@ -78,11 +84,14 @@ Ws resolve(void *base, const Layout &L) {
   w.W = w.E + MAX_NE;
   w.phout = (double *)(b + L.phout);
   w.phin = (double *)(b + L.phin);
-  w.phd = (double *)(b + L.phd);
+  w.phd = L.mixed ? nullptr : (double *)(b + L.phd);
   w.rsum = (double *)(b + L.rsum);
   w.phin32 = L.mixed ? (float *)(b + L.phin32) : nullptr;
   w.phd32 = L.mixed ? (float *)(b + L.phd32) : nullptr;
   w.lam = (double *)(b + L.lam);
+  w.slam = (double *)(b + L.slam);
+  w.g0 = (double *)(b + L.g0);
+  w.l0 = (double *)(b + L.l0);
   w.alpha = (double *)(b + L.alpha);
   w.ghost = (double *)(b + L.ghost);
   w.rnu = (double *)(b + L.rnu);
@@ -531,7 +540,7 @@ mgfld_status mgfld_step(const mgfld_dims *dims, const mgfld_problem *prob, mgfld
     const int *jac = tl.chord ? w.refac : nullptr;
     prof.begin(MGFLD_PROF_ASSEMBLE);
     MGFLD_CUDA(launch_assemble(p, w, state->psi, w.diag, tl.mixed, w.lower, w.upper, w.rhs, w.list_act, n_act,
-                               jac, s));
+                               jac, s, nullptr, it == 0));
     prof.end(MGFLD_PROF_ASSEMBLE, 1);
     const int *flist = tl.chord ? w.list_ref : w.list_act;
     const int nf = tl.chord ? n_ref : n_act;
@@ -604,7 +613,7 @@ mgfld_status mgfld_assemble(const mgfld_dims *dims, const mgfld_problem *prob, c
   const Prob p = make_prob(dims, prob);
   MGFLD_CUDA(launch_setup(p, w, state->psi, state->ye, state->T, s));
   MGFLD_CUDA(launch_assemble(p, w, state->psi, sys->diag, 0, sys->lower, sys->upper, sys->rhs, nullptr,
-                             dims->n_ray, nullptr, s));
+                             dims->n_ray, nullptr, s, nullptr, 1));
   return MGFLD_OK;
 }
 
