@@ -44,11 +44,30 @@ __global__ void k_assemble(Prob p, Ws w, const double *__restrict__ psi, TD *__r
   if (first) {                 // psi = psi^n: the setup already formed these sums
     gain = w.g0[g];
     lp = w.l0[g];
+  } else if (src_out && w.phin32) {
+    // MIXED, converged state psi_m + dpsi (dpsi = w.x, the last correction of this ray): the
+    // sums of the ray's last residual (at psi_m, kept in g0/l0) plus phin.dpsi and phout.dpsi,
+    // taken in FP32.  |dpsi| is below the tolerance, so the FP32 rounding (relative 2^-24 of
+    // |phin| |dpsi|) stays far below the FP64 rounding of the sums themselves.
+    const float *fi = w.phin32 + (zi * n + k) * n, *fd = w.phd32 + (zi * n + k) * n;
+    const double *dx = w.x + (g - k);
+    float dg = 0.f, dl = 0.f;
+    for (int kp = 0; kp < n; ++kp) {
+      const float d = (float)dx[kp];
+      dg = fmaf(fi[kp], d, dg);
+      dl = fmaf(fi[kp] - fd[kp], d, dl);
+    }
+    gain = w.g0[g] + (double)dg;
+    lp = w.l0[g] + (double)dl;
   } else {
     for (int kp = 0; kp < n; ++kp) {
       const double pv = ps[kp];
       gain += fin[kp] * pv;
       lp += fout[kp] * pv;
+    }
+    if (w.phin32 && !src_out) {   // MIXED: keep this residual's sums for the final sources
+      w.g0[g] = gain;
+      w.l0[g] = lp;
     }
   }
   const double loss = w.rsum[zi * n + k] - lp;          // sum_k' phout (1 - psi_k')

@@ -68,11 +68,18 @@ Layout make_layout(int n_ray, int n_r, int n, int precision) {
   L.list_ref = take(sizeof(int) * R);
   L.counters = take(sizeof(int) * 8);
   // Setup-only arrays share storage with buffers that are first written after the setup has
-  // consumed them: sqrt(lambda) (read by the limiter kernel) lives in rhs, and the NES sums at
-  // psi^n (read by the first residual, before the first solve or the final sources) in x and src.
+  // consumed them: sqrt(lambda) (read by the limiter kernel) lives in rhs, and (FP64) the NES
+  // sums at psi^n (read by the first residual, before the first solve or the final sources) in
+  // x and src.
   L.slam = L.rhs;
-  L.g0 = L.src;
-  L.l0 = L.x;
+  if (precision == MGFLD_MIXED) {
+    // MIXED keeps the NES sums of each ray's latest residual for the final sources.
+    L.g0 = take(sizeof(double) * F);
+    L.l0 = take(sizeof(double) * F);
+  } else {
+    L.g0 = L.src;
+    L.l0 = L.x;
+  }
   L.total = off;
   return L;
 }
