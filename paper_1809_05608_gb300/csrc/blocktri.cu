@@ -325,22 +325,32 @@ k_factor_w32(int n, int n_r, int n_sys, const TIn *__restrict__ diag, const TC *
     bool used = !row;
     int my_step = 0;
     int piv[NP];
+    // Pivot-search key as in the FP64 factor: |a| bits with the row index in the 5 low bits, so
+    // one warp max names the pivot row.  The pivot and next-pivot-column entries of the pivot
+    // row are broadcast first and the next pivot column is updated first, so that the next
+    // search overlaps the broadcast and update of the other columns.
+    int key = used ? -1 : (int)(((unsigned)__float_as_int(fabsf(a[0])) & ~31u) | (unsigned)(31 - r));
 #pragma unroll
     for (int pstep = 0; pstep < NP; ++pstep) {
-      const int key = used ? -1 : __float_as_int(fabsf(a[pstep]));
-      const int kmax = __reduce_max_sync(full, key);
-      const int best = __ffs(__ballot_sync(full, key == kmax)) - 1;
+      const int best = 31 - (__reduce_max_sync(full, key) & 31);
       piv[pstep] = best;
-      float prow[NP];
-#pragma unroll
-      for (int c = 0; c < NP; ++c) prow[c] = __shfl_sync(full, a[c], best);
       const bool me = (r == best);
-      const float inv = __frcp_rn(prow[pstep]);
-      const float f = me ? (1.f - inv) : a[pstep] * inv;
+      if (me) {
+        used = true;
+        my_step = pstep;
+      }
+      const float pp = __shfl_sync(full, a[pstep], best);
+      const float inv = __frcp_rn(pp);
+      const float f = fmaf(me ? -1.f : a[pstep], inv, me ? 1.f : 0.f);
+      if (pstep + 1 < NP) {
+        const float pn = __shfl_sync(full, a[pstep + 1], best);
+        a[pstep + 1] = fmaf(-f, pn, a[pstep + 1]);
+        key = used ? -1 : (int)(((unsigned)__float_as_int(fabsf(a[pstep + 1])) & ~31u) | (unsigned)(31 - r));
+      }
 #pragma unroll
-      for (int c = 0; c < NP; ++c) a[c] = a[c] - f * prow[c];
+      for (int c = 0; c < NP; ++c)
+        if (c != pstep + 1 && c != pstep) a[c] = fmaf(-f, __shfl_sync(full, a[c], best), a[c]);
       a[pstep] = me ? inv : -f;
-      if (me) { used = true; my_step = pstep; }
     }
     __syncwarp();
     if (row) {
@@ -450,7 +460,9 @@ k_solve_w32(int n, int n_r, int n_sys, const float *__restrict__ dinv, const dou
 // flight and returns.
 template <int NP>
 struct SolveRing {
-  static constexpr int STAGES = NP <= 24 ? 6 : 4;
+  // Ring depth: up to 12 zones ahead, with the ring of both warps under 44 KB of static smem.
+  static constexpr int FIT = 45056 / (2 * NP * NP * 4);
+  static constexpr int STAGES = FIT < 12 ? FIT : 12;
   static constexpr int WPC = 2;                              // warps (systems) per CTA
   static constexpr int SLOT = NP * NP * 4;                   // bytes: one inverse block
 };
@@ -510,7 +522,33 @@ __global__ void k_sysmax(int n, int n_r, const double *__restrict__ rhs, const i
   }
 }
 
-template <int NP>
+// Row r of a zone's inverse times the zone vector held in shared memory (vb).  VEC: n == NP,
+// rows 16-byte aligned, float4 loads; otherwise scalar loads masked to the n real columns.
+template <int NP, bool VEC>
+__device__ inline float row_dot(const float *__restrict__ row, const float *__restrict__ vb, int n) {
+  float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+  if (VEC) {
+#pragma unroll
+    for (int c = 0; c < NP; c += 4) {
+      const float4 m = *reinterpret_cast<const float4 *>(row + c);
+      const float4 v = *reinterpret_cast<const float4 *>(vb + c);
+      a0 = fmaf(m.x, v.x, a0);
+      a1 = fmaf(m.y, v.y, a1);
+      a2 = fmaf(m.z, v.z, a2);
+      a3 = fmaf(m.w, v.w, a3);
+    }
+  } else {
+#pragma unroll
+    for (int c = 0; c < NP; ++c)
+      if (c < n) {
+        if (c % 2 == 0) a0 = fmaf(row[c], vb[c], a0);
+        else a1 = fmaf(row[c], vb[c], a1);
+      }
+  }
+  return (a0 + a1) + (a2 + a3);
+}
+
+template <int NP, bool VEC>
 __global__ void __launch_bounds__(SolveRing<NP>::WPC * 32)
 k_solve_tma(int n, int n_r, int n_sys, const float *__restrict__ dinv, const float *__restrict__ lower,
             const float *__restrict__ upper, const double *__restrict__ rhs, double *__restrict__ x,
@@ -519,6 +557,7 @@ k_solve_tma(int n, int n_r, int n_sys, const float *__restrict__ dinv, const flo
   constexpr int S = R::STAGES;
   constexpr int D = 8;                                      // depth of the per-lane vector queue
   __shared__ __align__(128) unsigned char ring[R::WPC][S][NP * NP * 4];
+  __shared__ __align__(16) float vbuf[R::WPC][NP];          // the zone vector, broadcast through smem
   __shared__ __align__(8) unsigned long long bar[R::WPC][S];
   const unsigned full = 0xffffffffu;
   const int wid = threadIdx.x >> 5, r = threadIdx.x & 31;
@@ -555,23 +594,29 @@ k_solve_tma(int n, int n_r, int n_sys, const float *__restrict__ dinv, const flo
     }
     return ok;
   };
-  // Per-lane queue of the zone vectors (own row), D zones ahead, all in FP32 (no FP64-pipe
-  // conversion on the recurrence: the rhs is rescaled by exponent arithmetic).
-  float qa[D], qb[D];
-  auto fetch = [&](int u, float &va, float &vb) {
-    va = 0.f;
+  // Per-lane queue of the zone vectors (own row), D uses ahead in a ring of registers indexed
+  // by compile-time slots (the zone loop is unrolled by D), all in FP32: the rhs is rescaled by
+  // exponent arithmetic, so no FP64-pipe work sits on the recurrence.
+  // The loaded values are queued as loaded (the rhs as FP64) and converted when consumed, so
+  // each load has D zone steps to arrive.
+  double qa[D];
+  float qb[D];
+  auto fetch = [&](int u, double &va, float &vb) {
+    va = 0.0;
     vb = 0.f;
     if (!real || u >= 2 * n_r) return;
     const int i = zone_of(u);
     const size_t zr = base + (size_t)i * n + r;
     if (u < n_r) {
-      va = d2f_exp2(rhs[zr], kexp);
+      va = rhs[zr];
       vb = i > 0 ? lower[zr] : 0.f;
     } else {
-      va = g32[zr];                                 // forward result written by this lane
+      va = (double)g32[zr];                         // forward result written by this lane
       vb = i < n_r - 1 ? upper[zr] : 0.f;
     }
   };
+  float *vb = vbuf[wid];
+  const int rr = real ? r : 0;                      // lanes without a row read row 0 (result unused)
 
   int issued = -1;
   if (r == 0)
@@ -580,29 +625,25 @@ k_solve_tma(int n, int n_r, int n_sys, const float *__restrict__ dinv, const flo
 #pragma unroll
   for (int d = 0; d < D; ++d) fetch(d < n_r ? d : 2 * n_r, qa[d], qb[d]);
   float g_prev = 0.f;
-  for (int i = 0; i < n_r; ++i) {
-    const float b = qa[0], l = qb[0];
+  for (int i0 = 0; i0 < n_r; i0 += D) {
 #pragma unroll
-    for (int d = 0; d < D - 1; ++d) { qa[d] = qa[d + 1]; qb[d] = qb[d + 1]; }
-    fetch(i + D < n_r ? i + D : 2 * n_r, qa[D - 1], qb[D - 1]);
-    if (!wait(i, issued)) return;
-    const float *row = (const float *)ring[wid][i % S] + (size_t)r * n;
-    const float v = real ? b - l * g_prev : 0.f;
-    float acc0 = 0.f, acc1 = 0.f;
-#pragma unroll
-    for (int c = 0; c < NP; c += 2) {
-      const float v0 = __shfl_sync(full, v, c), v1 = __shfl_sync(full, v, c + 1);
-      if (real && c < n) acc0 = fmaf(row[c], v0, acc0);
-      if (real && c + 1 < n) acc1 = fmaf(row[c + 1], v1, acc1);
-    }
-    const float g = acc0 + acc1;
-    if (real) g32[base + (size_t)i * n + r] = g;
-    g_prev = g;
-    __syncwarp();
-    const int nu = i + S - 1;
-    if (nu < n_r) {
-      if (r == 0) issue(nu);
-      issued = nu;
+    for (int d = 0; d < D; ++d) {
+      const int i = i0 + d;
+      if (i >= n_r) break;
+      const float b = d2f_exp2(qa[d], kexp), l = qb[d];
+      fetch(i + D < n_r ? i + D : 2 * n_r, qa[d], qb[d]);
+      if (!wait(i, issued)) return;
+      if (r < NP) vb[r] = real ? b - l * g_prev : 0.f;
+      __syncwarp();
+      const float g = row_dot<NP, VEC>((const float *)ring[wid][i % S] + (size_t)rr * n, vb, n);
+      if (real) g32[base + (size_t)i * n + r] = g;
+      g_prev = g;
+      __syncwarp();
+      const int nu = i + S - 1;
+      if (nu < n_r) {
+        if (r == 0) issue(nu);
+        issued = nu;
+      }
     }
   }
   if (r == 0)
@@ -611,30 +652,26 @@ k_solve_tma(int n, int n_r, int n_sys, const float *__restrict__ dinv, const flo
 #pragma unroll
   for (int d = 0; d < D; ++d) fetch(n_r + d, qa[d], qb[d]);
   float x_next = 0.f;
-  for (int k = 0; k < n_r; ++k) {
-    const int u = n_r + k, i = n_r - 1 - k;
-    const float gz = qa[0], uu = qb[0];
+  for (int k0 = 0; k0 < n_r; k0 += D) {
 #pragma unroll
-    for (int d = 0; d < D - 1; ++d) { qa[d] = qa[d + 1]; qb[d] = qb[d + 1]; }
-    fetch(u + D, qa[D - 1], qb[D - 1]);
-    if (!wait(u, issued)) return;
-    const float *row = (const float *)ring[wid][u % S] + (size_t)r * n;
-    const float v = real ? uu * x_next : 0.f;
-    float acc0 = 0.f, acc1 = 0.f;
-#pragma unroll
-    for (int c = 0; c < NP; c += 2) {
-      const float v0 = __shfl_sync(full, v, c), v1 = __shfl_sync(full, v, c + 1);
-      if (real && c < n) acc0 = fmaf(row[c], v0, acc0);
-      if (real && c + 1 < n) acc1 = fmaf(row[c + 1], v1, acc1);
-    }
-    const float xi = gz - (acc0 + acc1);
-    if (real) x[base + (size_t)i * n + r] = f2d_exp2(xi, -kexp);
-    x_next = xi;
-    __syncwarp();
-    const int nu = u + S - 1;
-    if (nu < 2 * n_r) {
-      if (r == 0) issue(nu);
-      issued = nu;
+    for (int d = 0; d < D; ++d) {
+      const int k = k0 + d;
+      if (k >= n_r) break;
+      const int u = n_r + k, i = n_r - 1 - k;
+      const float gz = (float)qa[d], uu = qb[d];
+      fetch(u + D, qa[d], qb[d]);
+      if (!wait(u, issued)) return;
+      if (r < NP) vb[r] = real ? uu * x_next : 0.f;
+      __syncwarp();
+      const float xi = gz - row_dot<NP, VEC>((const float *)ring[wid][u % S] + (size_t)rr * n, vb, n);
+      if (real) x[base + (size_t)i * n + r] = f2d_exp2(xi, -kexp);
+      x_next = xi;
+      __syncwarp();
+      const int nu = u + S - 1;
+      if (nu < 2 * n_r) {
+        if (r == 0) issue(nu);
+        issued = nu;
+      }
     }
   }
 }
@@ -647,8 +684,12 @@ cudaError_t launch_solve_tma(int n, int n_r, int n_sys, const void *dinv, const 
   MGFLD_DISPATCH_NP(n, {
     using R = SolveRing<NP>;
     const unsigned grid = (unsigned)((n_sys + R::WPC - 1) / R::WPC);
-    k_solve_tma<NP><<<grid, R::WPC * 32, 0, s>>>(n, n_r, n_sys, (const float *)dinv, lower32, upper32, rhs, x,
-                                                 g32, ray_list, sys_exp, err);
+    if (n == NP)
+      k_solve_tma<NP, true><<<grid, R::WPC * 32, 0, s>>>(n, n_r, n_sys, (const float *)dinv, lower32, upper32, rhs,
+                                                         x, g32, ray_list, sys_exp, err);
+    else
+      k_solve_tma<NP, false><<<grid, R::WPC * 32, 0, s>>>(n, n_r, n_sys, (const float *)dinv, lower32, upper32,
+                                                          rhs, x, g32, ray_list, sys_exp, err);
     return cudaGetLastError();
   })
 }
