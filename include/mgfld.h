@@ -18,7 +18,8 @@
  *     owned by the caller.  The library never allocates or frees memory: the
  *     caller provides every buffer, including the workspace.
  *   - Sizes: n_ray rays, n_r radial zones, n_e energy groups (1..32), n_s = 4
- *     species in the order nu_e, nubar_e, nu_mu/tau, nubar_mu/tau.
+ *     species in the order nu_e, nubar_e, nu_mu/tau, nubar_mu/tau, with
+ *     n_ray * n_s * n_r * n_e < 2^31 (EINVAL otherwise; split the rays).
  *   - Units: cm, s, g/cm^3, MeV (T is kT in MeV).
  *   - Every call is asynchronous on `stream` (a cudaStream_t passed as void*;
  *     NULL is the legacy default stream) except where stated.

@@ -18,16 +18,19 @@ __global__ void k_assemble(Prob p, Ws w, const double *__restrict__ psi, TD *__r
                            const int *__restrict__ list, int n_list, const int *__restrict__ jac_flag,
                            double *__restrict__ src_out, int first) {
   const int n = p.n;
-  const size_t per_ray = (size_t)NS * p.n_r * n;
-  const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= (size_t)n_list * per_ray) return;
-  const int ray = list ? list[t / per_ray] : (int)(t / per_ray);
+  // 32-bit index arithmetic (element counts are below 2^31, checked on the host).
+  const unsigned per_ray = (unsigned)(NS * p.n_r * n);
+  const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (unsigned)n_list * per_ray) return;
+  const unsigned rl = t / per_ray;
+  const int ray = list ? list[rl] : (int)rl;
   // Thread order (zone, species, group) inside a ray: the four species of a zone share the
   // zone's NES kernel rows through L1.
-  const size_t local = t % per_ray;
-  const int k = (int)(local % n);
-  const int q = (int)((local / n) % NS);
-  const int i = (int)(local / ((size_t)n * NS));
+  const unsigned local = t - rl * per_ray;
+  const unsigned kq = local / (unsigned)n;
+  const int k = (int)(local - kq * n);
+  const int q = (int)(kq % NS);
+  const int i = (int)(kq / NS);
   const size_t g = (((size_t)ray * NS + q) * p.n_r + i) * n + k;   // (ray, q, i, k) storage index
   const size_t zi = (size_t)ray * p.n_r + i;
   const int last = p.n_r - 1;

@@ -172,11 +172,12 @@ __global__ void k_phi(Prob p, Ws w, const double *__restrict__ T, int zpb) {
 // 1/lambda = kappa_a + j + kappa_s + sum_k' [phin psi_k' + phout (1 - psi_k')].
 __global__ void k_jlam(Prob p, Ws w, const double *__restrict__ psi, const double *__restrict__ T) {
   const int n = p.n;
-  const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= (size_t)p.n_ray * p.n_r * n) return;
-  const int k = (int)(t % n);
-  const size_t zi = t / n;
-  const int ray = (int)(zi / p.n_r), i = (int)(zi % p.n_r);
+  const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (unsigned)(p.n_ray * p.n_r * n)) return;
+  const unsigned zu = t / (unsigned)n;
+  const int k = (int)(t - zu * n);
+  const size_t zi = zu;
+  const int ray = (int)(zu / (unsigned)p.n_r), i = (int)(zu - (unsigned)ray * p.n_r);
   const double *z = w.zone + zi * ZC_N;
   const double inv_a = z[ZC_INV_A];
   const double Ti = T[zi];
@@ -250,14 +251,15 @@ __global__ void k_nusphere(Prob p, Ws w) {
 // F = min(F_intrp, F_geom) at psi^n.
 __global__ void k_edges(Prob p, Ws w) {
   const int n = p.n;
-  const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= (size_t)p.n_ray * NS * p.n_r * n) return;
-  const int k = (int)(t % n);
-  size_t u = t / n;
-  const int i = (int)(u % p.n_r);
-  u /= p.n_r;
-  const int q = (int)(u % NS);
-  const int ray = (int)(u / NS);
+  const unsigned tu = blockIdx.x * blockDim.x + threadIdx.x;
+  if (tu >= (unsigned)(p.n_ray * NS * p.n_r * n)) return;
+  const size_t t = tu;
+  const unsigned u1 = tu / (unsigned)n;
+  const int k = (int)(tu - u1 * n);
+  const unsigned u2 = u1 / (unsigned)p.n_r;
+  const int i = (int)(u1 - u2 * p.n_r);
+  const int q = (int)(u2 % NS);
+  const int ray = (int)(u2 / NS);
   const int last = p.n_r - 1;
   if (i == last && p.bc == MGFLD_BC_REFLECT) {
     w.alpha[t] = 0.0;

@@ -170,18 +170,52 @@ __device__ inline void report_violation(Ws &w, int ray, float viol) {
   }
 }
 
+// The same for a whole block (every thread of the block calls it): one atomic per block when
+// the block lies in one ray, per warp otherwise.
+__device__ inline void report_violation_block(Ws &w, int ray, float viol) {
+  __shared__ float wmax[32];
+  __shared__ int wray[32];
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  const int ray0 = __shfl_sync(full, ray, 0);
+  const bool one = __all_sync(full, ray == ray0);
+  if (one) {
+    for (int off = 16; off > 0; off >>= 1) viol = fmaxf(viol, __shfl_down_sync(full, viol, off));
+  } else {
+    atomicMax(&w.viol[ray], (unsigned long long)__float_as_uint(viol));
+  }
+  if (lane == 0) {
+    wmax[wid] = one ? viol : 0.f;
+    wray[wid] = one ? ray : -1;
+  }
+  __syncthreads();
+  if (wid == 0) {
+    const float v = lane < nw ? wmax[lane] : 0.f;
+    const int rr = lane < nw ? wray[lane] : wray[0];
+    const bool same = __all_sync(full, rr == wray[0]) && wray[0] >= 0;
+    if (same) {
+      float m = v;
+      for (int off = 16; off > 0; off >>= 1) m = fmaxf(m, __shfl_down_sync(full, m, off));
+      if (lane == 0) atomicMax(&w.viol[rr], (unsigned long long)__float_as_uint(m));
+    } else if (lane < nw && rr >= 0) {
+      atomicMax(&w.viol[rr], (unsigned long long)__float_as_uint(v));
+    }
+  }
+}
+
 // psi += dpsi (Eq. a62aa) and the per-element convergence ratio |d psi| / (tol max(|psi|, tolmin))
 // of Eq. a62ab, one thread per (ray, q, i, k) of the active rays.  All 32 lanes of a warp reach
 // the reduction (out-of-range lanes carry ratio 0).
 __global__ void k_update_psi(Prob p, Ws w, Tol tl, double *__restrict__ psi, const int *__restrict__ list,
                              int n_list) {
-  const size_t per_ray = (size_t)NS * p.n_r * p.n;
-  const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const bool in = t < (size_t)n_list * per_ray;
-  const int ray = in ? list[t / per_ray] : list[0];
+  const unsigned per_ray = (unsigned)(NS * p.n_r * p.n);
+  const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
+  const bool in = t < (unsigned)n_list * per_ray;
+  const unsigned rl = t / per_ray;
+  const int ray = in ? list[rl] : list[0];
   float viol = 0.f;
   if (in) {
-    const size_t g = (size_t)ray * per_ray + t % per_ray;
+    const size_t g = (size_t)ray * per_ray + (t - rl * per_ray);
     const double d = w.x[g];
     const double v = psi[g] + d;
     psi[g] = v;
@@ -191,7 +225,7 @@ __global__ void k_update_psi(Prob p, Ws w, Tol tl, double *__restrict__ psi, con
       viol = INFINITY;
     }
   }
-  report_violation(w, ray, viol);
+  report_violation_block(w, ray, viol);
 }
 
 // One Newton step of the zone-local Ye equation (Eq. a62a) at the updated psi, with T held at
@@ -201,12 +235,13 @@ __global__ void k_update_psi(Prob p, Ws w, Tol tl, double *__restrict__ psi, con
 __global__ void k_update_ye(Prob p, Ws w, Tol tl, const double *__restrict__ psi, double *__restrict__ ye,
                             const double *__restrict__ T, const int *__restrict__ list, int n_list) {
   const int n = p.n;
-  const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const bool in = t < (size_t)n_list * p.n_r;
-  const int ray = in ? list[t / p.n_r] : list[0];
+  const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
+  const bool in = t < (unsigned)(n_list * p.n_r);
+  const unsigned rl = t / (unsigned)p.n_r;
+  const int ray = in ? list[rl] : list[0];
   float viol = 0.f;
   if (in) {
-    const int i = (int)(t % p.n_r);
+    const int i = (int)(t - rl * p.n_r);
     const size_t zi = (size_t)ray * p.n_r + i;
     const double *z = w.zone + zi * ZC_N;
     const double inv_a = z[ZC_INV_A];
@@ -451,7 +486,9 @@ static Eos make_eos(const mgfld_eos_params &e) {
 }
 
 bool dims_ok(const mgfld_dims *d) {
-  return d && d->n_ray >= 1 && d->n_r >= 1 && d->n_e >= 1 && d->n_e <= MAX_NE && d->n_s == NS;
+  if (!d || d->n_ray < 1 || d->n_r < 1 || d->n_e < 1 || d->n_e > MAX_NE || d->n_s != NS) return false;
+  // Kernels decompose element indices in 32-bit arithmetic.
+  return (long long)d->n_ray * NS * d->n_r * d->n_e < (1ll << 31);
 }
 
 bool prob_ok(const mgfld_problem *p) {
