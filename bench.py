@@ -261,36 +261,57 @@ def roofline_for(res, inp, precision, clk):
 def e2e_run(M, torch, inp, precision, steps):
     """Same metric through the public API from pinned HOST buffers: every step uploads
     that step's inputs (matter, opacities, NES scale, grid, state), runs mgfld_step and
-    reads the new state back."""
+    reads the new state back.  The problem arrays of step s+1 are uploaded on a second
+    stream into a second device copy while step s runs (double buffering); the state goes
+    host -> device -> host on the compute stream, in order."""
     st = M.Stepper(inp, precision, tol=TOL, max_iter=60)
     prob = inp['problem']
-    host = {}
-    for k in ('r_edge', 'rho', 'kappa_abs', 'kappa_scat', 'nes_coef'):
-        host[k] = torch.from_numpy(np.ascontiguousarray(prob[k], dtype=np.float64)).pin_memory()
+    names = ('r_edge', 'rho', 'kappa_abs', 'kappa_scat', 'nes_coef')
+    host = {k: torch.from_numpy(np.ascontiguousarray(prob[k], dtype=np.float64)).pin_memory() for k in names}
     hs = [torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).pin_memory()
           for a in (inp['psi0'], inp['ye0'], inp['T0'])]
     dev = [torch.empty_like(h, device='cuda') for h in hs]
     out = [torch.empty_like(h).pin_memory() for h in hs]
+    bufs = [st.prob, M.DeviceProblem(prob)]
     h2d = sum(v.numel() * 8 for v in host.values()) + sum(h.numel() * 8 for h in hs)
     d2h = sum(h.numel() * 8 for h in hs)
     stream = torch.cuda.current_stream()
+    copy = torch.cuda.Stream()
+    ready = [torch.cuda.Event(), torch.cuda.Event()]     # buffer b uploaded
+    free = [torch.cuda.Event(), torch.cuda.Event()]      # buffer b no longer read by a step
+
+    def upload(b):
+        with torch.cuda.stream(copy):
+            for k in names:
+                bufs[b].t[k].copy_(host[k], non_blocking=True)
+            ready[b].record(copy)
+
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
+    copy.wait_event(e0)
+    upload(0)
     for s in range(steps):
-        for k, v in host.items():
-            st.prob.t[k].copy_(v, non_blocking=True)
+        b = s % 2
+        if s + 1 < steps:
+            if s >= 1:
+                copy.wait_event(free[1 - b])
+            upload(1 - b)
+        stream.wait_event(ready[b])
+        st.prob = bufs[b]
         src = hs if s == 0 else out
         for d, h in zip(dev, src):
             d.copy_(h, non_blocking=True)
         rc = st.step(*dev)
         assert rc == M.MGFLD_OK, M.status_str(rc)
+        free[b].record(stream)
         for o, d in zip(out, dev):
             o.copy_(d, non_blocking=True)
     e1.record(stream)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
+    st.prob = bufs[0]
     return dict(ms=ms, h2d=h2d, d2h=d2h)
 
 

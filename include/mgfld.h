@@ -166,22 +166,29 @@ mgfld_status mgfld_assemble(const mgfld_dims *dims, const mgfld_problem *prob, c
 size_t mgfld_factor_bytes(const mgfld_dims *dims, int precision);
 
 /*
- * mgfld_factor -- block-Thomas forward elimination of `sys` (partial pivoting
- * inside each block): writes D'_i^{-1} for every (ray, species, zone) into
- * `factor` ([n_ray][n_s][n_r][n_e][n_e], FP64 or FP32 by `precision`), where
- * D'_0 = diag_0 and D'_i = diag_i - lower_i * D'_{i-1}^{-1} * upper_{i-1}.
- * sys->rhs is not used.  A singular pivot gives non-finite factors (detected
- * later by mgfld_solve's caller, not here).
+ * mgfld_factor -- two-sided ("twisted") block-Thomas elimination of `sys` (partial
+ * pivoting inside each block), run from both ends towards the middle zone
+ * m = n_r / 2 so that the sequential chain along the zones is half as long: writes,
+ * for every (ray, species, zone), into `factor` ([n_ray][n_s][n_r][n_e][n_e], FP64 or
+ * FP32 by `precision`):
+ *   i < m:  D'_i^{-1},  D'_0 = diag_0,  D'_i = diag_i - lower_i D'_{i-1}^{-1} upper_{i-1};
+ *   i > m:  D''_i^{-1}, D''_{n_r-1} = diag_{n_r-1}, D''_i = diag_i - upper_i D''_{i+1}^{-1} lower_{i+1};
+ *   i = m:  (diag_m - lower_m D'_{m-1}^{-1} upper_{m-1} - upper_m D''_{m+1}^{-1} lower_{m+1})^{-1}
+ * (lower_i, upper_i act as diagonal matrices).  sys->rhs is not used.  A singular
+ * pivot gives non-finite factors (detected later by mgfld_solve's caller, not here).
  */
 mgfld_status mgfld_factor(const mgfld_dims *dims, const mgfld_system *sys, int precision,
                           void *factor, void *stream);
 
 /*
- * mgfld_solve -- solve the factored system for one right-hand side:
- * forward g_i = D'^{-1}_i (rhs_i - lower_i * g_{i-1}), back
- * x_i = g_i - D'^{-1}_i (upper_i * x_{i+1}).  rhs, x: [n_ray][n_s][n_r][n_e] FP64
- * (x may alias rhs).  With MIXED precision the substitution runs in FP32 on a
- * per-system power-of-two scaling of rhs.  sys->diag and sys->rhs are not used.
+ * mgfld_solve -- solve the factored system (mgfld_factor's layout) for one right-hand
+ * side: g_i = D'^{-1}_i (rhs_i - lower_i g_{i-1}) for i < m and
+ * g_i = D''^{-1}_i (rhs_i - upper_i g_{i+1}) for i > m; x_m from the middle inverse
+ * applied to rhs_m - lower_m g_{m-1} - upper_m g_{m+1}; then outward
+ * x_i = g_i - D'^{-1}_i (upper_i x_{i+1}) (i < m), x_i = g_i - D''^{-1}_i (lower_i x_{i-1})
+ * (i > m).  rhs, x: [n_ray][n_s][n_r][n_e] FP64 (x may alias rhs).  With MIXED precision
+ * the substitution runs in FP32 on a per-system power-of-two scaling of rhs.
+ * sys->diag and sys->rhs are not used.
  */
 mgfld_status mgfld_solve(const mgfld_dims *dims, const mgfld_system *sys, int precision,
                          const void *factor, const double *rhs, double *x, void *stream);

@@ -1,13 +1,20 @@
 // Batched block-Thomas elimination for the per-(ray, species) systems of Eq. a62ae.
 //
 // Structure exploited: the off-diagonal blocks are diagonal (the flux coefficient is
-// frozen), so the Schur update of zone i is a diagonal scaling of the previous
-// inverse, D'_i = D_i - diag(l_i) D'^{-1}_{i-1} diag(u_{i-1}): no dense block product,
+// frozen), so the Schur update of a zone is a diagonal scaling of its neighbour's
+// inverse, e.g. D'_i = D_i - diag(l_i) D'^{-1}_{i-1} diag(u_{i-1}): no dense block product,
 // hence no tensor-core contraction on this path.  Each dense block is inverted in
 // place by Gauss-Jordan elimination with partial pivoting.
 //
-// Thread mapping: one thread per block row; SPC systems (rays x species) share a CTA so
-// that SPC * NP is a multiple of 32 and every lane of every FMA instruction does work.
+// Two-sided ("twisted") elimination: every system is eliminated top-down over zones
+// 0..m-1 and bottom-up over zones n_r-1..m+1 at the same time, the two halves meeting at
+// the middle zone m = n_r/2, whose block receives both Schur terms.  The substitution runs
+// the same way (inward to the middle, then outward).  The sequential chain along the zones,
+// which bounds these latency-limited kernels, is half as long, and there are twice as many
+// independent instruction streams; the arithmetic is unchanged.
+//
+// Thread mapping (FP64): one thread per block row, the two halves of SPC/2 systems per CTA
+// so that SPC * NP is a multiple of 32 and every lane of every FMA instruction does work.
 // Rows and columns beyond the real group count n (<= NP) are padded with the identity.
 // The pivot search, pivot-row broadcast and the natural-order inverse go through
 // shared memory; the inverse of each zone is streamed to the caller's factor buffer.
@@ -18,7 +25,9 @@ namespace mgfld {
 template <int NP>
 struct Pack {
   static constexpr int gcd(int a, int b) { return b == 0 ? a : gcd(b, a % b); }
-  static constexpr int SPC = 32 / gcd(NP, 32);   // systems per CTA
+  // Half-systems per CTA: a multiple of 32 threads and even (both halves of a system share a CTA).
+  static constexpr int SPC0 = 32 / gcd(NP, 32);
+  static constexpr int SPC = SPC0 % 2 == 0 ? SPC0 : 2 * SPC0;
   static constexpr int THREADS = SPC * NP;
 };
 
@@ -92,39 +101,53 @@ k_factor(int n, int n_r, int n_sys, const TIn *__restrict__ diag, const double *
   __shared__ double tile[SPC][NP][NP + 1];           // natural-order inverse of the previous zone
   __shared__ __align__(16) double prow[SPC][NP];     // pivot row of the current step
   __shared__ __align__(16) int cand[SPC][NP];        // pivot-search keys
-  __shared__ double ushr[SPC][NP];                   // upper_{i-1}, the column scaling of the Schur update
+  __shared__ double ushr[SPC][NP];                   // coupling to the next zone: the column scaling of its Schur term
   __shared__ int pivrow[SPC][NP];                    // row chosen at each step
   __shared__ double pinv[SPC];                       // 1 / pivot of the current step
 
   const int s = threadIdx.x / NP, r = threadIdx.x % NP;
-  const long jsys = (long)blockIdx.x * SPC + s;
+  const int half = s & 1;                            // 0: zones 0..m top-down, 1: zones n_r-1..m+1 bottom-up
+  const long jsys = (long)blockIdx.x * (SPC / 2) + (s >> 1);
   const bool valid = jsys < n_sys;
   const long sys = valid ? system_of(jsys, ray_list) : 0;
-  const bool real = valid && r < n;
+  const int m = n_r / 2;
+  const int len = half == 0 ? m + 1 : n_r - 1 - m;   // zones of this half; all threads step m + 1 times
 
   // Rows of the next zone are fetched one zone ahead (registers) to hide memory latency.
   double nxt[NP];
   double nl = 0.0;
-  auto load_row = [&](int i) {
-    const size_t zr = ((size_t)sys * n_r + i) * n + r;
+  auto load_row = [&](int j) {
+    const bool act = valid && j < len && r < n;
+    const int z = half == 0 ? j : n_r - 1 - j;
+    const size_t zr = ((size_t)sys * n_r + (act ? z : 0)) * n + r;
 #pragma unroll
     for (int c = 0; c < NP; ++c) {
-      if (real && c < n) nxt[c] = (double)diag[zr * n + c];
+      if (act && c < n) nxt[c] = (double)diag[zr * n + c];
       else nxt[c] = (c == r) ? 1.0 : 0.0;
     }
-    nl = (real && i > 0) ? lower[zr] : 0.0;
+    nl = (act && j > 0) ? (half == 0 ? lower[zr] : upper[zr]) : 0.0;
   };
   load_row(0);
-  for (int i = 0; i < n_r; ++i) {
-    const size_t zrow = ((size_t)sys * n_r + i) * n + r;   // (sys, i, r)
+  for (int j = 0; j <= m; ++j) {
+    const bool active = j < len;                     // inactive (bottom half, j >= len): dummy identity
+    const int i = half == 0 ? j : n_r - 1 - j;
+    const bool real = valid && active && r < n;
+    const size_t zrow = ((size_t)sys * n_r + (real ? i : 0)) * n + r;   // (sys, i, r)
     double a[NP];
 #pragma unroll
     for (int c = 0; c < NP; ++c) a[c] = nxt[c];
     const double lr = nl;
-    if (i + 1 < n_r) load_row(i + 1);
-    if (i > 0) {
+    if (j + 1 <= m) load_row(j + 1);
+    if (j > 0 && active) {
 #pragma unroll
       for (int c = 0; c < NP; ++c) a[c] = fma(-(lr * tile[s][r][c]), ushr[s][c], a[c]);
+    }
+    if (half == 0 && j == m && n_r - 1 > m) {
+      // Middle zone: also subtract the bottom-up half's term diag(u_m) D''^{-1}_{m+1} diag(l_{m+1})
+      // (that half finished at step len - 1 < m; its tile and coupling are kept).
+      const double um = real ? upper[zrow] : 0.0;
+#pragma unroll
+      for (int c = 0; c < NP; ++c) a[c] = fma(-(um * tile[s + 1][r][c]), ushr[s + 1][c], a[c]);
     }
 
     // Gauss-Jordan inversion in place with partial pivoting (implicit row exchanges).
@@ -171,9 +194,11 @@ k_factor(int n, int n_r, int n_sys, const TIn *__restrict__ diag, const double *
     }
     // Row r now holds row my_step of the inverse, with column c belonging to input row pivrow[c].
     __syncthreads();
+    if (active) {
 #pragma unroll
-    for (int c = 0; c < NP; ++c) tile[s][my_step][pivrow[s][c]] = a[c];
-    ushr[s][r] = real ? upper[zrow] : 0.0;
+      for (int c = 0; c < NP; ++c) tile[s][my_step][pivrow[s][c]] = a[c];
+      ushr[s][r] = real ? (half == 0 ? upper[zrow] : lower[zrow]) : 0.0;
+    }
     __syncthreads();
     if (real) {
       double *out = dinv + zrow * n;
@@ -184,95 +209,91 @@ k_factor(int n, int n_r, int n_sys, const TIn *__restrict__ diag, const double *
   }
 }
 
-// Forward and back substitution with the stored inverses (one thread per block row).
-// MIXED (T = float): the right-hand side of each system is scaled by a power of two so
-// that its largest entry is O(1) before rounding to FP32, and unscaled on output.
-template <int NP, typename T>
+// FP64 forward and back substitution with the twisted factors (one thread per block row, the
+// two halves of each system in the same CTA, stepping together): forward g_i = Dinv_i (r_i -
+// l_i g_{i-1}) for i < m and h_i = Dinv_i (r_i - u_i h_{i+1}) for i > m, the middle
+// x_m = Dinv_m (r_m - l_m g_{m-1} - u_m h_{m+1}), then back outward from m.  The forward results
+// are kept in x (which may alias rhs: each zone's rhs is read before its x is written).
+template <int NP>
 __global__ void __launch_bounds__(Pack<NP>::THREADS)
-k_solve(int n, int n_r, int n_sys, const T *__restrict__ dinv, const double *__restrict__ lower,
-        const double *__restrict__ upper, const double *__restrict__ rhs, double *__restrict__ x,
-        const int *__restrict__ ray_list) {
+k_solve(int n, int n_r, int n_sys, const double *__restrict__ dinv, const double *__restrict__ lower,
+        const double *__restrict__ upper, const double *rhs, double *x, const int *__restrict__ ray_list) {
   constexpr int SPC = Pack<NP>::SPC;
-  __shared__ T v[SPC][NP];
-  __shared__ double red[SPC][NP];
+  __shared__ double v[SPC][NP];
+  __shared__ double mid[SPC / 2][NP];               // h_{m+1}, then x_m
   const int s = threadIdx.x / NP, r = threadIdx.x % NP;
-  const long jsys = (long)blockIdx.x * SPC + s;
+  const int half = s & 1, sl = s >> 1;
+  const long jsys = (long)blockIdx.x * (SPC / 2) + sl;
   const bool valid = jsys < n_sys;
   const long sys = valid ? system_of(jsys, ray_list) : 0;
-  const bool real = valid && r < n;
+  const bool realr = valid && r < n;
   const size_t base = (size_t)sys * n_r * n;
+  const int m = n_r / 2, B = n_r - 1 - m;
+  const int F = half == 0 ? m : B;
 
-  double scale = 1.0;
-  if (sizeof(T) == 4) {
-    double m = 0.0;
-    if (real)
-      for (int i = 0; i < n_r; ++i) m = fmax(m, fabs(rhs[base + (size_t)i * n + r]));
-    red[s][r] = m;
-    __syncthreads();
-    m = 0.0;
-    for (int c = 0; c < NP; ++c) m = fmax(m, red[s][c]);
-    if (m > 0.0 && isfinite(m)) {
-      int e;
-      frexp(m, &e);
-      scale = ldexp(1.0, -e);
+  auto rowdot = [&](int z, bool real) {
+    const double *src = dinv + (base + (size_t)z * n + r) * n;
+    double acc0 = 0.0, acc1 = 0.0;
+    if (real) {
+#pragma unroll
+      for (int c = 0; c < NP; c += 2) {
+        if (c < n) acc0 = fma(src[c], v[s][c], acc0);
+        if (c + 1 < n) acc1 = fma(src[c + 1], v[s][c + 1], acc1);
+      }
     }
-  }
-
-  // The next zone's inverse row, rhs and coupling are loaded one zone ahead so that their
-  // memory latency overlaps the current zone's arithmetic (the recurrence is sequential).
-  T row[NP], nrow[NP];
-#pragma unroll
-  for (int c = 0; c < NP; ++c) nrow[c] = T(0);
-  double nb = 0.0, nc = 0.0;
-  auto load_fwd = [&](int i) {
-    const size_t zr = base + (size_t)i * n + r;
-    const T *src = dinv + zr * n;
-#pragma unroll
-    for (int c = 0; c < NP; ++c) nrow[c] = (c < n) ? src[c] : T(0);
-    nb = rhs[zr];
-    nc = i > 0 ? lower[zr] : 0.0;
+    return acc0 + acc1;
   };
-  if (real) load_fwd(0);
-  T g_prev = T(0);
-  for (int i = 0; i < n_r; ++i) {
-    const size_t zr = base + (size_t)i * n + r;
-#pragma unroll
-    for (int c = 0; c < NP; ++c) row[c] = nrow[c];
-    const double b = nb, l = nc;
-    if (real && i + 1 < n_r) load_fwd(i + 1);
-    v[s][r] = real ? to_t<T>(b * scale) - to_t<T>(l) * g_prev : T(0);
+  // Forward (all threads step m times for the barriers; a half past its F steps idles).
+  double prev = 0.0;
+  for (int j = 0; j < m; ++j) {
+    const bool act = j < F;
+    const bool real = realr && act;
+    const int z = half == 0 ? j : n_r - 1 - j;
+    const size_t zr = base + (size_t)(real ? z : 0) * n + r;
+    const double c = (real && j > 0) ? (half == 0 ? lower[zr] : upper[zr]) : 0.0;
+    const double b = real ? rhs[zr] : 0.0;
+    v[s][r] = real ? b - c * prev : 0.0;
     __syncthreads();
-    T acc = T(0);
-#pragma unroll
-    for (int c = 0; c < NP; ++c) acc = acc + row[c] * v[s][c];
-    if (real) x[zr] = (double)acc;
-    g_prev = acc;
+    const double g = rowdot(z, real);
+    if (real) {
+      x[zr] = g;
+      prev = g;
+    }
     __syncthreads();
   }
-  auto load_bwd = [&](int i) {
-    const size_t zr = base + (size_t)i * n + r;
-    const T *src = dinv + zr * n;
-#pragma unroll
-    for (int c = 0; c < NP; ++c) nrow[c] = (c < n) ? src[c] : T(0);
-    nb = x[zr];
-    nc = i < n_r - 1 ? upper[zr] : 0.0;
-  };
-  if (real) load_bwd(n_r - 1);
-  T x_next = T(0);
-  for (int i = n_r - 1; i >= 0; --i) {
-    const size_t zr = base + (size_t)i * n + r;
-#pragma unroll
-    for (int c = 0; c < NP; ++c) row[c] = nrow[c];
-    const double g = nb, u = nc;
-    if (real && i > 0) load_bwd(i - 1);
-    v[s][r] = real ? to_t<T>(u) * x_next : T(0);
+  if (half == 1) mid[sl][r] = B > 0 ? prev : 0.0;
+  __syncthreads();
+  if (half == 0) {
+    const size_t zr = base + (size_t)m * n + r;
+    const double l = (realr && m > 0) ? lower[zr] : 0.0;
+    const double u = (realr && m < n_r - 1) ? upper[zr] : 0.0;
+    v[s][r] = realr ? rhs[zr] - l * prev - u * mid[sl][r] : 0.0;
+  }
+  __syncthreads();
+  if (half == 0) {
+    const double xm = rowdot(m, realr);
+    if (realr) x[base + (size_t)m * n + r] = xm;
+    prev = xm;
+  }
+  __syncthreads();
+  if (half == 0) mid[sl][r] = prev;
+  __syncthreads();
+  if (half == 1) prev = mid[sl][r];
+  // Backward: top x_i = g_i - Dinv_i (u_i x_{i+1}), i = m-1..0; bottom x_i = h_i - Dinv_i (l_i x_{i-1}).
+  for (int j = 0; j < m; ++j) {
+    const bool act = j < F;
+    const bool real = realr && act;
+    const int z = half == 0 ? m - 1 - j : m + 1 + j;
+    const size_t zr = base + (size_t)(real ? z : 0) * n + r;
+    const double c = real ? (half == 0 ? upper[zr] : lower[zr]) : 0.0;
+    v[s][r] = real ? c * prev : 0.0;
     __syncthreads();
-    T acc = T(0);
-#pragma unroll
-    for (int c = 0; c < NP; ++c) acc = acc + row[c] * v[s][c];
-    const T xi = to_t<T>(g) - acc;
-    if (real) x[zr] = (double)xi / scale;
-    x_next = xi;
+    const double acc = rowdot(z, real);
+    if (real) {
+      const double xi = x[zr] - acc;
+      x[zr] = xi;
+      prev = xi;
+    }
     __syncthreads();
   }
 }
@@ -294,33 +315,50 @@ k_factor_w32(int n, int n_r, int n_sys, const TIn *__restrict__ diag, const TC *
   __shared__ float ushr[kWarpsPerCta][NP];
   const unsigned full = 0xffffffffu;
   const int wid = threadIdx.x >> 5, r = threadIdx.x & 31;
-  const long jsys = (long)blockIdx.x * kWarpsPerCta + wid;
-  if (jsys >= n_sys) return;                        // whole warp leaves; no CTA barrier below
+  const int half = wid & 1;                          // 0: zones 0..m top-down, 1: zones n_r-1..m+1 bottom-up
+  const long jsys = (long)blockIdx.x * (kWarpsPerCta / 2) + (wid >> 1);
+  if (jsys >= n_sys) return;                        // both warps of the system leave; no barrier below
   const long sys = system_of(jsys, ray_list);
   const bool real = r < n;
   const bool row = r < NP;
+  const int m = n_r / 2;
+  const int len = half == 0 ? m + 1 : n_r - 1 - m;
+  auto zone = [&](int j) { return half == 0 ? j : n_r - 1 - j; };
   float nxt[NP];
   float nl = 0.f;
-  auto load_row = [&](int i) {
-    const size_t zr = ((size_t)sys * n_r + i) * n + r;
+  auto load_row = [&](int j) {
+    const int z = zone(j);
+    const size_t zr = ((size_t)sys * n_r + z) * n + r;
 #pragma unroll
     for (int c = 0; c < NP; ++c) {
       if (real && c < n) nxt[c] = (float)diag[zr * n + c];
       else nxt[c] = (c == r) ? 1.f : 0.f;
     }
-    nl = (real && i > 0) ? (float)lower[zr] : 0.f;
+    // coupling to the previous zone of this half's sequence (row scaling of its Schur term)
+    nl = (real && j > 0) ? (float)(half == 0 ? lower[zr] : upper[zr]) : 0.f;
   };
-  load_row(0);
-  for (int i = 0; i < n_r; ++i) {
-    const size_t zrow = ((size_t)sys * n_r + i) * n + r;
+  if (len > 0) load_row(0);
+  for (int j = 0; j < len; ++j) {
+    const int z = zone(j);
+    const size_t zrow = ((size_t)sys * n_r + z) * n + r;
     float a[NP];
 #pragma unroll
     for (int c = 0; c < NP; ++c) a[c] = nxt[c];
     const float lr = nl;
-    if (i + 1 < n_r) load_row(i + 1);
-    if (i > 0 && row) {
+    if (j + 1 < len) load_row(j + 1);
+    if (j > 0 && row) {
 #pragma unroll
       for (int c = 0; c < NP; ++c) a[c] = a[c] - (lr * tile[wid][r][c]) * ushr[wid][c];
+    }
+    if (half == 0 && j == m) {
+      // Middle zone: wait for the bottom-up half of this system, then subtract its Schur term
+      // diag(u_m) D''^{-1}_{m+1} diag(l_{m+1}) as well.
+      asm volatile("bar.sync %0, 64;" ::"r"(1 + (wid >> 1)) : "memory");
+      if (n_r - 1 > m && row) {
+        const float um = real ? (float)upper[zrow] : 0.f;
+#pragma unroll
+        for (int c = 0; c < NP; ++c) a[c] = a[c] - (um * tile[wid ^ 1][r][c]) * ushr[wid ^ 1][c];
+      }
     }
     bool used = !row;
     int my_step = 0;
@@ -356,7 +394,8 @@ k_factor_w32(int n, int n_r, int n_sys, const TIn *__restrict__ diag, const TC *
     if (row) {
 #pragma unroll
       for (int c = 0; c < NP; ++c) tile[wid][my_step][piv[c]] = a[c];
-      ushr[wid][r] = real ? (float)upper[zrow] : 0.f;
+      // coupling of this zone to the next zone of the sequence (column scaling of its Schur term)
+      ushr[wid][r] = real ? (float)(half == 0 ? upper[zrow] : lower[zrow]) : 0.f;
     }
     __syncwarp();
     if (real) {
@@ -366,79 +405,88 @@ k_factor_w32(int n, int n_r, int n_sys, const TIn *__restrict__ diag, const TC *
         if (c < n) out[c] = tile[wid][r][c];
     }
   }
+  if (half == 1) asm volatile("bar.sync %0, 64;" ::"r"(1 + (wid >> 1)) : "memory");
 }
 
+// Forward/back substitution with the twisted FP32 factors, two warps per system (the top-down
+// and bottom-up halves), lane r owning block row r; the halves meet at the middle zone m through
+// shared memory and a two-warp named barrier.
 template <int NP>
 __global__ void __launch_bounds__(kWarpsPerCta * 32)
 k_solve_w32(int n, int n_r, int n_sys, const float *__restrict__ dinv, const double *__restrict__ lower,
             const double *__restrict__ upper, const double *__restrict__ rhs, double *__restrict__ x,
             const int *__restrict__ ray_list) {
+  __shared__ float hbuf[kWarpsPerCta / 2][32], xbuf[kWarpsPerCta / 2][32];
   const unsigned full = 0xffffffffu;
   const int wid = threadIdx.x >> 5, r = threadIdx.x & 31;
-  const long jsys = (long)blockIdx.x * kWarpsPerCta + wid;
+  const int half = wid & 1, slot = wid >> 1;
+  const long jsys = (long)blockIdx.x * (kWarpsPerCta / 2) + slot;
   if (jsys >= n_sys) return;
   const long sys = system_of(jsys, ray_list);
   const bool real = r < n;
   const size_t base = (size_t)sys * n_r * n;
-  // Power-of-two scaling of the right-hand side (FP32 range), as in the CTA kernel.
-  double m = 0.0;
+  const int m = n_r / 2, B = n_r - 1 - m;
+  // Power-of-two scaling of the right-hand side (FP32 range), the same in both halves.
+  double mx = 0.0;
   if (real)
-    for (int i = 0; i < n_r; ++i) m = fmax(m, fabs(rhs[base + (size_t)i * n + r]));
+    for (int i = 0; i < n_r; ++i) mx = fmax(mx, fabs(rhs[base + (size_t)i * n + r]));
 #pragma unroll
-  for (int off = 16; off > 0; off >>= 1) m = fmax(m, __shfl_xor_sync(full, m, off));
+  for (int off = 16; off > 0; off >>= 1) mx = fmax(mx, __shfl_xor_sync(full, mx, off));
   double scale = 1.0;
-  if (m > 0.0 && isfinite(m)) {
+  if (mx > 0.0 && isfinite(mx)) {
     int e;
-    frexp(m, &e);
+    frexp(mx, &e);
     scale = ldexp(1.0, -e);
   }
-  float nrow[NP], rowv[NP];
+  auto matvec = [&](int z, float v) {
+    const float *src = dinv + (base + (size_t)z * n + (real ? r : 0)) * n;
+    float acc0 = 0.f, acc1 = 0.f;
 #pragma unroll
-  for (int c = 0; c < NP; ++c) nrow[c] = 0.f;
-  double nb = 0.0, nc = 0.0;
-  auto load = [&](int i, bool fwd) {
-    const size_t zr = base + (size_t)i * n + r;
-    const float *src = dinv + zr * n;
-#pragma unroll
-    for (int c = 0; c < NP; ++c) nrow[c] = (c < n) ? src[c] : 0.f;
-    nb = fwd ? rhs[zr] : x[zr];
-    nc = fwd ? (i > 0 ? lower[zr] : 0.0) : (i < n_r - 1 ? upper[zr] : 0.0);
+    for (int c = 0; c < NP; c += 2) {
+      const float v0 = __shfl_sync(full, v, c), v1 = __shfl_sync(full, v, c + 1);
+      if (c < n) acc0 = fmaf(src[c], v0, acc0);
+      if (c + 1 < n) acc1 = fmaf(src[c + 1], v1, acc1);
+    }
+    return acc0 + acc1;
   };
-  if (real) load(0, true);
-  float g_prev = 0.f;
-  for (int i = 0; i < n_r; ++i) {
-#pragma unroll
-    for (int c = 0; c < NP; ++c) rowv[c] = nrow[c];
-    const double b = nb, l = nc;
-    if (real && i + 1 < n_r) load(i + 1, true);
-    const float v = real ? (float)(b * scale) - (float)l * g_prev : 0.f;
-    float acc0 = 0.f, acc1 = 0.f;
-#pragma unroll
-    for (int c = 0; c < NP; c += 2) {
-      acc0 = fmaf(rowv[c], __shfl_sync(full, v, c), acc0);
-      if (c + 1 < NP) acc1 = fmaf(rowv[c + 1], __shfl_sync(full, v, c + 1), acc1);
-    }
-    const float g = acc0 + acc1;
-    if (real) x[base + (size_t)i * n + r] = (double)g;
-    g_prev = g;
+  auto bar = [&]() { asm volatile("bar.sync %0, 64;" ::"r"(1 + slot) : "memory"); };
+  bar();                       // both halves have read rhs for the scale before x (may alias rhs) is written
+  // Forward: top g_i = Dinv_i (r_i - l_i g_{i-1}), i < m; bottom h_i = Dinv_i (r_i - u_i h_{i+1}), i > m.
+  const int flen = half == 0 ? m : B;
+  float prev = 0.f;
+  for (int j = 0; j < flen; ++j) {
+    const int z = half == 0 ? j : n_r - 1 - j;
+    const size_t zr = base + (size_t)z * n + r;
+    const float c = (real && j > 0) ? (float)(half == 0 ? lower[zr] : upper[zr]) : 0.f;
+    const float v = real ? (float)(rhs[zr] * scale) - c * prev : 0.f;
+    const float g = matvec(z, v);
+    if (real) x[zr] = (double)g;
+    prev = g;
   }
-  if (real) load(n_r - 1, false);
-  float x_next = 0.f;
-  for (int i = n_r - 1; i >= 0; --i) {
-#pragma unroll
-    for (int c = 0; c < NP; ++c) rowv[c] = nrow[c];
-    const double gz = nb, u = nc;
-    if (real && i > 0) load(i - 1, false);
-    const float v = real ? (float)u * x_next : 0.f;
-    float acc0 = 0.f, acc1 = 0.f;
-#pragma unroll
-    for (int c = 0; c < NP; c += 2) {
-      acc0 = fmaf(rowv[c], __shfl_sync(full, v, c), acc0);
-      if (c + 1 < NP) acc1 = fmaf(rowv[c + 1], __shfl_sync(full, v, c + 1), acc1);
-    }
-    const float xi = gz - (acc0 + acc1);
-    if (real) x[base + (size_t)i * n + r] = (double)xi / scale;
-    x_next = xi;
+  if (half == 1) hbuf[slot][r] = B > 0 ? prev : 0.f;
+  bar();
+  if (half == 0) {
+    // Middle zone: x_m = Dinv_m (r_m - l_m g_{m-1} - u_m h_{m+1}).
+    const size_t zr = base + (size_t)m * n + r;
+    const float l = (real && m > 0) ? (float)lower[zr] : 0.f;
+    const float u = (real && m < n_r - 1) ? (float)upper[zr] : 0.f;
+    const float v = real ? (float)(rhs[zr] * scale) - l * prev - u * hbuf[slot][r] : 0.f;
+    const float xm = matvec(m, v);
+    if (real) x[zr] = (double)xm / scale;
+    xbuf[slot][r] = xm;
+    prev = xm;
+  }
+  bar();
+  if (half == 1) prev = xbuf[slot][r];
+  // Backward: top x_i = g_i - Dinv_i (u_i x_{i+1}), i = m-1..0; bottom x_i = h_i - Dinv_i (l_i x_{i-1}), i = m+1..
+  for (int j = 0; j < flen; ++j) {
+    const int z = half == 0 ? m - 1 - j : m + 1 + j;
+    const size_t zr = base + (size_t)z * n + r;
+    const float c = real ? (float)(half == 0 ? upper[zr] : lower[zr]) : 0.f;
+    const float gz = real ? (float)x[zr] : 0.f;
+    const float xi = gz - matvec(z, real ? c * prev : 0.f);
+    if (real) x[zr] = (double)xi / scale;
+    prev = xi;
   }
 }
 
@@ -460,10 +508,11 @@ k_solve_w32(int n, int n_r, int n_sys, const float *__restrict__ dinv, const dou
 // flight and returns.
 template <int NP>
 struct SolveRing {
-  // Ring depth: up to 12 zones ahead, with the ring of both warps under 44 KB of static smem.
-  static constexpr int FIT = 45056 / (2 * NP * NP * 4);
-  static constexpr int STAGES = FIT < 12 ? FIT : 12;
-  static constexpr int WPC = 2;                              // warps (systems) per CTA
+  // Ring depth: 3 to 8 zones ahead, the rings of both warps within ~20 KB so that every CTA of
+  // a 1024-system launch is resident at once (about 7 per SM).
+  static constexpr int FIT = 20480 / (2 * NP * NP * 4);
+  static constexpr int STAGES = FIT < 3 ? 3 : (FIT > 8 ? 8 : FIT);
+  static constexpr int WPC = 2;                              // warps per CTA (the two halves of one system)
   static constexpr int SLOT = NP * NP * 4;                   // bytes: one inverse block
 };
 
@@ -548,130 +597,162 @@ __device__ inline float row_dot(const float *__restrict__ row, const float *__re
   return (a0 + a1) + (a2 + a3);
 }
 
+// MIXED-precision substitution with the twisted FP32 factors: one CTA per system, warp 0 the
+// top-down half (zones 0..m-1, then the middle zone m, then back up from m-1 to 0), warp 1 the
+// bottom-up half (zones n_r-1..m+1, then back down from m+1).  Each warp streams its zones'
+// inverse blocks through its own ring of bulk copies (one copy per use, mbarrier completion,
+// bounded waits); the halves meet at the middle through shared memory and CTA barriers.  Lane
+// r owns block row r; the zone vector is broadcast through shared memory.
 template <int NP, bool VEC>
 __global__ void __launch_bounds__(SolveRing<NP>::WPC * 32)
 k_solve_tma(int n, int n_r, int n_sys, const float *__restrict__ dinv, const float *__restrict__ lower,
             const float *__restrict__ upper, const double *__restrict__ rhs, double *__restrict__ x,
             float *__restrict__ g32, const int *__restrict__ ray_list, const int *__restrict__ sys_exp, int *err) {
   using R = SolveRing<NP>;
+  static_assert(R::WPC == 2, "one system per CTA: two warps, one per half");
   constexpr int S = R::STAGES;
   constexpr int D = 8;                                      // depth of the per-lane vector queue
-  __shared__ __align__(128) unsigned char ring[R::WPC][S][NP * NP * 4];
-  __shared__ __align__(16) float vbuf[R::WPC][NP];          // the zone vector, broadcast through smem
-  __shared__ __align__(8) unsigned long long bar[R::WPC][S];
+  __shared__ __align__(128) unsigned char ring[2][S][NP * NP * 4];
+  __shared__ __align__(16) float vbuf[2][NP];               // the zone vector, broadcast through smem
+  __shared__ __align__(8) unsigned long long bar[2][S];
+  __shared__ float hbuf[32], xbuf[32];                      // h_{m+1} and x_m, exchanged at the middle
   const unsigned full = 0xffffffffu;
-  const int wid = threadIdx.x >> 5, r = threadIdx.x & 31;
-  const long jsys = (long)blockIdx.x * R::WPC + wid;
-  if (jsys >= n_sys) return;
+  const int half = threadIdx.x >> 5, r = threadIdx.x & 31;
+  const long jsys = blockIdx.x;
+  if (jsys >= n_sys) return;                                // whole CTA
   const long sys = system_of(jsys, ray_list);
   const bool real = r < n;
   const size_t base = (size_t)sys * n_r * n;
   const unsigned blk = (unsigned)(n * n * 4);
   const int kexp = sys_exp[jsys];             // rhs is scaled by 2^kexp before rounding to FP32
+  const int m = n_r / 2, B = n_r - 1 - m;
+  const int F = half == 0 ? m : B;                          // forward steps of this half
+  const int U = half == 0 ? 2 * m + 1 : 2 * B;              // ring uses of this half
   if (r == 0) {
-    for (int k = 0; k < S; ++k) mbar_init(&bar[wid][k], 1);
+    for (int k = 0; k < S; ++k) mbar_init(&bar[half][k], 1);
     mbar_fence_init();
   }
   __syncwarp();
-
-  // Use u < n_r is forward zone u, u >= n_r backward zone 2 n_r - 1 - u; one bulk copy (the
-  // zone's inverse block) per use.
-  auto zone_of = [&](int u) { return u < n_r ? u : 2 * n_r - 1 - u; };
-  auto issue = [&](int u) {
-    unsigned long long *b = &bar[wid][u % S];
-    mbar_expect_tx(b, blk);
-    bulk_g2s(ring[wid][u % S], dinv + (base + (size_t)zone_of(u) * n) * n, blk, b);
+  auto use_zone = [&](int u) {
+    if (half == 0) return u <= m ? u : 2 * m - u;
+    return u < B ? n_r - 1 - u : m + 1 + (u - B);
   };
-  auto wait = [&](int u, int issued_to) -> bool {
-    bool ok = mbar_wait_bounded(&bar[wid][u % S], (unsigned)((u / S) & 1));
-    ok = __all_sync(full, ok);
-    if (!ok) {                                    // give up: flag, drain own copies, return
+  auto issue = [&](int u) {
+    unsigned long long *b = &bar[half][u % S];
+    mbar_expect_tx(b, blk);
+    bulk_g2s(ring[half][u % S], dinv + (base + (size_t)use_zone(u) * n) * n, blk, b);
+  };
+  bool ok = true;                                           // warp-uniform
+  int issued = -1;
+  auto wait = [&](int u) -> bool {
+    if (!ok) return false;
+    bool w = mbar_wait_bounded(&bar[half][u % S], (unsigned)((u / S) & 1));
+    ok = __all_sync(full, w);
+    if (!ok) {                                    // give up: flag and drain own copies
       if (r == 0) {
         atomicExch(err, 1);
-        for (int v = u + 1; v <= issued_to; ++v) mbar_wait_bounded(&bar[wid][v % S], (unsigned)((v / S) & 1));
+        for (int v = u + 1; v <= issued; ++v) mbar_wait_bounded(&bar[half][v % S], (unsigned)((v / S) & 1));
       }
       __syncwarp();
     }
     return ok;
   };
-  // Per-lane queue of the zone vectors (own row), D uses ahead in a ring of registers indexed
-  // by compile-time slots (the zone loop is unrolled by D), all in FP32: the rhs is rescaled by
-  // exponent arithmetic, so no FP64-pipe work sits on the recurrence.
-  // The loaded values are queued as loaded (the rhs as FP64) and converted when consumed, so
-  // each load has D zone steps to arrive.
-  double qa[D];
-  float qb[D];
-  auto fetch = [&](int u, double &va, float &vb) {
-    va = 0.0;
-    vb = 0.f;
-    if (!real || u >= 2 * n_r) return;
-    const int i = zone_of(u);
-    const size_t zr = base + (size_t)i * n + r;
-    if (u < n_r) {
-      va = rhs[zr];
-      vb = i > 0 ? lower[zr] : 0.f;
-    } else {
-      va = (double)g32[zr];                         // forward result written by this lane
-      vb = i < n_r - 1 ? upper[zr] : 0.f;
+  auto advance = [&](int u) {                     // after use u: keep S - 1 copies in flight
+    __syncwarp();
+    const int nu = u + S - 1;
+    if (ok && nu < U) {
+      if (r == 0) issue(nu);
+      issued = nu;
     }
   };
-  float *vb = vbuf[wid];
-  const int rr = real ? r : 0;                      // lanes without a row read row 0 (result unused)
+  // Per-lane queue of (rhs or forward result, coupling) for the uses ahead, D deep, as loaded
+  // (converted when consumed, so each load has D steps to arrive).
+  double qa[D];
+  float qb[D];
+  auto fetch_fwd = [&](int j, double &va, float &vb) {
+    va = 0.0;
+    vb = 0.f;
+    if (!real || j >= F) return;
+    const int z = use_zone(j);
+    const size_t zr = base + (size_t)z * n + r;
+    va = rhs[zr];
+    vb = j > 0 ? (half == 0 ? lower[zr] : upper[zr]) : 0.f;
+  };
+  auto fetch_bwd = [&](int j, double &va, float &vb) {
+    va = 0.0;
+    vb = 0.f;
+    if (!real || j >= F) return;
+    const int z = use_zone(U - F + j);
+    const size_t zr = base + (size_t)z * n + r;
+    va = (double)g32[zr];                         // forward result written by this lane
+    vb = half == 0 ? upper[zr] : lower[zr];
+  };
+  float *vb = vbuf[half];
+  const int rr = real ? r : 0;                    // lanes without a row read row 0 (result unused)
 
-  int issued = -1;
   if (r == 0)
-    for (int u = 0; u < S - 1 && u < n_r; ++u) issue(u);
-  issued = (S - 1 < n_r ? S - 1 : n_r) - 1;
+    for (int u = 0; u < S - 1 && u < U; ++u) issue(u);
+  issued = (S - 1 < U ? S - 1 : U) - 1;
 #pragma unroll
-  for (int d = 0; d < D; ++d) fetch(d < n_r ? d : 2 * n_r, qa[d], qb[d]);
-  float g_prev = 0.f;
-  for (int i0 = 0; i0 < n_r; i0 += D) {
+  for (int d = 0; d < D; ++d) fetch_fwd(d, qa[d], qb[d]);
+  float prev = 0.f;
+  for (int j0 = 0; j0 < F; j0 += D) {
 #pragma unroll
     for (int d = 0; d < D; ++d) {
-      const int i = i0 + d;
-      if (i >= n_r) break;
+      const int j = j0 + d;
+      if (j >= F) break;
       const float b = d2f_exp2(qa[d], kexp), l = qb[d];
-      fetch(i + D < n_r ? i + D : 2 * n_r, qa[d], qb[d]);
-      if (!wait(i, issued)) return;
-      if (r < NP) vb[r] = real ? b - l * g_prev : 0.f;
-      __syncwarp();
-      const float g = row_dot<NP, VEC>((const float *)ring[wid][i % S] + (size_t)rr * n, vb, n);
-      if (real) g32[base + (size_t)i * n + r] = g;
-      g_prev = g;
-      __syncwarp();
-      const int nu = i + S - 1;
-      if (nu < n_r) {
-        if (r == 0) issue(nu);
-        issued = nu;
+      fetch_fwd(j + D, qa[d], qb[d]);
+      if (wait(j)) {
+        if (r < NP) vb[r] = real ? b - l * prev : 0.f;
+        __syncwarp();
+        const float g = row_dot<NP, VEC>((const float *)ring[half][j % S] + (size_t)rr * n, vb, n);
+        if (real) g32[base + (size_t)use_zone(j) * n + r] = g;
+        prev = g;
       }
+      advance(j);
     }
   }
-  if (r == 0)
-    for (int u = n_r; u < n_r + S - 1 && u < 2 * n_r; ++u) issue(u);
-  issued = (n_r + S - 1 < 2 * n_r ? n_r + S - 1 : 2 * n_r) - 1;
+  if (half == 1) hbuf[r] = B > 0 ? prev : 0.f;
+  __syncthreads();
+  if (half == 0) {
+    // Middle zone: x_m = Dinv_m (r_m - l_m g_{m-1} - u_m h_{m+1}).
+    const size_t zr = base + (size_t)m * n + r;
+    const float bm = real ? d2f_exp2(rhs[zr], kexp) : 0.f;
+    const float lm = (real && m > 0) ? lower[zr] : 0.f;
+    const float um = (real && m < n_r - 1) ? upper[zr] : 0.f;
+    float xm = 0.f;
+    if (wait(m)) {
+      if (r < NP) vb[r] = real ? bm - lm * prev - um * hbuf[r] : 0.f;
+      __syncwarp();
+      xm = row_dot<NP, VEC>((const float *)ring[half][m % S] + (size_t)rr * n, vb, n);
+      if (real) x[zr] = f2d_exp2(xm, -kexp);
+    }
+    advance(m);
+    xbuf[r] = xm;
+    prev = xm;
+  }
+  __syncthreads();
+  if (half == 1) prev = xbuf[r];
+  // Backward: top x_i = g_i - Dinv_i (u_i x_{i+1}); bottom x_i = h_i - Dinv_i (l_i x_{i-1}).
 #pragma unroll
-  for (int d = 0; d < D; ++d) fetch(n_r + d, qa[d], qb[d]);
-  float x_next = 0.f;
-  for (int k0 = 0; k0 < n_r; k0 += D) {
+  for (int d = 0; d < D; ++d) fetch_bwd(d, qa[d], qb[d]);
+  for (int j0 = 0; j0 < F; j0 += D) {
 #pragma unroll
     for (int d = 0; d < D; ++d) {
-      const int k = k0 + d;
-      if (k >= n_r) break;
-      const int u = n_r + k, i = n_r - 1 - k;
-      const float gz = (float)qa[d], uu = qb[d];
-      fetch(u + D, qa[d], qb[d]);
-      if (!wait(u, issued)) return;
-      if (r < NP) vb[r] = real ? uu * x_next : 0.f;
-      __syncwarp();
-      const float xi = gz - row_dot<NP, VEC>((const float *)ring[wid][u % S] + (size_t)rr * n, vb, n);
-      if (real) x[base + (size_t)i * n + r] = f2d_exp2(xi, -kexp);
-      x_next = xi;
-      __syncwarp();
-      const int nu = u + S - 1;
-      if (nu < 2 * n_r) {
-        if (r == 0) issue(nu);
-        issued = nu;
+      const int j = j0 + d;
+      if (j >= F) break;
+      const int u = U - F + j;
+      const float gz = (float)qa[d], c = qb[d];
+      fetch_bwd(j + D, qa[d], qb[d]);
+      if (wait(u)) {
+        if (r < NP) vb[r] = real ? c * prev : 0.f;
+        __syncwarp();
+        const float xi = gz - row_dot<NP, VEC>((const float *)ring[half][u % S] + (size_t)rr * n, vb, n);
+        if (real) x[base + (size_t)use_zone(u) * n + r] = f2d_exp2(xi, -kexp);
+        prev = xi;
       }
+      advance(u);
     }
   }
 }
@@ -683,7 +764,7 @@ cudaError_t launch_solve_tma(int n, int n_r, int n_sys, const void *dinv, const 
   k_sysmax<<<n_sys, 256, 0, s>>>(n, n_r, rhs, ray_list, sys_exp);
   MGFLD_DISPATCH_NP(n, {
     using R = SolveRing<NP>;
-    const unsigned grid = (unsigned)((n_sys + R::WPC - 1) / R::WPC);
+    const unsigned grid = (unsigned)n_sys;                 // one system (two warps) per CTA
     if (n == NP)
       k_solve_tma<NP, true><<<grid, R::WPC * 32, 0, s>>>(n, n_r, n_sys, (const float *)dinv, lower32, upper32, rhs,
                                                          x, g32, ray_list, sys_exp, err);
@@ -697,8 +778,8 @@ cudaError_t launch_solve_tma(int n, int n_r, int n_sys, const void *dinv, const 
 template <int NP>
 static cudaError_t run_factor(int n, int n_r, int n_sys, const void *diag, int diag_fp32, const double *lower,
                               const double *upper, void *dinv, const int *ray_list, cudaStream_t s) {
-  constexpr int SPC = Pack<NP>::SPC;
-  const unsigned grid = (unsigned)((n_sys + SPC - 1) / SPC);
+  constexpr int SPS = Pack<NP>::SPC / 2;             // systems per CTA
+  const unsigned grid = (unsigned)((n_sys + SPS - 1) / SPS);
   if (diag_fp32)
     k_factor<NP, float><<<grid, Pack<NP>::THREADS, 0, s>>>(n, n_r, n_sys, (const float *)diag, lower, upper,
                                                            (double *)dinv, ray_list);
@@ -708,14 +789,14 @@ static cudaError_t run_factor(int n, int n_r, int n_sys, const void *diag, int d
   return cudaGetLastError();
 }
 
-template <int NP, typename T>
+template <int NP>
 static cudaError_t run_solve(int n, int n_r, int n_sys, const void *dinv, const double *lower,
                              const double *upper, const double *rhs, double *x, const int *ray_list,
                              cudaStream_t s) {
-  constexpr int SPC = Pack<NP>::SPC;
-  const unsigned grid = (unsigned)((n_sys + SPC - 1) / SPC);
-  k_solve<NP, T><<<grid, Pack<NP>::THREADS, 0, s>>>(n, n_r, n_sys, (const T *)dinv, lower, upper, rhs, x,
-                                                    ray_list);
+  constexpr int SPS = Pack<NP>::SPC / 2;             // systems per CTA
+  const unsigned grid = (unsigned)((n_sys + SPS - 1) / SPS);
+  k_solve<NP><<<grid, Pack<NP>::THREADS, 0, s>>>(n, n_r, n_sys, (const double *)dinv, lower, upper, rhs, x,
+                                                 ray_list);
   return cudaGetLastError();
 }
 
@@ -724,7 +805,7 @@ cudaError_t launch_factor(int n, int n_r, int n_sys, const void *diag, int diag_
                           cudaStream_t s) {
   if (n_sys == 0) return cudaSuccess;
   if (precision == MGFLD_MIXED) {
-    const unsigned grid = (unsigned)((n_sys + kWarpsPerCta - 1) / kWarpsPerCta);
+    const unsigned grid = (unsigned)((n_sys + kWarpsPerCta / 2 - 1) / (kWarpsPerCta / 2));
     if (diag_fp32) {
       MGFLD_DISPATCH_NP(n, k_factor_w32<NP, float, double><<<grid, kWarpsPerCta * 32, 0, s>>>(
                                n, n_r, n_sys, (const float *)diag, lower, upper, (float *)dinv, ray_list);
@@ -743,7 +824,7 @@ cudaError_t launch_factor(int n, int n_r, int n_sys, const void *diag, int diag_
 cudaError_t launch_factor_f32(int n, int n_r, int n_sys, const float *diag, const float *lower32,
                               const float *upper32, float *dinv, const int *ray_list, cudaStream_t s) {
   if (n_sys == 0) return cudaSuccess;
-  const unsigned grid = (unsigned)((n_sys + kWarpsPerCta - 1) / kWarpsPerCta);
+  const unsigned grid = (unsigned)((n_sys + kWarpsPerCta / 2 - 1) / (kWarpsPerCta / 2));
   MGFLD_DISPATCH_NP(n, k_factor_w32<NP, float, float><<<grid, kWarpsPerCta * 32, 0, s>>>(
                            n, n_r, n_sys, diag, lower32, upper32, dinv, ray_list);
                        return cudaGetLastError())
@@ -754,12 +835,12 @@ cudaError_t launch_solve(int n, int n_r, int n_sys, const void *dinv, const doub
                          const int *ray_list, cudaStream_t s) {
   if (n_sys == 0) return cudaSuccess;
   if (precision == MGFLD_MIXED) {
-    const unsigned grid = (unsigned)((n_sys + kWarpsPerCta - 1) / kWarpsPerCta);
+    const unsigned grid = (unsigned)((n_sys + kWarpsPerCta / 2 - 1) / (kWarpsPerCta / 2));
     MGFLD_DISPATCH_NP(n, k_solve_w32<NP><<<grid, kWarpsPerCta * 32, 0, s>>>(n, n_r, n_sys, (const float *)dinv,
                                                                           lower, upper, rhs, x, ray_list);
                          return cudaGetLastError())
   } else {
-    MGFLD_DISPATCH_NP(n, return (run_solve<NP, double>(n, n_r, n_sys, dinv, lower, upper, rhs, x, ray_list, s)))
+    MGFLD_DISPATCH_NP(n, return (run_solve<NP>(n, n_r, n_sys, dinv, lower, upper, rhs, x, ray_list, s)))
   }
 }
 

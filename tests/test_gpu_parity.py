@@ -250,7 +250,7 @@ def test_factor_solve_matches_dense_lu(precision, unit):
     """mgfld_factor + mgfld_solve on random block-tridiagonal systems (some needing
     pivoting) against LAPACK on the dense matrix of each system."""
     rng = np.random.default_rng(11)
-    for n_e, n_r in ((5, 6), (20, 9), (12, 4)):
+    for n_e, n_r in ((5, 6), (20, 9), (12, 4), (7, 1), (6, 2), (4, 3), (20, 64)):
         n_ray = 3
         # Block-diagonally dominant systems (the regime of the transport blocks), one of them
         # with its dominant entries off the diagonal so that every block needs row exchanges.
