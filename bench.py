@@ -357,6 +357,25 @@ def reference_arm(args, n_gpus, rank):
 
 # ------------------------------------------------------------------------- main
 
+def profile_step(path, n_rays):
+    """One implicit step of the first n_rays rays of the benchmark workload (FP64 Newton or the
+    mixed path), for ncu captures of single launches; exits non-zero on a failed step."""
+    import torch
+    from paper_1809_05608_gb300 import build as B
+    if not os.path.exists(B.LIB):
+        B.build()
+    from paper_1809_05608_gb300 import mgfld as M
+    inp = problems.make_problem(CONFIG_ID, rays=slice(0, n_rays))
+    prec = M.MGFLD_MIXED if path == 'mixed' else M.MGFLD_FP64
+    st = M.Stepper(inp, prec, tol=TOL, max_iter=60)
+    psi, ye, T = st.state_to_device(inp['psi0'], inp['ye0'], inp['T0'])
+    rc = st.step(psi, ye, T)
+    torch.cuda.synchronize()
+    print(f'profile step {path}: {n_rays} rays, status {M.status_str(rc)}, '
+          f'iterations {int(st.report["iters"].max())}', flush=True)
+    return 0 if rc == M.MGFLD_OK else 1
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument('--gpus', type=int, default=1)
@@ -365,7 +384,12 @@ def main():
     ap.add_argument('--impl', default='mgfld', choices=['mgfld', 'reference'])
     ap.add_argument('--oracle-rays', type=int, default=12)
     ap.add_argument('--no-cpu-baseline', action='store_true')
+    ap.add_argument('--profile-step', choices=['mixed', 'fp64'],
+                    help='profiling target: one implicit step of this path on --rays rays, no timing')
+    ap.add_argument('--rays', type=int, default=64)
     args = ap.parse_args()
+    if args.profile_step:
+        return profile_step(args.profile_step, args.rays)
     ws, rank, local = dist_info()
     n_gpus = max(args.gpus, ws)
     if args.impl == 'reference':
