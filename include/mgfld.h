@@ -209,7 +209,7 @@ mgfld_status mgfld_solve(const mgfld_dims *dims, const mgfld_system *sys, int pr
  * allocated or freed by this call.  Inputs and outputs are the caller's, as for
  * mgfld_step.
  *   - Returns MGFLD_ENOMEM, before touching the GPU, when mgfld_workspace_bytes(dims,
- *     opts->precision) exceeds MGFLD_NOALLOC_SCRATCH_BYTES (e.g. 3 rays of 512 zones x
+ *     opts->precision) exceeds MGFLD_NOALLOC_SCRATCH_BYTES (e.g. 4 rays of 512 zones x
  *     20 groups in FP64); split the rays into several calls.
  *   - Returns MGFLD_EINVAL if opts->profile is set (timing would create CUDA events).
  *   - The first call on each device looks up the array's device address with that
