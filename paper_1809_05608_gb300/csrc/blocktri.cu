@@ -508,10 +508,9 @@ k_solve_w32(int n, int n_r, int n_sys, const float *__restrict__ dinv, const dou
 // flight and returns.
 template <int NP>
 struct SolveRing {
-  // Ring depth: 3 to 8 zones ahead, the rings of both warps within ~20 KB so that every CTA of
-  // a 1024-system launch is resident at once (about 7 per SM).
-  static constexpr int FIT = 20480 / (2 * NP * NP * 4);
-  static constexpr int STAGES = FIT < 3 ? 3 : (FIT > 8 ? 8 : FIT);
+  // Ring depth: a power of two (slot and phase by masks), 8 for N <= 20 and 4 above, so that
+  // the rings of both warps (<= 26 KB) let every CTA of a 1024-system launch be resident.
+  static constexpr int STAGES = NP <= 20 ? 8 : 4;
   static constexpr int WPC = 2;                              // warps per CTA (the two halves of one system)
   static constexpr int SLOT = NP * NP * 4;                   // bytes: one inverse block
 };
@@ -611,6 +610,7 @@ k_solve_tma(int n, int n_r, int n_sys, const float *__restrict__ dinv, const flo
   using R = SolveRing<NP>;
   static_assert(R::WPC == 2, "one system per CTA: two warps, one per half");
   constexpr int S = R::STAGES;
+  static_assert((S & (S - 1)) == 0, "power-of-two ring");
   constexpr int D = 8;                                      // depth of the per-lane vector queue
   __shared__ __align__(128) unsigned char ring[2][S][NP * NP * 4];
   __shared__ __align__(16) float vbuf[2][NP];               // the zone vector, broadcast through smem
@@ -622,113 +622,113 @@ k_solve_tma(int n, int n_r, int n_sys, const float *__restrict__ dinv, const flo
   if (jsys >= n_sys) return;                                // whole CTA
   const long sys = system_of(jsys, ray_list);
   const bool real = r < n;
-  const size_t base = (size_t)sys * n_r * n;
+  const int rr = real ? r : 0;                              // lanes without a row use row 0 (unused)
   const unsigned blk = (unsigned)(n * n * 4);
   const int kexp = sys_exp[jsys];             // rhs is scaled by 2^kexp before rounding to FP32
   const int m = n_r / 2, B = n_r - 1 - m;
   const int F = half == 0 ? m : B;                          // forward steps of this half
   const int U = half == 0 ? 2 * m + 1 : 2 * B;              // ring uses of this half
+  // Zone sequences: forward zf0 + j dz, backward zb0 - j dz.
+  const int dz = half == 0 ? 1 : -1;
+  const int zf0 = half == 0 ? 0 : n_r - 1, zb0 = half == 0 ? m - 1 : m + 1;
+  // Per-lane element pointers of this system (row r of zone z is [z * n]).
+  const size_t sb = (size_t)sys * n_r * n;
+  const double *rhs_l = rhs + sb + rr;
+  const float *cin_l = (half == 0 ? lower : upper) + sb + rr;   // coupling used going inward
+  const float *cout_l = (half == 0 ? upper : lower) + sb + rr;  // coupling used going outward
+  float *g_l = g32 + sb + rr;
+  double *x_l = x + sb + rr;
+  const float *dsys = dinv + sb * n;
   if (r == 0) {
     for (int k = 0; k < S; ++k) mbar_init(&bar[half][k], 1);
     mbar_fence_init();
   }
   __syncwarp();
-  auto use_zone = [&](int u) {
-    if (half == 0) return u <= m ? u : 2 * m - u;
-    return u < B ? n_r - 1 - u : m + 1 + (u - B);
-  };
-  auto issue = [&](int u) {
-    unsigned long long *b = &bar[half][u % S];
+  // The bulk copies are issued by lane 0 in use order; it tracks the zone of the next use.
+  int iu = 0, iz = zf0;                                     // next use to issue and its zone
+  auto issue_next = [&]() {
+    unsigned long long *b = &bar[half][iu & (S - 1)];
     mbar_expect_tx(b, blk);
-    bulk_g2s(ring[half][u % S], dinv + (base + (size_t)use_zone(u) * n) * n, blk, b);
+    bulk_g2s(ring[half][iu & (S - 1)], dsys + (size_t)iz * n * n, blk, b);
+    ++iu;
+    // zone of use iu: forward ..., (top) the middle zone m, then backward
+    if (half == 0) iz = iu < m ? iu : (iu == m ? m : 2 * m - iu);
+    else iz = iu < B ? n_r - 1 - iu : m + 1 + (iu - B);
   };
   bool ok = true;                                           // warp-uniform
-  int issued = -1;
   auto wait = [&](int u) -> bool {
     if (!ok) return false;
-    bool w = mbar_wait_bounded(&bar[half][u % S], (unsigned)((u / S) & 1));
+    if (mbar_try_wait(&bar[half][u & (S - 1)], (unsigned)((u / S) & 1))) return true;
+    bool w = mbar_wait_bounded(&bar[half][u & (S - 1)], (unsigned)((u / S) & 1));
     ok = __all_sync(full, w);
     if (!ok) {                                    // give up: flag and drain own copies
       if (r == 0) {
         atomicExch(err, 1);
-        for (int v = u + 1; v <= issued; ++v) mbar_wait_bounded(&bar[half][v % S], (unsigned)((v / S) & 1));
+        for (int v = u + 1; v < iu; ++v) mbar_wait_bounded(&bar[half][v & (S - 1)], (unsigned)((v / S) & 1));
       }
       __syncwarp();
     }
     return ok;
   };
-  auto advance = [&](int u) {                     // after use u: keep S - 1 copies in flight
+  auto advance = [&]() {                          // keep S - 1 copies in flight
     __syncwarp();
-    const int nu = u + S - 1;
-    if (ok && nu < U) {
-      if (r == 0) issue(nu);
-      issued = nu;
-    }
+    if (r == 0 && ok && iu < U) issue_next();
   };
   // Per-lane queue of (rhs or forward result, coupling) for the uses ahead, D deep, as loaded
   // (converted when consumed, so each load has D steps to arrive).
   double qa[D];
   float qb[D];
-  auto fetch_fwd = [&](int j, double &va, float &vb) {
-    va = 0.0;
-    vb = 0.f;
-    if (!real || j >= F) return;
-    const int z = use_zone(j);
-    const size_t zr = base + (size_t)z * n + r;
-    va = rhs[zr];
-    vb = j > 0 ? (half == 0 ? lower[zr] : upper[zr]) : 0.f;
-  };
-  auto fetch_bwd = [&](int j, double &va, float &vb) {
-    va = 0.0;
-    vb = 0.f;
-    if (!real || j >= F) return;
-    const int z = use_zone(U - F + j);
-    const size_t zr = base + (size_t)z * n + r;
-    va = (double)g32[zr];                         // forward result written by this lane
-    vb = half == 0 ? upper[zr] : lower[zr];
-  };
   float *vb = vbuf[half];
-  const int rr = real ? r : 0;                    // lanes without a row read row 0 (result unused)
 
   if (r == 0)
-    for (int u = 0; u < S - 1 && u < U; ++u) issue(u);
-  issued = (S - 1 < U ? S - 1 : U) - 1;
+    for (int k = 0; k < S - 1 && k < U; ++k) issue_next();
+  iu = __shfl_sync(full, iu, 0);
+  iz = __shfl_sync(full, iz, 0);
 #pragma unroll
-  for (int d = 0; d < D; ++d) fetch_fwd(d, qa[d], qb[d]);
+  for (int d = 0; d < D; ++d) {
+    const int z = zf0 + d * dz;
+    qa[d] = (real && d < F) ? rhs_l[(size_t)z * n] : 0.0;
+    qb[d] = (real && d < F && d > 0) ? cin_l[(size_t)z * n] : 0.f;
+  }
   float prev = 0.f;
+  int zf = zf0;
   for (int j0 = 0; j0 < F; j0 += D) {
 #pragma unroll
     for (int d = 0; d < D; ++d) {
       const int j = j0 + d;
       if (j >= F) break;
       const float b = d2f_exp2(qa[d], kexp), l = qb[d];
-      fetch_fwd(j + D, qa[d], qb[d]);
+      const int zq = zf + D * dz;                 // refill this slot with the zone D steps ahead
+      const bool more = real && j + D < F;
+      qa[d] = more ? rhs_l[(size_t)zq * n] : 0.0;
+      qb[d] = more ? cin_l[(size_t)zq * n] : 0.f;
       if (wait(j)) {
         if (r < NP) vb[r] = real ? b - l * prev : 0.f;
         __syncwarp();
-        const float g = row_dot<NP, VEC>((const float *)ring[half][j % S] + (size_t)rr * n, vb, n);
-        if (real) g32[base + (size_t)use_zone(j) * n + r] = g;
+        const float g = row_dot<NP, VEC>((const float *)ring[half][j & (S - 1)] + (size_t)rr * n, vb, n);
+        if (real) g_l[(size_t)zf * n] = g;
         prev = g;
       }
-      advance(j);
+      advance();
+      zf += dz;
     }
   }
   if (half == 1) hbuf[r] = B > 0 ? prev : 0.f;
   __syncthreads();
   if (half == 0) {
     // Middle zone: x_m = Dinv_m (r_m - l_m g_{m-1} - u_m h_{m+1}).
-    const size_t zr = base + (size_t)m * n + r;
-    const float bm = real ? d2f_exp2(rhs[zr], kexp) : 0.f;
-    const float lm = (real && m > 0) ? lower[zr] : 0.f;
-    const float um = (real && m < n_r - 1) ? upper[zr] : 0.f;
+    const size_t zm = (size_t)m * n;
+    const float bm = real ? d2f_exp2(rhs_l[zm], kexp) : 0.f;
+    const float lm = (real && m > 0) ? lower[sb + zm + r] : 0.f;
+    const float um = (real && m < n_r - 1) ? upper[sb + zm + r] : 0.f;
     float xm = 0.f;
     if (wait(m)) {
       if (r < NP) vb[r] = real ? bm - lm * prev - um * hbuf[r] : 0.f;
       __syncwarp();
-      xm = row_dot<NP, VEC>((const float *)ring[half][m % S] + (size_t)rr * n, vb, n);
-      if (real) x[zr] = f2d_exp2(xm, -kexp);
+      xm = row_dot<NP, VEC>((const float *)ring[half][m & (S - 1)] + (size_t)rr * n, vb, n);
+      if (real) x_l[zm] = f2d_exp2(xm, -kexp);
     }
-    advance(m);
+    advance();
     xbuf[r] = xm;
     prev = xm;
   }
@@ -736,23 +736,33 @@ k_solve_tma(int n, int n_r, int n_sys, const float *__restrict__ dinv, const flo
   if (half == 1) prev = xbuf[r];
   // Backward: top x_i = g_i - Dinv_i (u_i x_{i+1}); bottom x_i = h_i - Dinv_i (l_i x_{i-1}).
 #pragma unroll
-  for (int d = 0; d < D; ++d) fetch_bwd(d, qa[d], qb[d]);
+  for (int d = 0; d < D; ++d) {
+    const int z = zb0 - d * dz;
+    qa[d] = (real && d < F) ? (double)g_l[(size_t)z * n] : 0.0;
+    qb[d] = (real && d < F) ? cout_l[(size_t)z * n] : 0.f;
+  }
+  int zb = zb0;
+  const int ub = U - F;                           // first backward use
   for (int j0 = 0; j0 < F; j0 += D) {
 #pragma unroll
     for (int d = 0; d < D; ++d) {
       const int j = j0 + d;
       if (j >= F) break;
-      const int u = U - F + j;
+      const int u = ub + j;
       const float gz = (float)qa[d], c = qb[d];
-      fetch_bwd(j + D, qa[d], qb[d]);
+      const int zq = zb - D * dz;
+      const bool more = real && j + D < F;
+      qa[d] = more ? (double)g_l[(size_t)zq * n] : 0.0;
+      qb[d] = more ? cout_l[(size_t)zq * n] : 0.f;
       if (wait(u)) {
         if (r < NP) vb[r] = real ? c * prev : 0.f;
         __syncwarp();
-        const float xi = gz - row_dot<NP, VEC>((const float *)ring[half][u % S] + (size_t)rr * n, vb, n);
-        if (real) x[base + (size_t)use_zone(u) * n + r] = f2d_exp2(xi, -kexp);
+        const float xi = gz - row_dot<NP, VEC>((const float *)ring[half][u & (S - 1)] + (size_t)rr * n, vb, n);
+        if (real) x_l[(size_t)zb * n] = f2d_exp2(xi, -kexp);
         prev = xi;
       }
-      advance(u);
+      advance();
+      zb -= dz;
     }
   }
 }
