@@ -150,7 +150,9 @@ __device__ inline double eos_e_cold(const Eos &e, double rho, double ye) {
   const double n_b = rho / e.mb;
   const double n_e = rho * ye / e.mb;
   const double n_n = rho * (1.0 - ye) / e.mb;
-  return (e.f1 * pow(n_e, e.g1) * e.rho_fac + e.f2 * pow(n_n, e.g2)) / n_b;
+  const double pe = e.g1_is_4_3 ? n_e * cbrt(n_e) : pow(n_e, e.g1);
+  const double pn = e.g2_is_5_2 ? n_n * n_n * sqrt(n_n) : pow(n_n, e.g2);
+  return (e.f1 * pe * e.rho_fac + e.f2 * pn) / n_b;
 }
 
 __device__ inline double species_mu(int q, double mu_nue) {

@@ -29,8 +29,9 @@ __global__ void k_zone(Prob p, Ws w, const double *__restrict__ ye, const double
   w.ye_n[t] = ye[t];
   w.e_n[t] = eos_e_cold(p.eos, rho, ye[t]) + p.eos.ec * T[t];
   const Eos &e = p.eos;
-  const double muA = e.g1 * e.f1 * pow(rho / e.mb, e.g1 - 1.0) * e.rho_fac;
-  const double muB = e.g2 * e.f2 * pow(rho / e.mb, e.g2 - 1.0);
+  const double nb = rho / e.mb;
+  const double muA = e.g1 * e.f1 * (e.g1_is_4_3 ? cbrt(nb) : pow(nb, e.g1 - 1.0)) * e.rho_fac;
+  const double muB = e.g2 * e.f2 * (e.g2_is_5_2 ? nb * sqrt(nb) : pow(nb, e.g2 - 1.0));
   double mu, dmu;
   mu_nue_zone(e, muA, muB, T[t], ye[t], mu, dmu);
   const double a = lapse_at(p, ray, i);
@@ -221,29 +222,57 @@ __global__ void k_jlam(Prob p, Ws w, const double *__restrict__ psi, const doubl
 // Neutrinosphere radius per (ray, q, k): where the optical depth integrated inward from
 // the outer edge reaches 2/3 (linear inside the zone), else the centre edge; then the
 // outer ghost ratio of Eq. a62af with R_nu clamped to the last zone centre.
+// One warp per (ray, q, k): lane c sums the optical depth of the c-th chunk of zones counted
+// from the outer edge, an exclusive warp scan gives each chunk the depth above it, each lane
+// looks for the crossing inside its chunk, and the outermost crossing wins.
 __global__ void k_nusphere(Prob p, Ws w) {
+  const unsigned full = 0xffffffffu;
   const int n = p.n;
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= p.n_ray * NS * n) return;
+  const int t = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (t >= p.n_ray * NS * n) return;                // whole warps leave together
   const int k = t % n, q = (t / n) % NS, ray = t / (n * NS);
   const double *re = p.r_edge + (size_t)ray * (p.n_r + 1);
   const size_t off = ((size_t)ray * NS + q) * p.n_r * n + k;
   const double *kt = w.kinv + off;                 // 1/lambda, so the scan needs no division
-  double tau_out = 0.0;
-  double rnu = re[0];
-  for (int i = p.n_r - 1; i >= 0; --i) {
+  const int L = (p.n_r + 31) / 32;                 // zones per chunk
+  const int top = p.n_r - 1 - lane * L;            // outermost zone of this lane's chunk
+  const int cnt = top < 0 ? 0 : (top + 1 < L ? top + 1 : L);
+  double s = 0.0;
+  for (int j = 0; j < cnt; ++j) {
+    const int i = top - j;
+    s += (re[i + 1] - re[i]) * kt[(size_t)i * n];
+  }
+  // exclusive prefix over lanes (outer chunks first)
+  double above = s;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const double v = __shfl_up_sync(full, above, o);
+    if (lane >= o) above += v;
+  }
+  double tau_out = above - s;
+  double rnu = 0.0;
+  bool hit = false;
+  for (int j = 0; j < cnt; ++j) {
+    const int i = top - j;
     const double dtau = (re[i + 1] - re[i]) * kt[(size_t)i * n];
     if (tau_out + dtau >= kTauNu) {
       rnu = re[i + 1] - (kTauNu - tau_out) * w.lam[off + (size_t)i * n];
+      hit = true;
       break;
     }
     tau_out += dtau;
   }
-  w.rnu[t] = rnu;
-  const double rI = 0.5 * (re[p.n_r - 1] + re[p.n_r]);
-  const double rg = 2.0 * re[p.n_r] - rI;
-  const double rn = fmin(rnu, rI);
-  w.ghost[t] = (rI * rI - 0.25 * rn * rn) / (rg * rg - 0.25 * rn * rn);
+  const unsigned hits = __ballot_sync(full, hit);
+  const int src = hits ? __ffs(hits) - 1 : 0;
+  rnu = hits ? __shfl_sync(full, rnu, src) : re[0];
+  if (lane == 0) {
+    w.rnu[t] = rnu;
+    const double rI = 0.5 * (re[p.n_r - 1] + re[p.n_r]);
+    const double rg = 2.0 * re[p.n_r] - rI;
+    const double rn = fmin(rnu, rI);
+    w.ghost[t] = (rI * rI - 0.25 * rn * rn) / (rg * rg - 0.25 * rn * rn);
+  }
 }
 
 // alpha_{i+1/2} = A_{i+1/2} D_{i+1/2} / a_{i+1/2}^2 with D = lambda_e F / (3 (R_{i+1} - R_i)),
@@ -331,7 +360,7 @@ cudaError_t launch_setup(const Prob &p, const Ws &w, const double *psi, const do
     k_phi<<<nblk(nz, zpb), zpb * phi_threads_per_zone(p.n), sm, s>>>(p, w, T, zpb);
   }
   k_jlam<<<nblk(nzk, B), B, 0, s>>>(p, w, psi, T);
-  k_nusphere<<<nblk((size_t)p.n_ray * NS * p.n, B), B, 0, s>>>(p, w);
+  k_nusphere<<<nblk((size_t)p.n_ray * NS * p.n * 32, B), B, 0, s>>>(p, w);   // a warp per (ray, q, k)
   k_edges<<<nblk(nall, B), B, 0, s>>>(p, w);
   return cudaGetLastError();
 }
