@@ -67,8 +67,13 @@ Prob make_prob(const mgfld_dims *d, const mgfld_problem *p);
 // thermal de Broglie terms of mu_p and mu_n cancel in mu_e + mu_p - mu_n).
 // ZC_E*: constants of the outer edge i+1/2 of zone i (for the last zone, the edge to the
 // ghost): 1/(3 (R_{i+1} - R_i)), 4 pi R_{i+1/2}^2 / a_{i+1/2}^2 and 1/R_{i+1/2}^2 (Eq. a59).
+// ZC_INV_T = 1/T^n; ZC_EMU, ZC_EMUI = e^{+-mu/T^n} for the factored emissivity exponentials
+// e^{(mu_q - eps)/T} = e^{mu_q/T} e^{-eps/T} of the mixed path (-1 where |mu/T| >= kEmuMax,
+// which takes the direct form).
 enum { ZC_PRE = 0, ZC_INV_ACDT = 1, ZC_INV_A = 2, ZC_VOL = 3, ZC_MU = 4, ZC_A = 5, ZC_ACDT = 6,
-       ZC_MUA = 7, ZC_MUB = 8, ZC_EI3DR = 9, ZC_EGEO = 10, ZC_EIR2 = 11, ZC_N = 12 };
+       ZC_MUA = 7, ZC_MUB = 8, ZC_EI3DR = 9, ZC_EGEO = 10, ZC_EIR2 = 11, ZC_INV_T = 12, ZC_EMU = 13,
+       ZC_EMUI = 14, ZC_N = 15 };
+constexpr double kEmuMax = 600.0;
 
 // Pointers resolved from a layout.
 struct Ws {

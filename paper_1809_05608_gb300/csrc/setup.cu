@@ -56,6 +56,17 @@ __global__ void k_zone(Prob p, Ws w, const double *__restrict__ ye, const double
   z[ZC_EI3DR] = 1.0 / (3.0 * (r_r - r_i));
   z[ZC_EGEO] = 4.0 * kPi * rp * rp / (a_e * a_e);
   z[ZC_EIR2] = 1.0 / (rp * rp);
+  const double inv_T = 1.0 / T[t];
+  const double xm = mu * inv_T;
+  z[ZC_INV_T] = inv_T;
+  if (fabs(xm) < kEmuMax) {
+    const double em = exp(xm);
+    z[ZC_EMU] = em;
+    z[ZC_EMUI] = 1.0 / em;
+  } else {
+    z[ZC_EMU] = -1.0;
+    z[ZC_EMUI] = -1.0;
+  }
 }
 
 // Weighted NES kernels of zone (ray, i) (Eqs. d7down, d7up): down/iso-scattering
@@ -80,6 +91,65 @@ static inline int phi_zones_per_block(int n) {
 }
 static inline size_t phi_smem_bytes(int n) { return (size_t)phi_zones_per_block(n) * phi_zone_bytes(n); }
 
+// Rows ka = t and kb = n-1-t of one zone's kernels into the staged tiles so (out) and si (in)
+// (row stride ld), from the zone's consecutive-group ratios gap[m] and weights cw[m]; returns
+// the two rows' sums of the out-kernel (equal rows of odd n: the middle row, both chains).
+// Down-scattering entries run along a row as P = prod gap (one multiply per step) with the
+// up-scattering partner o P = cw P^2; up-scattering entries likewise from Q = prod gap.
+__device__ inline void phi_chains(int n, int t, const double *gap, const double *cw, double *so, double *si, int ld,
+                                  double &rs_a, double &rs_b) {
+  const int ka = t, kb = n - 1 - t;                     // ka <= kb; equal for the middle row of odd n
+  double *oa = so + (size_t)ka * ld, *ia = si + (size_t)ka * ld;
+  double *ob = so + (size_t)kb * ld, *ib = si + (size_t)kb * ld;
+  double rsa = cw[ka], rsb = (ka == kb) ? 0.0 : cw[kb];
+  oa[ka] = cw[ka];
+  ia[ka] = cw[ka];
+  ob[kb] = cw[kb];
+  ib[kb] = cw[kb];
+  // Down-scattering (k' < k): row ka's ka entries, then row kb's kb entries (n - 1 steps).
+  double P = 1.0;
+  for (int j = 0; j < n - 1; ++j) {
+    const bool first = j < ka;
+    if (!first && ka == kb) break;                      // middle row: its chain is already done
+    const int kp = first ? ka - 1 - j : kb - 1 - (j - ka);
+    if (j == ka) P = 1.0;
+    P *= gap[kp + 1];                                   // e^{-(eps_k - eps_kp)/T}
+    const double o = cw[kp] * P;                        // down-scattering k -> kp
+    const double v = o * P;                             // up-scattering kp -> k: cw e^{-2(eps_k - eps_kp)/T}
+    if (first) { oa[kp] = o; ia[kp] = v; rsa += o; } else { ob[kp] = o; ib[kp] = v; rsb += o; }
+  }
+  // Up-scattering (k' > k): row kb's n-1-kb entries, then row ka's n-1-ka entries.
+  const int nb = n - 1 - kb;
+  double Q = 1.0;
+  for (int j = 0; j < n - 1; ++j) {
+    const bool first = j < nb;
+    if (!first && ka == kb) break;
+    const int kp = first ? kb + 1 + j : ka + 1 + (j - nb);
+    if (j == nb) Q = 1.0;
+    Q *= gap[kp];                                       // e^{-(eps_kp - eps_k)/T}
+    const double v = cw[kp] * Q;                        // down-scattering kp -> k
+    const double o = v * Q;                             // up-scattering k -> kp
+    if (first) { ob[kp] = o; ib[kp] = v; rsb += o; } else { oa[kp] = o; ia[kp] = v; rsa += o; }
+  }
+  if (kb != ka) {
+    rs_a = rsa;
+    rs_b = rsb;
+  } else {
+    rs_a = rs_b = rsa + rsb;
+  }
+}
+
+// The consecutive-group ratios e^{-(eps_m - eps_{m-1})/T} and weights C w_m = C W_m / a^3 of one
+// zone into shared memory, the zone's H threads striding over the groups.
+__device__ inline void phi_zone_consts(const Ws &w, int n, int t, int H, double inv_a, double Ti, double nes,
+                                       double *gap, double *cw) {
+  const double cc = kCNes * inv_a * inv_a * inv_a * nes;
+  for (int k = t; k < n; k += H) {
+    if (k > 0) gap[k] = exp(-(w.E[k] - w.E[k - 1]) * inv_a / Ti);
+    cw[k] = cc * w.W[k];
+  }
+}
+
 __global__ void k_phi(Prob p, Ws w, const double *__restrict__ T, int zpb) {
   extern __shared__ double smem[];
   const int n = p.n, H = (n + 1) / 2, ld = n + 1;
@@ -88,79 +158,39 @@ __global__ void k_phi(Prob p, Ws w, const double *__restrict__ T, int zpb) {
   double *sout = cwm + (size_t)zpb * n;                   // [zpb][n][n + 1]
   double *sin_ = sout + (size_t)zpb * n * ld;             // [zpb][n][n + 1]
   const int zl = threadIdx.x / H, t = threadIdx.x % H;
-  const size_t nz = (size_t)p.n_ray * p.n_r;
-  const size_t z0 = (size_t)blockIdx.x * zpb;
-  const size_t zi = z0 + zl;
+  const unsigned nz = (unsigned)(p.n_ray * p.n_r);
+  const unsigned z0 = blockIdx.x * (unsigned)zpb;
+  const unsigned zi = z0 + zl;
   const bool live = zl < zpb && zi < nz;
-  const int ray = live ? (int)(zi / p.n_r) : 0, i = live ? (int)(zi % p.n_r) : 0;
-  const double inv_a = live ? 1.0 / lapse_at(p, ray, i) : 1.0;
-  const double Ti = live ? T[zi] : 1.0;
   double *gap = gapm + (size_t)(live ? zl : 0) * n;
   double *cw = cwm + (size_t)(live ? zl : 0) * n;
   if (live) {
-    const double cc = kCNes * inv_a * inv_a * inv_a * (p.nes ? p.nes[zi] : 0.0);
-    for (int k = t; k < n; k += H) {
-      if (k > 0) gap[k] = exp(-(w.E[k] - w.E[k - 1]) * inv_a / Ti);
-      cw[k] = cc * w.W[k];
-    }
+    const int ray = (int)(zi / (unsigned)p.n_r), i = (int)(zi - (unsigned)ray * p.n_r);
+    phi_zone_consts(w, n, t, H, 1.0 / lapse_at(p, ray, i), T[zi], p.nes ? p.nes[zi] : 0.0, gap, cw);
   }
   __syncthreads();
   if (live) {
-    const int ka = t, kb = n - 1 - t;                   // ka <= kb; equal for the middle row of odd n
-    double *oa = sout + ((size_t)zl * n + ka) * ld, *ia = sin_ + ((size_t)zl * n + ka) * ld;
-    double *ob = sout + ((size_t)zl * n + kb) * ld, *ib = sin_ + ((size_t)zl * n + kb) * ld;
-    double rsa = cw[ka], rsb = (ka == kb) ? 0.0 : cw[kb];
-    oa[ka] = cw[ka];
-    ia[ka] = cw[ka];
-    ob[kb] = cw[kb];
-    ib[kb] = cw[kb];
-    // Down-scattering (k' < k): row ka's ka entries, then row kb's kb entries (n - 1 steps).
-    double P = 1.0;
-    for (int j = 0; j < n - 1; ++j) {
-      const bool first = j < ka;
-      if (!first && ka == kb) break;                    // middle row: its chain is already done
-      const int kp = first ? ka - 1 - j : kb - 1 - (j - ka);
-      if (j == ka) P = 1.0;
-      P *= gap[kp + 1];                                 // e^{-(eps_k - eps_kp)/T}
-      const double o = cw[kp] * P;                      // down-scattering k -> kp
-      const double v = cw[kp] * (P * P);                // up-scattering kp -> k
-      if (first) { oa[kp] = o; ia[kp] = v; rsa += o; } else { ob[kp] = o; ib[kp] = v; rsb += o; }
-    }
-    // Up-scattering (k' > k): row kb's n-1-kb entries, then row ka's n-1-ka entries.
-    const int nb = n - 1 - kb;
-    double Q = 1.0;
-    for (int j = 0; j < n - 1; ++j) {
-      const bool first = j < nb;
-      if (!first && ka == kb) break;
-      const int kp = first ? kb + 1 + j : ka + 1 + (j - nb);
-      if (j == nb) Q = 1.0;
-      Q *= gap[kp];                                     // e^{-(eps_kp - eps_k)/T}
-      const double o = cw[kp] * (Q * Q);                // up-scattering k -> kp
-      const double v = cw[kp] * Q;                      // down-scattering kp -> k
-      if (first) { ob[kp] = o; ib[kp] = v; rsb += o; } else { oa[kp] = o; ia[kp] = v; rsa += o; }
-    }
-    if (kb != ka) {
-      w.rsum[zi * n + ka] = rsa;
-      w.rsum[zi * n + kb] = rsb;
-    } else {
-      w.rsum[zi * n + ka] = rsa + rsb;                  // middle row of odd n: both chains are its own
-    }
+    double rsa, rsb;
+    phi_chains(n, t, gap, cw, sout + (size_t)zl * n * ld, sin_ + (size_t)zl * n * ld, ld, rsa, rsb);
+    w.rsum[(size_t)zi * n + t] = rsa;
+    if (n - 1 - t != t) w.rsum[(size_t)zi * n + (n - 1 - t)] = rsb;
   }
   __syncthreads();
-  // Coalesced copy of the block's zones (contiguous in [ray][zone][k][k'] order).  The FP32
-  // copies of the mixed path are made by exponent/mantissa bit arithmetic (integer pipe,
-  // truncating): only the difference in - out uses the FP64 pipe.
-  const size_t nzb = (z0 + zpb <= nz) ? (size_t)zpb : nz - z0;
-  const size_t cnt = nzb * n * n;
-  const size_t base = z0 * n * n;
-  for (size_t e = threadIdx.x; e < cnt; e += blockDim.x) {
-    const size_t row = e / n, col = e - row * n;
+  // Coalesced copy of the block's zones (contiguous in [ray][zone][k][k'] order).
+  const unsigned nzb = (z0 + zpb <= nz) ? (unsigned)zpb : nz - z0;
+  const unsigned cnt = nzb * n * n;
+  const size_t base = (size_t)z0 * n * n;
+  for (unsigned e = threadIdx.x; e < cnt; e += blockDim.x) {
+    const unsigned row = e / (unsigned)n, col = e - row * n;
     const double o = sout[row * ld + col], v = sin_[row * ld + col];
     w.phout[base + e] = o;
     w.phin[base + e] = v;
     if (w.phin32) {
-      w.phin32[base + e] = d2f_exp2(v, 0);
-      w.phd32[base + e] = d2f_exp2(v - o, 0);
+      // FP32 copies for the mixed path's Jacobian by exponent/mantissa bit arithmetic (integer
+      // pipe, truncating); in - out is taken in FP32 (a preconditioner entry).
+      const float vf = d2f_exp2(v, 0);
+      w.phin32[base + e] = vf;
+      w.phd32[base + e] = __fsub_rn(vf, d2f_exp2(o, 0));
     } else {
       w.phd[base + e] = v - o;
     }
@@ -187,20 +217,27 @@ __global__ void k_jlam(Prob p, Ws w, const double *__restrict__ psi, const doubl
   const double *fin = w.phin + (zi * n + k) * n;
   const double *fout = w.phout + (zi * n + k) * n;
   const double rs = w.rsum[zi * n + k];
+  // MIXED: e^{(mu_q - eps)/T} = e^{mu_q/T} e^{-eps/T} with the zone's factors (one exponential
+  // per thread); the FP64 path, and zones with |mu/T| too large for the factors, take the
+  // direct form.
+  const double emu = w.phin32 ? z[ZC_EMU] : -1.0;
+  const double ex = emu > 0.0 ? exp(-eps * z[ZC_INV_T]) : 0.0;
   double e_mu0 = 0.0;
   for (int q = 0; q < NS; ++q) {
     const size_t g = (((size_t)ray * NS + q) * p.n_r + i) * n + k;
     const double sc = p.scale ? p.scale[q * n + k] : 1.0;
     const double kap = p.kabs[g] * sc, ksc = p.kscat[g] * sc;
-    double j;
-    if (q == 3) {
-      j = kap * e_mu0;                     // same exponent as q = 2 (mu = 0)
+    double e1;
+    if (emu > 0.0) {
+      e1 = q == 0 ? ex * emu : (q == 1 ? ex * z[ZC_EMUI] : ex);
+    } else if (q == 3) {
+      e1 = e_mu0;                          // same exponent as q = 2 (mu = 0)
     } else {
       bool live;
-      j = emissivity(1.0, species_mu(q, mu), eps, Ti, live);
-      if (q == 2) e_mu0 = j;
-      j *= kap;
+      e1 = emissivity(1.0, species_mu(q, mu), eps, Ti, live);
+      if (q == 2) e_mu0 = e1;
     }
+    const double j = kap * e1;
     w.jbuf[g] = j;
     const double *ps = psi + (g - k);
     double gain = 0.0, lp = 0.0;
