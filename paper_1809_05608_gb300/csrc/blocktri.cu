@@ -299,111 +299,209 @@ k_solve(int n, int n_r, int n_sys, const double *__restrict__ dinv, const double
 }
 
 // ---------------------------------------------------------------------------------------
-// Warp-synchronous FP32 variants (MIXED precision): one warp per (ray, species) system, lane r
-// owns block row r (NP <= 32), no CTA-wide barriers.  The pivot is found with a warp max
-// reduction on integer keys, the pivot row is broadcast with shuffles, and the per-zone
-// natural-order inverse goes through a per-warp shared-memory tile.  FP32 arithmetic is 63x
-// cheaper than FP64 on this GPU, so these kernels are bound by the dependency chain along
-// the zones, which the warp form shortens.
+// Warp-synchronous FP32 variants (MIXED precision): one warp per half of a (ray, species)
+// system, lane r owns block row r (NP <= 32), no CTA-wide barriers.  FP32 arithmetic is 63x
+// cheaper than FP64 on this GPU, so these kernels are bound by the dependency chain along the
+// zones and by the instruction and shared-memory traffic of each zone step.
 constexpr int kWarpsPerCta = 4;
 
+// Per-thread 16-byte asynchronous global-to-shared copies (completion waited by the issuing thread).
+__device__ inline void cp_async16(void *dst, const void *src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((unsigned)__cvta_generic_to_shared(dst)), "l"(src)
+               : "memory");
+}
+__device__ inline void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ inline void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+// Packed FP32 helpers (two lanes of arithmetic per instruction).
+__device__ inline void fma2_row(float *a, float s, const float *p, int c) {
+  const float2 r = __ffma2_rn(make_float2(s, s), make_float2(p[c], p[c + 1]), make_float2(a[c], a[c + 1]));
+  a[c] = r.x;
+  a[c + 1] = r.y;
+}
+
+// In-place Gauss-Jordan inverse with partial pivoting of the warp's NP x NP zone block, lane r
+// holding row r.  The pivot is found with a warp max reduction on integer keys (|a| bits with
+// the row index in the 5 low bits), the pivot row is broadcast through a double-buffered
+// shared-memory row (one 16-byte store per 4 entries by its owner, broadcast 16-byte loads by
+// every lane), and the eliminations run as packed FP32 FMAs.  Returns with a[] holding row
+// my_step of the inverse with column c belonging to natural column piv(c) (byte c % 4 of
+// piv[c / 4]).
+template <int NP>
+__device__ inline void gj_invert(float *a, float (*prow)[NP], int r, bool row, int &my_step, unsigned *piv) {
+  const unsigned full = 0xffffffffu;
+  bool used = !row;
+  my_step = 0;
+  int key = used ? -1 : (int)(((unsigned)__float_as_int(fabsf(a[0])) & ~31u) | (unsigned)(31 - r));
+#pragma unroll
+  for (int ps = 0; ps < NP; ++ps) {
+    const int best = 31 - (__reduce_max_sync(full, key) & 31);
+    if (ps % 4 == 0) piv[ps / 4] = (unsigned)best;      // four 8-bit pivot rows per register
+    else piv[ps / 4] |= (unsigned)best << (8 * (ps % 4));
+    const bool me = (r == best);
+    float *pb = prow[ps & 1];
+    if (me) {
+      used = true;
+      my_step = ps;
+#pragma unroll
+      for (int c = 0; c < NP; c += 4)
+        *reinterpret_cast<float4 *>(pb + c) = make_float4(a[c], a[c + 1], a[c + 2], a[c + 3]);
+    }
+    __syncwarp();
+    float pv[NP];
+#pragma unroll
+    for (int c = 0; c < NP; c += 4) {
+      const float4 v = *reinterpret_cast<const float4 *>(pb + c);
+      pv[c] = v.x;
+      pv[c + 1] = v.y;
+      pv[c + 2] = v.z;
+      pv[c + 3] = v.w;
+    }
+    const float inv = __frcp_rn(pv[ps]);
+    const float f = fmaf(me ? -1.f : a[ps], inv, me ? 1.f : 0.f);
+    // the pair holding the next pivot column first, so that the next search can start
+    if (ps + 1 < NP) {
+      const int cn = (ps + 1) & ~1;
+      fma2_row(a, -f, pv, cn);
+      key = used ? -1 : (int)(((unsigned)__float_as_int(fabsf(a[ps + 1])) & ~31u) | (unsigned)(31 - r));
+#pragma unroll
+      for (int c = 0; c < NP; c += 2)
+        if (c != cn) fma2_row(a, -f, pv, c);
+    } else {
+#pragma unroll
+      for (int c = 0; c < NP; c += 2) fma2_row(a, -f, pv, c);
+    }
+    a[ps] = me ? inv : -f;
+  }
+}
+
+// Warps per CTA of the factor: four (two systems), two for the widest blocks so that the
+// static shared memory (two row buffers and the inverse tile per warp) stays under 48 KB.
+template <int NP> __host__ __device__ constexpr int fw_wpc() { return NP > 24 ? 2 : 4; }
+
+// At most 128 registers (NP <= 24), so that four CTAs (eight systems) fit on an SM and the
+// 256-ray workload's 512 CTAs run in a single wave on 152 SMs.
 template <int NP, typename TIn, typename TC>
-__global__ void __launch_bounds__(kWarpsPerCta * 32)
+__global__ void __launch_bounds__(fw_wpc<NP>() * 32, 4)
 k_factor_w32(int n, int n_r, int n_sys, const TIn *__restrict__ diag, const TC *__restrict__ lower,
              const TC *__restrict__ upper, float *__restrict__ dinv, const int *__restrict__ ray_list) {
-  __shared__ float tile[kWarpsPerCta][NP][NP + 1];
-  __shared__ float ushr[kWarpsPerCta][NP];
-  const unsigned full = 0xffffffffu;
+  static_assert(NP % 4 == 0, "rows of NP floats in 16-byte pieces");
+  // tile: the natural-order inverse of each warp's last zone (read by the other half at the
+  // middle zone); ushr: that zone's coupling to the next zone of the sequence; prow: pivot rows.
+  constexpr int W = fw_wpc<NP>();
+  __shared__ __align__(16) float tile[W][NP][NP];
+  __shared__ __align__(16) float ushr[W][NP];
+  __shared__ __align__(16) float prow[W][2][NP];
+  __shared__ __align__(16) float rowbuf[W][2][NP][NP];
   const int wid = threadIdx.x >> 5, r = threadIdx.x & 31;
   const int half = wid & 1;                          // 0: zones 0..m top-down, 1: zones n_r-1..m+1 bottom-up
-  const long jsys = (long)blockIdx.x * (kWarpsPerCta / 2) + (wid >> 1);
+  const long jsys = (long)blockIdx.x * (W / 2) + (wid >> 1);
   if (jsys >= n_sys) return;                        // both warps of the system leave; no barrier below
   const long sys = system_of(jsys, ray_list);
   const bool real = r < n;
   const bool row = r < NP;
+  const bool vec = (n == NP) && sizeof(TIn) == 4;    // 16-byte row loads and stores
   const int m = n_r / 2;
   const int len = half == 0 ? m + 1 : n_r - 1 - m;
   auto zone = [&](int j) { return half == 0 ? j : n_r - 1 - j; };
-  float nxt[NP];
-  float nl = 0.f;
+  // Next zone's rows, fetched one zone ahead into a double-buffered shared-memory block (each
+  // lane its own row: 16-byte asynchronous copies on the fast path, so no registers hold the
+  // prefetch), and its couplings into registers.  The coupling loads are unconditional (lanes
+  // without a row read row 0) with the conditions applied when the values are consumed, so that
+  // no instruction waits on a load in the zone it was issued.
+  const int rr = real ? r : 0;
+  TC nl_raw = TC(0), nu_raw = TC(0);
   auto load_row = [&](int j) {
     const int z = zone(j);
-    const size_t zr = ((size_t)sys * n_r + z) * n + r;
+    const size_t zr = ((size_t)sys * n_r + z) * n + rr;
+    float *dst = &rowbuf[wid][j & 1][row ? r : 0][0];
+    if (vec) {
+      if (row) {
 #pragma unroll
-    for (int c = 0; c < NP; ++c) {
-      if (real && c < n) nxt[c] = (float)diag[zr * n + c];
-      else nxt[c] = (c == r) ? 1.f : 0.f;
+        for (int c = 0; c < NP; c += 4) cp_async16(dst + c, diag + zr * n + c);
+      }
+      cp_async_commit();
+    } else if (row) {
+#pragma unroll
+      for (int c = 0; c < NP; ++c) dst[c] = (real && c < n) ? (float)diag[zr * n + c] : ((c == r) ? 1.f : 0.f);
     }
-    // coupling to the previous zone of this half's sequence (row scaling of its Schur term)
-    nl = (real && j > 0) ? (float)(half == 0 ? lower[zr] : upper[zr]) : 0.f;
+    // couplings to the previous zone of this half's sequence (row scaling of its Schur term)
+    // and to the next one (column scaling of this zone's Schur term)
+    nl_raw = half == 0 ? lower[zr] : upper[zr];
+    nu_raw = half == 0 ? upper[zr] : lower[zr];
   };
   if (len > 0) load_row(0);
   for (int j = 0; j < len; ++j) {
     const int z = zone(j);
     const size_t zrow = ((size_t)sys * n_r + z) * n + r;
     float a[NP];
+    if (vec) cp_async_wait_all();
+    if (row) {
 #pragma unroll
-    for (int c = 0; c < NP; ++c) a[c] = nxt[c];
-    const float lr = nl;
+      for (int c = 0; c < NP; c += 4) {
+        const float4 v = *reinterpret_cast<const float4 *>(&rowbuf[wid][j & 1][r][c]);
+        a[c] = v.x;
+        a[c + 1] = v.y;
+        a[c + 2] = v.z;
+        a[c + 3] = v.w;
+      }
+    } else {
+#pragma unroll
+      for (int c = 0; c < NP; ++c) a[c] = 0.f;
+    }
+    const float lr = (real && j > 0) ? (float)nl_raw : 0.f;
+    const float ur = real ? (float)nu_raw : 0.f;
     if (j + 1 < len) load_row(j + 1);
     if (j > 0 && row) {
+      // a -= diag(l) Dinv_prev diag(u_prev): row scale lr, column scale ushr; row r of the
+      // previous zone's inverse is still in this warp's tile.
 #pragma unroll
-      for (int c = 0; c < NP; ++c) a[c] = a[c] - (lr * tile[wid][r][c]) * ushr[wid][c];
+      for (int c = 0; c < NP; c += 4) {
+        const float4 u = *reinterpret_cast<const float4 *>(&ushr[wid][c]);
+        const float4 d = *reinterpret_cast<const float4 *>(&tile[wid][r][c]);
+        const float2 t0 = __fmul2_rn(make_float2(-lr, -lr), make_float2(d.x, d.y));
+        const float2 t1 = __fmul2_rn(make_float2(-lr, -lr), make_float2(d.z, d.w));
+        const float2 r0 = __ffma2_rn(t0, make_float2(u.x, u.y), make_float2(a[c], a[c + 1]));
+        const float2 r1 = __ffma2_rn(t1, make_float2(u.z, u.w), make_float2(a[c + 2], a[c + 3]));
+        a[c] = r0.x;
+        a[c + 1] = r0.y;
+        a[c + 2] = r1.x;
+        a[c + 3] = r1.y;
+      }
     }
     if (half == 0 && j == m) {
       // Middle zone: wait for the bottom-up half of this system, then subtract its Schur term
       // diag(u_m) D''^{-1}_{m+1} diag(l_{m+1}) as well.
       asm volatile("bar.sync %0, 64;" ::"r"(1 + (wid >> 1)) : "memory");
       if (n_r - 1 > m && row) {
-        const float um = real ? (float)upper[zrow] : 0.f;
+        const float um = ur;                         // u_m: half 0's coupling to zone m + 1
 #pragma unroll
         for (int c = 0; c < NP; ++c) a[c] = a[c] - (um * tile[wid ^ 1][r][c]) * ushr[wid ^ 1][c];
       }
     }
-    bool used = !row;
-    int my_step = 0;
-    int piv[NP];
-    // Pivot-search key as in the FP64 factor: |a| bits with the row index in the 5 low bits, so
-    // one warp max names the pivot row.  The pivot and next-pivot-column entries of the pivot
-    // row are broadcast first and the next pivot column is updated first, so that the next
-    // search overlaps the broadcast and update of the other columns.
-    int key = used ? -1 : (int)(((unsigned)__float_as_int(fabsf(a[0])) & ~31u) | (unsigned)(31 - r));
-#pragma unroll
-    for (int pstep = 0; pstep < NP; ++pstep) {
-      const int best = 31 - (__reduce_max_sync(full, key) & 31);
-      piv[pstep] = best;
-      const bool me = (r == best);
-      if (me) {
-        used = true;
-        my_step = pstep;
-      }
-      const float pp = __shfl_sync(full, a[pstep], best);
-      const float inv = __frcp_rn(pp);
-      const float f = fmaf(me ? -1.f : a[pstep], inv, me ? 1.f : 0.f);
-      if (pstep + 1 < NP) {
-        const float pn = __shfl_sync(full, a[pstep + 1], best);
-        a[pstep + 1] = fmaf(-f, pn, a[pstep + 1]);
-        key = used ? -1 : (int)(((unsigned)__float_as_int(fabsf(a[pstep + 1])) & ~31u) | (unsigned)(31 - r));
-      }
-#pragma unroll
-      for (int c = 0; c < NP; ++c)
-        if (c != pstep + 1 && c != pstep) a[c] = fmaf(-f, __shfl_sync(full, a[c], best), a[c]);
-      a[pstep] = me ? inv : -f;
-    }
-    __syncwarp();
+    int my_step;
+    unsigned piv[NP / 4];
+    gj_invert<NP>(a, prow[wid], r, row, my_step, piv);
+    __syncwarp();                  // every lane has read the previous zone's tile row
     if (row) {
 #pragma unroll
-      for (int c = 0; c < NP; ++c) tile[wid][my_step][piv[c]] = a[c];
-      // coupling of this zone to the next zone of the sequence (column scaling of its Schur term)
-      ushr[wid][r] = real ? (float)(half == 0 ? upper[zrow] : lower[zrow]) : 0.f;
+      for (int c = 0; c < NP; ++c) tile[wid][my_step][(piv[c / 4] >> (8 * (c % 4))) & 0xffu] = a[c];
     }
     __syncwarp();
+    if (row) ushr[wid][r] = ur;   // column scaling of this zone's Schur term in the next zone
     if (real) {
       float *out = dinv + zrow * n;
+      if (vec) {
 #pragma unroll
-      for (int c = 0; c < NP; ++c)
-        if (c < n) out[c] = tile[wid][r][c];
+        for (int c = 0; c < NP; c += 4)
+          *reinterpret_cast<float4 *>(out + c) = *reinterpret_cast<const float4 *>(&tile[wid][r][c]);
+      } else {
+#pragma unroll
+        for (int c = 0; c < NP; ++c)
+          if (c < n) out[c] = tile[wid][r][c];
+      }
     }
+    __syncwarp();
   }
   if (half == 1) asm volatile("bar.sync %0, 64;" ::"r"(1 + (wid >> 1)) : "memory");
 }
@@ -674,10 +772,15 @@ k_solve_tma(int n, int n_r, int n_sys, const float *__restrict__ dinv, const flo
     __syncwarp();
     if (r == 0 && ok && iu < U) issue_next();
   };
-  // Per-lane queue of (rhs or forward result, coupling) for the uses ahead, D deep, as loaded
-  // (converted when consumed, so each load has D steps to arrive).
+  // Per-lane queue of (rhs or forward result, coupling) for the uses ahead, D deep.  The loads
+  // are unconditional (clamped to a valid zone) and converted or masked when consumed, so each
+  // load has D steps to arrive and no instruction waits on it earlier.
   double qa[D];
-  float qb[D];
+  float qb[D], qg[D];
+  // the middle zone's right-hand side and couplings (top-down half), fetched up front
+  const size_t zm = (size_t)m * n;
+  const double bm_raw = rhs_l[zm];
+  const float lm_raw = cin_l[zm], um_raw = cout_l[zm];
   float *vb = vbuf[half];
 
   if (r == 0)
@@ -687,8 +790,9 @@ k_solve_tma(int n, int n_r, int n_sys, const float *__restrict__ dinv, const flo
 #pragma unroll
   for (int d = 0; d < D; ++d) {
     const int z = zf0 + d * dz;
-    qa[d] = (real && d < F) ? rhs_l[(size_t)z * n] : 0.0;
-    qb[d] = (real && d < F && d > 0) ? cin_l[(size_t)z * n] : 0.f;
+    const int zc = d < F ? z : zf0;
+    qa[d] = rhs_l[(size_t)zc * n];
+    qb[d] = cin_l[(size_t)zc * n];
   }
   float prev = 0.f;
   int zf = zf0;
@@ -697,11 +801,12 @@ k_solve_tma(int n, int n_r, int n_sys, const float *__restrict__ dinv, const flo
     for (int d = 0; d < D; ++d) {
       const int j = j0 + d;
       if (j >= F) break;
-      const float b = d2f_exp2(qa[d], kexp), l = qb[d];
+      const float b = d2f_exp2(qa[d], kexp), l = j > 0 ? qb[d] : 0.f;
       const int zq = zf + D * dz;                 // refill this slot with the zone D steps ahead
       const bool more = real && j + D < F;
-      qa[d] = more ? rhs_l[(size_t)zq * n] : 0.0;
-      qb[d] = more ? cin_l[(size_t)zq * n] : 0.f;
+      const int zqc = more ? zq : zf;
+      qa[d] = rhs_l[(size_t)zqc * n];
+      qb[d] = cin_l[(size_t)zqc * n];
       if (wait(j)) {
         if (r < NP) vb[r] = real ? b - l * prev : 0.f;
         __syncwarp();
@@ -717,10 +822,9 @@ k_solve_tma(int n, int n_r, int n_sys, const float *__restrict__ dinv, const flo
   __syncthreads();
   if (half == 0) {
     // Middle zone: x_m = Dinv_m (r_m - l_m g_{m-1} - u_m h_{m+1}).
-    const size_t zm = (size_t)m * n;
-    const float bm = real ? d2f_exp2(rhs_l[zm], kexp) : 0.f;
-    const float lm = (real && m > 0) ? lower[sb + zm + r] : 0.f;
-    const float um = (real && m < n_r - 1) ? upper[sb + zm + r] : 0.f;
+    const float bm = real ? d2f_exp2(bm_raw, kexp) : 0.f;
+    const float lm = (real && m > 0) ? lm_raw : 0.f;
+    const float um = (real && m < n_r - 1) ? um_raw : 0.f;
     float xm = 0.f;
     if (wait(m)) {
       if (r < NP) vb[r] = real ? bm - lm * prev - um * hbuf[r] : 0.f;
@@ -738,8 +842,9 @@ k_solve_tma(int n, int n_r, int n_sys, const float *__restrict__ dinv, const flo
 #pragma unroll
   for (int d = 0; d < D; ++d) {
     const int z = zb0 - d * dz;
-    qa[d] = (real && d < F) ? (double)g_l[(size_t)z * n] : 0.0;
-    qb[d] = (real && d < F) ? cout_l[(size_t)z * n] : 0.f;
+    const int zc = d < F ? z : m;                 // m: a valid zone whatever F is
+    qg[d] = g_l[(size_t)zc * n];
+    qb[d] = cout_l[(size_t)zc * n];
   }
   int zb = zb0;
   const int ub = U - F;                           // first backward use
@@ -749,11 +854,12 @@ k_solve_tma(int n, int n_r, int n_sys, const float *__restrict__ dinv, const flo
       const int j = j0 + d;
       if (j >= F) break;
       const int u = ub + j;
-      const float gz = (float)qa[d], c = qb[d];
+      const float gz = qg[d], c = qb[d];
       const int zq = zb - D * dz;
       const bool more = real && j + D < F;
-      qa[d] = more ? (double)g_l[(size_t)zq * n] : 0.0;
-      qb[d] = more ? cout_l[(size_t)zq * n] : 0.f;
+      const int zqc = more ? zq : zb;
+      qg[d] = g_l[(size_t)zqc * n];
+      qb[d] = cout_l[(size_t)zqc * n];
       if (wait(u)) {
         if (r < NP) vb[r] = real ? c * prev : 0.f;
         __syncwarp();
@@ -815,15 +921,18 @@ cudaError_t launch_factor(int n, int n_r, int n_sys, const void *diag, int diag_
                           cudaStream_t s) {
   if (n_sys == 0) return cudaSuccess;
   if (precision == MGFLD_MIXED) {
-    const unsigned grid = (unsigned)((n_sys + kWarpsPerCta / 2 - 1) / (kWarpsPerCta / 2));
     if (diag_fp32) {
-      MGFLD_DISPATCH_NP(n, k_factor_w32<NP, float, double><<<grid, kWarpsPerCta * 32, 0, s>>>(
-                               n, n_r, n_sys, (const float *)diag, lower, upper, (float *)dinv, ray_list);
-                           return cudaGetLastError())
+      MGFLD_DISPATCH_NP(n, constexpr int W = fw_wpc<NP>();
+                        const unsigned grid = (unsigned)((n_sys + W / 2 - 1) / (W / 2));
+                        k_factor_w32<NP, float, double><<<grid, W * 32, 0, s>>>(
+                            n, n_r, n_sys, (const float *)diag, lower, upper, (float *)dinv, ray_list);
+                        return cudaGetLastError())
     } else {
-      MGFLD_DISPATCH_NP(n, k_factor_w32<NP, double, double><<<grid, kWarpsPerCta * 32, 0, s>>>(
-                               n, n_r, n_sys, (const double *)diag, lower, upper, (float *)dinv, ray_list);
-                           return cudaGetLastError())
+      MGFLD_DISPATCH_NP(n, constexpr int W = fw_wpc<NP>();
+                        const unsigned grid = (unsigned)((n_sys + W / 2 - 1) / (W / 2));
+                        k_factor_w32<NP, double, double><<<grid, W * 32, 0, s>>>(
+                            n, n_r, n_sys, (const double *)diag, lower, upper, (float *)dinv, ray_list);
+                        return cudaGetLastError())
     }
   } else {
     MGFLD_DISPATCH_NP(n, return (run_factor<NP>(n, n_r, n_sys, diag, diag_fp32, lower, upper, dinv,
@@ -834,10 +943,11 @@ cudaError_t launch_factor(int n, int n_r, int n_sys, const void *diag, int diag_
 cudaError_t launch_factor_f32(int n, int n_r, int n_sys, const float *diag, const float *lower32,
                               const float *upper32, float *dinv, const int *ray_list, cudaStream_t s) {
   if (n_sys == 0) return cudaSuccess;
-  const unsigned grid = (unsigned)((n_sys + kWarpsPerCta / 2 - 1) / (kWarpsPerCta / 2));
-  MGFLD_DISPATCH_NP(n, k_factor_w32<NP, float, float><<<grid, kWarpsPerCta * 32, 0, s>>>(
-                           n, n_r, n_sys, diag, lower32, upper32, dinv, ray_list);
-                       return cudaGetLastError())
+  MGFLD_DISPATCH_NP(n, constexpr int W = fw_wpc<NP>();
+                    const unsigned grid = (unsigned)((n_sys + W / 2 - 1) / (W / 2));
+                    k_factor_w32<NP, float, float><<<grid, W * 32, 0, s>>>(n, n_r, n_sys, diag, lower32, upper32,
+                                                                            dinv, ray_list);
+                    return cudaGetLastError())
 }
 
 cudaError_t launch_solve(int n, int n_r, int n_sys, const void *dinv, const double *lower,
