@@ -96,16 +96,48 @@ __global__ void k_assemble(Prob p, Ws w, const double *__restrict__ psi, TD *__r
   if (jac_flag && !jac_flag[ray]) return;
   const double dg = inv_acdt + pre * (al_out * (1.0 - gh) + al_in) + j + kap + (gain + loss);
   TD *row = diag + g * n;
-  // dS_k/dpsi_k' = (1 - psi_k) phin + psi_k phout = phin - psi_k phd, entered with a minus.
+  // dS_k/dpsi_k' = (1 - psi_k) phin + psi_k phout = phin - psi_k phd, entered with a minus;
+  // dg joins the diagonal entry in FP64.  Rows are written 16 bytes at a time where n allows
+  // (the rows of one warp's threads are 16-byte aligned and contiguous per species).
   if (sizeof(TD) == 4 && w.phin32) {
     const float *fi = w.phin32 + (zi * n + k) * n, *fd = w.phd32 + (zi * n + k) * n;
     const float pf = (float)pk;
-    for (int kp = 0; kp < n; ++kp) row[kp] = TD(fmaf(pf, fd[kp], -fi[kp]));
+    const float dk = (float)((double)fmaf(pf, fd[k], -fi[k]) + dg);
+    if ((n & 3) == 0) {
+      for (int c = 0; c < n; c += 4) {
+        const float4 a = *reinterpret_cast<const float4 *>(fi + c);
+        const float4 d = *reinterpret_cast<const float4 *>(fd + c);
+        float4 v = make_float4(fmaf(pf, d.x, -a.x), fmaf(pf, d.y, -a.y), fmaf(pf, d.z, -a.z), fmaf(pf, d.w, -a.w));
+        if (k == c) v.x = dk;
+        if (k == c + 1) v.y = dk;
+        if (k == c + 2) v.z = dk;
+        if (k == c + 3) v.w = dk;
+        *reinterpret_cast<float4 *>(row + c) = v;
+      }
+    } else {
+      for (int kp = 0; kp < n; ++kp) row[kp] = TD(kp == k ? dk : fmaf(pf, fd[kp], -fi[kp]));
+    }
   } else {
     const double *fd = w.phd + (zi * n + k) * n;
-    for (int kp = 0; kp < n; ++kp) row[kp] = TD(fma(pk, fd[kp], -fin[kp]));
+    const double dk = fma(pk, fd[k], -fin[k]) + dg;
+    bool done = false;
+    if constexpr (sizeof(TD) == 8) {
+      if ((n & 1) == 0) {
+        for (int c = 0; c < n; c += 2) {
+          const double2 a = *reinterpret_cast<const double2 *>(fin + c);
+          const double2 d = *reinterpret_cast<const double2 *>(fd + c);
+          double2 v = make_double2(fma(pk, d.x, -a.x), fma(pk, d.y, -a.y));
+          if (k == c) v.x = dk;
+          if (k == c + 1) v.y = dk;
+          *reinterpret_cast<double2 *>(row + c) = v;
+        }
+        done = true;
+      }
+    }
+    if (!done) {
+      for (int kp = 0; kp < n; ++kp) row[kp] = TD(kp == k ? dk : fma(pk, fd[kp], -fin[kp]));
+    }
   }
-  row[k] = TD(double(row[k]) + dg);
   lower[g] = -pre * al_in;
   upper[g] = i < last ? -pre * al_out : 0.0;
   if (w.lower32) {

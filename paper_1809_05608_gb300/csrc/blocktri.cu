@@ -328,7 +328,7 @@ __device__ inline void fma2_row(float *a, float s, const float *p, int c) {
 // my_step of the inverse with column c belonging to natural column piv(c) (byte c % 4 of
 // piv[c / 4]).
 template <int NP>
-__device__ inline void gj_invert(float *a, float (*prow)[NP], int r, bool row, int &my_step, unsigned *piv) {
+__device__ inline void gj_invert(float *a, float (*prow)[NP + 4], int r, bool row, int &my_step, unsigned *piv) {
   const unsigned full = 0xffffffffu;
   bool used = !row;
   my_step = 0;
@@ -375,13 +375,60 @@ __device__ inline void gj_invert(float *a, float (*prow)[NP], int r, bool row, i
   }
 }
 
+// In-place Gauss-Jordan inverse without row exchanges, lane r holding row r: at step ps lane
+// ps publishes its row and the reciprocal of its pivot through a double-buffered shared-memory
+// row, and every lane eliminates with packed FP32 FMAs (the owner scales its row by the same
+// formula).  No reduction sits on the chain of pivot steps, and row r of the inverse ends in
+// lane r.  Returns false (the same in every lane) when a pivot was zero or not finite.
+// Used for the mixed path's zone blocks: with the group weights w_k of the NES moments, a
+// diagonal block is a Z-matrix whose weighted column sums are 1/(a c dt) + transport + kappa_a
+// + j > 0 (number conservation of the NES terms), so it and its Schur complements are
+// M-matrices, for which elimination without pivoting is stable.
+template <int NP>
+__device__ inline bool gj_invert_np(float *a, float (*prow)[NP + 4], int r) {
+  bool ok = true;
+#pragma unroll
+  for (int ps = 0; ps < NP; ++ps) {
+    float *pb = prow[ps & 1];
+    const bool me = (r == ps);
+    if (me) {
+      const float inv = __frcp_rn(a[ps]);
+      ok = isfinite(inv) && a[ps] != 0.f;
+#pragma unroll
+      for (int c = 0; c < NP; c += 4)
+        *reinterpret_cast<float4 *>(pb + c) = make_float4(a[c], a[c + 1], a[c + 2], a[c + 3]);
+      pb[NP] = inv;
+    }
+    __syncwarp();
+    float pv[NP];
+#pragma unroll
+    for (int c = 0; c < NP; c += 4) {
+      const float4 v = *reinterpret_cast<const float4 *>(pb + c);
+      pv[c] = v.x;
+      pv[c + 1] = v.y;
+      pv[c + 2] = v.z;
+      pv[c + 3] = v.w;
+    }
+    const float inv = pb[NP];
+    const float f = me ? fmaf(-1.f, inv, 1.f) : a[ps] * inv;
+#pragma unroll
+    for (int c = 0; c < NP; c += 2) fma2_row(a, -f, pv, c);
+    a[ps] = me ? inv : -f;
+  }
+  return __all_sync(0xffffffffu, ok);
+}
+
 // Warps per CTA of the factor: four (two systems), two for the widest blocks so that the
 // static shared memory (two row buffers and the inverse tile per warp) stays under 48 KB.
 template <int NP> __host__ __device__ constexpr int fw_wpc() { return NP > 24 ? 2 : 4; }
 
 // At most 128 registers (NP <= 24), so that four CTAs (eight systems) fit on an SM and the
 // 256-ray workload's 512 CTAs run in a single wave on 152 SMs.
-template <int NP, typename TIn, typename TC>
+// PIVOT: partial pivoting in every zone (the C ABI's factor of arbitrary systems); otherwise
+// elimination without row exchanges (the outer iteration's M-matrix blocks, see gj_invert_np)
+// with partial pivoting only for a zone whose unpivoted elimination met a zero or non-finite
+// pivot.
+template <int NP, typename TIn, typename TC, bool PIVOT>
 __global__ void __launch_bounds__(fw_wpc<NP>() * 32, 4)
 k_factor_w32(int n, int n_r, int n_sys, const TIn *__restrict__ diag, const TC *__restrict__ lower,
              const TC *__restrict__ upper, float *__restrict__ dinv, const int *__restrict__ ray_list) {
@@ -391,7 +438,7 @@ k_factor_w32(int n, int n_r, int n_sys, const TIn *__restrict__ diag, const TC *
   constexpr int W = fw_wpc<NP>();
   __shared__ __align__(16) float tile[W][NP][NP];
   __shared__ __align__(16) float ushr[W][NP];
-  __shared__ __align__(16) float prow[W][2][NP];
+  __shared__ __align__(16) float prow[W][2][NP + 4];
   __shared__ __align__(16) float rowbuf[W][2][NP][NP];
   const int wid = threadIdx.x >> 5, r = threadIdx.x & 31;
   const int half = wid & 1;                          // 0: zones 0..m top-down, 1: zones n_r-1..m+1 bottom-up
@@ -434,58 +481,72 @@ k_factor_w32(int n, int n_r, int n_sys, const TIn *__restrict__ diag, const TC *
   for (int j = 0; j < len; ++j) {
     const int z = zone(j);
     const size_t zrow = ((size_t)sys * n_r + z) * n + r;
-    float a[NP];
     if (vec) cp_async_wait_all();
-    if (row) {
-#pragma unroll
-      for (int c = 0; c < NP; c += 4) {
-        const float4 v = *reinterpret_cast<const float4 *>(&rowbuf[wid][j & 1][r][c]);
-        a[c] = v.x;
-        a[c + 1] = v.y;
-        a[c + 2] = v.z;
-        a[c + 3] = v.w;
-      }
-    } else {
-#pragma unroll
-      for (int c = 0; c < NP; ++c) a[c] = 0.f;
-    }
     const float lr = (real && j > 0) ? (float)nl_raw : 0.f;
     const float ur = real ? (float)nu_raw : 0.f;
     if (j + 1 < len) load_row(j + 1);
-    if (j > 0 && row) {
-      // a -= diag(l) Dinv_prev diag(u_prev): row scale lr, column scale ushr; row r of the
-      // previous zone's inverse is still in this warp's tile.
+    // Middle zone: wait for the bottom-up half of this system (its last tile and coupling).
+    const bool mid = half == 0 && j == m;
+    if (mid) asm volatile("bar.sync %0, 64;" ::"r"(1 + (wid >> 1)) : "memory");
+    float a[NP];
+    // The zone's Schur complement from its raw rows (still in the row buffer) and the previous
+    // zone's inverse (still in this warp's tile), so that it can be rebuilt for the fallback.
+    auto build_a = [&]() {
+      if (row) {
 #pragma unroll
-      for (int c = 0; c < NP; c += 4) {
-        const float4 u = *reinterpret_cast<const float4 *>(&ushr[wid][c]);
-        const float4 d = *reinterpret_cast<const float4 *>(&tile[wid][r][c]);
-        const float2 t0 = __fmul2_rn(make_float2(-lr, -lr), make_float2(d.x, d.y));
-        const float2 t1 = __fmul2_rn(make_float2(-lr, -lr), make_float2(d.z, d.w));
-        const float2 r0 = __ffma2_rn(t0, make_float2(u.x, u.y), make_float2(a[c], a[c + 1]));
-        const float2 r1 = __ffma2_rn(t1, make_float2(u.z, u.w), make_float2(a[c + 2], a[c + 3]));
-        a[c] = r0.x;
-        a[c + 1] = r0.y;
-        a[c + 2] = r1.x;
-        a[c + 3] = r1.y;
-      }
-    }
-    if (half == 0 && j == m) {
-      // Middle zone: wait for the bottom-up half of this system, then subtract its Schur term
-      // diag(u_m) D''^{-1}_{m+1} diag(l_{m+1}) as well.
-      asm volatile("bar.sync %0, 64;" ::"r"(1 + (wid >> 1)) : "memory");
-      if (n_r - 1 > m && row) {
-        const float um = ur;                         // u_m: half 0's coupling to zone m + 1
+        for (int c = 0; c < NP; c += 4) {
+          const float4 v = *reinterpret_cast<const float4 *>(&rowbuf[wid][j & 1][r][c]);
+          a[c] = v.x;
+          a[c + 1] = v.y;
+          a[c + 2] = v.z;
+          a[c + 3] = v.w;
+        }
+      } else {
 #pragma unroll
-        for (int c = 0; c < NP; ++c) a[c] = a[c] - (um * tile[wid ^ 1][r][c]) * ushr[wid ^ 1][c];
+        for (int c = 0; c < NP; ++c) a[c] = 0.f;
       }
-    }
-    int my_step;
-    unsigned piv[NP / 4];
-    gj_invert<NP>(a, prow[wid], r, row, my_step, piv);
+      if (j > 0 && row) {
+        // a -= diag(l) Dinv_prev diag(u_prev): row scale lr, column scale ushr
+#pragma unroll
+        for (int c = 0; c < NP; c += 4) {
+          const float4 u = *reinterpret_cast<const float4 *>(&ushr[wid][c]);
+          const float4 d = *reinterpret_cast<const float4 *>(&tile[wid][r][c]);
+          const float2 t0 = __fmul2_rn(make_float2(-lr, -lr), make_float2(d.x, d.y));
+          const float2 t1 = __fmul2_rn(make_float2(-lr, -lr), make_float2(d.z, d.w));
+          const float2 r0 = __ffma2_rn(t0, make_float2(u.x, u.y), make_float2(a[c], a[c + 1]));
+          const float2 r1 = __ffma2_rn(t1, make_float2(u.z, u.w), make_float2(a[c + 2], a[c + 3]));
+          a[c] = r0.x;
+          a[c + 1] = r0.y;
+          a[c + 2] = r1.x;
+          a[c + 3] = r1.y;
+        }
+      }
+      if (mid && n_r - 1 > m && row) {
+        // the bottom-up half's Schur term diag(u_m) D''^{-1}_{m+1} diag(l_{m+1}) as well
+#pragma unroll
+        for (int c = 0; c < NP; ++c) a[c] = a[c] - (ur * tile[wid ^ 1][r][c]) * ushr[wid ^ 1][c];
+      }
+    };
+    build_a();
+    const bool ok = PIVOT ? false : gj_invert_np<NP>(a, prow[wid], r);
     __syncwarp();                  // every lane has read the previous zone's tile row
-    if (row) {
+    if (ok) {
+      if (row) {
 #pragma unroll
-      for (int c = 0; c < NP; ++c) tile[wid][my_step][(piv[c / 4] >> (8 * (c % 4))) & 0xffu] = a[c];
+        for (int c = 0; c < NP; c += 4)
+          *reinterpret_cast<float4 *>(&tile[wid][r][c]) = make_float4(a[c], a[c + 1], a[c + 2], a[c + 3]);
+      }
+    } else {
+      // pivoting requested, or a zero or non-finite pivot: the block with partial pivoting
+      if (!PIVOT) build_a();
+      int my_step;
+      unsigned piv[NP / 4];
+      gj_invert<NP>(a, prow[wid], r, row, my_step, piv);
+      __syncwarp();
+      if (row) {
+#pragma unroll
+        for (int c = 0; c < NP; ++c) tile[wid][my_step][(piv[c / 4] >> (8 * (c % 4))) & 0xffu] = a[c];
+      }
     }
     __syncwarp();
     if (row) ushr[wid][r] = ur;   // column scaling of this zone's Schur term in the next zone
@@ -924,13 +985,13 @@ cudaError_t launch_factor(int n, int n_r, int n_sys, const void *diag, int diag_
     if (diag_fp32) {
       MGFLD_DISPATCH_NP(n, constexpr int W = fw_wpc<NP>();
                         const unsigned grid = (unsigned)((n_sys + W / 2 - 1) / (W / 2));
-                        k_factor_w32<NP, float, double><<<grid, W * 32, 0, s>>>(
+                        k_factor_w32<NP, float, double, true><<<grid, W * 32, 0, s>>>(
                             n, n_r, n_sys, (const float *)diag, lower, upper, (float *)dinv, ray_list);
                         return cudaGetLastError())
     } else {
       MGFLD_DISPATCH_NP(n, constexpr int W = fw_wpc<NP>();
                         const unsigned grid = (unsigned)((n_sys + W / 2 - 1) / (W / 2));
-                        k_factor_w32<NP, double, double><<<grid, W * 32, 0, s>>>(
+                        k_factor_w32<NP, double, double, true><<<grid, W * 32, 0, s>>>(
                             n, n_r, n_sys, (const double *)diag, lower, upper, (float *)dinv, ray_list);
                         return cudaGetLastError())
     }
@@ -945,7 +1006,7 @@ cudaError_t launch_factor_f32(int n, int n_r, int n_sys, const float *diag, cons
   if (n_sys == 0) return cudaSuccess;
   MGFLD_DISPATCH_NP(n, constexpr int W = fw_wpc<NP>();
                     const unsigned grid = (unsigned)((n_sys + W / 2 - 1) / (W / 2));
-                    k_factor_w32<NP, float, float><<<grid, W * 32, 0, s>>>(n, n_r, n_sys, diag, lower32, upper32,
+                    k_factor_w32<NP, float, float, false><<<grid, W * 32, 0, s>>>(n, n_r, n_sys, diag, lower32, upper32,
                                                                             dinv, ray_list);
                     return cudaGetLastError())
 }
