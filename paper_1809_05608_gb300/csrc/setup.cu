@@ -362,12 +362,19 @@ __global__ void k_edges(Prob p, Ws w) {
     const double rnu = w.rnu[gq];
     bool geom = false;
     double m2 = 1.0;
+    const double sp = psi_e + x;
     if (re[i + 1] > rnu && x > psi_e) {
       m2 = fmax(1.0 - rnu * rnu * z[ZC_EIR2], 0.0);
-      const double sp = psi_e + x, df = x - psi_e;
+      const double df = x - psi_e;
       geom = m2 * (sp * sp) < df * df;
     }
-    F = geom ? 0.5 * (1.0 + sqrt(m2)) * psi_e / x : psi_e / (psi_e + x);
+    // one quotient for both branches: numerator and denominator selected first
+    double num = psi_e, den = sp;
+    if (geom) {
+      num = 0.5 * (1.0 + sqrt(m2)) * psi_e;
+      den = x;
+    }
+    F = num / den;
   }
   w.alpha[t] = lam_e * F * z[ZC_EI3DR] * z[ZC_EGEO];
 }
