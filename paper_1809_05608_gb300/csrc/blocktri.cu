@@ -310,8 +310,23 @@ __device__ inline void cp_async16(void *dst, const void *src) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((unsigned)__cvta_generic_to_shared(dst)), "l"(src)
                : "memory");
 }
+__device__ inline void cp_async4(void *dst, const void *src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((unsigned)__cvta_generic_to_shared(dst)), "l"(src)
+               : "memory");
+}
 __device__ inline void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ inline void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+template <int N> __device__ inline void cp_async_wait_group() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// FP32 reciprocal: the hardware approximation (rcp.approx.ftz) refined by one Newton step, a
+// few multiply-adds instead of the correctly rounded library reciprocal; ample for the FP32
+// preconditioner.  rcp(0) = inf and rcp(NaN) = NaN as before.
+__device__ inline float rcp_nr(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  const float e = fmaf(-x, r, 1.f);
+  return isfinite(r) ? fmaf(r, e, r) : r;
+}
 
 // Packed FP32 helpers (two lanes of arithmetic per instruction).
 __device__ inline void fma2_row(float *a, float s, const float *p, int c) {
@@ -357,7 +372,7 @@ __device__ inline void gj_invert(float *a, float (*prow)[NP + 4], int r, bool ro
       pv[c + 2] = v.z;
       pv[c + 3] = v.w;
     }
-    const float inv = __frcp_rn(pv[ps]);
+    const float inv = rcp_nr(pv[ps]);
     const float f = fmaf(me ? -1.f : a[ps], inv, me ? 1.f : 0.f);
     // the pair holding the next pivot column first, so that the next search can start
     if (ps + 1 < NP) {
@@ -392,7 +407,7 @@ __device__ inline bool gj_invert_np(float *a, float (*prow)[NP + 4], int r) {
     float *pb = prow[ps & 1];
     const bool me = (r == ps);
     if (me) {
-      const float inv = __frcp_rn(a[ps]);
+      const float inv = rcp_nr(a[ps]);
       ok = isfinite(inv) && a[ps] != 0.f;
 #pragma unroll
       for (int c = 0; c < NP; c += 4)
@@ -705,15 +720,19 @@ __device__ inline bool mbar_wait_bounded(unsigned long long *bar, unsigned parit
   return false;
 }
 
-// Per-system max |rhs| (for the power-of-two scaling of the FP32 solve), one CTA per system,
-// coalesced over the system's contiguous n_r x n right-hand side.
+// Per-system power-of-two scaling of the FP32 solve: k with max |rhs| 2^k in [0.5, 1) (the
+// exponent field of the maximum), then the scaled right-hand side rounded to FP32 once, so that
+// the substitution reads FP32 values.  One CTA per listed system; its n_r x n right-hand side is
+// contiguous (coalesced loads; the second pass reads it from L2).
 __global__ void k_sysmax(int n, int n_r, const double *__restrict__ rhs, const int *__restrict__ ray_list,
-                         int *__restrict__ sys_exp) {
+                         int *__restrict__ sys_exp, float *__restrict__ rhs32) {
   __shared__ double red[256];
+  __shared__ int kexp_s;
   const long sys = system_of(blockIdx.x, ray_list);
-  const size_t base = (size_t)sys * n_r * n, cnt = (size_t)n_r * n;
+  const size_t base = (size_t)sys * n_r * n;
+  const unsigned cnt = (unsigned)(n_r * n);
   double m = 0.0;
-  for (size_t e = threadIdx.x; e < cnt; e += blockDim.x) m = fmax(m, fabs(rhs[base + e]));
+  for (unsigned e = threadIdx.x; e < cnt; e += blockDim.x) m = fmax(m, fabs(rhs[base + e]));
   red[threadIdx.x] = m;
   __syncthreads();
   for (int h = blockDim.x / 2; h > 0; h >>= 1) {
@@ -721,12 +740,16 @@ __global__ void k_sysmax(int n, int n_r, const double *__restrict__ rhs, const i
     __syncthreads();
   }
   if (threadIdx.x == 0) {
-    // k with max |rhs| 2^k in [0.5, 1): the exponent field read off the bit pattern.
     m = red[0];
     const long long b = __double_as_longlong(m);
     const int e = (int)((b >> 52) & 0x7ff);
-    sys_exp[blockIdx.x] = (m > 0.0 && e < 0x7ff) ? 1022 - e : 0;
+    const int k = (m > 0.0 && e < 0x7ff) ? 1022 - e : 0;
+    sys_exp[blockIdx.x] = k;
+    kexp_s = k;
   }
+  __syncthreads();
+  const int k = kexp_s;
+  for (unsigned e = threadIdx.x; e < cnt; e += blockDim.x) rhs32[base + e] = d2f_exp2(rhs[base + e], k);
 }
 
 // Row r of a zone's inverse times the zone vector held in shared memory (vb).  VEC: n == NP,
@@ -760,19 +783,23 @@ __device__ inline float row_dot(const float *__restrict__ row, const float *__re
 // bottom-up half (zones n_r-1..m+1, then back down from m+1).  Each warp streams its zones'
 // inverse blocks through its own ring of bulk copies (one copy per use, mbarrier completion,
 // bounded waits); the halves meet at the middle through shared memory and CTA barriers.  Lane
-// r owns block row r; the zone vector is broadcast through shared memory.
+// r owns block row r; the zone vector is broadcast through shared memory.  The right-hand side
+// arrives scaled and rounded to FP32 (k_sysmax); the result is scaled back by an exact FP64
+// multiplication by 2^-k.  Offsets inside a system are 32-bit.  Every block is read twice (the
+// inward and the outward sweep), so the kernel is bound by the HBM bandwidth of those reads.
 template <int NP, bool VEC>
 __global__ void __launch_bounds__(SolveRing<NP>::WPC * 32)
 k_solve_tma(int n, int n_r, int n_sys, const float *__restrict__ dinv, const float *__restrict__ lower,
-            const float *__restrict__ upper, const double *__restrict__ rhs, double *__restrict__ x,
+            const float *__restrict__ upper, const float *__restrict__ rhs32, double *__restrict__ x,
             float *__restrict__ g32, const int *__restrict__ ray_list, const int *__restrict__ sys_exp, int *err) {
   using R = SolveRing<NP>;
   static_assert(R::WPC == 2, "one system per CTA: two warps, one per half");
   constexpr int S = R::STAGES;
-  static_assert((S & (S - 1)) == 0, "power-of-two ring");
+  static_assert((S & (S - 1)) == 0 && S % 4 == 0, "power-of-two ring, refilled four slots at a time");
   constexpr int D = 8;                                      // depth of the per-lane vector queue
   __shared__ __align__(128) unsigned char ring[2][S][NP * NP * 4];
   __shared__ __align__(16) float vbuf[2][NP];               // the zone vector, broadcast through smem
+  __shared__ __align__(16) float qbuf[2][D][2][32];         // per-lane queue: (rhs or g, coupling)
   __shared__ __align__(8) unsigned long long bar[2][S];
   __shared__ float hbuf[32], xbuf[32];                      // h_{m+1} and x_m, exchanged at the middle
   const unsigned full = 0xffffffffu;
@@ -783,36 +810,42 @@ k_solve_tma(int n, int n_r, int n_sys, const float *__restrict__ dinv, const flo
   const bool real = r < n;
   const int rr = real ? r : 0;                              // lanes without a row use row 0 (unused)
   const unsigned blk = (unsigned)(n * n * 4);
-  const int kexp = sys_exp[jsys];             // rhs is scaled by 2^kexp before rounding to FP32
+  const double unscale = ldexp(1.0, -sys_exp[jsys]);       // rhs was scaled by 2^k before rounding
   const int m = n_r / 2, B = n_r - 1 - m;
   const int F = half == 0 ? m : B;                          // forward steps of this half
   const int U = half == 0 ? 2 * m + 1 : 2 * B;              // ring uses of this half
-  // Zone sequences: forward zf0 + j dz, backward zb0 - j dz.
+  // Zone sequences: forward zf0 + j dz, backward zb0 - j dz; element offsets z n (32-bit).
   const int dz = half == 0 ? 1 : -1;
+  const int dzn = dz * n;
   const int zf0 = half == 0 ? 0 : n_r - 1, zb0 = half == 0 ? m - 1 : m + 1;
   // Per-lane element pointers of this system (row r of zone z is [z * n]).
   const size_t sb = (size_t)sys * n_r * n;
-  const double *rhs_l = rhs + sb + rr;
+  const float *rhs_l = rhs32 + sb + rr;
   const float *cin_l = (half == 0 ? lower : upper) + sb + rr;   // coupling used going inward
   const float *cout_l = (half == 0 ? upper : lower) + sb + rr;  // coupling used going outward
   float *g_l = g32 + sb + rr;
   double *x_l = x + sb + rr;
   const float *dsys = dinv + sb * n;
+  const unsigned rowoff = (unsigned)rr * (unsigned)n * 4u; // byte offset of row r in a slot
   if (r == 0) {
     for (int k = 0; k < S; ++k) mbar_init(&bar[half][k], 1);
     mbar_fence_init();
   }
   __syncwarp();
-  // The bulk copies are issued by lane 0 in use order; it tracks the zone of the next use.
-  int iu = 0, iz = zf0;                                     // next use to issue and its zone
+  // Lane 0 issues the bulk copies in use order, tracking the source block of the next use:
+  // top-down half +1 zone up to the middle, then -1; bottom-up half -1 to zone m + 1, which is
+  // used twice (last forward, first backward), then +1.  All S slots are filled up front, then
+  // four at a time once the four uses that held them are consumed.
+  int iu = 0;
+  const float *src = dsys + (size_t)zf0 * n * n;
+  const int bstep = n * n;
   auto issue_next = [&]() {
     unsigned long long *b = &bar[half][iu & (S - 1)];
     mbar_expect_tx(b, blk);
-    bulk_g2s(ring[half][iu & (S - 1)], dsys + (size_t)iz * n * n, blk, b);
+    bulk_g2s(ring[half][iu & (S - 1)], src, blk, b);
     ++iu;
-    // zone of use iu: forward ..., (top) the middle zone m, then backward
-    if (half == 0) iz = iu < m ? iu : (iu == m ? m : 2 * m - iu);
-    else iz = iu < B ? n_r - 1 - iu : m + 1 + (iu - B);
+    if (half == 0) src += iu <= m ? bstep : -bstep;
+    else src += iu < B ? -bstep : (iu == B ? 0 : bstep);
   };
   bool ok = true;                                           // warp-uniform
   auto wait = [&](int u) -> bool {
@@ -829,71 +862,68 @@ k_solve_tma(int n, int n_r, int n_sys, const float *__restrict__ dinv, const flo
     }
     return ok;
   };
-  auto advance = [&]() {                          // keep S - 1 copies in flight
-    __syncwarp();
-    if (r == 0 && ok && iu < U) issue_next();
+  auto advance = [&](int u) {                     // use u consumed: refill four slots after every fourth
+    if ((u & 3) == 3) {
+      __syncwarp();
+      if (r == 0 && ok)
+        for (int k = 0; k < 4 && iu < U; ++k) issue_next();
+    }
   };
-  // Per-lane queue of (rhs or forward result, coupling) for the uses ahead, D deep.  The loads
-  // are unconditional (clamped to a valid zone) and converted or masked when consumed, so each
-  // load has D steps to arrive and no instruction waits on it earlier.
-  double qa[D];
-  float qb[D], qg[D];
+  auto slot_row = [&](int u) {
+    return reinterpret_cast<const float *>(ring[half][u & (S - 1)] + rowoff);
+  };
+  // Per-lane queue of (rhs or forward result, coupling) for the uses D ahead, in shared memory
+  // through 4-byte asynchronous copies: one copy group per use, waited for with
+  // cp.async.wait_group D-1, so that no register load is outstanding across the recurrence.
+  float (*q)[2][32] = qbuf[half];
+  auto fill = [&](int d, const float *a, const float *c, int zo) {
+    cp_async4(&q[d][0][r], a + zo);
+    cp_async4(&q[d][1][r], c + zo);
+    cp_async_commit();
+  };
   // the middle zone's right-hand side and couplings (top-down half), fetched up front
-  const size_t zm = (size_t)m * n;
-  const double bm_raw = rhs_l[zm];
-  const float lm_raw = cin_l[zm], um_raw = cout_l[zm];
+  const int zm = m * n;
+  const float bm_raw = rhs_l[zm], lm_raw = cin_l[zm], um_raw = cout_l[zm];
   float *vb = vbuf[half];
 
   if (r == 0)
-    for (int k = 0; k < S - 1 && k < U; ++k) issue_next();
+    for (int k = 0; k < S && k < U; ++k) issue_next();
   iu = __shfl_sync(full, iu, 0);
-  iz = __shfl_sync(full, iz, 0);
 #pragma unroll
-  for (int d = 0; d < D; ++d) {
-    const int z = zf0 + d * dz;
-    const int zc = d < F ? z : zf0;
-    qa[d] = rhs_l[(size_t)zc * n];
-    qb[d] = cin_l[(size_t)zc * n];
-  }
+  for (int d = 0; d < D; ++d) fill(d, rhs_l, cin_l, (d < F ? zf0 + d * dz : zf0) * n);
   float prev = 0.f;
-  int zf = zf0;
-  for (int j0 = 0; j0 < F; j0 += D) {
-#pragma unroll
-    for (int d = 0; d < D; ++d) {
-      const int j = j0 + d;
-      if (j >= F) break;
-      const float b = d2f_exp2(qa[d], kexp), l = j > 0 ? qb[d] : 0.f;
-      const int zq = zf + D * dz;                 // refill this slot with the zone D steps ahead
-      const bool more = real && j + D < F;
-      const int zqc = more ? zq : zf;
-      qa[d] = rhs_l[(size_t)zqc * n];
-      qb[d] = cin_l[(size_t)zqc * n];
-      if (wait(j)) {
-        if (r < NP) vb[r] = real ? b - l * prev : 0.f;
-        __syncwarp();
-        const float g = row_dot<NP, VEC>((const float *)ring[half][j & (S - 1)] + (size_t)rr * n, vb, n);
-        if (real) g_l[(size_t)zf * n] = g;
-        prev = g;
-      }
-      advance();
-      zf += dz;
+  int zfo = zf0 * n;                              // element offset of the current forward zone
+  for (int j = 0; j < F; ++j) {
+    const int d = j & (D - 1);
+    cp_async_wait_group<D - 1>();
+    const float b = q[d][0][r], l = j > 0 ? q[d][1][r] : 0.f;
+    if (wait(j)) {
+      if (r < NP) vb[r] = real ? b - l * prev : 0.f;
+      __syncwarp();
+      const float g = row_dot<NP, VEC>(slot_row(j), vb, n);
+      if (real) g_l[zfo] = g;
+      prev = g;
     }
+    fill(d, rhs_l, cin_l, j + D < F ? zfo + D * dzn : zfo);   // the slot just read: the zone D ahead
+    advance(j);
+    zfo += dzn;
   }
+  cp_async_wait_all();
   if (half == 1) hbuf[r] = B > 0 ? prev : 0.f;
   __syncthreads();
   if (half == 0) {
     // Middle zone: x_m = Dinv_m (r_m - l_m g_{m-1} - u_m h_{m+1}).
-    const float bm = real ? d2f_exp2(bm_raw, kexp) : 0.f;
+    const float bm = real ? bm_raw : 0.f;
     const float lm = (real && m > 0) ? lm_raw : 0.f;
     const float um = (real && m < n_r - 1) ? um_raw : 0.f;
     float xm = 0.f;
     if (wait(m)) {
       if (r < NP) vb[r] = real ? bm - lm * prev - um * hbuf[r] : 0.f;
       __syncwarp();
-      xm = row_dot<NP, VEC>((const float *)ring[half][m & (S - 1)] + (size_t)rr * n, vb, n);
-      if (real) x_l[zm] = f2d_exp2(xm, -kexp);
+      xm = row_dot<NP, VEC>(slot_row(m), vb, n);
+      if (real) x_l[zm] = (double)xm * unscale;
     }
-    advance();
+    advance(m);
     xbuf[r] = xm;
     prev = xm;
   }
@@ -901,53 +931,42 @@ k_solve_tma(int n, int n_r, int n_sys, const float *__restrict__ dinv, const flo
   if (half == 1) prev = xbuf[r];
   // Backward: top x_i = g_i - Dinv_i (u_i x_{i+1}); bottom x_i = h_i - Dinv_i (l_i x_{i-1}).
 #pragma unroll
-  for (int d = 0; d < D; ++d) {
-    const int z = zb0 - d * dz;
-    const int zc = d < F ? z : m;                 // m: a valid zone whatever F is
-    qg[d] = g_l[(size_t)zc * n];
-    qb[d] = cout_l[(size_t)zc * n];
-  }
-  int zb = zb0;
+  for (int d = 0; d < D; ++d) fill(d, g_l, cout_l, (d < F ? zb0 - d * dz : m) * n);   // m: valid whatever F is
+  int zbo = zb0 * n;
   const int ub = U - F;                           // first backward use
-  for (int j0 = 0; j0 < F; j0 += D) {
-#pragma unroll
-    for (int d = 0; d < D; ++d) {
-      const int j = j0 + d;
-      if (j >= F) break;
-      const int u = ub + j;
-      const float gz = qg[d], c = qb[d];
-      const int zq = zb - D * dz;
-      const bool more = real && j + D < F;
-      const int zqc = more ? zq : zb;
-      qg[d] = g_l[(size_t)zqc * n];
-      qb[d] = cout_l[(size_t)zqc * n];
-      if (wait(u)) {
-        if (r < NP) vb[r] = real ? c * prev : 0.f;
-        __syncwarp();
-        const float xi = gz - row_dot<NP, VEC>((const float *)ring[half][u & (S - 1)] + (size_t)rr * n, vb, n);
-        if (real) x_l[(size_t)zb * n] = f2d_exp2(xi, -kexp);
-        prev = xi;
-      }
-      advance();
-      zb -= dz;
+  for (int j = 0; j < F; ++j) {
+    const int d = j & (D - 1);
+    const int u = ub + j;
+    cp_async_wait_group<D - 1>();
+    const float gz = q[d][0][r], c = q[d][1][r];
+    if (wait(u)) {
+      if (r < NP) vb[r] = real ? c * prev : 0.f;
+      __syncwarp();
+      const float xi = gz - row_dot<NP, VEC>(slot_row(u), vb, n);
+      if (real) x_l[zbo] = (double)xi * unscale;
+      prev = xi;
     }
+    fill(d, g_l, cout_l, j + D < F ? zbo - D * dzn : zbo);
+    advance(u);
+    zbo -= dzn;
   }
+  cp_async_wait_all();
 }
 
 cudaError_t launch_solve_tma(int n, int n_r, int n_sys, const void *dinv, const float *lower32,
-                             const float *upper32, const double *rhs, double *x, float *g32,
+                             const float *upper32, const double *rhs, float *rhs32, double *x, float *g32,
                              const int *ray_list, int *sys_exp, int *err, cudaStream_t s) {
   if (n_sys == 0) return cudaSuccess;
-  k_sysmax<<<n_sys, 256, 0, s>>>(n, n_r, rhs, ray_list, sys_exp);
+  k_sysmax<<<n_sys, 256, 0, s>>>(n, n_r, rhs, ray_list, sys_exp, rhs32);
   MGFLD_DISPATCH_NP(n, {
     using R = SolveRing<NP>;
     const unsigned grid = (unsigned)n_sys;                 // one system (two warps) per CTA
     if (n == NP)
-      k_solve_tma<NP, true><<<grid, R::WPC * 32, 0, s>>>(n, n_r, n_sys, (const float *)dinv, lower32, upper32, rhs,
+      k_solve_tma<NP, true><<<grid, R::WPC * 32, 0, s>>>(n, n_r, n_sys, (const float *)dinv, lower32, upper32, rhs32,
                                                          x, g32, ray_list, sys_exp, err);
     else
       k_solve_tma<NP, false><<<grid, R::WPC * 32, 0, s>>>(n, n_r, n_sys, (const float *)dinv, lower32, upper32,
-                                                          rhs, x, g32, ray_list, sys_exp, err);
+                                                          rhs32, x, g32, ray_list, sys_exp, err);
     return cudaGetLastError();
   })
 }

@@ -48,7 +48,7 @@ struct Layout {
   int mixed;
   size_t groups, phout, phin, phd, rsum, phin32, phd32, lam, slam, g0, l0, alpha, ghost, rnu, jbuf, psi_n, ye_n, e_n,
       zone, src;
-  size_t diag, lower, upper, rhs, x, dinv, zled, sscale, kinv, lower32, upper32, g32;
+  size_t diag, lower, upper, rhs, x, dinv, zled, sscale, kinv, lower32, upper32, g32, rhs32;
   size_t viol, vprev, active, iters, status, refac, nfact, nanflag, list_act, list_ref, counters;
   size_t total;
 };
@@ -96,6 +96,7 @@ struct Ws {
   int *sscale;              // per listed system: exponent k of the 2^k scaling of the FP32 solve
   float *lower32, *upper32; // FP32 copies of the (step-constant) coupling coefficients, MIXED only
   float *g32;               // forward-substitution results of the FP32 solve
+  float *rhs32;             // the FP32 solve's scaled right-hand side
   double *kinv;             // per (ray, q, i, k): 1/lambda^(t) at psi^n (transport opacity)
   unsigned long long *viol; // per-ray max violation ratio (double bits, non-negative)
   double *vprev;
@@ -189,7 +190,7 @@ cudaError_t launch_factor(int n, int n_r, int n_sys, const void *diag, int diag_
 // MIXED-precision solve fed by bulk asynchronous copies; requires even n, 16-byte aligned
 // arrays and rhs != x.  Sets *err on a bounded-wait timeout.
 cudaError_t launch_solve_tma(int n, int n_r, int n_sys, const void *dinv, const float *lower32,
-                             const float *upper32, const double *rhs, double *x, float *g32,
+                             const float *upper32, const double *rhs, float *rhs32, double *x, float *g32,
                              const int *ray_list, int *sys_exp, int *err, cudaStream_t s);
 
 // Exact power-of-two rescaling between FP64 and FP32 by exponent arithmetic on the bit

@@ -55,6 +55,7 @@ Layout make_layout(int n_ray, int n_r, int n, int precision) {
   L.lower32 = take(precision == MGFLD_MIXED ? sizeof(float) * F : 0);
   L.upper32 = take(precision == MGFLD_MIXED ? sizeof(float) * F : 0);
   L.g32 = take(precision == MGFLD_MIXED ? sizeof(float) * F : 0);
+  L.rhs32 = take(precision == MGFLD_MIXED ? sizeof(float) * F : 0);
   L.kinv = take(sizeof(double) * F);
   L.viol = take(sizeof(unsigned long long) * R);
   L.vprev = take(sizeof(double) * R);
@@ -119,6 +120,7 @@ Ws resolve(void *base, const Layout &L) {
   w.lower32 = L.mixed ? (float *)(b + L.lower32) : nullptr;
   w.upper32 = L.mixed ? (float *)(b + L.upper32) : nullptr;
   w.g32 = L.mixed ? (float *)(b + L.g32) : nullptr;
+  w.rhs32 = L.mixed ? (float *)(b + L.rhs32) : nullptr;
   w.kinv = (double *)(b + L.kinv);
   w.viol = (unsigned long long *)(b + L.viol);
   w.vprev = (double *)(b + L.vprev);
@@ -599,7 +601,7 @@ mgfld_status mgfld_step(const mgfld_dims *dims, const mgfld_problem *prob, mgfld
     }
     prof.begin(MGFLD_PROF_SOLVE);
     if (tl.mixed && n % 2 == 0)
-      MGFLD_CUDA(launch_solve_tma(n, NR, n_act * NS, w.dinv, w.lower32, w.upper32, w.rhs, w.x, w.g32,
+      MGFLD_CUDA(launch_solve_tma(n, NR, n_act * NS, w.dinv, w.lower32, w.upper32, w.rhs, w.rhs32, w.x, w.g32,
                                   w.list_act, w.sscale, w.counters + 3, s));
     else
       MGFLD_CUDA(launch_solve(n, NR, n_act * NS, w.dinv, w.lower, w.upper, w.rhs, w.x, opts->precision,
