@@ -42,6 +42,18 @@ FP32_FLOP_PER_CLK_SM = 256.0    # 128 FFMA lanes per clock per SM
 N_SM = 152
 
 
+def _measured_hbm_gbs():
+    """The measured HBM copy bandwidth of this machine's GPUs, else the recorded fallback."""
+    try:
+        with open(os.path.join(ROOT, 'MEASURED_PEAKS.json')) as f:
+            return float(json.load(f)['hbm_gbs'])
+    except (OSError, ValueError, KeyError):
+        return 6800.0
+
+
+PEAK_HBM_GBS = _measured_hbm_gbs()
+
+
 def dist_info():
     ws = int(os.environ.get('WORLD_SIZE', '1'))
     rank = int(os.environ.get('RANK', '0'))
@@ -258,6 +270,31 @@ def roofline_for(res, inp, precision, clk):
                 kernel_ms_per_launch=prof[dom]['ms'] / launches, kernel_share=prof[dom]['ms'] / res['ms'])
 
 
+def solve_roofline(res, inp):
+    """HBM roofline of the mixed path's FP32 substitution (k_sysmax + k_solve_tma per solve).
+
+    Bytes per (zone, system) and solve: every FP32 inverse block read by the inward and by the
+    outward sweep (2 N^2 x 4 B; the 839 MB of blocks of the 256-ray workload do not stay in the
+    129 MB L2 between the sweeps), plus the vectors: rhs read (8 N), its FP32 copy written and
+    read (2 x 4 N), the two couplings (2 x 4 N), the forward result written and read (2 x 4 N)
+    and x written (8 N)."""
+    n_ray, n_s, n_r, n = inp['psi0'].shape
+    prof = res['prof']['solve']
+    solves = prof['launches']
+    per_unit = 2 * n * n * 4 + 8 * n + 8 * n + 8 * n + 8 * n + 8 * n
+    # iterations of the active rays: res['iters'] counts (ray, iteration) pairs over the timed steps
+    nbytes = per_unit * n_s * n_r * res['iters']
+    achieved = nbytes / (prof['ms'] * 1e-3) / 1e9
+    tr = traffic_record('k_solve_tma')
+    traffic = None
+    if tr is not None and solves:
+        traffic = tr['bytes'] / tr['units'] * (res['iters'] * n_s / solves)
+    return dict(bound='hbm', kernel='k_solve_tma', achieved=achieved, peak=PEAK_HBM_GBS, unit='GB/s',
+                frac=achieved / PEAK_HBM_GBS, traffic=traffic, peak_source='measured copy bandwidth (of measured)',
+                bytes_per_zone_system=per_unit, kernel_ms_per_launch=prof['ms'] / max(solves, 1),
+                kernel_share=prof['ms'] / res['ms'])
+
+
 def e2e_run(M, torch, inp, precision, steps):
     """Same metric through the public API from pinned HOST buffers: every step uploads
     that step's inputs (matter, opacities, NES scale, grid, state), runs mgfld_step and
@@ -455,7 +492,7 @@ def main():
                     l2='working set %.1f GB per GPU, larger than the 129 MB L2 (no flush needed)' % work_gb,
                     outer_iterations_per_step=mixed['max_iters'],
                     factorizations_per_ray_step=mixed['nfact'] / (RAYS_PER_RANK * args.steps)),
-        roofline=roof, cpu_baseline=cpu, clocks=mixed['clocks'],
+        roofline=roof, roofline_solve=solve_roofline(mixed, inp), cpu_baseline=cpu, clocks=mixed['clocks'],
         e2e=dict(value=job_throughput(ups, ws, e2e_ms), unit=UNIT, h2d_bytes_per_step=e2e['h2d'],
                  d2h_bytes_per_step=e2e['d2h']),
         gpu_launches=launches,
