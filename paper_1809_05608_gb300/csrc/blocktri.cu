@@ -409,9 +409,9 @@ __device__ inline bool gj_invert_np(float *a, float (*prow)[NP + 4], int r) {
     if (me) {
       const float inv = rcp_nr(a[ps]);
       ok = isfinite(inv) && a[ps] != 0.f;
+      // 8-byte stores of the register pairs that the packed FMAs keep (no repacking moves)
 #pragma unroll
-      for (int c = 0; c < NP; c += 4)
-        *reinterpret_cast<float4 *>(pb + c) = make_float4(a[c], a[c + 1], a[c + 2], a[c + 3]);
+      for (int c = 0; c < NP; c += 2) *reinterpret_cast<float2 *>(pb + c) = make_float2(a[c], a[c + 1]);
       pb[NP] = inv;
     }
     __syncwarp();
@@ -548,8 +548,7 @@ k_factor_w32(int n, int n_r, int n_sys, const TIn *__restrict__ diag, const TC *
     if (ok) {
       if (row) {
 #pragma unroll
-        for (int c = 0; c < NP; c += 4)
-          *reinterpret_cast<float4 *>(&tile[wid][r][c]) = make_float4(a[c], a[c + 1], a[c + 2], a[c + 3]);
+        for (int c = 0; c < NP; c += 2) *reinterpret_cast<float2 *>(&tile[wid][r][c]) = make_float2(a[c], a[c + 1]);
       }
     } else {
       // pivoting requested, or a zero or non-finite pivot: the block with partial pivoting
