@@ -29,8 +29,9 @@ Readings (the paper is silent or garbled here; the GPU path takes the same ones)
       balance of Eq. p7 solved with the sum over k that the printed Eq. p8 drops; xi = 1 when the
       denominator vanishes (no flux).
   E6  The limiter runs k = 0 .. N-3 (0-based: every group that has two groups above it), in
-      increasing k, with Eq. a81c/a81d's coefficients on the target grid; a removal that would
-      drive psi_{k+2} negative is scaled down to empty it exactly.
+      increasing k, with Eq. a81c/a81d's coefficients on the target grid, and acts only on an
+      overfilled group; a removal that would drive psi_{k+2} below zero is scaled down to empty
+      it exactly (no removal when psi_{k+2} <= 0).
   E7  eta1 (the flux factor psi1/psi0) is an input, clamped to [0, 1]; absent, eta2 = 1/3.
 """
 import numpy as np
@@ -200,8 +201,9 @@ def limit_occupation(psi, epsc, deps):
         c_up = (e2 - e0) * w[..., k] / ((e2 - e1) * w[..., k + 1])          # Eq. a81c
         c_dn = (e1 - e0) * w[..., k] / ((e2 - e1) * w[..., k + 2])          # Eq. a81d
         d = np.maximum(psi[..., k] - 1.0, 0.0)
-        # a removal from k + 2 larger than its content is scaled down to empty it
-        d = np.where(c_dn * d > psi[..., k + 2], psi[..., k + 2] / c_dn, d)
+        # a removal from k + 2 larger than its (non-negative part of the) content is scaled down
+        # to empty it; groups that are not overfilled are left alone
+        d = np.minimum(d, np.maximum(psi[..., k + 2], 0.0) / c_dn)
         psi[..., k] -= d
         psi[..., k + 1] += c_up * d
         psi[..., k + 2] -= c_dn * d

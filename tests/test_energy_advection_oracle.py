@@ -156,3 +156,17 @@ def test_occupation_limiter_conserves_number_and_energy():
     assert abs(np.sum(out * w * c) - np.sum(psi * w * c)) < 1e-14 * np.sum(psi * w * c)
     assert np.all(out[:n - 2] <= 1.0 + 1e-15) and np.all(out >= 0.0)
     assert np.all(out[:5] == psi[:5])           # groups below the first overfilled one untouched
+
+
+def test_occupation_limiter_leaves_groups_that_are_not_overfilled():
+    """The limiter acts on psi > 1 only: negative occupations above (the remap has no positivity
+    limiter) are not touched, and an overfilled group cannot draw a group below zero."""
+    c = E.group_centres(EDGES[:-1], EDGES[1:])
+    d = np.diff(EDGES)
+    psi = np.full(20, 0.3)
+    psi[7] = -1e-9
+    out = E.limit_occupation(psi[None], c[None], d[None])[0]
+    assert np.array_equal(out, psi)
+    psi[5] = 1.2                                 # group 7 (= 5 + 2) holds nothing to remove
+    out = E.limit_occupation(psi[None], c[None], d[None])[0]
+    assert out[5] == psi[5] and out[7] == psi[7]
