@@ -269,6 +269,49 @@ mgfld_status mgfld_adjoint(const mgfld_dims *dims, const mgfld_problem *prob, co
                            const mgfld_state *state_np1, mgfld_adjoint_io *io, void *ws, size_t ws_bytes,
                            void *stream);
 
+/* ----------------------------------------------------------------------------------------------
+ * Energy advection (Sec. "Neutrino Energy Advection Step", Eqs. a78-a81d; the remap of App.
+ * "Neutrino Energy Advection due to Changes in the Lapse", Eqs. p5-p8; the PPM interpolation of
+ * Sec. "PPM Interpolation Scheme", Eqs. h9-h17, h22-h24, h31-h35, Cartesian form; the Minerbo
+ * closure, Eqs. a86-a87).  The step that follows the transport step in the operator split: after a
+ * hydrodynamics step changed rho, R and the lapse a of each zone, the occupations psi0 of each
+ * (ray, species, zone) are
+ *   1. shifted in energy (Eqs. a78-a80): every group edge E_{k+-1/2} moves by the factor
+ *      1 + (da/a - dR/R) - (db/b - dR/R) eta2, b = 1/(4 pi R^2 rho), eta2 the Minerbo Eddington
+ *      factor of the flux factor eta1 at the edge (mean of the two adjacent groups), with the
+ *      neutrino number of every group kept (psi scaled by (rho a^3)^{n+1}/(rho a^3)^n x
+ *      (E^2 dE)^n / (E^2 dE)^{shifted});
+ *   2. remapped back to the grid E_{k+-1/2} / a^{n+1} (Eq. a81, p1): parabolic profiles of
+ *      eps^2 psi over the shifted groups, the number in each slice swept across a target edge
+ *      as the flux (zero at the lowest and highest edge, Eq. p5), all fluxes of the system
+ *      scaled by one factor xi that keeps the energy (Eqs. p6-p8; xi = 1 without flux);
+ *   3. optionally limited to psi <= 1 (Eqs. a81a-a81d), in increasing group order, moving the
+ *      excess of group k to k+1 and k+2 with number and energy kept.
+ * Neutrino number per comoving mass is conserved exactly; the remap conserves energy exactly.
+ * The swept fraction of a group is clamped to [0, 1] (edges are assumed to move by less than a
+ * group width in one step).
+ * -------------------------------------------------------------------------------------------- */
+typedef struct {
+  const double *r_edge_n, *r_edge_np1;   /* [n_ray][n_r+1] areal radii of the zone edges before /
+                                            after (cm); the zone's R is the mean of its edges */
+  const double *rho_n, *rho_np1;         /* [n_ray][n_r] density before / after (g/cm^3) */
+  const double *lapse_n, *lapse_np1;     /* [n_ray][n_r] lapse before / after, or NULL (= 1) */
+  const double *e_edge;                  /* [n_e+1] group edges at infinity (MeV), increasing */
+  const double *eta1;                    /* [n_ray][n_s][n_r][n_e] flux factors psi1/psi0 (clamped
+                                            to [0, 1]), or NULL: eta2 = 1/3 (diffusion limit) */
+  int limit;                             /* nonzero: apply step 3 */
+} mgfld_eadv_problem;
+
+/*
+ * mgfld_energy_advect -- one energy-advection step, in place on psi [n_ray][n_s][n_r][n_e]
+ * (device, FP64; n_s = 4, 3 <= n_e <= 32).  xi (device, [n_ray][n_s][n_r], or NULL) receives the
+ * energy-fixing factor of each system.  All pointers are caller-owned device memory; no
+ * workspace.  Asynchronous on `stream`.  Returns OK, EINVAL (bad dims or a required pointer
+ * missing) or ECUDA (launch error).
+ */
+mgfld_status mgfld_energy_advect(const mgfld_dims *dims, const mgfld_eadv_problem *prob, double *psi,
+                                 double *xi, void *stream);
+
 /* Human-readable name of a status code (static string). */
 const char *mgfld_status_str(mgfld_status s);
 

@@ -22,7 +22,7 @@ N_SPECIES = 4
 
 EXPORTED = ('mgfld_eos_default', 'mgfld_workspace_bytes', 'mgfld_step', 'mgfld_assemble',
             'mgfld_factor_bytes', 'mgfld_factor', 'mgfld_solve', 'mgfld_status_str', 'mgfld_step_noalloc',
-            'mgfld_adjoint_workspace_bytes', 'mgfld_adjoint')
+            'mgfld_adjoint_workspace_bytes', 'mgfld_adjoint', 'mgfld_energy_advect')
 NOALLOC_SCRATCH_BYTES = 64 << 20
 
 
@@ -70,6 +70,12 @@ class AdjointIO(ctypes.Structure):
                 ('sweep_change', ctypes.c_double)]
 
 
+class EadvProblem(ctypes.Structure):
+    _fields_ = [('r_edge_n', ctypes.c_void_p), ('r_edge_np1', ctypes.c_void_p), ('rho_n', ctypes.c_void_p),
+                ('rho_np1', ctypes.c_void_p), ('lapse_n', ctypes.c_void_p), ('lapse_np1', ctypes.c_void_p),
+                ('e_edge', ctypes.c_void_p), ('eta1', ctypes.c_void_p), ('limit', ctypes.c_int)]
+
+
 _lib = None
 
 
@@ -107,6 +113,8 @@ def lib():
     L.mgfld_adjoint.restype = ctypes.c_int
     L.mgfld_adjoint.argtypes = [P(Dims), P(Problem), P(State), P(State), P(AdjointIO), ctypes.c_void_p,
                                 ctypes.c_size_t, ctypes.c_void_p]
+    L.mgfld_energy_advect.restype = ctypes.c_int
+    L.mgfld_energy_advect.argtypes = [P(Dims), P(EadvProblem), ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
     L.mgfld_status_str.restype = ctypes.c_char_p
     L.mgfld_status_str.argtypes = [ctypes.c_int]
     _lib = L
@@ -308,3 +316,19 @@ class Stepper:
             if rc == MGFLD_ENAN or (rc == MGFLD_ENOCONV and worst != MGFLD_ENAN):
                 worst = rc
         return worst
+
+
+def eadv_problem(t, limit=True):
+    """C struct for mgfld_energy_advect from a dict of device tensors: r_edge_n, r_edge_np1
+    [n_ray, n_r+1], rho_n, rho_np1 [n_ray, n_r], optional lapse_n, lapse_np1 [n_ray, n_r],
+    e_edge [n_e+1], optional eta1 [n_ray, 4, n_r, n_e] (FP64, contiguous; kept alive by the caller)."""
+    return EadvProblem(_ptr(t['r_edge_n']), _ptr(t['r_edge_np1']), _ptr(t['rho_n']), _ptr(t['rho_np1']),
+                       _ptr(t.get('lapse_n')), _ptr(t.get('lapse_np1')), _ptr(t['e_edge']), _ptr(t.get('eta1')),
+                       1 if limit else 0)
+
+
+def mgfld_energy_advect(dims, eadv_struct, psi, xi=None, stream=None):
+    """One energy-advection step in place on psi [n_ray, 4, n_r, n_e] (device FP64); xi [n_ray, 4,
+    n_r] (optional) receives each system's energy-fixing factor.  Returns the mgfld status."""
+    return lib().mgfld_energy_advect(ctypes.byref(dims), ctypes.byref(eadv_struct), _ptr(psi), _ptr(xi),
+                                     _stream(stream))

@@ -35,6 +35,7 @@ BASE_SEED = 180905608
 N_SPECIES = 4
 
 FIELD_RHO, FIELD_T, FIELD_KAPPA = 1, 2, 3
+FIELD_HYDRO = 4
 
 
 @dataclasses.dataclass(frozen=True)
@@ -165,4 +166,60 @@ def subset_rays(inp, rays):
     out['problem'] = prob
     for key in ('psi0', 'ye0', 'T0'):
         out[key] = np.ascontiguousarray(inp[key][rays])
+    return out
+
+
+def _smooth_coeffs(rng, n_ray, modes=4):
+    return rng.standard_normal((n_ray, modes))
+
+
+def _smooth_eval(c, x, amp):
+    """Per-ray smooth profiles amp * sum_m c_m sin(m pi x) / modes at the points x."""
+    m = np.arange(1, c.shape[1] + 1)
+    return amp * (c[:, :, None] * np.sin(np.pi * m[None, :, None] * x[None, None, :])).sum(axis=1) / c.shape[1]
+
+
+def make_energy_advection(config: int, rays=None, n_ray=None, n_r=None, n_e=None):
+    """Inputs of one energy-advection step on configuration `config`'s profile family.
+
+    The zone state before the step is the transport profile (edges, rho) with the lapse
+    a = sqrt(1 - 0.2 R_1 / R) (0.89 at the inner edge to 1); a hydrodynamics step is imitated by
+    smooth seeded per-ray relative changes: of the density g (amplitude 1e-2), of the edge radii
+    -g/3 (homologous compression or expansion) plus an independent part of amplitude 3e-4, and of
+    the lapse (amplitude 1e-4).  psi is the transport profile's Fermi-Dirac occupation, with the electron
+    neutrinos degenerate (chemical potential 3 T) where rho > 1e12 g/cm^3.  The flux factor eta1
+    rises from 0.02 inside to 0.82 outside an energy-dependent neutrinosphere radius
+    30 km (E / 10 MeV)^(1/2), over a 5 km width.  Returns a dict of numpy arrays."""
+    base = make_problem(config, n_ray=n_ray, n_r=n_r, n_e=n_e)
+    prob = base['problem']
+    r_edge, rho, e_edge = prob['r_edge'], prob['rho'], prob['e_edge']
+    NRAY, NR = rho.shape
+    NE = len(e_edge) - 1
+    rc = 0.5 * (r_edge[:, 1:] + r_edge[:, :-1])
+    x_edge = np.log(r_edge[0] / r_edge[0, 0]) / np.log(r_edge[0, -1] / r_edge[0, 0])
+    x_mid = 0.5 * (x_edge[1:] + x_edge[:-1])
+    rng = np.random.default_rng(_seed(config, FIELD_HYDRO))
+    c_g, c_r, c_a = (_smooth_coeffs(rng, NRAY) for _ in range(3))
+    d_rho = _smooth_eval(c_g, x_mid, 1e-2)
+    d_r = -_smooth_eval(c_g, x_edge, 1e-2) / 3.0 + _smooth_eval(c_r, x_edge, 3e-4)
+    d_a = _smooth_eval(c_a, x_mid, 1e-4)
+    lapse_n = np.sqrt(1.0 - 0.2 * rc[:, :1] / rc)
+    e_g = np.sqrt(e_edge[1:] * e_edge[:-1])
+    T = base['T0']
+    mu = np.where(rho > 1e12, 3.0 * T, 0.0)
+    psi = np.array(base['psi0'], copy=True)
+    x = (e_g[None, None, :] - mu[:, :, None]) / T[:, :, None]
+    z = np.exp(-np.abs(x))
+    psi[:, 0] = np.where(x > 0.0, z / (1.0 + z), 1.0 / (1.0 + z))
+    r_nu = 30.0 * KM * np.sqrt(e_g / 10.0)
+    eta1 = 0.02 + 0.4 * (1.0 + np.tanh((rc[:, :, None] - r_nu[None, None, :]) / (5.0 * KM)))
+    eta1 = np.ascontiguousarray(np.broadcast_to(eta1[:, None], (NRAY, N_SPECIES, NR, NE)))
+    out = dict(e_edge=e_edge, r_edge_n=r_edge, r_edge_np1=np.ascontiguousarray(r_edge * (1.0 + d_r)),
+               rho_n=rho, rho_np1=np.ascontiguousarray(rho * (1.0 + d_rho)),
+               lapse_n=np.ascontiguousarray(lapse_n),
+               lapse_np1=np.ascontiguousarray(lapse_n * (1.0 + d_a)),
+               psi=np.ascontiguousarray(psi), eta1=eta1, spec=base['spec'])
+    if rays is not None:
+        for key in ('r_edge_n', 'r_edge_np1', 'rho_n', 'rho_np1', 'lapse_n', 'lapse_np1', 'psi', 'eta1'):
+            out[key] = np.ascontiguousarray(out[key][rays])
     return out

@@ -1,0 +1,164 @@
+"""GPU energy-advection step (mgfld_energy_advect through the C ABI) against the CPU oracle.
+
+Error measure: per (ray, species, zone) system, max_k |psi_gpu - psi_oracle| / max_k |psi_oracle|
+(normwise over the groups).  Both sides evaluate the same FP64 formulas; the PPM limiters are
+continuous, so they differ by rounding (FMA contraction on the GPU) amplified by the energy-fixing
+factor's conditioning, which is poor where the displacement changes sign across the groups."""
+import numpy as np
+import pytest
+
+from oracle import energy_advection_oracle as E
+from paper_1809_05608_gb300 import problems
+
+torch = pytest.importorskip('torch')
+pytestmark = pytest.mark.gpu
+
+M = None
+TOL = 1e-11
+
+
+@pytest.fixture(scope='module', autouse=True)
+def _lib():
+    global M
+    if not torch.cuda.is_available():
+        pytest.skip('no CUDA device')
+    from paper_1809_05608_gb300 import mgfld
+    M = mgfld
+    M.lib()
+
+
+def _centres(r_edge):
+    return 0.5 * (r_edge[:, 1:] + r_edge[:, :-1])
+
+
+def run_oracle(inp, use_eta1=True, use_lapse=True, limit=True):
+    b = lambda a: np.broadcast_to(a[:, None, :], (a.shape[0], 4, a.shape[1]))
+    ones = np.ones_like(inp['rho_n'])
+    a0 = inp['lapse_n'] if use_lapse else ones
+    a1 = inp['lapse_np1'] if use_lapse else ones
+    return E.step(inp['e_edge'], b(a0), b(a1), b(_centres(inp['r_edge_n'])), b(_centres(inp['r_edge_np1'])),
+                  b(inp['rho_n']), b(inp['rho_np1']), inp['psi'], inp['eta1'] if use_eta1 else None, limit=limit)
+
+
+def run_gpu(inp, use_eta1=True, use_lapse=True, limit=True):
+    dev = {k: torch.as_tensor(np.ascontiguousarray(v), device='cuda')
+           for k, v in inp.items() if isinstance(v, np.ndarray)}
+    if not use_eta1:
+        dev.pop('eta1')
+    if not use_lapse:
+        dev.pop('lapse_n')
+        dev.pop('lapse_np1')
+    n_ray, n_s, n_r, n_e = inp['psi'].shape
+    dims = M.Dims(n_ray, n_r, n_e, n_s)
+    psi = dev['psi'].clone()
+    xi = torch.empty(n_ray, n_s, n_r, dtype=torch.float64, device='cuda')
+    rc = M.mgfld_energy_advect(dims, M.eadv_problem(dev, limit), psi, xi)
+    torch.cuda.synchronize()
+    assert rc == M.MGFLD_OK, M.status_str(rc)
+    return psi.cpu().numpy(), xi.cpu().numpy()
+
+
+def normwise(a, b):
+    den = np.max(np.abs(b), axis=-1)
+    return float(np.max(np.max(np.abs(a - b), axis=-1) / np.where(den > 0, den, 1.0)))
+
+
+def xi_sensitivity(ref):
+    """Per system: how far psi moves for a unit relative error of xi, times the relative rounding
+    amplification of xi = (E_b - S1) / S2 (Eqs. p6-p8): kappa = (|E_b| + |S1| + |xi| sum|div eps|)
+    / |S2|, psi_k moving by d xi |div_k| / w_k.  Large where the fluxes nearly cancel in S2."""
+    eps_d, eps_t, F = ref['eps_d'], ref['eps_t'], ref['F']
+    nd = ref['psi_d'] * E.cube_moment(eps_d[..., :-1], eps_d[..., 1:])
+    cd = E.group_centres(eps_d[..., :-1], eps_d[..., 1:])
+    ct = E.group_centres(eps_t[..., :-1], eps_t[..., 1:])
+    div = F[..., :-1] - F[..., 1:]
+    eb, s1, s2 = (np.sum(v, axis=-1) for v in (nd * cd, nd * ct, div * ct))
+    kappa = (np.abs(eb) + np.abs(s1) + np.abs(ref['xi']) * np.sum(np.abs(div * ct), axis=-1))
+    kappa = kappa / np.maximum(np.abs(s2), 1e-300)
+    w_t = E.cube_moment(eps_t[..., :-1], eps_t[..., 1:])
+    return kappa * np.max(np.abs(div) / w_t, axis=-1), kappa
+
+
+def check_parity(psi, ref):
+    """|psi_gpu - psi_oracle| <= 1e-13 max|psi| + 1e-14 x the xi sensitivity, per system (1e-14
+    is ~100 unit roundoffs for the few dozen operations of each sum)."""
+    err = np.max(np.abs(psi - ref['psi']), axis=-1)
+    bound = 1e-13 * np.max(np.abs(ref['psi']), axis=-1) + 1e-14 * xi_sensitivity(ref)[0]
+    worst = float(np.max(err / np.maximum(bound, 1e-300)))
+    print(f'normwise {normwise(psi, ref["psi"]):.2e}, worst error / bound {worst:.2e}')
+    assert worst <= 1.0
+
+
+CASES = [
+    ('single ray 64 x 12', dict(config=1)),
+    ('2 rays 40 x 7 groups', dict(config=2, n_ray=2, n_r=40, n_e=7)),
+    ('1 ray 24 x 32 groups', dict(config=2, n_ray=1, n_r=24, n_e=32)),
+    ('3 rays 512 x 20', dict(config=2, rays=[0, 101, 255])),
+]
+
+
+@pytest.mark.parametrize('name,kw', CASES, ids=[c[0] for c in CASES])
+@pytest.mark.parametrize('use_eta1,use_lapse', [(True, True), (False, False)])
+def test_energy_advection_matches_oracle(name, kw, use_eta1, use_lapse):
+    inp = problems.make_energy_advection(**kw)
+    ref = run_oracle(inp, use_eta1, use_lapse)
+    psi, xi = run_gpu(inp, use_eta1, use_lapse)
+    check_parity(psi, ref)
+    # systems whose energy fix is well conditioned match to near FP64 rounding in the plain norm
+    sens, kappa = xi_sensitivity(ref)
+    well = sens < 1e2 * np.max(np.abs(ref['psi']), axis=-1)
+    assert well.mean() > 0.5
+    assert normwise(psi[well], ref['psi'][well]) < TOL
+    # xi to its own conditioning: (relative rounding of the sums) x kappa
+    assert np.all(np.abs(xi - ref['xi']) <= 1e-13 + 1e-14 * kappa * np.abs(ref['xi']))
+
+
+def test_occupation_limiter_path():
+    """A compression of degenerate spectra (psi = 0.9999 in the low groups) pushes psi above one;
+    the limiter (Eqs. a81a-a81d) brings it back, on both sides."""
+    inp = problems.make_energy_advection(config=2, n_ray=2, n_r=16, n_e=20)
+    inp['psi'][:, :, :, :8] = 0.9999
+    inp['rho_np1'] = inp['rho_n'] * 1.02
+    inp['r_edge_np1'] = inp['r_edge_n'].copy()
+    inp['lapse_np1'] = inp['lapse_n'].copy()
+    unlimited = run_oracle(inp, limit=False)['psi']
+    assert unlimited.max() > 1.0                 # the case exercises the limiter
+    ref = run_oracle(inp)
+    psi, _ = run_gpu(inp)
+    assert np.all(ref['psi'][..., :-2] <= 1.0 + 1e-15)
+    check_parity(psi, ref)
+
+
+def test_full_size_conservation_and_sampled_parity():
+    """The 256-ray workload in the launch configuration the benchmark times: neutrino number per
+    comoving mass conserved by every system, and three rays against the oracle."""
+    inp = problems.make_energy_advection(config=2)
+    psi, xi = run_gpu(inp)
+    n0, _ = E.number_energy(inp['psi'], inp['e_edge'], np.broadcast_to(inp['lapse_n'][:, None], psi.shape[:-1]))
+    n1, _ = E.number_energy(psi, inp['e_edge'], np.broadcast_to(inp['lapse_np1'][:, None], psi.shape[:-1]))
+    rho0 = np.broadcast_to(inp['rho_n'][:, None], n0.shape)
+    rho1 = np.broadcast_to(inp['rho_np1'][:, None], n0.shape)
+    # the limiter moves number between groups without loss; the scale is the system's number
+    # (floored far below every system that holds neutrinos)
+    ref0 = n0 / rho0
+    assert np.max(np.abs(n1 / rho1 - ref0) / (ref0 + 1e-30 * ref0.max())) < 1e-12
+    rays = [0, 128, 255]
+    sub = dict(inp)
+    for key in ('r_edge_n', 'r_edge_np1', 'rho_n', 'rho_np1', 'lapse_n', 'lapse_np1', 'psi', 'eta1'):
+        sub[key] = np.ascontiguousarray(inp[key][rays])
+    ref = run_oracle(sub)
+    check_parity(psi[rays], ref)
+
+
+def test_bad_arguments():
+    inp = problems.make_energy_advection(config=2, n_ray=1, n_r=8, n_e=2)
+    dev = {k: torch.as_tensor(np.ascontiguousarray(v), device='cuda')
+           for k, v in inp.items() if isinstance(v, np.ndarray)}
+    psi = dev['psi'].clone()
+    assert M.mgfld_energy_advect(M.Dims(1, 8, 2, 4), M.eadv_problem(dev), psi) == M.MGFLD_EINVAL
+    inp = problems.make_energy_advection(config=2, n_ray=1, n_r=8, n_e=6)
+    dev = {k: torch.as_tensor(np.ascontiguousarray(v), device='cuda')
+           for k, v in inp.items() if isinstance(v, np.ndarray)}
+    dev.pop('rho_np1')
+    dev['rho_np1'] = None
+    assert M.mgfld_energy_advect(M.Dims(1, 8, 6, 4), M.eadv_problem(dev), dev['psi']) == M.MGFLD_EINVAL
