@@ -47,6 +47,23 @@ identically here and documented with the project's design notes):
       j = kappa_a exp((mu - eps)/T) (Kirchhoff); the exponent is capped at 700
       so that 1/(1 - f_eq) stays finite.
   R11 Gain-region heating weights each zone by its lapse (proper time a_i dt).
+
+Transport through a shock (Sec. "Transport through a Shock", Eqs. a90-a99), taken when the
+problem carries zone velocities u:
+  S1  dpsi0_shock (Eq. a91) and dpsi1_shock (Eq. a97) are formed at the start of the step, from
+      psi^n, like lambda and the limiter (R2): Eq. a93 writes every flux coefficient at n+1 and the
+      frozen reading treats them alike.  The shock terms are then constants of the step and the
+      Jacobian of Eq. a62ae is unchanged.
+  S2  psi1 = eta1 psi^n and psi2 = eta2 psi^n at zone centres, with the flux factor eta1 an input
+      (clamped to [0, 1]; absent, eta1 = 0) and eta2 from the Minerbo closure (Eqs. a86-a87).
+  S3  The psi2 of Eq. a97 at edge i+1/2 is zone i+1's (the frame-(i+1) moment that Eq. a96
+      transforms), on zone i's energy grid (the grid is velocity independent).
+  S4  The group-edge values of Eqs. a92/a98 at the lowest and highest group edges are zero, so the
+      energy-space terms telescope: dpsi1_shock carries no neutrino number (as Eq. a96 carries
+      none in the continuum) and dpsi0_shock removes beta sum_k eps^2 d eps psi1.
+  S5  beta_{i+1/2} = (u_{i+1} - u_i)/c at the interior edges, u zone-centred; the terms are
+      multiplied by a roll-in weight rising linearly from 0 at |beta| = 0.01 to 1 at 0.02; the
+      outermost edge (no zone above) and the centre edge carry none.
 """
 from __future__ import annotations
 
@@ -283,6 +300,8 @@ def setup_step(prob, psi_n, ye_n, T_n):
     f.ghost = ghost_factor(f.rc, r_edge, f.r_nu)
     f.alpha, f.D = edge_coefficients(f)
     f.e_n = e_int(f.rho, f.T_n, f.ye_n, eos)
+    u = prob.get('u')
+    f.shock = None if u is None else shock_corrections(f, prob['e_edge'], u, prob.get('eta1'))
     return f
 
 
@@ -358,6 +377,63 @@ def edge_coefficients(f):
 
 
 # ----------------------------------------------------------------------------
+# Transport through a shock (Eqs. a90-a99), readings S1-S5
+# ----------------------------------------------------------------------------
+
+SHOCK_ROLL_IN = (0.01, 0.02)        # |u_{i+1} - u_i| / c where the shock terms start / are whole
+
+
+def shock_beta(u):
+    """beta_{i+1/2} (Eq. a90) at the n_r - 1 interior edges and the roll-in weight (S5)."""
+    u = np.asarray(u, dtype=np.float64)
+    beta = (u[:, 1:] - u[:, :-1]) / C_LIGHT
+    lo, hi = SHOCK_ROLL_IN
+    return beta, np.clip((np.abs(beta) - lo) / (hi - lo), 0.0, 1.0)
+
+
+def group_edge_mean(m):
+    """m_{k+1/2} = (m_k + m_{k+1})/2 (Eqs. a92, a98) at the N + 1 group edges, zero at the
+    lowest and highest edge (S4)."""
+    out = np.zeros(m.shape[:-1] + (m.shape[-1] + 1,))
+    out[..., 1:-1] = 0.5 * (m[..., :-1] + m[..., 1:])
+    return out
+
+
+def energy_divergence(eps_lo, eps_hi, m):
+    """(eps_+^3 m_{k+1/2} - eps_-^3 m_{k-1/2}) / ((eps_+^3 - eps_-^3)/3): the energy-space term
+    of Eqs. a91 and a97 (the discrete (1/eps^2) d(eps^3 m)/d eps of Eq. a96)."""
+    me = group_edge_mean(m)
+    return (eps_hi**3 * me[..., 1:] - eps_lo**3 * me[..., :-1]) / ((eps_hi**3 - eps_lo**3) / 3.0)
+
+
+def shock_corrections(f, e_edge, u, eta1):
+    """(dpsi0, dpsi1, A/a^2) for the outer edge i+1/2 of every zone, [n_ray, 4, n_r, n_e]:
+    dpsi0 = psi^up_i - psi_i of Eq. a91 (frame change of zone i's psi0 into frame i+1),
+    dpsi1 = the frame-(i+1) to frame-i change of the edge flux, Eq. a97, and A_{i+1/2}/a_{i+1/2}^2
+    (Eq. a99).  Zero at the outermost edge."""
+    from oracle.energy_advection_oracle import minerbo_eta2
+    beta, wgt = shock_beta(u)
+    bw = (beta * wgt)[:, None, :, None]                          # [n_ray, 1, n_r - 1, 1]
+    x = np.zeros_like(f.psi_n) if eta1 is None else np.clip(np.asarray(eta1, dtype=np.float64), 0.0, 1.0)
+    psi1 = x * f.psi_n                                           # S2
+    psi2 = minerbo_eta2(x) * f.psi_n
+    E = np.asarray(e_edge, dtype=np.float64)
+    lo = E[:-1][None, None, :] / f.lapse[:, :, None]             # zone i's comoving group edges
+    hi = E[1:][None, None, :] / f.lapse[:, :, None]
+    lo, hi = lo[:, None, :-1], hi[:, None, :-1]                  # zones 0 .. n_r - 2
+    dpsi0 = np.zeros_like(f.psi_n)
+    dpsi1 = np.zeros_like(f.psi_n)
+    p1 = psi1[:, :, :-1]
+    dpsi0[:, :, :-1] = bw * (-p1 + energy_divergence(lo, hi, p1))           # Eq. a91
+    dpsi1[:, :, :-1] = -bw * energy_divergence(lo, hi, psi2[:, :, 1:])      # Eq. a97 (S3)
+    a_e = np.empty_like(f.lapse)
+    a_e[:, :-1] = 0.5 * (f.lapse[:, :-1] + f.lapse[:, 1:])                  # R7
+    a_e[:, -1] = f.lapse[:, -1]
+    aa = (f.area[:, 1:] / a_e**2)[:, None, :, None]
+    return dpsi0, dpsi1, aa
+
+
+# ----------------------------------------------------------------------------
 # Residual (Eqs. a58, a59, a62a) and exact Jacobian (Eqs. a62ac-a62ae)
 # ----------------------------------------------------------------------------
 
@@ -371,15 +447,23 @@ def sources(f, psi, ye):
 
 
 def flux_divergence(f, psi):
-    """(a_i^2/V_i) [A psi1/a^2 |_{i+1/2} - A psi1/a^2 |_{i-1/2}] of Eq. a58 with Eq. a59."""
+    """(a_i^2/V_i) [A psi1/a^2 |_{i+1/2} - A psi1/a^2 |_{i-1/2}] of Eq. a58 with Eq. a59, or, with
+    a shock, Eq. a99 with Eq. a93.  Also returns A psi1/a^2 at every outer edge (in the frame of
+    the zone above it)."""
     psi_r = np.empty_like(psi)
     psi_r[:, :, :-1] = psi[:, :, 1:]
     psi_r[:, :, -1] = f.ghost * psi[:, :, -1]
-    flux_out = -f.alpha * (psi_r - psi)            # A psi1 / a^2 at i+1/2
+    pre = (f.lapse**2 / f.vol)[:, None, :, None]
+    if f.shock is None:
+        flux_out = -f.alpha * (psi_r - psi)        # A psi1 / a^2 at i+1/2
+        frame = 0.0
+    else:
+        dpsi0, dpsi1, aa = f.shock
+        flux_out = -f.alpha * (psi_r - psi - dpsi0)            # Eq. a93
+        frame = aa * dpsi1                                      # Eq. a99: the flux seen from zone i
     flux_in = np.zeros_like(flux_out)
     flux_in[:, :, 1:] = flux_out[:, :, :-1]        # zero flux at the centre edge
-    pre = (f.lapse**2 / f.vol)[:, None, :, None]
-    return pre * (flux_out - flux_in), flux_out
+    return pre * (flux_out + frame - flux_in), flux_out
 
 
 def residual(f, psi, ye):

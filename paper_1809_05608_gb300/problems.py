@@ -36,6 +36,7 @@ N_SPECIES = 4
 
 FIELD_RHO, FIELD_T, FIELD_KAPPA = 1, 2, 3
 FIELD_HYDRO = 4
+FIELD_SHOCK = 5
 
 
 @dataclasses.dataclass(frozen=True)
@@ -159,13 +160,44 @@ def make_problem(config: int, rays=None, n_ray=None, n_r=None, n_e=None):
 def subset_rays(inp, rays):
     """Restrict every per-ray array of an input dict to the selected rays."""
     prob = dict(inp['problem'])
-    for key in ('r_edge', 'lapse', 'rho', 'kappa_abs', 'kappa_scat', 'nes_coef'):
+    for key in ('r_edge', 'lapse', 'rho', 'kappa_abs', 'kappa_scat', 'nes_coef', 'u', 'eta1'):
         if prob.get(key) is not None:
             prob[key] = np.ascontiguousarray(prob[key][rays])
     out = dict(inp)
     out['problem'] = prob
     for key in ('psi0', 'ye0', 'T0'):
         out[key] = np.ascontiguousarray(inp[key][rays])
+    return out
+
+
+def flux_factor(rc, e_g):
+    """Synthetic flux factor eta1 [n_ray, n_r, n_e]: 0.02 inside to 0.82 outside an
+    energy-dependent neutrinosphere radius 30 km (E / 10 MeV)^(1/2), over a 5 km width."""
+    r_nu = 30.0 * KM * np.sqrt(e_g / 10.0)
+    return 0.02 + 0.4 * (1.0 + np.tanh((rc[:, :, None] - r_nu[None, None, :]) / (5.0 * KM)))
+
+
+def make_shock_problem(config: int, rays=None, n_ray=None, n_r=None, n_e=None, beta_max=0.2):
+    """Configuration `config` with an imposed accretion-shock velocity and a flux factor, for
+    the shock-transport terms.  The velocity follows the imposed-shock test profile (Eq. t8):
+    zero inside r_s - 15 km, falling linearly to -beta_max c at r_s, and -beta_max c (r_s / r)^2
+    outside, with the shock radius r_s = 150 km (1 + d) varying by ray (d the recipe's seeded
+    angular perturbation, |d| <= 0.05).  eta1 as in flux_factor, shared by the species."""
+    out = make_problem(config, n_ray=n_ray, n_r=n_r, n_e=n_e)
+    spec = out['spec']
+    prob = dict(out['problem'])
+    r_edge, e_edge = prob['r_edge'], prob['e_edge']
+    rc = 0.5 * (r_edge[:, 1:] + r_edge[:, :-1])
+    r_s = 150.0 * KM * (1.0 + angular_perturbation(spec, config, FIELD_SHOCK))[:, None]
+    ramp = -beta_max * (rc - (r_s - 15.0 * KM)) / (15.0 * KM)
+    beta = np.where(rc < r_s - 15.0 * KM, 0.0, np.where(rc < r_s, ramp, -beta_max * (r_s / rc) ** 2))
+    prob['u'] = np.ascontiguousarray(beta * 2.99792458e10)
+    e_g = np.sqrt(e_edge[1:] * e_edge[:-1])
+    eta1 = flux_factor(rc, e_g)
+    prob['eta1'] = np.ascontiguousarray(np.broadcast_to(eta1[:, None], rc.shape[:1] + (N_SPECIES,) + eta1.shape[1:]))
+    out = dict(out, problem=prob)
+    if rays is not None:
+        out = subset_rays(out, rays)
     return out
 
 
