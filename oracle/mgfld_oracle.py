@@ -298,7 +298,7 @@ def setup_step(prob, psi_n, ye_n, T_n):
     f.lam = 1.0 / inv_lam
     f.r_nu = neutrinosphere(f.lam, r_edge)
     f.ghost = ghost_factor(f.rc, r_edge, f.r_nu)
-    f.alpha, f.D = edge_coefficients(f)
+    f.alpha, f.D, f.F = edge_coefficients(f)
     f.e_n = e_int(f.rho, f.T_n, f.ye_n, eos)
     u = prob.get('u')
     f.shock = None if u is None else shock_corrections(f, prob['e_edge'], u, prob.get('eta1'))
@@ -337,8 +337,8 @@ def ghost_factor(rc, r_edge, r_nu):
 def edge_coefficients(f):
     """Frozen flux coefficients at the outer edge i+1/2 of every zone (Eqs. a59, a20-a26a).
 
-    Returns alpha = A_{i+1/2} D_{i+1/2} / a_{i+1/2}^2 and D = lambda F / (3 (R_{i+1} - R_i)),
-    both [n_ray, 4, n_r, n_e]; psi^(1)_{i+1/2} = -D (psi_{i+1} - psi_i)."""
+    Returns alpha = A_{i+1/2} D_{i+1/2} / a_{i+1/2}^2, D = lambda F / (3 (R_{i+1} - R_i)) and the
+    limiter F itself, all [n_ray, 4, n_r, n_e]; psi^(1)_{i+1/2} = -D (psi_{i+1} - psi_i)."""
     psi, lam = f.psi_n, f.lam
     n_r = f.n_r
     psi_r = np.empty_like(psi)
@@ -373,7 +373,7 @@ def edge_coefficients(f):
     alpha = f.area[:, 1:][:, None, :, None] * D / (a_e**2)[:, None, :, None]
     if f.outer_bc == BC_REFLECT:
         alpha[:, :, -1, :] = 0.0
-    return alpha, D
+    return alpha, D, F
 
 
 # ----------------------------------------------------------------------------

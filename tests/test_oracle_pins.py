@@ -146,7 +146,7 @@ def _frozen(inp):
 def test_flux_limiter_diffusion_limit_a21():
     f = _frozen(SP.strong(n_ray=1, n_r=10, n_e=3))
     f.lam = np.full_like(f.lam, 1e-9)
-    alpha, D = O.edge_coefficients(f)
+    alpha, D, _ = O.edge_coefficients(f)
     dR = np.diff(np.concatenate([f.rc, (2 * f.r_edge[:, -1] - f.rc[:, -1])[:, None]], axis=1), axis=1)
     F = D[..., :-1, :] * 3 * dR[:, None, :-1, None] / 1e-9
     live = 0.5 * (f.psi_n[..., :-1, :] + f.psi_n[..., 1:, :]) > 1e-300   # reading R3 sets F = 0 else
@@ -163,12 +163,12 @@ def test_flux_limiter_free_streaming_a22_and_geometric_a26b():
     assert live.sum() > 20
     # Neutrinosphere outside the grid: interpolation limiter only -> |psi1| -> psi_edge.
     f.r_nu = np.full_like(f.r_nu, 1e30)
-    _, D = O.edge_coefficients(f)
+    _, D, _ = O.edge_coefficients(f)
     psi1 = -D[..., :-1, :] * (psi_r - psi)
     assert np.max(np.abs(np.abs(psi1) / (0.5 * (psi + psi_r)) - 1.0)[live]) < 1e-12
     # Neutrinosphere at the centre: geometric limiter -> |psi1| = (1 + mu_nu)/2 psi_edge (Eq. a26b).
     f.r_nu = np.full_like(f.r_nu, f.r_edge[0, 0])
-    _, D = O.edge_coefficients(f)
+    _, D, _ = O.edge_coefficients(f)
     psi1 = -D[..., :-1, :] * (psi_r - psi)
     mu = np.sqrt(1 - (f.r_edge[0, 0] / f.r_edge[0, 1:-1]) ** 2)[None, None, :, None]
     ratio = np.abs(psi1) / (0.5 * (1 + mu) * 0.5 * (psi + psi_r))
