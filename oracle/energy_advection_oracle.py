@@ -33,6 +33,10 @@ Readings (the paper is silent or garbled here; the GPU path takes the same ones)
       overfilled group; a removal that would drive psi_{k+2} below zero is scaled down to empty
       it exactly (no removal when psi_{k+2} <= 0).
   E7  eta1 (the flux factor psi1/psi0) is an input, clamped to [0, 1]; absent, eta2 = 1/3.
+  E8  At a shock the shock-transport terms take over from energy advection (Sec. "Transport
+      through a Shock": rolled in as energy advection is rolled out): zone i's displacement in
+      Eq. a79 is scaled by 1 - max(w_{i-1/2}, w_{i+1/2}), w the roll-in weights of its two edges
+      (mgfld_oracle.shock_beta); Eq. a78's number factor is kept, so number is still conserved.
 """
 import numpy as np
 
@@ -67,7 +71,19 @@ def edge_eddington(eta2):
     return out
 
 
-def lagrangian_shift(e_edge, a_n, a_np1, r_n, r_np1, rho_n, rho_np1, eta2, psi):
+def shock_keep(u):
+    """Reading E8: the fraction 1 - max(w_{i-1/2}, w_{i+1/2}) of the displacement kept in each
+    zone, [n_ray, n_r], from zone-centred velocities u [n_ray, n_r]."""
+    from oracle.mgfld_oracle import shock_beta
+    _, w = shock_beta(u)
+    lo = np.zeros(np.shape(u))
+    hi = np.zeros(np.shape(u))
+    lo[:, 1:] = w
+    hi[:, :-1] = w
+    return 1.0 - np.maximum(lo, hi)
+
+
+def lagrangian_shift(e_edge, a_n, a_np1, r_n, r_np1, rho_n, rho_np1, eta2, psi, keep=None):
     """Step 1, Eqs. a78-a80, for systems along the leading axes and groups on the last axis.
 
     e_edge [N+1] are the group edges at infinity (MeV); a, r (zone-centre areal radius) and rho
@@ -81,8 +97,11 @@ def lagrangian_shift(e_edge, a_n, a_np1, r_n, r_np1, rho_n, rho_np1, eta2, psi):
     da_a = (a_np1 - a_n) / a_n
     dr_r = (r_np1 - r_n) / r_n
     db_b = (b_np1 - b_n) / b_n
-    # Eq. a79 at the edges (reading E1)
-    s = 1.0 + (da_a - dr_r) - (db_b - dr_r) * edge_eddington(eta2)
+    # Eq. a79 at the edges (reading E1), rolled out at a shock (reading E8)
+    disp = (da_a - dr_r) - (db_b - dr_r) * edge_eddington(eta2)
+    if keep is not None:
+        disp = np.asarray(keep, dtype=np.float64)[..., None] * disp
+    s = 1.0 + disp
     E = np.broadcast_to(np.asarray(e_edge, dtype=np.float64), s.shape)
     E_d = s * E
     # Eq. a78: (rho a^3)^{n'+1} / (rho a^3)^n x (E^2 dE)^n / (E^2 dE)^{n'+1}, the group moments
@@ -210,13 +229,14 @@ def limit_occupation(psi, epsc, deps):
     return psi
 
 
-def step(e_edge, a_n, a_np1, r_n, r_np1, rho_n, rho_np1, psi, eta1=None, limit=True):
+def step(e_edge, a_n, a_np1, r_n, r_np1, rho_n, rho_np1, psi, eta1=None, limit=True, keep=None):
     """One energy-advection step (Sec. "Neutrino Energy Advection Step"): psi [..., N] on the grid
-    E / a^n in, psi on the grid E / a^{n+1} out.  The zone quantities (a, r, rho) have the shape of
-    psi without its last axis.  Returns dict(psi, xi, psi_d, eps_d, eps_t, F)."""
+    E / a^n in, psi on the grid E / a^{n+1} out.  The zone quantities (a, r, rho, and keep, the
+    displacement fraction of reading E8) have the shape of psi without its last axis.
+    Returns dict(psi, xi, psi_d, eps_d, eps_t, F)."""
     psi = np.asarray(psi, dtype=np.float64)
     eta2 = np.full(psi.shape, 1.0 / 3.0) if eta1 is None else minerbo_eta2(eta1)
-    eps_d, psi_d, nd = lagrangian_shift(e_edge, a_n, a_np1, r_n, r_np1, rho_n, rho_np1, eta2, psi)
+    eps_d, psi_d, nd = lagrangian_shift(e_edge, a_n, a_np1, r_n, r_np1, rho_n, rho_np1, eta2, psi, keep)
     a_np1b = np.asarray(a_np1, dtype=np.float64)[..., None]
     eps_t = np.broadcast_to(np.asarray(e_edge, dtype=np.float64), eps_d.shape) / a_np1b
     dxd = eps_d[..., 1:] - eps_d[..., :-1]

@@ -170,3 +170,21 @@ def test_occupation_limiter_leaves_groups_that_are_not_overfilled():
     psi[5] = 1.2                                 # group 7 (= 5 + 2) holds nothing to remove
     out = E.limit_occupation(psi[None], c[None], d[None])[0]
     assert out[5] == psi[5] and out[7] == psi[7]
+
+
+def test_rollout_at_a_shock():
+    """Reading E8: with the displacement fully rolled out the grid does not move, so no slice
+    crosses an edge and psi only takes Eq. a78's number factor; keep = 1 is the plain step; the
+    zones on either side of a shock edge keep 1 - w of their displacement."""
+    psi, a_n, a1, r_n, r1, rho_n, rho1, eta1 = _random_case(4, scale=1e-2)
+    out0 = E.step(EDGES, a_n, a1, r_n, r1, rho_n, rho1, psi, eta1, limit=False, keep=np.zeros(a_n.shape))
+    factor = (rho1 * a1**3) / (rho_n * a_n**3)
+    assert np.max(np.abs(out0['psi'] - psi * factor[..., None]) / np.abs(psi * factor[..., None])) < 1e-15
+    assert np.all(out0['F'] == 0.0)
+    full = E.step(EDGES, a_n, a1, r_n, r1, rho_n, rho1, psi, eta1, limit=False)
+    ones = E.step(EDGES, a_n, a1, r_n, r1, rho_n, rho1, psi, eta1, limit=False, keep=np.ones(a_n.shape))
+    assert np.array_equal(full['psi'], ones['psi'])
+    c = 2.99792458e10
+    u = np.array([[0.0, 0.0, -0.015 * c, -0.05 * c, -0.05 * c, -0.05 * c]])
+    keep = E.shock_keep(u)
+    assert np.allclose(keep, [[1.0, 0.5, 0.0, 0.0, 1.0, 1.0]], rtol=0, atol=1e-12)
