@@ -52,6 +52,11 @@ def _measured_hbm_gbs():
 
 
 PEAK_HBM_GBS = _measured_hbm_gbs()
+# FP64 operations of one energy-advection update (+, x, /, sqrt one each, FMA two), counted from
+# the formulas the step evaluates per (system, group): Minerbo eta2 16, shifted edge 10, Eq. a78
+# and the cell average 25, slope 27, interface value 45, parabola 14, flux 16, energy sums 7,
+# Eq. p6 and the new psi 7, the zone constants shared over the groups 1.
+EADV_FLOPS_PER_UPDATE = 168
 
 
 def dist_info():
@@ -69,6 +74,14 @@ def shard(n_gpus, rank, rays_per_rank=RAYS_PER_RANK):
 
 def workload(n_gpus, rank, rays_per_rank=RAYS_PER_RANK):
     inp = problems.make_problem(CONFIG_ID, n_ray=rays_per_rank * n_gpus)
+    if n_gpus > 1:
+        inp = problems.subset_rays(inp, shard(n_gpus, rank, rays_per_rank))
+    return inp
+
+
+def shock_workload(n_gpus, rank, rays_per_rank=RAYS_PER_RANK):
+    """The same rays with an imposed accretion-shock velocity profile and a flux factor."""
+    inp = problems.make_shock_problem(CONFIG_ID, n_ray=rays_per_rank * n_gpus)
     if n_gpus > 1:
         inp = problems.subset_rays(inp, shard(n_gpus, rank, rays_per_rank))
     return inp
@@ -368,6 +381,99 @@ def oracle_sample(inp, n_rays, n_steps=1):
                        f'{wall:.1f} s wall', wall_s=wall)
 
 
+def energy_advection_run(M, torch, n_gpus, rank, steps, warmup, cpu_rays=0):
+    """The energy-advection step (mgfld_energy_advect) on the same rays: device-resident inputs,
+    `warmup` untimed steps, then `steps` steps timed with CUDA events on the launching stream
+    (psi is advanced in place; the zone changes repeat every step).  Algorithmic traffic per
+    update: psi read and written, eta1 read (24 B; the per-zone arrays are < 1 %)."""
+    from paper_1809_05608_gb300 import problems as P
+    inp = P.make_energy_advection(CONFIG_ID, n_ray=RAYS_PER_RANK * n_gpus)
+    if n_gpus > 1:
+        sl = shard(n_gpus, rank)
+        for key in ('r_edge_n', 'r_edge_np1', 'rho_n', 'rho_np1', 'lapse_n', 'lapse_np1', 'psi', 'eta1'):
+            inp[key] = np.ascontiguousarray(inp[key][sl])
+    dev = {k: torch.as_tensor(np.ascontiguousarray(v), device='cuda') for k, v in inp.items()
+           if isinstance(v, np.ndarray)}
+    n_ray, n_s, n_r, n_e = inp['psi'].shape
+    dims = M.Dims(n_ray, n_r, n_e, n_s)
+    st = M.eadv_problem(dev)
+    psi = dev['psi'].clone()
+    stream = torch.cuda.current_stream()
+    for _ in range(warmup):
+        assert M.mgfld_energy_advect(dims, st, psi, None, stream) == M.MGFLD_OK
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        M.mgfld_energy_advect(dims, st, psi, None, stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    ups = n_ray * n_s * n_r * n_e
+    gbs = 24.0 * ups / (ms * 1e-3) / 1e9
+    tfs = EADV_FLOPS_PER_UPDATE * ups / (ms * 1e-3) / 1e12
+    peak64 = FP64_FLOP_PER_CLK_SM * N_SM * 2.070e9 / 1e12
+    # The kernel is bound by the FP64 pipe (divisions, square roots and the PPM arithmetic on
+    # 24 B per update), not by HBM; both figures are reported, the FP64 one as the roofline.
+    out = dict(metric='energy-advection updates/s', value=ups / (ms * 1e-3), unit=UNIT, ms_per_step=ms,
+               steps=steps, warmup=warmup, dtype='f64',
+               config=dict(workload=f'{n_ray} rays x {n_r} zones x {n_e} groups x {n_s} species, one step per '
+                                    'launch, psi advanced in place',
+                           l2='reads 168 MB (psi, eta1) and writes 84 MB per step, larger than the 129 MB L2'),
+               roofline=dict(bound='alu', pipe='fp64', kernel='k_energy_advect', achieved=tfs, peak=peak64,
+                             unit='TFLOP/s', frac=tfs / peak64, traffic=None,
+                             flops_per_update=EADV_FLOPS_PER_UPDATE,
+                             peak_source='derived: %g flop/clk/SM x 152 SMs x 2070 MHz max SM clock'
+                                         % FP64_FLOP_PER_CLK_SM),
+               roofline_hbm=dict(bound='hbm', achieved=gbs, peak=PEAK_HBM_GBS, unit='GB/s', frac=gbs / PEAK_HBM_GBS,
+                                 bytes_per_update=24, peak_source='measured copy bandwidth (of measured)'))
+    if cpu_rays:
+        from oracle import energy_advection_oracle as EO
+        sub = {k: (np.ascontiguousarray(v[:cpu_rays]) if isinstance(v, np.ndarray) and v.ndim > 1 else v)
+               for k, v in inp.items()}
+        rc0 = 0.5 * (sub['r_edge_n'][:, 1:] + sub['r_edge_n'][:, :-1])
+        rc1 = 0.5 * (sub['r_edge_np1'][:, 1:] + sub['r_edge_np1'][:, :-1])
+        b = lambda a: np.broadcast_to(a[:, None, :], (a.shape[0], n_s, a.shape[1]))
+        c0, w0 = time.process_time(), time.perf_counter()
+        EO.step(sub['e_edge'], b(sub['lapse_n']), b(sub['lapse_np1']), b(rc0), b(rc1), b(sub['rho_n']),
+                b(sub['rho_np1']), sub['psi'], sub['eta1'])
+        wall = time.perf_counter() - w0
+        out['cpu_baseline'] = dict(value=cpu_rays * n_s * n_r * n_e / wall, unit=UNIT,
+                                   cores=max(1, int(round((time.process_time() - c0) / wall))), kind='oracle',
+                                   sample=f'{cpu_rays} of the {n_ray} rays x 1 step, FP64 numpy, {wall:.2f} s wall')
+    return out
+
+
+def stress_lapse_run(M, torch, inp, steps, warmup):
+    """mgfld_stress_lapse (the neutrino stress and the lapse, Eqs. a62e-a62l) on the benchmark rays'
+    state: device-resident inputs, `warmup` untimed calls, `steps` calls timed with CUDA events on
+    the launching stream.  Each call forms the transport coefficients of the state (the setup
+    kernels of the step) before the stress and lapse kernels, which the setup dominates."""
+    p, m = problems.stress_inputs(inp)
+    n_ray, n_s, n_r, n_e = inp['psi0'].shape
+    dims = M.Dims(n_ray, n_r, n_e, n_s)
+    dp = M.DeviceProblem(inp['problem'])
+    dev = lambda a: torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64), device='cuda')
+    psi, ye, T, pd, md = dev(inp['psi0']), dev(inp['ye0']), dev(inp['T0']), dev(p), dev(m)
+    ws = torch.empty(M.mgfld_workspace_bytes(dims, M.MGFLD_FP64), dtype=torch.uint8, device='cuda')
+    out = {k: torch.empty(n_ray, n_r, dtype=torch.float64, device='cuda') for k in ('f_edge', 'f_zone', 'lapse')}
+    stream = torch.cuda.current_stream()
+    for _ in range(warmup):
+        assert M.mgfld_stress_lapse(dims, dp.struct, psi, ye, T, ws, p=pd, m_inner=md, stream=stream, **out) == 0
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        M.mgfld_stress_lapse(dims, dp.struct, psi, ye, T, ws, p=pd, m_inner=md, stream=stream, **out)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    ups = n_ray * n_s * n_r * n_e
+    return dict(metric='stress-and-lapse updates/s', value=ups / (ms * 1e-3), unit=UNIT, ms_per_call=ms,
+                steps=steps, warmup=warmup, dtype='f64', launches_per_call=9,
+                note='one call = the 7 setup kernels of the transport step on the state, k_stress, k_lapse')
+
+
 def reference_arm(args, n_gpus, rank):
     if rank != 0:
         return 0
@@ -395,15 +501,35 @@ def reference_arm(args, n_gpus, rank):
 # ------------------------------------------------------------------------- main
 
 def profile_step(path, n_rays):
-    """One implicit step of the first n_rays rays of the benchmark workload (FP64 Newton or the
-    mixed path), for ncu captures of single launches; exits non-zero on a failed step."""
+    """One implicit step of the first n_rays rays of the benchmark workload (FP64 Newton, the
+    mixed path, or the mixed path with the shock terms), or two energy-advection steps, for ncu
+    captures of single launches; exits non-zero on a failed step."""
     import torch
     from paper_1809_05608_gb300 import build as B
     if not os.path.exists(B.LIB):
         B.build()
     from paper_1809_05608_gb300 import mgfld as M
-    inp = problems.make_problem(CONFIG_ID, rays=slice(0, n_rays))
-    prec = M.MGFLD_MIXED if path == 'mixed' else M.MGFLD_FP64
+    if path == 'eadv':
+        inp = problems.make_energy_advection(CONFIG_ID, rays=slice(0, n_rays))
+        dev = {k: torch.as_tensor(np.ascontiguousarray(v), device='cuda') for k, v in inp.items()
+               if isinstance(v, np.ndarray)}
+        n_ray, n_s, n_r, n_e = inp['psi'].shape
+        rc = 0
+        for _ in range(2):
+            rc = rc or M.mgfld_energy_advect(M.Dims(n_ray, n_r, n_e, n_s), M.eadv_problem(dev), dev['psi'])
+        torch.cuda.synchronize()
+        print(f'profile step eadv: {n_rays} rays, status {M.status_str(rc)}', flush=True)
+        return 0 if rc == M.MGFLD_OK else 1
+    if path == 'stress':
+        inp = problems.make_problem(CONFIG_ID, rays=slice(0, n_rays))
+        res = stress_lapse_run(M, torch, inp, 1, 1)
+        print(f'profile step stress: {n_rays} rays, {res["ms_per_call"]:.3f} ms', flush=True)
+        return 0
+    if path == 'shock':
+        inp = problems.make_shock_problem(CONFIG_ID, rays=slice(0, n_rays))
+    else:
+        inp = problems.make_problem(CONFIG_ID, rays=slice(0, n_rays))
+    prec = M.MGFLD_FP64 if path == 'fp64' else M.MGFLD_MIXED
     st = M.Stepper(inp, prec, tol=TOL, max_iter=60)
     psi, ye, T = st.state_to_device(inp['psi0'], inp['ye0'], inp['T0'])
     rc = st.step(psi, ye, T)
@@ -421,8 +547,10 @@ def main():
     ap.add_argument('--impl', default='mgfld', choices=['mgfld', 'reference'])
     ap.add_argument('--oracle-rays', type=int, default=12)
     ap.add_argument('--no-cpu-baseline', action='store_true')
-    ap.add_argument('--profile-step', choices=['mixed', 'fp64'],
-                    help='profiling target: one implicit step of this path on --rays rays, no timing')
+    ap.add_argument('--profile-step', choices=['mixed', 'fp64', 'shock', 'eadv', 'stress'],
+                    help='profiling target: one implicit step of this path (shock: the mixed path with '
+                         'the shock terms; eadv: two energy-advection steps; stress: two stress-and-lapse '
+                         'calls) on --rays rays, no timing')
     ap.add_argument('--rays', type=int, default=64)
     args = ap.parse_args()
     if args.profile_step:
@@ -469,12 +597,18 @@ def main():
     ms_newton = max_over_ranks(newton['ms']) / args.steps
     value = job_throughput(ups, ws, ms_mixed)
     value64 = job_throughput(ups, ws, ms_fp64)
+    # the same step with the shock-transport terms (Eqs. a90-a99) on the imposed shock profile
+    shock = run_path(M, torch, shock_workload(n_gpus, rank), M.MGFLD_MIXED, args.steps, args.warmup, barrier)
+    ms_shock = max_over_ranks(shock['ms']) / args.steps
     e2e = e2e_run(M, torch, inp, M.MGFLD_MIXED, args.steps)
     e2e_ms = max_over_ranks(e2e['ms']) / args.steps
     roof = roofline_for(mixed, inp, M.MGFLD_MIXED, mixed['clocks'])
     roof64 = roofline_for(fp64, inp, M.MGFLD_FP64, None)
     roof_newton = roofline_for(newton, inp, M.MGFLD_FP64, None)
     launches = sum(v['launches'] for v in mixed['prof'].values())
+    stress = stress_lapse_run(M, torch, inp, args.steps, args.warmup)
+    eadv = energy_advection_run(M, torch, n_gpus, rank, args.steps, args.warmup,
+                                cpu_rays=0 if (rank != 0 or args.no_cpu_baseline) else 64)
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         cpu = oracle_sample(inp, args.oracle_rays)
@@ -508,7 +642,17 @@ def main():
                               kernel_ms={k: v['ms'] for k, v in newton['prof'].items()},
                               outer_iterations_per_step=newton['max_iters'],
                               factorizations_per_ray_step=newton['nfact'] / (RAYS_PER_RANK * args.steps)),
-        mixed_over_fp64=value / value64)
+        shock_path=dict(value=job_throughput(ups, ws, ms_shock), unit=UNIT, ms_per_step=ms_shock,
+                        dtype='f32 factor + f64 residual/update',
+                        workload='the same rays with the imposed accretion-shock velocity (zero inside '
+                                 'r_s - 15 km, -0.2c at r_s ~ 150 km, -0.2c (r_s/r)^2 outside) and a '
+                                 'synthetic flux factor; shock terms of Eqs. a91-a99 at the shock',
+                        kernel_ms={k: v['ms'] for k, v in shock['prof'].items()},
+                        outer_iterations_per_step=shock['max_iters'],
+                        gpu_launches=sum(v['launches'] for v in shock['prof'].values())),
+        mixed_over_fp64=value / value64,
+        energy_advection=eadv,
+        stress_lapse=stress)
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()

@@ -72,6 +72,19 @@ typedef struct {
   mgfld_eos_params eos;
   double dt;                /* time step (s) */
   int outer_bc;             /* mgfld_outer_bc */
+  /* Transport through a shock (Sec. "Transport through a Shock", Eqs. a90-a99), both optional:
+   * u     [n_ray][n_r] zone-centred fluid velocity (cm/s), or NULL for no shock terms.  At each
+   *       interior edge i+1/2, beta = (u_{i+1} - u_i)/c; the frame corrections dpsi0_shock (Eq. a91,
+   *       the flux of Eq. a93) and dpsi1_shock (Eq. a97, the bracket of Eq. a99) are weighted by a
+   *       roll-in rising linearly from 0 at |beta| = 0.01 to 1 at |beta| = 0.02, and are formed
+   *       at psi^n for the step (like the diffusion coefficient), so the Newton system keeps its
+   *       block structure.  The outermost edge and the centre edge carry none.
+   * eta1  [n_ray][n_s][n_r][n_e] flux factor psi1/psi0 at zone centres (clamped to [0, 1]) from
+   *       which psi1 = eta1 psi^n and psi2 = eta2(eta1) psi^n (Minerbo closure, Eqs. a86-a87) are
+   *       formed, or NULL for eta1 = 0.  Read only when u is set.
+   * The shock terms are not differentiated: mgfld_adjoint returns MGFLD_EINVAL when u is set. */
+  const double *u;
+  const double *eta1;
 } mgfld_problem;
 
 /* State at t^n on entry, t^{n+1} on exit (in place). */
@@ -99,7 +112,7 @@ typedef struct {
 
 /* Kernel categories of mgfld_step_opts.profile. */
 enum {
-  MGFLD_PROF_SETUP = 0,    /* frozen coefficients: groups, EoS, NES kernels, mean free path, limiter (6 kernels) */
+  MGFLD_PROF_SETUP = 0,    /* frozen coefficients: groups, EoS, NES kernels, mean free path, limiter, shock terms */
   MGFLD_PROF_ASSEMBLE = 1, /* residual and Jacobian rows (k_assemble) */
   MGFLD_PROF_FACTOR = 2,   /* block-Thomas elimination with in-block Gauss-Jordan (k_factor) */
   MGFLD_PROF_SOLVE = 3,    /* forward/back substitution (k_solve) */
@@ -300,6 +313,12 @@ typedef struct {
   const double *eta1;                    /* [n_ray][n_s][n_r][n_e] flux factors psi1/psi0 (clamped
                                             to [0, 1]), or NULL: eta2 = 1/3 (diffusion limit) */
   int limit;                             /* nonzero: apply step 3 */
+  const double *u;                       /* [n_ray][n_r] zone-centred fluid velocity (cm/s), or NULL.
+                                            At a shock the shock-transport terms of mgfld_problem.u
+                                            replace energy advection: zone i's displacement (Eq.
+                                            a79) is scaled by 1 - max(w_{i-1/2}, w_{i+1/2}), w the
+                                            roll-in weights of its edges (0 at |u_{i+1} - u_i| =
+                                            0.01c, 1 at 0.02c); the number factor of Eq. a78 stays */
 } mgfld_eadv_problem;
 
 /*
@@ -311,6 +330,41 @@ typedef struct {
  */
 mgfld_status mgfld_energy_advect(const mgfld_dims *dims, const mgfld_eadv_problem *prob, double *psi,
                                  double *xi, void *stream);
+
+/*
+ * Neutrino stress and lapse update (Sec. "Solution of the Transport Equations", Eqs. a62e-a62l).
+ *   p        [n_ray][n_r] matter pressure at zone centres (erg/cm^3); required when lapse is set.
+ *   m_inner  [n_ray] rest mass inside the innermost edge R_{1/2} (g), or NULL for 0.
+ *   f_edge   [n_ray][n_r] out: the stress (force per unit mass on the matter, cm/s^2, outward
+ *            positive) at each zone's outer edge, Eq. a62e with the difference of Eq. a62f; the
+ *            outermost edge uses the transport's ghost zone (Eq. a62af), none with a reflecting
+ *            edge.  Or NULL.
+ *   f_zone   [n_ray][n_r] out: the zone value, the mean of its two edges (Eq. a62i; the centre
+ *            edge carries none), or NULL.
+ *   lapse    [n_ray][n_r] out: the lapse at zone centres, Eqs. a62k-a62l: the exterior
+ *            sqrt(1 - 2 G M / (c^2 R_{I+1/2})) of the enclosed rest mass M = m_inner + sum rho V in
+ *            the last zone, then inward a_i = a_{i+1} exp[(p_{i+1} - p_i - Delta M_{i+1/2}
+ *            f_{i+1/2} / (4 pi R_{i+1/2}^2)) / (rho_{i+1/2} c^2)] (edge values the means of the two
+ *            zones), or NULL.
+ * All device pointers, caller-owned.
+ */
+typedef struct {
+  const double *p;
+  const double *m_inner;
+  double *f_edge, *f_zone, *lapse;
+} mgfld_stress_io;
+
+/*
+ * mgfld_stress_lapse -- the neutrino stress of the state (psi, Ye, T) of problem `prob` and the
+ * lapse it supports.  The flux limiter F^{n+1} of Eq. a62e is evaluated at this state with the
+ * transport step's own coefficients (mean free path, neutrinosphere, ghost factor); energies are
+ * each zone's comoving group energies E/a (prob->lapse is the lapse the state was computed on).
+ * prob->u is ignored.  ws: at least mgfld_workspace_bytes(dims, MGFLD_FP64) bytes, 256-byte
+ * aligned, scratch.  Asynchronous on `stream`.  Returns OK, EINVAL (bad arguments, or lapse
+ * without p), ENOMEM (workspace too small) or ECUDA.
+ */
+mgfld_status mgfld_stress_lapse(const mgfld_dims *dims, const mgfld_problem *prob, const mgfld_state *state,
+                                const mgfld_stress_io *io, void *ws, size_t ws_bytes, void *stream);
 
 /* Human-readable name of a status code (static string). */
 const char *mgfld_status_str(mgfld_status s);

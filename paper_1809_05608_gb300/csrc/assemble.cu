@@ -3,6 +3,7 @@
 // One thread owns the equation of (ray, species q, zone i, group k):
 //   G = (psi - psi^n)/(a c dt) + (a^2/V)[A psi1/a^2 |_{i+1/2} - A psi1/a^2 |_{i-1/2}] - S,
 //   psi1_{i+1/2} = -D_{i+1/2} (psi_{i+1} - psi_i)              (Eq. a59, D frozen at psi^n)
+//   (with a shock, Eqs. a93/a99: a step constant joins the bracket, see k_shock)
 //   S = j (1 - psi) - kappa_a psi                             (Eq. a55)
 //     + C [(1 - psi_k) sum_k' w_k' Phi_in[k,k'] psi_k' - psi_k sum_k' w_k' Phi_out[k,k'] (1 - psi_k')]
 //                                                              (Eq. d8, Phi_1 = 0; Phi_in[k,k'] = Phi_out[k',k])
@@ -90,7 +91,9 @@ __global__ void k_assemble(Prob p, Ws w, const double *__restrict__ psi, TD *__r
   const double p_left = i > 0 ? ps[k - (ptrdiff_t)n] : pk;
   const double flux_out = -al_out * (p_right - pk);
   const double flux_in = -al_in * (pk - p_left);
-  const double G = (pk - w.psi_n[g]) * inv_acdt + pre * (flux_out - flux_in) - S;
+  // shock transport: the step-constant frame terms of Eqs. a93 and a99 (formed at psi^n)
+  const double sh = p.u ? w.shock[g] : 0.0;
+  const double G = (pk - w.psi_n[g]) * inv_acdt + pre * (flux_out - flux_in + sh) - S;
   rhs[g] = -G;
 
   if (jac_flag && !jac_flag[ray]) return;

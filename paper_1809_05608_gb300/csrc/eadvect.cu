@@ -7,38 +7,42 @@
 // A block takes SPB consecutive (ray, species, zone) systems and one thread per (system, group):
 // the systems' rows of psi (and eta1) are contiguous, so loads and stores are coalesced; each
 // phase of the remap (shifted edges, cell averages, slopes, interface values, parabolas, fluxes)
-// runs over the elements in shared memory between block barriers, and the per-system parts (the
-// zone's constants, the three energy sums of xi, the sequential limiter) run on the system's
-// first thread.  All arithmetic is FP64.  The PPM limiters are continuous in their inputs, so
-// rounding differences against a CPU evaluation (FMA contraction) move results by rounding only.
+// runs over the elements in shared memory between block barriers.  All arithmetic is FP64, and
+// the FP64 pipe bounds the kernel (every FP64 warp instruction occupies it for the same time,
+// however few lanes are active), so the work is arranged to keep FP64 instructions few and
+// warp-wide: the zone's constants are spread over the system's first threads, quotients that
+// share a denominator are formed with one division (slopes, interface values), cube moments and
+// cell averages use the factored form (hi^3 - lo^3)/(hi - lo) = hi^2 + hi lo + lo^2, the grid at
+// infinity (moments, centres) is formed once per block, and the three energy sums of xi are a
+// tree reduction over the system's threads.  Only the occupation limiter, rarely active, is
+// sequential.  The PPM limiters are continuous in their inputs, so these rearrangements move
+// results by rounding only.
 #include "mgfld_internal.cuh"
 
 namespace mgfld {
 
 constexpr int kEadvThreads = 256;
-
-__device__ inline double cube_moment(double lo, double hi) { return (hi * hi * hi - lo * lo * lo) / 3.0; }
-__device__ inline double centre(double lo, double hi) { return sqrt((hi * hi + hi * lo + lo * lo) / 3.0); }
-
-// Minerbo closure (Eqs. a86-a87) with eta2_thick = 1/3 and eta2_thin = 1.
-__device__ inline double minerbo_eta2(double eta1) {
-  const double x = fmin(fmax(eta1, 0.0), 1.0);
-  const double p = 1.0 / 3.0 + 2.0 * x * x / 15.0 * (3.0 - x + 3.0 * x * x);
-  return 1.5 * (1.0 - p) * (1.0 / 3.0) + 0.5 * (3.0 * p - 1.0);
-}
+constexpr double kThird = 1.0 / 3.0;
 
 struct EadvArgs {
   int n_ray, n_r, n, spb, limit;
-  const double *r_n, *r_np1, *rho_n, *rho_np1, *a_n, *a_np1, *e_edge, *eta1;
+  const double *r_n, *r_np1, *rho_n, *rho_np1, *a_n, *a_np1, *e_edge, *eta1, *u;
   double *psi, *xi;
 };
 
-// Shared-memory layout per system (stride per array, in doubles):
-//   E_d[n+1] shifted edges at infinity, eps_t[n+1] target edges, nd[n] numbers on the shifted
-//   groups, A[n+4], X[n+4] cell averages and widths with two ghost groups at each end, dm[n+4]
-//   monotonised slopes, face[n+4] interface values, aL/aR/a6[n], F[n+1] fluxes, eta2[n], zc[4]
-//   zone constants (da/a - dR/R, db/b - dR/R, a^{n+1}, the number factor of Eq. a78), sums[4].
-__host__ __device__ inline int eadv_stride(int n) { return 13 * (n + 5) + 8; }
+// Shared memory: a block header of 3 MAX_NE doubles (per group of the grid at infinity: the
+// moment E^2 dE = (E_+^3 - E_-^3)/3, its reciprocal, the centre E_k of Eq. a01b), then per
+// system (stride per array, in doubles): E_d[n+1] shifted edges at infinity, nd[n] numbers on
+// the shifted groups, A[n+4], X[n+4] cell averages and widths with two ghost groups at each end,
+// dm[n+4] monotonised slopes, face[n+4] interface values, aL/aR/a6[n], F[n+1] fluxes, eta2[n]
+// (later the target centres), epsd_c[n] shifted centres, red[3][n+5] reduction scratch, zc[10]
+// zone constants (a^{n+1}/a^n, R^{n+1}/R^n, b^{n+1}/b^n, the number factor of Eq. a78, 1/a^{n+1},
+// the kept fraction of the displacement, xi, the limiter flag, (a^{n+1})^3).
+constexpr int kEadvHeader = 3 * MAX_NE;
+__host__ __device__ inline int eadv_stride(int n) { return 15 * (n + 5) + 10; }
+__host__ __device__ inline size_t eadv_smem(int spb, int n) {
+  return sizeof(double) * ((size_t)kEadvHeader + (size_t)spb * eadv_stride(n));
+}
 
 __global__ void __launch_bounds__(kEadvThreads) k_energy_advect(EadvArgs g) {
   extern __shared__ double sh[];
@@ -49,101 +53,137 @@ __global__ void __launch_bounds__(kEadvThreads) k_energy_advect(EadvArgs g) {
   const int sl = tid / n, k = tid - sl * n;
   const unsigned sg = s0 + (unsigned)sl;
   const bool live = sl < spb && sg < n_sys;
-  double *base = sh + (size_t)(live ? sl : 0) * st;
-  double *E_d = base, *eps_t = E_d + (n + 5), *nd = eps_t + (n + 5), *A = nd + (n + 5), *X = A + (n + 5);
+  double *cmE = sh, *icmE = sh + MAX_NE, *Ec = sh + 2 * MAX_NE;
+  double *base = sh + kEadvHeader + (size_t)(live ? sl : 0) * st;
+  double *E_d = base, *nd = E_d + (n + 5), *A = nd + (n + 5), *X = A + (n + 5);
   double *dm = X + (n + 5), *face = dm + (n + 5), *aL = face + (n + 5), *aR = aL + (n + 5), *a6 = aR + (n + 5);
-  double *F = a6 + (n + 5), *eta2 = F + (n + 5), *epsd_c = eta2 + (n + 5), *zc = epsd_c + (n + 5);
+  double *F = a6 + (n + 5), *eta2 = F + (n + 5), *epsd_c = eta2 + (n + 5), *red = epsd_c + (n + 5);
+  double *zc = red + 3 * (n + 5);
   // system (ray, q, i) and its zone
   const unsigned ray = live ? sg / (NS * (unsigned)g.n_r) : 0;
   const unsigned i = live ? sg % (unsigned)g.n_r : 0;
   const size_t zi = (size_t)ray * g.n_r + i;
   const size_t el = (size_t)sg * n + k;
   double psi0 = 0.0;
-  // Phase 1: the zone's constants (first thread of the system) and eta2 per group.
+  // Phase 1: the grid at infinity (block), eta2 per group, and the zone's constants, the
+  // system's threads sharing the five divisions: a^{n+1}/a^n, 1/a^{n+1}, R^{n+1}/R^n (R the
+  // zone-centre areal radius, the mean of its edges), b^{n+1}/b^n with b = 1/(4 pi R^2 rho), and
+  // the number factor (rho a^3)^{n+1}/(rho a^3)^n of Eq. a78; the first thread adds the kept
+  // fraction of the displacement.
+  if (tid < n) {
+    const double lo = g.e_edge[tid], hi = g.e_edge[tid + 1];
+    const double q = hi * hi + hi * lo + lo * lo;
+    cmE[tid] = (hi - lo) * q * kThird;
+    icmE[tid] = 1.0 / cmE[tid];
+    Ec[tid] = sqrt(q * kThird);
+  }
   if (live) {
     psi0 = g.psi[el];
-    eta2[k] = g.eta1 ? minerbo_eta2(g.eta1[el]) : 1.0 / 3.0;
+    eta2[k] = g.eta1 ? minerbo_eta2(g.eta1[el]) : kThird;
+    // quotient j of the zone (every thread of the system takes one or two, same code path):
+    // 0 a^{n+1}/a^n, 1 1/a^{n+1}, 2 R^{n+1}/R^n, 3 b^{n+1}/b^n, 4 the number factor
+    const double *re0 = g.r_n + ray * (size_t)(g.n_r + 1) + i, *re1 = g.r_np1 + ray * (size_t)(g.n_r + 1) + i;
+    const double a0 = g.a_n ? g.a_n[zi] : 1.0, a1 = g.a_np1 ? g.a_np1[zi] : 1.0;
+    const double rho0 = g.rho_n[zi], rho1 = g.rho_np1[zi];
+    const double r0 = re0[0] + re0[1], r1 = re1[0] + re1[1];
+    for (int j = k; j < 5; j += n) {
+      const double num = j == 0 ? a1 : j == 1 ? 1.0 : j == 2 ? r1 : j == 3 ? r0 * r0 * rho0 : rho1 * a1 * a1 * a1;
+      const double den = j == 0 ? a0 : j == 1 ? a1 : j == 2 ? r0 : j == 3 ? r1 * r1 * rho1 : rho0 * a0 * a0 * a0;
+      zc[j < 2 ? 4 * j : j - 1] = num / den;    // slots 0, 4, 1, 2, 3
+    }
     if (k == 0) {
-      const double *re0 = g.r_n + ray * (size_t)(g.n_r + 1) + i, *re1 = g.r_np1 + ray * (size_t)(g.n_r + 1) + i;
-      const double r0 = 0.5 * (re0[0] + re0[1]), r1 = 0.5 * (re1[0] + re1[1]);
-      const double rho0 = g.rho_n[zi], rho1 = g.rho_np1[zi];
-      const double a0 = g.a_n ? g.a_n[zi] : 1.0, a1 = g.a_np1 ? g.a_np1[zi] : 1.0;
-      const double b0 = 1.0 / (4.0 * kPi * r0 * r0 * rho0), b1 = 1.0 / (4.0 * kPi * r1 * r1 * rho1);
-      const double da_a = (a1 - a0) / a0, dr_r = (r1 - r0) / r0, db_b = (b1 - b0) / b0;
-      zc[0] = da_a - dr_r;
-      zc[1] = db_b - dr_r;
-      zc[2] = a1;
-      zc[3] = (rho1 * a1 * a1 * a1) / (rho0 * a0 * a0 * a0);
+      zc[7] = 0.0;
+      zc[8] = a1 * a1 * a1;
+      // at a shock the displacement is rolled out by the roll-in weights of the zone's edges
+      double keep = 1.0;
+      if (g.u) {
+        const double *u = g.u + (size_t)ray * g.n_r;
+        double wmax = 0.0;
+        for (int e = -1; e <= 0; ++e) {               // edges i-1/2 and i+1/2
+          const int lo = (int)i + e;
+          if (lo < 0 || lo + 1 >= g.n_r) continue;
+          const double beta = (u[lo + 1] - u[lo]) / kC;
+          wmax = fmax(wmax, fmin(fmax((fabs(beta) - kShockOn) / (kShockFull - kShockOn), 0.0), 1.0));
+        }
+        keep = 1.0 - wmax;
+      }
+      zc[5] = keep;
     }
   }
   __syncthreads();
-  // Phase 2: shifted edges (Eq. a79 at the edges, eta2 the mean of the adjacent groups) and the
-  // target edges E / a^{n+1} (Eq. p1); thread k takes edge k, the last group also edge n.
+  // Phase 2: shifted edges (Eq. a79 at the edges, eta2 the mean of the adjacent groups):
+  // E_d = E (1 + keep [(da/a - dR/R) - (db/b - dR/R) eta2]); thread k takes edge k, the last
+  // group also edge n.
   if (live) {
-    const double a1 = zc[2];
+    const double tr = zc[1], keep = zc[5];
+    const double c0 = keep * (zc[0] - tr), c1 = keep * (zc[2] - tr);
     const double e2k = k == 0 ? eta2[0] : 0.5 * (eta2[k - 1] + eta2[k]);
-    const double Ek = g.e_edge[k];
-    E_d[k] = (1.0 + zc[0] - zc[1] * e2k) * Ek;
-    eps_t[k] = Ek / a1;
-    if (k == n - 1) {
-      const double En = g.e_edge[n];
-      E_d[n] = (1.0 + zc[0] - zc[1] * eta2[n - 1]) * En;
-      eps_t[n] = En / a1;
-    }
+    E_d[k] = (1.0 + c0 - c1 * e2k) * g.e_edge[k];
+    if (k == n - 1) E_d[n] = (1.0 + c0 - c1 * eta2[n - 1]) * g.e_edge[n];
   }
   __syncthreads();
-  // Phase 3: Eq. a78 (psi on the shifted group, its number nd) and the cell averages eps^2 psi
-  // of the parabolic remap, with two zero-slope ghost groups at each end.
+  // Phase 3: Eq. a78 (psi on the shifted group), its number nd and the cell average eps^2 psi
+  // of the parabolic remap (number per unit comoving energy), with two zero-slope ghost groups at
+  // each end; the shifted group centre (Eq. a01b).
   if (live) {
-    const double a1 = zc[2];
-    const double El = g.e_edge[k], Eh = g.e_edge[k + 1];
-    const double psi_d = zc[3] * (cube_moment(El, Eh) / cube_moment(E_d[k], E_d[k + 1])) * psi0;
-    const double lo = E_d[k] / a1, hi = E_d[k + 1] / a1;
-    const double num = psi_d * cube_moment(lo, hi);
+    const double ia1 = zc[4];
+    const double Dl = E_d[k], Dh = E_d[k + 1];
+    const double qD = Dh * Dh + Dh * Dl + Dl * Dl;
+    const double psi_d = zc[3] * cmE[k] / ((Dh - Dl) * qD * kThird) * psi0;
+    const double lo = Dl * ia1, hi = Dh * ia1;
+    const double q = hi * hi + hi * lo + lo * lo;
     const double dx = hi - lo;
-    nd[k] = num;
-    epsd_c[k] = centre(lo, hi);
-    A[k + 2] = num / dx;
+    const double avg = psi_d * q * kThird;
+    nd[k] = avg * dx;
+    epsd_c[k] = sqrt(q * kThird);
+    A[k + 2] = avg;
     X[k + 2] = dx;
     if (k == 0) {
-      A[0] = A[1] = num / dx;
+      A[0] = A[1] = avg;
       X[0] = X[1] = dx;
     }
     if (k == n - 1) {
-      A[n + 2] = A[n + 3] = num / dx;
+      A[n + 2] = A[n + 3] = avg;
       X[n + 2] = X[n + 3] = dx;
     }
   }
   __syncthreads();
-  // Phase 4: average slopes (Eq. h9) monotonised (Eq. h11) at extended groups 1..n+2.
+  // Phase 4: average slopes (Eq. h9) monotonised (Eq. h11) at the groups (extended index
+  // 2..n+1), the two quotients of Eq. h9 over a common denominator.  The ghost groups copy their
+  // neighbour, so one of their two differences is zero and the limiter makes their slopes zero.
   auto slope = [&](int j) {
     const double xl = X[j - 1], x0 = X[j], xr = X[j + 1];
     const double dp = A[j + 1] - A[j], dn = A[j] - A[j - 1];
-    const double s = x0 / (xl + x0 + xr) * ((2.0 * xl + x0) / (xr + x0) * dp + (x0 + 2.0 * xr) / (xl + x0) * dn);
+    const double sl_ = xl + x0, sr = xr + x0;
+    const double s = x0 * ((2.0 * xl + x0) * sl_ * dp + (x0 + 2.0 * xr) * sr * dn) / ((xl + x0 + xr) * sr * sl_);
     const double lim = fmin(fabs(s), fmin(2.0 * fabs(dp), 2.0 * fabs(dn)));
     dm[j] = dp * dn > 0.0 ? copysign(lim, s) : 0.0;
   };
   if (live) {
-    slope(k + 1);
-    if (k < 2) slope(n + 1 + k);
+    slope(k + 2);
+    if (k < 2) dm[k == 0 ? 1 : n + 2] = 0.0;
   }
   __syncthreads();
   // Phase 5: interface values between extended groups j and j+1, j = 1..n+1 (Eq. h12, the cubic
-  // through the group integrals), limited to the range of the two averages (Eqs. h15-h16).
+  // through the group integrals), limited to the range of the two averages (Eqs. h15-h16); the
+  // five quotients over one denominator (x0 + x1)(2 x0 + x1)(x0 + 2 x1)(xl + x0 + x1 + x2).  At
+  // the two end interfaces the ghost's average equals the group's, so the limiter returns it.
   auto interface = [&](int j) {
     const double xl = X[j - 1], x0 = X[j], x1 = X[j + 1], x2 = X[j + 2];
     const double d = A[j + 1] - A[j];
+    const double P = 2.0 * x0 + x1, Q = x0 + 2.0 * x1, s01 = x0 + x1;
     const double tot = xl + x0 + x1 + x2;
-    double t = (2.0 * x1 * x0 / (x0 + x1)) * ((xl + x0) / (2.0 * x0 + x1) - (x2 + x1) / (2.0 * x1 + x0)) * d;
-    t = t - x0 * (xl + x0) / (2.0 * x0 + x1) * dm[j + 1] + x1 * (x1 + x2) / (x0 + 2.0 * x1) * dm[j];
-    double f = A[j] + x0 / (x0 + x1) * d + t / tot;
+    const double tn = 2.0 * x0 * x1 * ((xl + x0) * Q - (x2 + x1) * P) * d
+                      - s01 * (x0 * (xl + x0) * Q * dm[j + 1] - x1 * (x1 + x2) * P * dm[j]);
+    double f = A[j] + (x0 * d * P * Q * tot + tn) / (s01 * P * Q * tot);
     f = fmax(f, fmin(A[j], A[j + 1]));
     f = fmin(f, fmax(A[j], A[j + 1]));
     face[j] = f;
   };
   if (live) {
-    interface(k + 1);
-    if (k == 0) interface(n + 1);
+    if (k < n - 1) interface(k + 2);
+    else face[1] = A[2];
+    if (k == 0) face[n + 1] = A[n + 1];
   }
   __syncthreads();
   // Phase 6: the parabola of each shifted group (Eqs. h17, h22-h24) with the monotonicity
@@ -162,77 +202,85 @@ __global__ void __launch_bounds__(kEadvThreads) k_energy_advect(EadvArgs g) {
   __syncthreads();
   // Phase 7: the flux across target edge k (Eq. p5): the number in the slice between the shifted
   // and the target edge, from the parabola of the group the slice belongs to; zero at the two
-  // outer edges.  Also the target group centres (eta2 is no longer needed: its storage is reused).
+  // outer edges.  Also the target group centres E_k / a^{n+1} (eta2's storage is reused).
   double *ct = eta2;
   if (live) {
-    const double a1 = zc[2];
-    ct[k] = centre(eps_t[k], eps_t[k + 1]);
+    const double ia1 = zc[4];
+    ct[k] = Ec[k] * ia1;
     if (k == 0) {
       F[0] = 0.0;
       F[n] = 0.0;
     } else {
-      const double d = eps_t[k] - E_d[k] / a1;
-      double f = 0.0;
-      if (d < 0.0) {                  // top of group k-1 moves up into target group k
-        const double dx = X[k + 1];
-        const double y = fmin(fmax(-d / dx, 0.0), 1.0);
-        const double avg = aR[k - 1] - 0.5 * y * ((aR[k - 1] - aL[k - 1]) - (1.0 - 2.0 * y / 3.0) * a6[k - 1]);
-        f = avg * y * dx;
-      } else if (d > 0.0) {           // bottom of group k moves down into target group k-1
-        const double dx = X[k + 2];
-        const double y = fmin(fmax(d / dx, 0.0), 1.0);
-        const double avg = aL[k] + 0.5 * y * ((aR[k] - aL[k]) + (1.0 - 2.0 * y / 3.0) * a6[k]);
-        f = -avg * y * dx;
-      }
-      F[k] = f;
+      // d < 0: the top of group k-1 moves up into target group k (slice from its right end);
+      // d > 0: the bottom of group k moves down into target group k-1 (from its left end).
+      const double d = (g.e_edge[k] - E_d[k]) * ia1;
+      const bool up = d < 0.0;
+      const int gsrc = up ? k - 1 : k;
+      const double dir = up ? -1.0 : 1.0;
+      const double dx = X[gsrc + 2];
+      const double y = fmin(fmax(fabs(d) / dx, 0.0), 1.0);
+      const double end = up ? aR[gsrc] : aL[gsrc];
+      const double avg = end + dir * 0.5 * y * ((aR[gsrc] - aL[gsrc]) + dir * (1.0 - 2.0 * kThird * y) * a6[gsrc]);
+      F[k] = -dir * avg * y * dx;
     }
   }
   __syncthreads();
-  // Phase 8: xi (Eqs. p6-p8): the factor on the flux divergence that gives the target groups the
-  // energy the shifted groups hold (1 without flux).
-  double *sums = zc + 4;
-  if (live && k == 0) {
-    double eb = 0.0, s1 = 0.0, s2 = 0.0;
-    for (int kk = 0; kk < n; ++kk) {
-      eb += nd[kk] * epsd_c[kk];
-      s1 += nd[kk] * ct[kk];
-      s2 += (F[kk] - F[kk + 1]) * ct[kk];
-    }
-    sums[0] = s2 != 0.0 ? (eb - s1) / s2 : 1.0;
-  }
-  __syncthreads();
-  // Phase 9: Eq. p6 and psi on the target groups (kept in nd).
+  // Phase 8: the three sums of xi (Eqs. p6-p8) over the system's groups by a tree over its
+  // threads: energy held by the shifted groups, the same numbers at the target centres, and the
+  // flux divergence at the target centres.
+  double *r0 = red, *r1 = red + (n + 5), *r2 = red + 2 * (n + 5);
   if (live) {
-    const double xi = sums[0];
-    const double num = nd[k] + xi * (F[k] - F[k + 1]);
-    nd[k] = num / cube_moment(eps_t[k], eps_t[k + 1]);
+    const double div = F[k] - F[k + 1];
+    r0[k] = nd[k] * epsd_c[k];
+    r1[k] = nd[k] * ct[k];
+    r2[k] = div * ct[k];
+  }
+  int top = 1;
+  while (top * 2 < n) top *= 2;
+  for (int s = top; s >= 1; s >>= 1) {
+    __syncthreads();
+    if (live && k < s && k + s < n) {
+      r0[k] += r0[k + s];
+      r1[k] += r1[k + s];
+      r2[k] += r2[k + s];
+    }
   }
   __syncthreads();
-  // Phase 10: the occupation limiter (Eqs. a81a-a81d), sequential over groups k = 0..n-3.
-  if (live && g.limit && k == 0) {
-    bool over = false;
-    for (int kk = 0; kk < n - 2; ++kk) over |= nd[kk] > 1.0;
-    if (over) {
-      for (int kk = 0; kk < n - 2; ++kk) {
-        double d = nd[kk] - 1.0;
-        if (!(d > 0.0)) continue;
-        const double e0 = ct[kk], e1 = ct[kk + 1], e2 = ct[kk + 2];
-        const double w0 = e0 * e0 * (eps_t[kk + 1] - eps_t[kk]);
-        const double w1 = e1 * e1 * (eps_t[kk + 2] - eps_t[kk + 1]);
-        const double w2 = e2 * e2 * (eps_t[kk + 3] - eps_t[kk + 2]);
-        const double c_up = (e2 - e0) * w0 / ((e2 - e1) * w1);
-        const double c_dn = (e1 - e0) * w0 / ((e2 - e1) * w2);
-        d = fmin(d, fmax(nd[kk + 2], 0.0) / c_dn);   // never take group k + 2 below zero
-        nd[kk] -= d;
-        nd[kk + 1] += c_up * d;
-        nd[kk + 2] -= c_dn * d;
-      }
+  // Phase 9: xi (1 without flux), Eq. p6 and psi on the target groups, whose moment is
+  // E^2 dE / (a^{n+1})^3; groups below the top two that end above one flag the limiter.
+  if (live) {
+    const double s2 = r2[0];
+    const double xi = s2 != 0.0 ? (r0[0] - r1[0]) / s2 : 1.0;
+    const double num = nd[k] + xi * (F[k] - F[k + 1]);
+    const double v = num * zc[8] * icmE[k];
+    nd[k] = v;
+    if (k == 0) zc[6] = xi;
+    if (k < n - 2 && v > 1.0) zc[7] = 1.0;     // benign race: every writer stores 1
+  }
+  __syncthreads();
+  // Phase 10: the occupation limiter (Eqs. a81a-a81d), sequential over groups k = 0..n-3, only
+  // in systems that have an overfilled group.
+  if (live && g.limit && k == 0 && zc[7] != 0.0) {
+    const double ia1 = zc[4];
+    for (int kk = 0; kk < n - 2; ++kk) {
+      double d = nd[kk] - 1.0;
+      if (!(d > 0.0)) continue;
+      const double e0 = ct[kk], e1 = ct[kk + 1], e2 = ct[kk + 2];
+      const double w0 = e0 * e0 * (g.e_edge[kk + 1] - g.e_edge[kk]) * ia1;
+      const double w1 = e1 * e1 * (g.e_edge[kk + 2] - g.e_edge[kk + 1]) * ia1;
+      const double w2 = e2 * e2 * (g.e_edge[kk + 3] - g.e_edge[kk + 2]) * ia1;
+      const double c_up = (e2 - e0) * w0 / ((e2 - e1) * w1);
+      const double c_dn = (e1 - e0) * w0 / ((e2 - e1) * w2);
+      d = fmin(d, fmax(nd[kk + 2], 0.0) / c_dn);   // never take group k + 2 below zero
+      nd[kk] -= d;
+      nd[kk + 1] += c_up * d;
+      nd[kk + 2] -= c_dn * d;
     }
   }
   __syncthreads();
   if (live) {
     g.psi[el] = nd[k];
-    if (k == 0 && g.xi) g.xi[sg] = sums[0];
+    if (k == 0 && g.xi) g.xi[sg] = zc[6];
   }
 }
 
@@ -259,12 +307,13 @@ extern "C" mgfld_status mgfld_energy_advect(const mgfld_dims *dims, const mgfld_
   g.a_np1 = prob->lapse_np1;
   g.e_edge = prob->e_edge;
   g.eta1 = prob->eta1;
+  g.u = prob->u;
   g.psi = psi;
   g.xi = xi;
   const size_t n_sys = (size_t)g.n_ray * NS * g.n_r;
   const unsigned grid = (unsigned)((n_sys + g.spb - 1) / g.spb);
   const unsigned threads = (unsigned)((g.spb * g.n + 31) / 32 * 32);
-  const size_t smem = sizeof(double) * (size_t)g.spb * eadv_stride(g.n);
+  const size_t smem = eadv_smem(g.spb, g.n);
   if (smem > 48 * 1024 &&
       cudaFuncSetAttribute(k_energy_advect, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
     return MGFLD_ECUDA;

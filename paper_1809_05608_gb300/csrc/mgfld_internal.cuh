@@ -40,6 +40,7 @@ struct Prob {
   int n_ray, n_r, n, bc;
   double dt;
   const double *r_edge, *lapse, *e_edge, *rho, *kabs, *kscat, *nes, *scale;
+  const double *u, *eta1;   // shock transport (Eqs. a90-a99): zone velocity and flux factor, or NULL
   Eos eos;
 };
 
@@ -47,7 +48,7 @@ struct Prob {
 struct Layout {
   int mixed;
   size_t groups, phout, phin, phd, rsum, phin32, phd32, lam, slam, g0, l0, alpha, ghost, rnu, jbuf, psi_n, ye_n, e_n,
-      zone, src;
+      zone, src, shock;
   size_t diag, lower, upper, rhs, x, dinv, zled, sscale, kinv, lower32, upper32, g32, rhs32;
   size_t viol, vprev, active, iters, status, refac, nfact, nanflag, list_act, list_ref, counters;
   size_t total;
@@ -69,11 +70,22 @@ Prob make_prob(const mgfld_dims *d, const mgfld_problem *p);
 // ghost): 1/(3 (R_{i+1} - R_i)), 4 pi R_{i+1/2}^2 / a_{i+1/2}^2 and 1/R_{i+1/2}^2 (Eq. a59).
 // ZC_INV_T = 1/T^n; ZC_EMU, ZC_EMUI = e^{+-mu/T^n} for the factored emissivity exponentials
 // e^{(mu_q - eps)/T} = e^{mu_q/T} e^{-eps/T} of the mixed path (-1 where |mu/T| >= kEmuMax,
-// which takes the direct form).
+// which takes the direct form).  ZC_SHOCK: beta_{i+1/2} times its roll-in weight at the outer
+// edge (Eq. a90; zero without velocities and at the outermost edge).
 enum { ZC_PRE = 0, ZC_INV_ACDT = 1, ZC_INV_A = 2, ZC_VOL = 3, ZC_MU = 4, ZC_A = 5, ZC_ACDT = 6,
        ZC_MUA = 7, ZC_MUB = 8, ZC_EI3DR = 9, ZC_EGEO = 10, ZC_EIR2 = 11, ZC_INV_T = 12, ZC_EMU = 13,
-       ZC_EMUI = 14, ZC_N = 15 };
+       ZC_EMUI = 14, ZC_SHOCK = 15, ZC_N = 16 };
 constexpr double kEmuMax = 600.0;
+
+// Roll-in of the shock terms: |u_{i+1} - u_i| / c where they start and where they are whole.
+constexpr double kShockOn = 0.01, kShockFull = 0.02;
+
+// Minerbo closure (Eqs. a86-a87) with eta2_thick = 1/3 and eta2_thin = 1, eta1 clamped to [0, 1].
+__device__ inline double minerbo_eta2(double eta1) {
+  const double x = fmin(fmax(eta1, 0.0), 1.0);
+  const double p = 1.0 / 3.0 + 2.0 * x * x / 15.0 * (3.0 - x + 3.0 * x * x);
+  return 1.5 * (1.0 - p) * (1.0 / 3.0) + 0.5 * (3.0 * p - 1.0);
+}
 
 // Pointers resolved from a layout.
 struct Ws {
@@ -90,6 +102,9 @@ struct Ws {
   double *g0, *l0;          // per (ray, q, i, k): the NES sums phin.psi^n and phout.psi^n (first iteration)
   double *zone;             // per zone [n_ray][n_r][ZC_N]: see ZC_* below
   double *src;              // per (ray, q, i, k): total source S at the converged state
+  double *shock;            // per (ray, q, i, k): the step-constant shock term of Eq. a99's bracket
+  double *lim;              // per (ray, q, i, k), or null: the flux limiter at the outer edge (kept
+                            // by the setup for the neutrino stress)
   double *diag, *lower, *upper, *rhs, *x;
   void *dinv;
   double *zled;             // per-zone ledger terms [n_ray][n_r][8]

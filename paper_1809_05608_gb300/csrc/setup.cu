@@ -56,6 +56,13 @@ __global__ void k_zone(Prob p, Ws w, const double *__restrict__ ye, const double
   z[ZC_EI3DR] = 1.0 / (3.0 * (r_r - r_i));
   z[ZC_EGEO] = 4.0 * kPi * rp * rp / (a_e * a_e);
   z[ZC_EIR2] = 1.0 / (rp * rp);
+  if (p.u && i < last) {       // shock roll-in at the outer edge (Eq. a90)
+    const double *u = p.u + (size_t)ray * p.n_r;
+    const double beta = (u[i + 1] - u[i]) / kC;
+    z[ZC_SHOCK] = beta * fmin(fmax((fabs(beta) - kShockOn) / (kShockFull - kShockOn), 0.0), 1.0);
+  } else {
+    z[ZC_SHOCK] = 0.0;
+  }
   const double inv_T = 1.0 / T[t];
   const double xm = mu * inv_T;
   z[ZC_INV_T] = inv_T;
@@ -329,6 +336,7 @@ __global__ void k_edges(Prob p, Ws w) {
   const int last = p.n_r - 1;
   if (i == last && p.bc == MGFLD_BC_REFLECT) {
     w.alpha[t] = 0.0;
+    if (w.lim) w.lim[t] = 0.0;
     return;
   }
   const double *re = p.r_edge + (size_t)ray * (p.n_r + 1);
@@ -377,6 +385,67 @@ __global__ void k_edges(Prob p, Ws w) {
     F = num / den;
   }
   w.alpha[t] = lam_e * F * z[ZC_EI3DR] * z[ZC_EGEO];
+  if (w.lim) w.lim[t] = F;
+}
+
+// Moment m_k = eta psi^n_k of one zone's row: eta = eta1 (psi1), or eta2(eta1) (psi2).
+__device__ inline double shock_moment(const Prob &p, const Ws &w, size_t row, int k, bool second) {
+  const double x = p.eta1 ? fmin(fmax(p.eta1[row + k], 0.0), 1.0) : 0.0;
+  return (second ? minerbo_eta2(x) : x) * w.psi_n[row + k];
+}
+
+// (E_+^3 m_{k+1/2} - E_-^3 m_{k-1/2}) / ((E_+^3 - E_-^3)/3) with m_{k+1/2} the mean of the adjacent
+// groups (Eqs. a92, a98), zero at the lowest and highest group edge.  Written with the energies
+// at infinity: the ratio is the same on every zone's comoving grid E/a.
+__device__ inline double shock_ediv(const Prob &p, const Ws &w, size_t row, int k, bool second) {
+  const int n = p.n;
+  const double mk = shock_moment(p, w, row, k, second);
+  const double up = k + 1 < n ? 0.5 * (mk + shock_moment(p, w, row, k + 1, second)) : 0.0;
+  const double dn = k > 0 ? 0.5 * (shock_moment(p, w, row, k - 1, second) + mk) : 0.0;
+  const double el = p.e_edge[k], eh = p.e_edge[k + 1];
+  const double el3 = el * el * el, eh3 = eh * eh * eh;
+  return (eh3 * up - el3 * dn) / ((eh3 - el3) / 3.0);
+}
+
+// Per (ray, q, i, k): the step constant that joins the bracket of Eq. a99 (times A/a^2 = the
+// flux terms of Eq. a58),
+//   shock = alpha_{i+1/2} dpsi0_i + (A/a^2)_{i+1/2} dpsi1_{i+1/2} - alpha_{i-1/2} dpsi0_{i-1},
+// dpsi0_i = bw_{i+1/2} (-psi1_{i,k} + Ediv(psi1_i)_k)   (Eq. a91: zone i's psi0 seen from frame i+1,
+// entering the flux of Eq. a93 at both zones sharing the edge), and
+// dpsi1_{i+1/2} = -bw_{i+1/2} Ediv(psi2_{i+1})_k          (Eq. a97: the edge flux brought from
+// frame i+1 back to frame i, for zone i only).  Formed at psi^n like the flux coefficients;
+// bw = beta times its roll-in weight comes per edge from the zone constants (ZC_SHOCK), so the
+// zones away from a shock only store a zero.
+__global__ void k_shock(Prob p, Ws w) {
+  const int n = p.n;
+  const unsigned tu = blockIdx.x * blockDim.x + threadIdx.x;
+  if (tu >= (unsigned)(p.n_ray * NS * p.n_r * n)) return;
+  const size_t t = tu;
+  const unsigned u1 = tu / (unsigned)n;
+  const int k = (int)(tu - u1 * n);
+  const unsigned u2 = u1 / (unsigned)p.n_r;
+  const int i = (int)(u1 - u2 * p.n_r);
+  const int ray = (int)(u2 / NS);
+  const int last = p.n_r - 1;
+  const size_t row = t - k;                      // zone i's group row
+  const double *z = w.zone + ((size_t)ray * p.n_r + i) * ZC_N;
+  double sh = 0.0;
+  if (i < last) {
+    const double bw = z[ZC_SHOCK];
+    if (bw != 0.0) {
+      const double d0 = bw * (-shock_moment(p, w, row, k, false) + shock_ediv(p, w, row, k, false));
+      const double d1 = -bw * shock_ediv(p, w, row + n, k, true);
+      sh += w.alpha[t] * d0 + z[ZC_EGEO] * d1;
+    }
+  }
+  if (i > 0) {
+    const double bw = z[ZC_SHOCK - ZC_N];          // edge i-1/2, zone i-1's constant
+    if (bw != 0.0) {
+      const double d0 = bw * (-shock_moment(p, w, row - n, k, false) + shock_ediv(p, w, row - n, k, false));
+      sh -= w.alpha[t - n] * d0;
+    }
+  }
+  w.shock[t] = sh;
 }
 
 static inline unsigned nblk(size_t n, unsigned b) { return (unsigned)((n + b - 1) / b); }
@@ -406,6 +475,7 @@ cudaError_t launch_setup(const Prob &p, const Ws &w, const double *psi, const do
   k_jlam<<<nblk(nzk, B), B, 0, s>>>(p, w, psi, T);
   k_nusphere<<<nblk((size_t)p.n_ray * NS * p.n * 32, B), B, 0, s>>>(p, w);   // a warp per (ray, q, k)
   k_edges<<<nblk(nall, B), B, 0, s>>>(p, w);
+  if (p.u) k_shock<<<nblk(nall, B), B, 0, s>>>(p, w);
   return cudaGetLastError();
 }
 

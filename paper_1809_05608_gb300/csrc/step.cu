@@ -44,6 +44,7 @@ Layout make_layout(int n_ray, int n_r, int n, int precision) {
   L.e_n = take(sizeof(double) * Z);
   L.zone = take(sizeof(double) * Z * ZC_N);
   L.src = take(sizeof(double) * F);
+  L.shock = take(sizeof(double) * F);
   L.diag = take((precision == MGFLD_MIXED ? sizeof(float) : sizeof(double)) * B);
   L.lower = take(sizeof(double) * F);
   L.upper = take(sizeof(double) * F);
@@ -109,6 +110,8 @@ Ws resolve(void *base, const Layout &L) {
   w.e_n = (double *)(b + L.e_n);
   w.zone = (double *)(b + L.zone);
   w.src = (double *)(b + L.src);
+  w.shock = (double *)(b + L.shock);
+  w.lim = nullptr;
   w.diag = (double *)(b + L.diag);
   w.lower = (double *)(b + L.lower);
   w.upper = (double *)(b + L.upper);
@@ -503,6 +506,7 @@ Prob make_prob(const mgfld_dims *d, const mgfld_problem *p) {
   q.n_ray = d->n_ray; q.n_r = d->n_r; q.n = d->n_e; q.bc = p->outer_bc; q.dt = p->dt;
   q.r_edge = p->r_edge; q.lapse = p->lapse; q.e_edge = p->e_edge; q.rho = p->rho;
   q.kabs = p->kappa_abs; q.kscat = p->kappa_scat; q.nes = p->nes_coef; q.scale = p->scale;
+  q.u = p->u; q.eta1 = p->eta1;
   q.eos = make_eos(p->eos);
   return q;
 }
@@ -579,7 +583,7 @@ mgfld_status mgfld_step(const mgfld_dims *dims, const mgfld_problem *prob, mgfld
   k_init<<<nblk(R, 128), 128, 0, s>>>(R, w);
   MGFLD_CUDA(cudaGetLastError());
   MGFLD_CUDA(cudaMemsetAsync(w.counters, 0, sizeof(int) * 8, s));
-  prof.end(MGFLD_PROF_SETUP, 7);
+  prof.end(MGFLD_PROF_SETUP, p.u ? 8 : 7);
   int n_act = R, n_ref = R;
   int host_counters[8];
   for (int it = 0; it < opts->max_iter && n_act > 0; ++it) {

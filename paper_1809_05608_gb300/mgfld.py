@@ -22,7 +22,7 @@ N_SPECIES = 4
 
 EXPORTED = ('mgfld_eos_default', 'mgfld_workspace_bytes', 'mgfld_step', 'mgfld_assemble',
             'mgfld_factor_bytes', 'mgfld_factor', 'mgfld_solve', 'mgfld_status_str', 'mgfld_step_noalloc',
-            'mgfld_adjoint_workspace_bytes', 'mgfld_adjoint', 'mgfld_energy_advect')
+            'mgfld_adjoint_workspace_bytes', 'mgfld_adjoint', 'mgfld_energy_advect', 'mgfld_stress_lapse')
 NOALLOC_SCRATCH_BYTES = 64 << 20
 
 
@@ -39,7 +39,8 @@ class Problem(ctypes.Structure):
     _fields_ = [('r_edge', ctypes.c_void_p), ('lapse', ctypes.c_void_p), ('e_edge', ctypes.c_void_p),
                 ('rho', ctypes.c_void_p), ('kappa_abs', ctypes.c_void_p), ('kappa_scat', ctypes.c_void_p),
                 ('nes_coef', ctypes.c_void_p), ('scale', ctypes.c_void_p), ('eos', EosParams),
-                ('dt', ctypes.c_double), ('outer_bc', ctypes.c_int)]
+                ('dt', ctypes.c_double), ('outer_bc', ctypes.c_int), ('u', ctypes.c_void_p),
+                ('eta1', ctypes.c_void_p)]
 
 
 class State(ctypes.Structure):
@@ -73,7 +74,13 @@ class AdjointIO(ctypes.Structure):
 class EadvProblem(ctypes.Structure):
     _fields_ = [('r_edge_n', ctypes.c_void_p), ('r_edge_np1', ctypes.c_void_p), ('rho_n', ctypes.c_void_p),
                 ('rho_np1', ctypes.c_void_p), ('lapse_n', ctypes.c_void_p), ('lapse_np1', ctypes.c_void_p),
-                ('e_edge', ctypes.c_void_p), ('eta1', ctypes.c_void_p), ('limit', ctypes.c_int)]
+                ('e_edge', ctypes.c_void_p), ('eta1', ctypes.c_void_p), ('limit', ctypes.c_int),
+                ('u', ctypes.c_void_p)]
+
+
+class StressIO(ctypes.Structure):
+    _fields_ = [('p', ctypes.c_void_p), ('m_inner', ctypes.c_void_p), ('f_edge', ctypes.c_void_p),
+                ('f_zone', ctypes.c_void_p), ('lapse', ctypes.c_void_p)]
 
 
 _lib = None
@@ -113,6 +120,9 @@ def lib():
     L.mgfld_adjoint.restype = ctypes.c_int
     L.mgfld_adjoint.argtypes = [P(Dims), P(Problem), P(State), P(State), P(AdjointIO), ctypes.c_void_p,
                                 ctypes.c_size_t, ctypes.c_void_p]
+    L.mgfld_stress_lapse.restype = ctypes.c_int
+    L.mgfld_stress_lapse.argtypes = [P(Dims), P(Problem), P(State), P(StressIO), ctypes.c_void_p, ctypes.c_size_t,
+                                     ctypes.c_void_p]
     L.mgfld_energy_advect.restype = ctypes.c_int
     L.mgfld_energy_advect.argtypes = [P(Dims), P(EadvProblem), ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
     L.mgfld_status_str.restype = ctypes.c_char_p
@@ -153,18 +163,20 @@ class DeviceProblem:
     the matching C struct.  `prob` is a dict with the fields of mgfld_problem."""
 
     FIELDS = ('r_edge', 'lapse', 'e_edge', 'rho', 'kappa_abs', 'kappa_scat', 'nes_coef', 'scale')
+    SHOCK_FIELDS = ('u', 'eta1')
 
     def __init__(self, prob, device='cuda'):
         import torch
         self.t = {}
-        for f in self.FIELDS:
+        for f in self.FIELDS + self.SHOCK_FIELDS:
             v = prob.get(f)
             self.t[f] = None if v is None else torch.as_tensor(
                 np.array(v, dtype=np.float64, order='C'), device=device)
         self.dt = float(prob['dt'])
         self.outer_bc = int(prob.get('outer_bc', MGFLD_BC_GHOST))
         self.eos = lib().mgfld_eos_default()
-        self.struct = Problem(*[_ptr(self.t[f]) for f in self.FIELDS], self.eos, self.dt, self.outer_bc)
+        self.struct = Problem(*[_ptr(self.t[f]) for f in self.FIELDS], self.eos, self.dt, self.outer_bc,
+                              *[_ptr(self.t[f]) for f in self.SHOCK_FIELDS])
 
     def rays(self, lo, hi, n_r, n_e):
         """C struct viewing rays [lo, hi) only (rays are independent; used for chunking)."""
@@ -173,7 +185,8 @@ class DeviceProblem:
             return None if t is None else ctypes.c_void_p(t.data_ptr() + 8 * lo * per_ray)
         return Problem(off('r_edge', n_r + 1), off('lapse', n_r), _ptr(self.t['e_edge']), off('rho', n_r),
                        off('kappa_abs', N_SPECIES * n_r * n_e), off('kappa_scat', N_SPECIES * n_r * n_e),
-                       off('nes_coef', n_r), _ptr(self.t['scale']), self.eos, self.dt, self.outer_bc)
+                       off('nes_coef', n_r), _ptr(self.t['scale']), self.eos, self.dt, self.outer_bc,
+                       off('u', n_r), off('eta1', N_SPECIES * n_r * n_e))
 
 
 PROF_NAMES = ('setup', 'assemble', 'factor', 'solve', 'update', 'finish')
@@ -321,10 +334,22 @@ class Stepper:
 def eadv_problem(t, limit=True):
     """C struct for mgfld_energy_advect from a dict of device tensors: r_edge_n, r_edge_np1
     [n_ray, n_r+1], rho_n, rho_np1 [n_ray, n_r], optional lapse_n, lapse_np1 [n_ray, n_r],
-    e_edge [n_e+1], optional eta1 [n_ray, 4, n_r, n_e] (FP64, contiguous; kept alive by the caller)."""
+    e_edge [n_e+1], optional eta1 [n_ray, 4, n_r, n_e], optional u [n_ray, n_r] (the zone velocity
+    that rolls energy advection out at a shock) (FP64, contiguous; kept alive by the caller)."""
     return EadvProblem(_ptr(t['r_edge_n']), _ptr(t['r_edge_np1']), _ptr(t['rho_n']), _ptr(t['rho_np1']),
                        _ptr(t.get('lapse_n')), _ptr(t.get('lapse_np1')), _ptr(t['e_edge']), _ptr(t.get('eta1')),
-                       1 if limit else 0)
+                       1 if limit else 0, _ptr(t.get('u')))
+
+
+def mgfld_stress_lapse(dims, problem_struct, psi, ye, T, ws, p=None, m_inner=None, f_edge=None, f_zone=None,
+                       lapse=None, stream=None):
+    """Neutrino stress (edge and zone values) and the lapse of a device state; `ws` a uint8 device
+    tensor of at least mgfld_workspace_bytes(dims, MGFLD_FP64) bytes; outputs [n_ray, n_r] FP64
+    device tensors or None.  Returns the mgfld status."""
+    st = State(_ptr(psi), _ptr(ye), _ptr(T))
+    io = StressIO(_ptr(p), _ptr(m_inner), _ptr(f_edge), _ptr(f_zone), _ptr(lapse))
+    return lib().mgfld_stress_lapse(ctypes.byref(dims), ctypes.byref(problem_struct), ctypes.byref(st),
+                                    ctypes.byref(io), _ptr(ws), ws.numel(), _stream(stream))
 
 
 def mgfld_energy_advect(dims, eadv_struct, psi, xi=None, stream=None):

@@ -201,6 +201,19 @@ def make_shock_problem(config: int, rays=None, n_ray=None, n_r=None, n_e=None, b
     return out
 
 
+def stress_inputs(inp):
+    """Matter pressure and inner mass for the neutrino stress and the lapse on a transport
+    workload: p = 1.2435e15 (Ye rho)^(4/3) + rho kT / m_B (relativistic degenerate electrons plus
+    ideal nucleons, erg/cm^3), and the mass inside the innermost edge that a uniform sphere of the
+    innermost zone's density would hold (g).  Returns (p [n_ray, n_r], m_inner [n_ray])."""
+    prob = inp['problem']
+    rho, T, ye = prob['rho'], inp['T0'], inp['ye0']
+    p = 1.2435e15 * (ye * rho) ** (4.0 / 3.0) + rho * T * 1.602176634e-6 / 1.674927e-24
+    r0 = prob['r_edge'][:, 0]
+    m_inner = 4.0 * np.pi / 3.0 * r0 ** 3 * rho[:, 0]
+    return np.ascontiguousarray(p), np.ascontiguousarray(m_inner)
+
+
 def _smooth_coeffs(rng, n_ray, modes=4):
     return rng.standard_normal((n_ray, modes))
 

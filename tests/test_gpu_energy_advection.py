@@ -36,8 +36,10 @@ def run_oracle(inp, use_eta1=True, use_lapse=True, limit=True):
     ones = np.ones_like(inp['rho_n'])
     a0 = inp['lapse_n'] if use_lapse else ones
     a1 = inp['lapse_np1'] if use_lapse else ones
+    keep = None if inp.get('u') is None else b(E.shock_keep(inp['u']))
     return E.step(inp['e_edge'], b(a0), b(a1), b(_centres(inp['r_edge_n'])), b(_centres(inp['r_edge_np1'])),
-                  b(inp['rho_n']), b(inp['rho_np1']), inp['psi'], inp['eta1'] if use_eta1 else None, limit=limit)
+                  b(inp['rho_n']), b(inp['rho_np1']), inp['psi'], inp['eta1'] if use_eta1 else None, limit=limit,
+                  keep=keep)
 
 
 def run_gpu(inp, use_eta1=True, use_lapse=True, limit=True):
@@ -127,6 +129,22 @@ def test_occupation_limiter_path():
     psi, _ = run_gpu(inp)
     assert np.all(ref['psi'][..., :-2] <= 1.0 + 1e-15)
     check_parity(psi, ref)
+
+
+def test_rollout_at_the_imposed_shock():
+    """Zone velocities of the imposed accretion shock: the zones at the shock keep none or part
+    of their displacement (reading E8), on both sides."""
+    rays = [0, 101, 255]
+    inp = problems.make_energy_advection(config=2, rays=rays)
+    inp['u'] = problems.make_shock_problem(2, rays=rays)['problem']['u']
+    keep = E.shock_keep(inp['u'])
+    assert np.any(keep == 0.0) and np.any((keep > 0.0) & (keep < 1.0))
+    ref = run_oracle(inp)
+    psi, xi = run_gpu(inp)
+    check_parity(psi, ref)
+    plain = dict(inp)
+    plain.pop('u')
+    assert normwise(run_oracle(plain)['psi'], ref['psi']) > 1e-6     # the rollout changes the result
 
 
 def test_full_size_conservation_and_sampled_parity():
