@@ -47,6 +47,11 @@ identically here and documented with the project's design notes):
       j = kappa_a exp((mu - eps)/T) (Kirchhoff); the exponent is capped at 700
       so that 1/(1 - f_eq) stays finite.
   R11 Gain-region heating weights each zone by its lapse (proper time a_i dt).
+  R12 (optional, the paper-literal form of Eq. a59) lambda^(t) and F at n+1: the flux
+      coefficients (mean free path with j at the iterate's Ye and the NES rates at its psi,
+      neutrinosphere, ghost factor, limiter, shock terms) are formed again at every outer iterate
+      with T = T^n, and the Jacobian holds them fixed (Picard on D); the root then satisfies
+      Eqs. a58/a59 with the coefficients of the root itself.
 
 Transport through a shock (Sec. "Transport through a Shock", Eqs. a90-a99), taken when the
 problem carries zone velocities u:
@@ -290,19 +295,26 @@ def setup_step(prob, psi_n, ye_n, T_n):
     coef = np.zeros((n_ray, n_r)) if coef is None else np.asarray(coef, dtype=np.float64)
     f.phi_out, f.phi_in = nes_kernels(f.eps, f.T_n, coef)     # at T^n (Sec. LTS: T held fixed)
 
-    # Transport mean free path at psi^n, Ye^n (Eq. a17 with a55, d8c, d8), reading R2.
-    mu_q, _ = species_mu(f.rho, f.T_n, f.ye_n, eos)
-    j_n, _ = emissivity(f.kappa_abs, f.eps, mu_q, f.T_n)
-    inv_lam = (f.kappa_abs + j_n + f.kappa_scat
-               + nes_inverse_mfp(f.psi_n, f.w, f.phi_out, f.phi_in))
-    f.lam = 1.0 / inv_lam
-    f.r_nu = neutrinosphere(f.lam, r_edge)
-    f.ghost = ghost_factor(f.rc, r_edge, f.r_nu)
-    f.alpha, f.D, f.F = edge_coefficients(f)
     f.e_n = e_int(f.rho, f.T_n, f.ye_n, eos)
-    u = prob.get('u')
-    f.shock = None if u is None else shock_corrections(f, prob['e_edge'], u, prob.get('eta1'))
+    f.e_edge = np.asarray(prob['e_edge'], dtype=np.float64)
+    f.u, f.eta1 = prob.get('u'), prob.get('eta1')
+    flux_coefficients(f, f.psi_n, f.ye_n)                     # at psi^n, Ye^n: reading R2
     return f
+
+
+def flux_coefficients(f, psi, ye):
+    """The transport mean free path (Eq. a17 with a55, d8c, d8), the neutrinosphere and ghost
+    factor (R4, R5), the edge coefficients of Eq. a59 with the limiter (a20-a26a) and, with zone
+    velocities, the shock terms (Eqs. a91, a97), all at the state (psi, Ye) with T = T^n; set on f.
+    The step forms them at psi^n, Ye^n (R2), or at every outer iterate (reading R12)."""
+    mu_q, _ = species_mu(f.rho, f.T_n, ye, f.eos)
+    j, _ = emissivity(f.kappa_abs, f.eps, mu_q, f.T_n)
+    inv_lam = (f.kappa_abs + j + f.kappa_scat + nes_inverse_mfp(psi, f.w, f.phi_out, f.phi_in))
+    f.lam = 1.0 / inv_lam
+    f.r_nu = neutrinosphere(f.lam, f.r_edge)
+    f.ghost = ghost_factor(f.rc, f.r_edge, f.r_nu)
+    f.alpha, f.D, f.F = edge_coefficients(f, psi)
+    f.shock = None if f.u is None else shock_corrections(f, f.e_edge, f.u, f.eta1, psi)
 
 
 def neutrinosphere(lam, r_edge):
@@ -334,12 +346,13 @@ def ghost_factor(rc, r_edge, r_nu):
     return (r_i**2 - 0.25 * rn**2) / (r_g**2 - 0.25 * rn**2)
 
 
-def edge_coefficients(f):
+def edge_coefficients(f, psi=None):
     """Frozen flux coefficients at the outer edge i+1/2 of every zone (Eqs. a59, a20-a26a).
 
     Returns alpha = A_{i+1/2} D_{i+1/2} / a_{i+1/2}^2, D = lambda F / (3 (R_{i+1} - R_i)) and the
     limiter F itself, all [n_ray, 4, n_r, n_e]; psi^(1)_{i+1/2} = -D (psi_{i+1} - psi_i)."""
-    psi, lam = f.psi_n, f.lam
+    psi = f.psi_n if psi is None else psi
+    lam = f.lam
     n_r = f.n_r
     psi_r = np.empty_like(psi)
     psi_r[:, :, :-1] = psi[:, :, 1:]
@@ -371,8 +384,29 @@ def edge_coefficients(f):
     D = lam_e * F / (3.0 * dR)
     a_e = 0.5 * (f.lapse + a_r)
     alpha = f.area[:, 1:][:, None, :, None] * D / (a_e**2)[:, None, :, None]
+    # Derivatives of the edge flux A psi1/a^2 = -K Phi, Phi = F (psi_r - psi) and K = alpha / F,
+    # with respect to psi_i and psi_{i+1} through the limiter (lambda and R_nu held), on the
+    # branch the limiter selects (reading R12); with b = lambda_e/(3 dR), s = sign(d psi):
+    #   F_intrp: Phi = e d/(e + b|d|),  F_geom: Phi = (h/b) e s,  d psi = 0: Phi = d.
+    K = f.area[:, 1:][:, None, :, None] * lam_e / (3.0 * dR) / (a_e**2)[:, None, :, None]
+    b = lam_e / (3.0 * dR)
+    s = np.sign(dpsi)
+    den = psi_e + b * np.abs(dpsi)
+    with np.errstate(divide='ignore', invalid='ignore'):
+        geo = F == f_geo
+        h_b = 0.5 * (1.0 + mu) / b
+        phi = psi_e * dpsi / den
+        dl = np.where(geo, 0.5 * h_b * s, ((0.5 * dpsi - psi_e) - phi * (0.5 - b * s)) / den)
+        dr = np.where(geo, 0.5 * h_b * s, ((0.5 * dpsi + psi_e) - phi * (0.5 + b * s)) / den)
+    dl = np.where(dpsi == 0.0, -1.0, dl)
+    dr = np.where(dpsi == 0.0, 1.0, dr)
+    dl = np.where(psi_e <= 1e-300, 0.0, dl)
+    dr = np.where(psi_e <= 1e-300, 0.0, dr)
+    f.jl, f.jr = -K * dl, -K * dr
     if f.outer_bc == BC_REFLECT:
         alpha[:, :, -1, :] = 0.0
+        f.jl[:, :, -1, :] = 0.0
+        f.jr[:, :, -1, :] = 0.0
     return alpha, D, F
 
 
@@ -406,7 +440,7 @@ def energy_divergence(eps_lo, eps_hi, m):
     return (eps_hi**3 * me[..., 1:] - eps_lo**3 * me[..., :-1]) / ((eps_hi**3 - eps_lo**3) / 3.0)
 
 
-def shock_corrections(f, e_edge, u, eta1):
+def shock_corrections(f, e_edge, u, eta1, psi=None):
     """(dpsi0, dpsi1, A/a^2) for the outer edge i+1/2 of every zone, [n_ray, 4, n_r, n_e]:
     dpsi0 = psi^up_i - psi_i of Eq. a91 (frame change of zone i's psi0 into frame i+1),
     dpsi1 = the frame-(i+1) to frame-i change of the edge flux, Eq. a97, and A_{i+1/2}/a_{i+1/2}^2
@@ -414,15 +448,16 @@ def shock_corrections(f, e_edge, u, eta1):
     from oracle.energy_advection_oracle import minerbo_eta2
     beta, wgt = shock_beta(u)
     bw = (beta * wgt)[:, None, :, None]                          # [n_ray, 1, n_r - 1, 1]
-    x = np.zeros_like(f.psi_n) if eta1 is None else np.clip(np.asarray(eta1, dtype=np.float64), 0.0, 1.0)
-    psi1 = x * f.psi_n                                           # S2
-    psi2 = minerbo_eta2(x) * f.psi_n
+    psi = f.psi_n if psi is None else psi
+    x = np.zeros_like(psi) if eta1 is None else np.clip(np.asarray(eta1, dtype=np.float64), 0.0, 1.0)
+    psi1 = x * psi                                               # S2
+    psi2 = minerbo_eta2(x) * psi
     E = np.asarray(e_edge, dtype=np.float64)
     lo = E[:-1][None, None, :] / f.lapse[:, :, None]             # zone i's comoving group edges
     hi = E[1:][None, None, :] / f.lapse[:, :, None]
     lo, hi = lo[:, None, :-1], hi[:, None, :-1]                  # zones 0 .. n_r - 2
-    dpsi0 = np.zeros_like(f.psi_n)
-    dpsi1 = np.zeros_like(f.psi_n)
+    dpsi0 = np.zeros_like(psi)
+    dpsi1 = np.zeros_like(psi)
     p1 = psi1[:, :, :-1]
     dpsi0[:, :, :-1] = bw * (-p1 + energy_divergence(lo, hi, p1))           # Eq. a91
     dpsi1[:, :, :-1] = -bw * energy_divergence(lo, hi, psi2[:, :, 1:])      # Eq. a97 (S3)
@@ -488,11 +523,18 @@ def jacobian(f, psi, ye):
     _, s_ae, j, dmu_q, live = sources(f, psi, ye)
     a = f.lapse
     pre = (a**2 / f.vol)[:, None, :, None]
-    alpha_out = f.alpha
-    alpha_in = np.zeros_like(alpha_out)
-    alpha_in[:, :, 1:] = alpha_out[:, :, :-1]
-    ghost_term = np.zeros_like(alpha_out)
+    # d(flux at i+1/2)/d psi_i and d/d psi_{i+1}: alpha and -alpha with frozen coefficients (R2);
+    # at the iterate (R12) with the limiter's own dependence on psi_i, psi_{i+1}
+    if getattr(f, 'coef_iterate', False):
+        jl, jr = f.jl, f.jr
+    else:
+        jl, jr = f.alpha, -f.alpha
+    ghost_term = np.zeros_like(jl)
     ghost_term[:, :, -1, :] = f.ghost[:, :, :]
+    jr_in = np.zeros_like(jr)
+    jr_in[:, :, 1:] = jr[:, :, :-1]
+    jl_in = np.zeros_like(jl)
+    jl_in[:, :, 1:] = jl[:, :, :-1]
 
     # d S_nes,k / d psi_k' (full matrix) per (ray, species, zone).
     w = f.w
@@ -501,7 +543,7 @@ def jacobian(f, psi, ye):
     diag_nes = C_NES * (np.einsum('rikm,rim,rqim->rqik', f.phi_in, w, psi)
                         + np.einsum('rikm,rim,rqim->rqik', f.phi_out, w, 1.0 - psi))
     diag = (1.0 / (a[:, None, :, None] * C_LIGHT * f.dt)
-            + pre * (alpha_out * (1.0 - ghost_term) + alpha_in)
+            + pre * (jl + ghost_term * jr - jr_in)
             + j + f.kappa_abs + diag_nes)
     A = np.zeros((n_ray, n_r, M, M))
     for q in range(N_SPECIES):
@@ -521,8 +563,8 @@ def jacobian(f, psi, ye):
     A[:, :, M - 1, M - 1] += 1.0 / (a * C_LIGHT * f.dt)
     Bm = np.zeros((n_ray, n_r, M))
     Bp = np.zeros((n_ray, n_r, M))
-    Bm[:, :, :M - 1] = (-pre * alpha_in).transpose(0, 2, 1, 3).reshape(n_ray, n_r, M - 1)
-    up = -pre * alpha_out
+    Bm[:, :, :M - 1] = (-pre * jl_in).transpose(0, 2, 1, 3).reshape(n_ray, n_r, M - 1)
+    up = pre * jr
     up[:, :, -1, :] = 0.0            # the ghost is folded into the diagonal
     Bp[:, :, :M - 1] = up.transpose(0, 2, 1, 3).reshape(n_ray, n_r, M - 1)
     return A, Bm, Bp
@@ -598,19 +640,26 @@ def rel_change(d_psi, psi):
     return num / den
 
 
-def newton_solve(f, max_iter=50, rtol=1e-14):
+def newton_solve(f, max_iter=50, rtol=1e-14, coef_iterate=False):
     """Newton iteration on the coupled system (Eqs. a62aa, a62ae) to the root.
 
     Stops once the normwise relative correction (per ray and species) is <= rtol, or
     when it has reached the rounding level (below 1e-10 and no longer halving); the
     root is then accurate to rounding because the convergence is quadratic.
+    With coef_iterate (reading R12) the flux coefficients are formed again at every iterate
+    after the first and the Jacobian adds the limiter's dependence on the two zones of each edge
+    (the mean free path's, through the NES rates of all groups, and the neutrinosphere's are held:
+    the iteration is then nearly quadratic on the benchmark rays).
     Returns psi, Ye, iterations, last correction."""
     psi = f.psi_n.copy()
     ye = f.ye_n.copy()
     prev = np.inf
     it = 0
     err = np.inf
+    f.coef_iterate = coef_iterate
     for it in range(1, max_iter + 1):
+        if coef_iterate and it > 1:
+            flux_coefficients(f, psi, ye)
         G, GY = residual(f, psi, ye)
         A, Bm, Bp = jacobian(f, psi, ye)
         du = block_thomas(A, Bm, Bp, -pack(G, GY))
@@ -640,12 +689,13 @@ def ledger_energy(f, psi, e):
     return matter + nu
 
 
-def step(prob, psi_n, ye_n, T_n, max_iter=50, rtol=1e-14):
+def step(prob, psi_n, ye_n, T_n, max_iter=50, rtol=1e-14, coef_iterate=False):
     """One implicit transport step.  Returns a dict with psi, ye, T, e, iterations,
     the ledgers [n_ray, 8] = (lepton before, after, boundary loss, residual,
-    energy before, after, boundary loss, residual) and the gain-region heating."""
+    energy before, after, boundary loss, residual) and the gain-region heating.
+    coef_iterate: the flux coefficients at the outer iterate (reading R12) instead of at psi^n."""
     f = setup_step(prob, psi_n, ye_n, T_n)
-    psi, ye, iters, err = newton_solve(f, max_iter=max_iter, rtol=rtol)
+    psi, ye, iters, err = newton_solve(f, max_iter=max_iter, rtol=rtol, coef_iterate=coef_iterate)
     S, _, _, _, _ = sources(f, psi, ye)
     a = f.lapse
     # Eq. a62b: internal energy update with the converged sources.
