@@ -49,9 +49,13 @@ identically here and documented with the project's design notes):
   R11 Gain-region heating weights each zone by its lapse (proper time a_i dt).
   R12 (optional, the paper-literal form of Eq. a59) lambda^(t) and F at n+1: the flux
       coefficients (mean free path with j at the iterate's Ye and the NES rates at its psi,
-      neutrinosphere, ghost factor, limiter, shock terms) are formed again at every outer iterate
-      with T = T^n, and the Jacobian holds them fixed (Picard on D); the root then satisfies
-      Eqs. a58/a59 with the coefficients of the root itself.
+      neutrinosphere, ghost factor, limiter) are formed again at every outer iterate with
+      T = T^n; the Jacobian adds the limiter's derivative on the two zones of each edge and holds
+      the rest (the mean free path couples all groups through NES, the neutrinosphere all zones).
+      The root then satisfies Eqs. a58/a59 with the coefficients of the root itself.  It is not
+      combined with the shock terms: their flux part multiplies the limiter (Eq. a93), whose
+      derivative then needs the frame shift of every edge, and without it the iteration took
+      ~30 outer iterations.
 
 Transport through a shock (Sec. "Transport through a Shock", Eqs. a90-a99), taken when the
 problem carries zone velocities u:
@@ -305,8 +309,8 @@ def setup_step(prob, psi_n, ye_n, T_n):
 def flux_coefficients(f, psi, ye):
     """The transport mean free path (Eq. a17 with a55, d8c, d8), the neutrinosphere and ghost
     factor (R4, R5), the edge coefficients of Eq. a59 with the limiter (a20-a26a) and, with zone
-    velocities, the shock terms (Eqs. a91, a97), all at the state (psi, Ye) with T = T^n; set on f.
-    The step forms them at psi^n, Ye^n (R2), or at every outer iterate (reading R12)."""
+    velocities, the shock terms (Eqs. a91, a97), all at the state (psi, Ye) with T = T^n; set on
+    f.  The step forms them at psi^n, Ye^n (R2), or with reading R12 at every outer iterate."""
     mu_q, _ = species_mu(f.rho, f.T_n, ye, f.eos)
     j, _ = emissivity(f.kappa_abs, f.eps, mu_q, f.T_n)
     inv_lam = (f.kappa_abs + j + f.kappa_scat + nes_inverse_mfp(psi, f.w, f.phi_out, f.phi_in))
@@ -656,6 +660,8 @@ def newton_solve(f, max_iter=50, rtol=1e-14, coef_iterate=False):
     prev = np.inf
     it = 0
     err = np.inf
+    if coef_iterate and f.u is not None:
+        raise NotImplementedError('reading R12 is not combined with the shock terms')
     f.coef_iterate = coef_iterate
     for it in range(1, max_iter + 1):
         if coef_iterate and it > 1:

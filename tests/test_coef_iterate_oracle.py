@@ -96,3 +96,20 @@ def test_jacobian_carries_the_limiter_derivative():
     f.coef_iterate = False
     _, _, Bp0 = O.jacobian(f, psi, ye)
     assert np.max(np.abs(Bp0 - Bp)) > 1e-3 * np.max(np.abs(Bp))
+
+
+def test_not_combined_with_the_shock_terms():
+    """Refused by the argument checks (host only; the fake pointers are never dereferenced)."""
+    import ctypes
+    from paper_1809_05608_gb300 import mgfld
+    fake = ctypes.c_void_p(0x10000)
+    prob = mgfld.Problem(*[fake] * 8, mgfld.lib().mgfld_eos_default(), 1e-6, 0, fake, None)
+    st = mgfld.State(fake, fake, fake)
+    dims = mgfld.Dims(1, 8, 4, 4)
+    opts = mgfld.step_opts(coef_iterate=True)
+    rc = mgfld.lib().mgfld_step(ctypes.byref(dims), ctypes.byref(prob), ctypes.byref(st), ctypes.byref(opts),
+                                None, ctypes.c_void_p(0x100000), 1 << 30, None)
+    assert rc == mgfld.MGFLD_EINVAL
+    with pytest.raises(NotImplementedError):
+        inp = problems.make_shock_problem(1)
+        O.step(inp['problem'], inp['psi0'], inp['ye0'], inp['T0'], coef_iterate=True)
