@@ -193,8 +193,9 @@ def traffic_record(kernel):
 
 # ------------------------------------------------------------------------- GPU arm
 
-def run_path(M, torch, inp, precision, steps, warmup, barrier, clocks=None, refactor_ratio=None):
-    st = M.Stepper(inp, precision, tol=TOL, max_iter=60, refactor_ratio=refactor_ratio)
+def run_path(M, torch, inp, precision, steps, warmup, barrier, clocks=None, refactor_ratio=None,
+             coef_iterate=False):
+    st = M.Stepper(inp, precision, tol=TOL, max_iter=60, refactor_ratio=refactor_ratio, coef_iterate=coef_iterate)
     if clocks:
         clocks.start()
     psi, ye, T = st.state_to_device(inp['psi0'], inp['ye0'], inp['T0'])
@@ -600,6 +601,9 @@ def main():
     # the same step with the shock-transport terms (Eqs. a90-a99) on the imposed shock profile
     shock = run_path(M, torch, shock_workload(n_gpus, rank), M.MGFLD_MIXED, args.steps, args.warmup, barrier)
     ms_shock = max_over_ranks(shock['ms']) / args.steps
+    # the paper-literal n+1 flux coefficients of Eq. a59, formed again at every outer iterate
+    lit = run_path(M, torch, inp, M.MGFLD_MIXED, args.steps, args.warmup, barrier, coef_iterate=True)
+    ms_lit = max_over_ranks(lit['ms']) / args.steps
     e2e = e2e_run(M, torch, inp, M.MGFLD_MIXED, args.steps)
     e2e_ms = max_over_ranks(e2e['ms']) / args.steps
     roof = roofline_for(mixed, inp, M.MGFLD_MIXED, mixed['clocks'])
@@ -650,6 +654,13 @@ def main():
                         kernel_ms={k: v['ms'] for k, v in shock['prof'].items()},
                         outer_iterations_per_step=shock['max_iters'],
                         gpu_launches=sum(v['launches'] for v in shock['prof'].values())),
+        coef_iterate_path=dict(value=job_throughput(ups, ws, ms_lit), unit=UNIT, ms_per_step=ms_lit,
+                               dtype='f32 factor + f64 residual/update',
+                               workload='the same rays with the flux coefficients of Eq. a59 (mean free path, '
+                                        'limiter, neutrinosphere) formed again at every outer iterate',
+                               kernel_ms={k: v['ms'] for k, v in lit['prof'].items()},
+                               outer_iterations_per_step=lit['max_iters'],
+                               gpu_launches=sum(v['launches'] for v in lit['prof'].values())),
         mixed_over_fp64=value / value64,
         energy_advection=eadv,
         stress_lapse=stress)

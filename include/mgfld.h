@@ -108,6 +108,13 @@ typedef struct {
   double *profile;     /* HOST pointer to double[MGFLD_PROF_N][2] or NULL.  When set, each kernel
                           category is bracketed by CUDA events on `stream` and its elapsed
                           milliseconds and launch count are ADDED to profile[c][0], profile[c][1]. */
+  int coef_iterate;    /* 0: the flux coefficients of Eq. a59 (transport mean free path, limiter,
+                          neutrinosphere, ghost factor) are formed once at psi^n, Ye^n.
+                          Nonzero: the paper-literal n+1 coefficients of Eq. a59 - formed again at
+                          every outer iterate (T held at T^n), the Jacobian adding the limiter's
+                          derivative on the two zones of each edge (the mean free path's and the
+                          neutrinosphere's dependence on psi are held within an iteration).  Not
+                          combined with the shock terms: EINVAL when prob->u is set */
 } mgfld_step_opts;
 
 /* Kernel categories of mgfld_step_opts.profile. */

@@ -97,7 +97,17 @@ __global__ void k_assemble(Prob p, Ws w, const double *__restrict__ psi, TD *__r
   rhs[g] = -G;
 
   if (jac_flag && !jac_flag[ray]) return;
-  const double dg = inv_acdt + pre * (al_out * (1.0 - gh) + al_in) + j + kap + (gain + loss);
+  // flux parts of the row: d(flux at i+1/2)/d psi_i = jl, d/d psi_{i+1} = jr; alpha and -alpha with
+  // the frozen coefficients, with the limiter's own derivative when they follow the iterate
+  double jdiag = al_out * (1.0 - gh) + al_in, jlow = al_in, jup = al_out;
+  if (w.jl) {
+    const double jl_out = w.jl[g], jr_out = w.jr[g];
+    const double jl_in = i > 0 ? w.jl[g - n] : 0.0, jr_in = i > 0 ? w.jr[g - n] : 0.0;
+    jdiag = jl_out + gh * jr_out - jr_in;
+    jlow = jl_in;
+    jup = -jr_out;
+  }
+  const double dg = inv_acdt + pre * jdiag + j + kap + (gain + loss);
   TD *row = diag + g * n;
   // dS_k/dpsi_k' = (1 - psi_k) phin + psi_k phout = phin - psi_k phd, entered with a minus;
   // dg joins the diagonal entry in FP64.  Rows are written 16 bytes at a time where n allows
@@ -141,8 +151,8 @@ __global__ void k_assemble(Prob p, Ws w, const double *__restrict__ psi, TD *__r
       for (int kp = 0; kp < n; ++kp) row[kp] = TD(kp == k ? dk : fma(pk, fd[kp], -fin[kp]));
     }
   }
-  lower[g] = -pre * al_in;
-  upper[g] = i < last ? -pre * al_out : 0.0;
+  lower[g] = -pre * jlow;
+  upper[g] = i < last ? -pre * jup : 0.0;
   if (w.lower32) {
     w.lower32[g] = (float)lower[g];
     w.upper32[g] = (float)upper[g];

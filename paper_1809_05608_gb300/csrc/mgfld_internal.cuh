@@ -105,6 +105,9 @@ struct Ws {
   double *shock;            // per (ray, q, i, k): the step-constant shock term of Eq. a99's bracket
   double *lim;              // per (ray, q, i, k), or null: the flux limiter at the outer edge (kept
                             // by the setup for the neutrino stress)
+  double *jl, *jr;          // per (ray, q, i, k), or null: d(edge flux A psi1/a^2)/d psi_i and
+                            // d/d psi_{i+1} with the limiter's own dependence (coefficients at the
+                            // outer iterate); null: the frozen coefficients' alpha and -alpha
   double *diag, *lower, *upper, *rhs, *x;
   void *dinv;
   double *zled;             // per-zone ledger terms [n_ray][n_r][8]
@@ -192,6 +195,11 @@ __device__ inline unsigned long long dbits(double v) { return (unsigned long lon
 // ---------------------------------------------------------------- launchers
 
 cudaError_t launch_groups(const Prob &p, const Ws &w, cudaStream_t s);
+// The flux coefficients again at the state psi (mean free path with the NES rates at psi and the
+// emissivity of the current Ye, neutrinosphere and ghost factor, limiter and its derivatives);
+// the setup's other products (NES kernels, zone constants, psi^n) are kept.  Not combined with
+// the shock terms (refused by mgfld_step).
+cudaError_t launch_coef_iterate(const Prob &p, const Ws &w, const double *psi, cudaStream_t s);
 cudaError_t launch_setup(const Prob &p, const Ws &w, const double *psi, const double *ye, const double *T,
                          cudaStream_t s);
 // diag is double (FP64 path, C ABI) or float (MIXED: the Jacobian feeds the FP32 factor only).

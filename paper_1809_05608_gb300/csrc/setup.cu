@@ -322,7 +322,7 @@ __global__ void k_nusphere(Prob p, Ws w) {
 // alpha_{i+1/2} = A_{i+1/2} D_{i+1/2} / a_{i+1/2}^2 with D = lambda_e F / (3 (R_{i+1} - R_i)),
 // lambda_e = sqrt(lambda_i lambda_{i+1}) (the product of the stored square roots),
 // F = min(F_intrp, F_geom) at psi^n.
-__global__ void k_edges(Prob p, Ws w) {
+__global__ void k_edges(Prob p, Ws w, const double *__restrict__ psi_src) {
   const int n = p.n;
   const unsigned tu = blockIdx.x * blockDim.x + threadIdx.x;
   if (tu >= (unsigned)(p.n_ray * NS * p.n_r * n)) return;
@@ -337,15 +337,16 @@ __global__ void k_edges(Prob p, Ws w) {
   if (i == last && p.bc == MGFLD_BC_REFLECT) {
     w.alpha[t] = 0.0;
     if (w.lim) w.lim[t] = 0.0;
+    if (w.jl) w.jl[t] = w.jr[t] = 0.0;
     return;
   }
   const double *re = p.r_edge + (size_t)ray * (p.n_r + 1);
   const int gq = (ray * NS + q) * n + k;
-  const double psi_i = w.psi_n[t];
+  const double psi_i = psi_src[t];
   const double sl_i = w.slam[t];
   double psi_r, sl_r;
   if (i < last) {
-    psi_r = w.psi_n[t + n];
+    psi_r = psi_src[t + n];
     sl_r = w.slam[t + n];
   } else {
     psi_r = w.ghost[gq] * psi_i;
@@ -356,12 +357,18 @@ __global__ void k_edges(Prob p, Ws w) {
   const double psi_e = 0.5 * (psi_i + psi_r);
   const double *z = w.zone + ((size_t)ray * p.n_r + i) * ZC_N;
   double F;
+  // derivatives of Phi = F (psi_r - psi_i) with respect to psi_i and psi_r on the branch the
+  // limiter selects (lambda and R_nu held), for the coefficients at the outer iterate
+  double dl = 0.0, dr = 0.0;
   if (psi_e <= 1e-300) {
     F = 0.0;
   } else if (dpsi == 0.0) {
     F = 1.0;
+    dl = -1.0;
+    dr = 1.0;
   } else {
-    const double x = lam_e * fabs(dpsi) * z[ZC_EI3DR];       // lambda |d psi/dR| / 3
+    const double b = lam_e * z[ZC_EI3DR];
+    const double x = b * fabs(dpsi);                         // lambda |d psi/dR| / 3
     // F = min(F_intrp, F_geom) with F_intrp = psi_e/(psi_e + x) and, outside the
     // neutrinosphere, F_geom = h psi_e / x, h = (1 + mu_nu)/2, mu_nu = sqrt(1 - rho^2),
     // rho = R_nu / R_{i+1/2}.  F_geom is the smaller one exactly when h psi_e < (1 - h) x, i.e.
@@ -383,25 +390,72 @@ __global__ void k_edges(Prob p, Ws w) {
       den = x;
     }
     F = num / den;
+    if (w.jl) {
+      const double s = dpsi > 0.0 ? 1.0 : -1.0;
+      if (geom) {                       // Phi = (h / b) psi_e s
+        dl = dr = 0.25 * (1.0 + sqrt(m2)) / b * s;
+      } else {                          // Phi = psi_e d / (psi_e + b |d|)
+        const double phi = psi_e * dpsi / sp;
+        dl = ((0.5 * dpsi - psi_e) - phi * (0.5 - b * s)) / sp;
+        dr = ((0.5 * dpsi + psi_e) - phi * (0.5 + b * s)) / sp;
+      }
+    }
   }
-  w.alpha[t] = lam_e * F * z[ZC_EI3DR] * z[ZC_EGEO];
+  const double K = lam_e * z[ZC_EI3DR] * z[ZC_EGEO];
+  w.alpha[t] = K * F;
   if (w.lim) w.lim[t] = F;
+  if (w.jl) {
+    w.jl[t] = -K * dl;
+    w.jr[t] = -K * dr;
+  }
 }
 
-// Moment m_k = eta psi^n_k of one zone's row: eta = eta1 (psi1), or eta2(eta1) (psi2).
-__device__ inline double shock_moment(const Prob &p, const Ws &w, size_t row, int k, bool second) {
+// The transport mean free path at the outer iterate: as k_jlam with the NES rates at psi and the
+// emissivity the iteration keeps at the current Ye (jbuf); psi^n, the first residual's sums and
+// the emissivity are not touched.
+__global__ void k_lam_iter(Prob p, Ws w, const double *__restrict__ psi) {
+  const int n = p.n;
+  const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (unsigned)(p.n_ray * p.n_r * n)) return;
+  const unsigned zu = t / (unsigned)n;
+  const int k = (int)(t - zu * n);
+  const size_t zi = zu;
+  const int ray = (int)(zu / (unsigned)p.n_r), i = (int)(zu - (unsigned)ray * p.n_r);
+  const double *fin = w.phin + (zi * n + k) * n;
+  const double *fout = w.phout + (zi * n + k) * n;
+  const double rs = w.rsum[zi * n + k];
+  for (int q = 0; q < NS; ++q) {
+    const size_t g = (((size_t)ray * NS + q) * p.n_r + i) * n + k;
+    const double sc = p.scale ? p.scale[q * n + k] : 1.0;
+    const double kap = p.kabs[g] * sc, ksc = p.kscat[g] * sc;
+    const double *ps = psi + (g - k);
+    double gain = 0.0, lp = 0.0;
+    for (int kp = 0; kp < n; ++kp) {
+      gain += fin[kp] * ps[kp];
+      lp += fout[kp] * ps[kp];
+    }
+    const double kt = kap + w.jbuf[g] + ksc + gain + (rs - lp);
+    const double y = rsqrt(kt);
+    w.kinv[g] = kt;
+    w.slam[g] = y;
+    w.lam[g] = y * y;
+  }
+}
+
+// Moment m_k = eta psi_k of one zone's row: eta = eta1 (psi1), or eta2(eta1) (psi2).
+__device__ inline double shock_moment(const Prob &p, const double *psi, size_t row, int k, bool second) {
   const double x = p.eta1 ? fmin(fmax(p.eta1[row + k], 0.0), 1.0) : 0.0;
-  return (second ? minerbo_eta2(x) : x) * w.psi_n[row + k];
+  return (second ? minerbo_eta2(x) : x) * psi[row + k];
 }
 
 // (E_+^3 m_{k+1/2} - E_-^3 m_{k-1/2}) / ((E_+^3 - E_-^3)/3) with m_{k+1/2} the mean of the adjacent
 // groups (Eqs. a92, a98), zero at the lowest and highest group edge.  Written with the energies
 // at infinity: the ratio is the same on every zone's comoving grid E/a.
-__device__ inline double shock_ediv(const Prob &p, const Ws &w, size_t row, int k, bool second) {
+__device__ inline double shock_ediv(const Prob &p, const double *psi, size_t row, int k, bool second) {
   const int n = p.n;
-  const double mk = shock_moment(p, w, row, k, second);
-  const double up = k + 1 < n ? 0.5 * (mk + shock_moment(p, w, row, k + 1, second)) : 0.0;
-  const double dn = k > 0 ? 0.5 * (shock_moment(p, w, row, k - 1, second) + mk) : 0.0;
+  const double mk = shock_moment(p, psi, row, k, second);
+  const double up = k + 1 < n ? 0.5 * (mk + shock_moment(p, psi, row, k + 1, second)) : 0.0;
+  const double dn = k > 0 ? 0.5 * (shock_moment(p, psi, row, k - 1, second) + mk) : 0.0;
   const double el = p.e_edge[k], eh = p.e_edge[k + 1];
   const double el3 = el * el * el, eh3 = eh * eh * eh;
   return (eh3 * up - el3 * dn) / ((eh3 - el3) / 3.0);
@@ -416,7 +470,7 @@ __device__ inline double shock_ediv(const Prob &p, const Ws &w, size_t row, int 
 // frame i+1 back to frame i, for zone i only).  Formed at psi^n like the flux coefficients;
 // bw = beta times its roll-in weight comes per edge from the zone constants (ZC_SHOCK), so the
 // zones away from a shock only store a zero.
-__global__ void k_shock(Prob p, Ws w) {
+__global__ void k_shock(Prob p, Ws w, const double *__restrict__ psi) {
   const int n = p.n;
   const unsigned tu = blockIdx.x * blockDim.x + threadIdx.x;
   if (tu >= (unsigned)(p.n_ray * NS * p.n_r * n)) return;
@@ -433,15 +487,15 @@ __global__ void k_shock(Prob p, Ws w) {
   if (i < last) {
     const double bw = z[ZC_SHOCK];
     if (bw != 0.0) {
-      const double d0 = bw * (-shock_moment(p, w, row, k, false) + shock_ediv(p, w, row, k, false));
-      const double d1 = -bw * shock_ediv(p, w, row + n, k, true);
+      const double d0 = bw * (-shock_moment(p, psi, row, k, false) + shock_ediv(p, psi, row, k, false));
+      const double d1 = -bw * shock_ediv(p, psi, row + n, k, true);
       sh += w.alpha[t] * d0 + z[ZC_EGEO] * d1;
     }
   }
   if (i > 0) {
     const double bw = z[ZC_SHOCK - ZC_N];          // edge i-1/2, zone i-1's constant
     if (bw != 0.0) {
-      const double d0 = bw * (-shock_moment(p, w, row - n, k, false) + shock_ediv(p, w, row - n, k, false));
+      const double d0 = bw * (-shock_moment(p, psi, row - n, k, false) + shock_ediv(p, psi, row - n, k, false));
       sh -= w.alpha[t - n] * d0;
     }
   }
@@ -474,8 +528,18 @@ cudaError_t launch_setup(const Prob &p, const Ws &w, const double *psi, const do
   }
   k_jlam<<<nblk(nzk, B), B, 0, s>>>(p, w, psi, T);
   k_nusphere<<<nblk((size_t)p.n_ray * NS * p.n * 32, B), B, 0, s>>>(p, w);   // a warp per (ray, q, k)
-  k_edges<<<nblk(nall, B), B, 0, s>>>(p, w);
-  if (p.u) k_shock<<<nblk(nall, B), B, 0, s>>>(p, w);
+  k_edges<<<nblk(nall, B), B, 0, s>>>(p, w, w.psi_n);
+  if (p.u) k_shock<<<nblk(nall, B), B, 0, s>>>(p, w, w.psi_n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_coef_iterate(const Prob &p, const Ws &w, const double *psi, cudaStream_t s) {
+  const unsigned B = 256;
+  const size_t nzk = (size_t)p.n_ray * p.n_r * p.n;
+  const size_t nall = nzk * NS;
+  k_lam_iter<<<nblk(nzk, B), B, 0, s>>>(p, w, psi);
+  k_nusphere<<<nblk((size_t)p.n_ray * NS * p.n * 32, B), B, 0, s>>>(p, w);
+  k_edges<<<nblk(nall, B), B, 0, s>>>(p, w, psi);
   return cudaGetLastError();
 }
 

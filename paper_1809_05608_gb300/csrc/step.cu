@@ -112,6 +112,7 @@ Ws resolve(void *base, const Layout &L) {
   w.src = (double *)(b + L.src);
   w.shock = (double *)(b + L.shock);
   w.lim = nullptr;
+  w.jl = w.jr = nullptr;       // set by mgfld_step when the coefficients follow the iterate
   w.diag = (double *)(b + L.diag);
   w.lower = (double *)(b + L.lower);
   w.upper = (double *)(b + L.upper);
@@ -562,11 +563,18 @@ mgfld_status mgfld_step(const mgfld_dims *dims, const mgfld_problem *prob, mgfld
   if ((opts->precision != MGFLD_FP64 && opts->precision != MGFLD_MIXED) || opts->max_iter < 1 ||
       !(opts->tol > 0.0) || !(opts->tol_ye > 0.0) || !(opts->tolmin_psi >= 0.0) || !(opts->tolmin_ye >= 0.0))
     return MGFLD_EINVAL;
+  if (opts->coef_iterate && prob->u) return MGFLD_EINVAL;
   if (((uintptr_t)ws & 255u) != 0) return MGFLD_EINVAL;
   const Layout L = make_layout(dims->n_ray, dims->n_r, dims->n_e, opts->precision);
   if (ws_bytes < L.total) return MGFLD_ENOMEM;
   cudaStream_t s = (cudaStream_t)stream;
-  const Ws w = resolve(ws, L);
+  Ws w = resolve(ws, L);
+  if (opts->coef_iterate) {
+    // the limiter's derivatives take the storage of 1/lambda and lambda, which the neutrinosphere
+    // scan has consumed before the limiter kernel writes them (setup and every iteration)
+    w.jl = w.kinv;
+    w.jr = w.lam;
+  }
   const Prob p = make_prob(dims, prob);
   Tol tl;
   tl.tol = opts->tol; tl.tolmin = opts->tolmin_psi; tl.tol_ye = opts->tol_ye; tl.tolmin_ye = opts->tolmin_ye;
@@ -588,6 +596,12 @@ mgfld_status mgfld_step(const mgfld_dims *dims, const mgfld_problem *prob, mgfld
   int host_counters[8];
   for (int it = 0; it < opts->max_iter && n_act > 0; ++it) {
     const int *jac = tl.chord ? w.refac : nullptr;
+    if (opts->coef_iterate && it > 0) {
+      // the flux coefficients of Eq. a59 at the current iterate (psi and Ye updated in place)
+      prof.begin(MGFLD_PROF_SETUP);
+      MGFLD_CUDA(launch_coef_iterate(p, w, state->psi, s));
+      prof.end(MGFLD_PROF_SETUP, 3);
+    }
     prof.begin(MGFLD_PROF_ASSEMBLE);
     MGFLD_CUDA(launch_assemble(p, w, state->psi, w.diag, tl.mixed, w.lower, w.upper, w.rhs, w.list_act, n_act,
                                jac, s, nullptr, it == 0));

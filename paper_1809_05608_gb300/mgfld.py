@@ -50,7 +50,7 @@ class State(ctypes.Structure):
 class StepOpts(ctypes.Structure):
     _fields_ = [('precision', ctypes.c_int), ('tol', ctypes.c_double), ('tolmin_psi', ctypes.c_double),
                 ('tol_ye', ctypes.c_double), ('tolmin_ye', ctypes.c_double), ('max_iter', ctypes.c_int),
-                ('refactor_ratio', ctypes.c_double), ('profile', ctypes.c_void_p)]
+                ('refactor_ratio', ctypes.c_double), ('profile', ctypes.c_void_p), ('coef_iterate', ctypes.c_int)]
 
 
 class StepReport(ctypes.Structure):
@@ -193,15 +193,16 @@ PROF_NAMES = ('setup', 'assemble', 'factor', 'solve', 'update', 'finish')
 
 
 def step_opts(precision=MGFLD_FP64, tol=1e-10, tolmin_psi=1.0, tol_ye=None, tolmin_ye=0.1, max_iter=40,
-              refactor_ratio=None, profile=None):
+              refactor_ratio=None, profile=None, coef_iterate=False):
     """`refactor_ratio`: None gives 0.1 for MIXED and Newton (0) for FP64; a positive value makes
     FP64 reuse its factors too.  `profile`: optional ctypes (c_double * 12) array accumulating
-    per-category (milliseconds, launches) for the categories of PROF_NAMES."""
+    per-category (milliseconds, launches) for the categories of PROF_NAMES.  `coef_iterate`: the
+    flux coefficients of Eq. a59 at the outer iterate (n+1) instead of at psi^n."""
     if refactor_ratio is None:
         refactor_ratio = 0.1 if precision == MGFLD_MIXED else 0.0
     return StepOpts(int(precision), float(tol), float(tolmin_psi), float(tol if tol_ye is None else tol_ye),
                     float(tolmin_ye), int(max_iter), float(refactor_ratio),
-                    None if profile is None else ctypes.cast(profile, ctypes.c_void_p))
+                    None if profile is None else ctypes.cast(profile, ctypes.c_void_p), 1 if coef_iterate else 0)
 
 
 # ---------------------------------------------------------------------------- entry points
