@@ -211,8 +211,8 @@ class Step:
 def step_vjp(prob, psi_n, ye_n, T_n, scale, psi1, ye1, psi1_bar, ye1_bar, T1_bar, heat_weight=1.0):
     """Gradients of L = <psi1_bar, psi1> + <ye1_bar, ye1> + <T1_bar, T1> + heat_weight * sum(H)
     with respect to (psi_n, ye_n, T_n, scale), for one step whose root is (psi1, ye1)."""
-    if prob.get('u') is not None:
-        raise NotImplementedError('the shock terms (Eqs. a91-a99) are not differentiated')
+    if prob.get('u') is not None or prob.get('pair_coef') is not None:
+        raise NotImplementedError('the shock (Eqs. a91-a99) and pair (Eq. d14) terms are not differentiated')
     p = [_t(psi_n).requires_grad_(), _t(ye_n).requires_grad_(), _t(T_n).requires_grad_(),
          _t(scale).requires_grad_()]
     st = Step(prob, *p)

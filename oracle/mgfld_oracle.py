@@ -47,6 +47,12 @@ identically here and documented with the project's design notes):
       j = kappa_a exp((mu - eps)/T) (Kirchhoff); the exponent is capped at 700
       so that 1/(1 - f_eq) stays finite.
   R11 Gain-region heating weights each zone by its lapse (proper time a_i dt).
+  P1  Optional synthetic pair term (Eq. d14, zeroth moment): Legendre order 0 only (Phi_1 = 0,
+      as R6 for NES), no angular correction (chi = 1), annihilation kernel Phi0^a = pair_coef
+      (per zone, cm^3/s, energy independent), creation Phi0^p = exp(-(eps + eps')/T) Phi0^a
+      (Eq. d12 with the pair energy eps + eps' given to the e-e+ pair); partners nu_e/nubar_e and
+      nu_mu,tau/nubar_mu,tau.  It enters the sources (hence Eq. a62b) but not lambda^(t) (a1) and,
+      being symmetric in the pair, leaves the lepton number and Eq. a62a unchanged.
   R12 (optional, the paper-literal form of Eq. a59) lambda^(t) and F at n+1: the flux
       coefficients (mean free path with j at the iterate's Ye and the NES rates at its psi,
       neutrinosphere, ghost factor, limiter) are formed again at every outer iterate with
@@ -245,6 +251,29 @@ def nes_source(psi, w, phi_out, phi_in):
     return C_NES * ((1.0 - psi) * gain - psi * loss)
 
 
+PAIR_PARTNER = np.array([1, 0, 3, 2])   # nu_e <-> nubar_e, nu_mu,tau <-> nubar_mu,tau
+
+
+def pair_kernels(eps, T, coef):
+    """Synthetic pair kernels (reading P1): annihilation Phi0^a(eps, eps') = coef, creation
+    Phi0^p = exp(-(eps + eps')/T) Phi0^a (Eq. d12 with E_e- + E_e+ = eps + eps'), per zone
+    [n_ray, n_r, n_e, n_e]; the species' own energies on the rows, the partner's on the columns."""
+    e = eps[:, :, :, None] + eps[:, :, None, :]
+    cb = np.broadcast_to(coef[:, :, None, None], e.shape)
+    return cb, cb * np.exp(-e / T[:, :, None, None])
+
+
+def pair_source(psi, w, phi_a, phi_p):
+    """Zeroth-moment pair source per unit length, Eq. d14 with Phi_1 = 0 and chi = 1 (reading P1),
+    divided by c like the NES source:
+    S_k = C [(1 - psi_k) sum_k' w_k' Phi^p[k,k'] (1 - psibar_k') - psi_k sum_k' w_k' Phi^a[k,k'] psibar_k'],
+    psibar the partner species' occupation."""
+    bar = psi[:, PAIR_PARTNER]
+    make = np.einsum('rikm,rim,rqim->rqik', phi_p, w, 1.0 - bar)
+    kill = np.einsum('rikm,rim,rqim->rqik', phi_a, w, bar)
+    return C_NES * ((1.0 - psi) * make - psi * kill)
+
+
 def nes_inverse_mfp(psi, w, phi_out, phi_in):
     """NES contribution to 1/lambda^(t): Eq. a17 applied to the first moment of Eq. d8 (Phi_1 = 0)."""
     return C_NES * (np.einsum('rikm,rim,rqim->rqik', phi_in, w, psi)
@@ -298,6 +327,8 @@ def setup_step(prob, psi_n, ye_n, T_n):
     coef = prob.get('nes_coef')
     coef = np.zeros((n_ray, n_r)) if coef is None else np.asarray(coef, dtype=np.float64)
     f.phi_out, f.phi_in = nes_kernels(f.eps, f.T_n, coef)     # at T^n (Sec. LTS: T held fixed)
+    pc = prob.get('pair_coef')
+    f.pair_a, f.pair_p = (None, None) if pc is None else pair_kernels(f.eps, f.T_n, np.asarray(pc, dtype=np.float64))
 
     f.e_n = e_int(f.rho, f.T_n, f.ye_n, eos)
     f.e_edge = np.asarray(prob['e_edge'], dtype=np.float64)
@@ -482,6 +513,8 @@ def sources(f, psi, ye):
     j, live = emissivity(f.kappa_abs, f.eps, mu_q, f.T_n)
     s_ae = absem_source(psi, j, f.kappa_abs)
     s_nes = nes_source(psi, f.w, f.phi_out, f.phi_in)
+    if f.pair_a is not None:
+        s_nes = s_nes + pair_source(psi, f.w, f.pair_a, f.pair_p)
     return s_ae + s_nes, s_ae, j, dmu_q, live
 
 
@@ -549,10 +582,20 @@ def jacobian(f, psi, ye):
     diag = (1.0 / (a[:, None, :, None] * C_LIGHT * f.dt)
             + pre * (jl + ghost_term * jr - jr_in)
             + j + f.kappa_abs + diag_nes)
+    if f.pair_a is not None:
+        # d S_pair,k / d psi_k (own species, diagonal) and d S_pair,k / d psibar_k' (partner)
+        bar = psi[:, PAIR_PARTNER]
+        diag = diag + C_NES * (np.einsum('rikm,rim,rqim->rqik', f.pair_p, w, 1.0 - bar)
+                               + np.einsum('rikm,rim,rqim->rqik', f.pair_a, w, bar))
+        dP = -C_NES * (np.einsum('rikm,rim,rqik->rqikm', f.pair_p, w, 1.0 - psi)
+                       + np.einsum('rikm,rim,rqik->rqikm', f.pair_a, w, psi))
     A = np.zeros((n_ray, n_r, M, M))
     for q in range(N_SPECIES):
         sl = slice(q * n_e, (q + 1) * n_e)
         A[:, :, sl, sl] = -dS[:, q]
+        if f.pair_a is not None:
+            qb = PAIR_PARTNER[q]
+            A[:, :, sl, qb * n_e:(qb + 1) * n_e] = -dP[:, q]
         idx = np.arange(q * n_e, (q + 1) * n_e)
         A[:, :, idx, idx] += diag[:, q]
         # d G_q / d Ye = -(1 - psi) dj/dYe, dj/dYe = j dmu/dYe / T (zero where capped).

@@ -5,9 +5,10 @@ from paper_1809_05608_gb300 import problems
 
 
 def strong(n_ray=2, n_r=8, n_e=5, kabs=1e16, kscat=1e14, nes=1.0, lapse=False, config=2,
-           bc=0, dt=1e-6):
+           bc=0, dt=1e-6, pair=0.0):
     """The synthetic profile at reduced size with opacities scaled up so that
-    absorption/emission, scattering and NES all matter within one step."""
+    absorption/emission, scattering and NES all matter within one step; pair > 0 adds the
+    synthetic pair process with the annihilation kernel pair x 1e-41 rho (cm^3/s)."""
     inp = problems.make_problem(config, n_ray=n_ray, n_r=n_r, n_e=n_e)
     p = dict(inp['problem'])
     p['kappa_abs'] = p['kappa_abs'] * kabs
@@ -15,6 +16,8 @@ def strong(n_ray=2, n_r=8, n_e=5, kabs=1e16, kscat=1e14, nes=1.0, lapse=False, c
     p['nes_coef'] = p['nes_coef'] * nes
     p['outer_bc'] = bc
     p['dt'] = dt
+    if pair > 0.0:
+        p['pair_coef'] = 1e-41 * pair * p['rho']
     if lapse:
         rc = 0.5 * (p['r_edge'][:, 1:] + p['r_edge'][:, :-1])
         p['lapse'] = np.sqrt(1.0 - 0.2 * rc[:, :1] / rc)   # 0.89 .. 1, varies along the ray
