@@ -85,6 +85,14 @@ typedef struct {
    * The shock terms are not differentiated: mgfld_adjoint returns MGFLD_EINVAL when u is set. */
   const double *u;
   const double *eta1;
+  /* Synthetic pair process (Eq. d14, zeroth moment, Legendre order 0): pair_coef [n_ray][n_r] the
+   * annihilation kernel (cm^3/s), the creation kernel exp(-(eps + eps')/T^n) times it (Eq. d12),
+   * nu_e paired with nubar_e and nu_mu,tau with nubar_mu,tau.  Must be NULL: mgfld_step,
+   * mgfld_assemble and mgfld_adjoint return MGFLD_EINVAL when it is set.  The process couples
+   * each species to its partner group by group, which the per-species blocks of this library do
+   * not hold; with the partner's derivative left to the outer iteration the pair mode does not
+   * converge (it needs coupled 2 n_e x 2 n_e species-pair blocks). */
+  const double *pair_coef;
 } mgfld_problem;
 
 /* State at t^n on entry, t^{n+1} on exit (in place). */

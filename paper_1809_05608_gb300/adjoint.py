@@ -44,7 +44,7 @@ class AdjointRunner:
     def _problem(self, scale):
         p = self.prob.struct
         return M.Problem(p.r_edge, p.lapse, p.e_edge, p.rho, p.kappa_abs, p.kappa_scat, p.nes_coef,
-                         M._ptr(scale), p.eos, p.dt, p.outer_bc, p.u, p.eta1)
+                         M._ptr(scale), p.eos, p.dt, p.outer_bc, p.u, p.eta1, p.pair_coef)
 
     def _step(self, ps, psi, ye, T):
         rc = M.mgfld_step(self.dims, ps, psi, ye, T, self.opts, self.ws,

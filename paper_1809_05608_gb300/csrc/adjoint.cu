@@ -647,7 +647,7 @@ mgfld_status mgfld_adjoint(const mgfld_dims *dims, const mgfld_problem *prob, co
       !state_np1 || !state_np1->psi || !state_np1->ye || !io || !io->psi_bar_out || !io->ye_bar_out ||
       !io->T_bar_out || !ws || !(io->sweep_tol >= 0.0) || io->max_sweeps < 0)
     return MGFLD_EINVAL;
-  if (prob->u) return MGFLD_EINVAL;   // the shock terms (Eqs. a91-a99) are not differentiated
+  if (prob->u || prob->pair_coef) return MGFLD_EINVAL;   // shock and pair terms are not differentiated
   if (((uintptr_t)ws & 255u) != 0) return MGFLD_EINVAL;
   if (ws_bytes < make_adj_layout(dims->n_ray, dims->n_r, dims->n_e).total) return MGFLD_ENOMEM;
   return adjoint_step(make_prob(dims, prob), state_n, state_np1, io, ws, (cudaStream_t)stream);

@@ -564,6 +564,7 @@ mgfld_status mgfld_step(const mgfld_dims *dims, const mgfld_problem *prob, mgfld
       !(opts->tol > 0.0) || !(opts->tol_ye > 0.0) || !(opts->tolmin_psi >= 0.0) || !(opts->tolmin_ye >= 0.0))
     return MGFLD_EINVAL;
   if (opts->coef_iterate && prob->u) return MGFLD_EINVAL;
+  if (prob->pair_coef) return MGFLD_EINVAL;       // species-pair blocks are not built
   if (((uintptr_t)ws & 255u) != 0) return MGFLD_EINVAL;
   const Layout L = make_layout(dims->n_ray, dims->n_r, dims->n_e, opts->precision);
   if (ws_bytes < L.total) return MGFLD_ENOMEM;
@@ -667,7 +668,7 @@ mgfld_status mgfld_step(const mgfld_dims *dims, const mgfld_problem *prob, mgfld
 mgfld_status mgfld_assemble(const mgfld_dims *dims, const mgfld_problem *prob, const mgfld_state *state,
                             mgfld_system *sys, void *ws, size_t ws_bytes, void *stream) {
   if (!dims_ok(dims) || !prob_ok(prob) || !state || !state->psi || !state->ye || !state->T || !sys ||
-      !sys->diag || !sys->lower || !sys->upper || !sys->rhs || !ws)
+      !sys->diag || !sys->lower || !sys->upper || !sys->rhs || !ws || prob->pair_coef)
     return MGFLD_EINVAL;
   if (((uintptr_t)ws & 255u) != 0) return MGFLD_EINVAL;
   const Layout L = make_layout(dims->n_ray, dims->n_r, dims->n_e, MGFLD_FP64);

@@ -40,7 +40,7 @@ class Problem(ctypes.Structure):
                 ('rho', ctypes.c_void_p), ('kappa_abs', ctypes.c_void_p), ('kappa_scat', ctypes.c_void_p),
                 ('nes_coef', ctypes.c_void_p), ('scale', ctypes.c_void_p), ('eos', EosParams),
                 ('dt', ctypes.c_double), ('outer_bc', ctypes.c_int), ('u', ctypes.c_void_p),
-                ('eta1', ctypes.c_void_p)]
+                ('eta1', ctypes.c_void_p), ('pair_coef', ctypes.c_void_p)]
 
 
 class State(ctypes.Structure):
@@ -163,12 +163,12 @@ class DeviceProblem:
     the matching C struct.  `prob` is a dict with the fields of mgfld_problem."""
 
     FIELDS = ('r_edge', 'lapse', 'e_edge', 'rho', 'kappa_abs', 'kappa_scat', 'nes_coef', 'scale')
-    SHOCK_FIELDS = ('u', 'eta1')
+    OPTIONAL_FIELDS = ('u', 'eta1', 'pair_coef')
 
     def __init__(self, prob, device='cuda'):
         import torch
         self.t = {}
-        for f in self.FIELDS + self.SHOCK_FIELDS:
+        for f in self.FIELDS + self.OPTIONAL_FIELDS:
             v = prob.get(f)
             self.t[f] = None if v is None else torch.as_tensor(
                 np.array(v, dtype=np.float64, order='C'), device=device)
@@ -176,7 +176,7 @@ class DeviceProblem:
         self.outer_bc = int(prob.get('outer_bc', MGFLD_BC_GHOST))
         self.eos = lib().mgfld_eos_default()
         self.struct = Problem(*[_ptr(self.t[f]) for f in self.FIELDS], self.eos, self.dt, self.outer_bc,
-                              *[_ptr(self.t[f]) for f in self.SHOCK_FIELDS])
+                              *[_ptr(self.t[f]) for f in self.OPTIONAL_FIELDS])
 
     def rays(self, lo, hi, n_r, n_e):
         """C struct viewing rays [lo, hi) only (rays are independent; used for chunking)."""
@@ -186,7 +186,7 @@ class DeviceProblem:
         return Problem(off('r_edge', n_r + 1), off('lapse', n_r), _ptr(self.t['e_edge']), off('rho', n_r),
                        off('kappa_abs', N_SPECIES * n_r * n_e), off('kappa_scat', N_SPECIES * n_r * n_e),
                        off('nes_coef', n_r), _ptr(self.t['scale']), self.eos, self.dt, self.outer_bc,
-                       off('u', n_r), off('eta1', N_SPECIES * n_r * n_e))
+                       off('u', n_r), off('eta1', N_SPECIES * n_r * n_e), off('pair_coef', n_r))
 
 
 PROF_NAMES = ('setup', 'assemble', 'factor', 'solve', 'update', 'finish')

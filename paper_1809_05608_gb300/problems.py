@@ -160,7 +160,7 @@ def make_problem(config: int, rays=None, n_ray=None, n_r=None, n_e=None):
 def subset_rays(inp, rays):
     """Restrict every per-ray array of an input dict to the selected rays."""
     prob = dict(inp['problem'])
-    for key in ('r_edge', 'lapse', 'rho', 'kappa_abs', 'kappa_scat', 'nes_coef', 'u', 'eta1'):
+    for key in ('r_edge', 'lapse', 'rho', 'kappa_abs', 'kappa_scat', 'nes_coef', 'u', 'eta1', 'pair_coef'):
         if prob.get(key) is not None:
             prob[key] = np.ascontiguousarray(prob[key][rays])
     out = dict(inp)

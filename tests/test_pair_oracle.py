@@ -100,3 +100,36 @@ def test_equilibrium_with_pairs_is_a_fixed_point():
     out = O.step(p, psi, ye, T)
     assert np.max(O.rel_change(out['psi'] - psi, psi)) < 1e-13
     assert np.max(np.abs(out['T'] / T - 1)) < 1e-13
+
+
+def test_adjoint_refuses_pairs_before_touching_the_device():
+    """mgfld_adjoint does not differentiate the pair process: refused by the argument checks
+    (host only; the fake pointers are never dereferenced)."""
+    import ctypes
+    from paper_1809_05608_gb300 import mgfld as M
+    fake = ctypes.c_void_p(0x10000)
+    prob = M.Problem(*[fake] * 8, M.lib().mgfld_eos_default(), 1e-6, 0, None, None, fake)
+    st = M.State(fake, fake, fake)
+    io = M.AdjointIO(None, None, None, 1.0, fake, fake, fake, None, 0, 0.0, 0, 0.0)
+    dims = M.Dims(1, 8, 4, 4)
+    rc = M.lib().mgfld_adjoint(ctypes.byref(dims), ctypes.byref(prob), ctypes.byref(st), ctypes.byref(st),
+                               ctypes.byref(io), ctypes.c_void_p(0x100000), 1 << 30, None)
+    assert rc == M.MGFLD_EINVAL
+
+
+def test_gpu_step_refuses_the_pair_process():
+    """The library's per-species blocks do not hold the partner coupling: mgfld_step and
+    mgfld_assemble refuse a problem with pair_coef in their argument checks (host only)."""
+    import ctypes
+    from paper_1809_05608_gb300 import mgfld as M
+    fake = ctypes.c_void_p(0x10000)
+    prob = M.Problem(*[fake] * 8, M.lib().mgfld_eos_default(), 1e-6, 0, None, None, fake)
+    st = M.State(fake, fake, fake)
+    dims = M.Dims(1, 8, 4, 4)
+    rc = M.lib().mgfld_step(ctypes.byref(dims), ctypes.byref(prob), ctypes.byref(st),
+                            ctypes.byref(M.step_opts()), None, ctypes.c_void_p(0x100000), 1 << 30, None)
+    assert rc == M.MGFLD_EINVAL
+    sys_ = M.System(fake, fake, fake, fake)
+    rc = M.lib().mgfld_assemble(ctypes.byref(dims), ctypes.byref(prob), ctypes.byref(st), ctypes.byref(sys_),
+                                ctypes.c_void_p(0x100000), 1 << 30, None)
+    assert rc == M.MGFLD_EINVAL
