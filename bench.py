@@ -368,18 +368,31 @@ def e2e_run(M, torch, inp, precision, steps):
 
 # ------------------------------------------------------------------------- CPU oracle
 
-def oracle_sample(inp, n_rays, n_steps=1):
+def oracle_sample(inp, n_rays, n_steps=1, **step_kw):
     """Time the CPU oracle, as it stands, on the first n_rays rays for n_steps steps."""
     from oracle import mgfld_oracle as O
     sub = problems.subset_rays(inp, slice(0, n_rays))
     c0, w0 = time.process_time(), time.perf_counter()
-    O.run_steps(sub['problem'], sub['psi0'], sub['ye0'], sub['T0'], n_steps)
+    O.run_steps(sub['problem'], sub['psi0'], sub['ye0'], sub['T0'], n_steps, **step_kw)
     wall = time.perf_counter() - w0
     cpu = time.process_time() - c0
     ups = updates_per_step(sub) * n_steps / wall
     return dict(value=ups, unit=UNIT, cores=max(1, int(round(cpu / wall))), kind='oracle',
                 sample=f'{n_rays} of the 256 rays x {n_steps} implicit step(s), FP64 numpy/LAPACK, '
                        f'{wall:.1f} s wall', wall_s=wall)
+
+
+def stress_oracle_sample(inp, n_rays):
+    """Time the stress-and-lapse oracle, as it stands, on the first n_rays rays' state."""
+    from oracle import stress_lapse_oracle as S
+    sub = problems.subset_rays(inp, slice(0, n_rays))
+    p, m = problems.stress_inputs(sub)
+    c0, w0 = time.process_time(), time.perf_counter()
+    S.stress_and_lapse(sub['problem'], sub['psi0'], sub['ye0'], sub['T0'], p, m)
+    wall = time.perf_counter() - w0
+    return dict(value=updates_per_step(sub) / wall, unit=UNIT, kind='oracle',
+                cores=max(1, int(round((time.process_time() - c0) / wall))),
+                sample=f'{n_rays} of the 256 rays, one call, FP64 numpy, {wall:.2f} s wall')
 
 
 def energy_advection_run(M, torch, n_gpus, rank, steps, warmup, cpu_rays=0):
@@ -613,10 +626,16 @@ def main():
     stress = stress_lapse_run(M, torch, inp, args.steps, args.warmup)
     eadv = energy_advection_run(M, torch, n_gpus, rank, args.steps, args.warmup,
                                 cpu_rays=0 if (rank != 0 or args.no_cpu_baseline) else 64)
-    cpu = None
+    cpu = cpu_shock = cpu_lit = cpu_stress = None
     if rank == 0 and not args.no_cpu_baseline:
         cpu = oracle_sample(inp, args.oracle_rays)
         cpu.pop('wall_s')
+        # the oracle on 2-ray samples of the other step lines (rays are independent)
+        cpu_shock = oracle_sample(shock_workload(n_gpus, rank), 2)
+        cpu_shock.pop('wall_s')
+        cpu_lit = oracle_sample(inp, 2, coef_iterate=True)
+        cpu_lit.pop('wall_s')
+        cpu_stress = stress_oracle_sample(inp, 16)
     if rank != 0:
         return 0
     work_gb = (mixed['stepper'].ws.numel() + sum(t.numel() * 8 for t in mixed['stepper'].prob.t.values()
@@ -652,6 +671,8 @@ def main():
                                  'r_s - 15 km, -0.2c at r_s ~ 150 km, -0.2c (r_s/r)^2 outside) and a '
                                  'synthetic flux factor; shock terms of Eqs. a91-a99 at the shock',
                         kernel_ms={k: v['ms'] for k, v in shock['prof'].items()},
+                        roofline=roofline_for(shock, inp, M.MGFLD_MIXED, None), cpu_baseline=cpu_shock,
+                        dominant_category=max(shock['prof'], key=lambda c: shock['prof'][c]['ms']),
                         outer_iterations_per_step=shock['max_iters'],
                         gpu_launches=sum(v['launches'] for v in shock['prof'].values())),
         coef_iterate_path=dict(value=job_throughput(ups, ws, ms_lit), unit=UNIT, ms_per_step=ms_lit,
@@ -659,11 +680,13 @@ def main():
                                workload='the same rays with the flux coefficients of Eq. a59 (mean free path, '
                                         'limiter, neutrinosphere) formed again at every outer iterate',
                                kernel_ms={k: v['ms'] for k, v in lit['prof'].items()},
+                               roofline=roofline_for(lit, inp, M.MGFLD_MIXED, None), cpu_baseline=cpu_lit,
+                               dominant_category=max(lit['prof'], key=lambda c: lit['prof'][c]['ms']),
                                outer_iterations_per_step=lit['max_iters'],
                                gpu_launches=sum(v['launches'] for v in lit['prof'].values())),
         mixed_over_fp64=value / value64,
         energy_advection=eadv,
-        stress_lapse=stress)
+        stress_lapse=dict(stress, cpu_baseline=cpu_stress))
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
