@@ -1,0 +1,87 @@
+"""The two largest workloads at their full sizes, in the launch configuration a user runs them:
+
+* the 3D-scale mixed-precision step, 4096 rays (64 theta x 64 phi) x 540 zones x 20 groups x 4
+  species, one launch of all rays: every ray converges to 1e-10 with per-ray iteration counts that
+  differ between rays, sampled rays match the oracle, lepton number balances in every ray;
+* the adjoint workload, 512 rays x 512 x 20, 20 FP64 steps with a checkpoint every 5: the
+  gradient of the gain-region heating with respect to opacity scales matches central differences
+  of the GPU forward map itself (the oracle cannot run 512 rays x 20 steps in a test)."""
+import numpy as np
+import pytest
+
+from oracle import mgfld_oracle as O
+from paper_1809_05608_gb300 import problems
+
+torch = pytest.importorskip('torch')
+pytestmark = pytest.mark.gpu
+
+M = None
+ADJ = None
+
+
+@pytest.fixture(scope='module', autouse=True)
+def _lib():
+    global M, ADJ
+    if not torch.cuda.is_available():
+        pytest.skip('no CUDA device')
+    from paper_1809_05608_gb300 import adjoint, mgfld
+    M, ADJ = mgfld, adjoint
+    M.lib()
+
+
+def _dev(a):
+    return torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64), device='cuda')
+
+
+def test_3d_scale_mixed_full_launch():
+    full = problems.make_problem(4)
+    n_ray, _, n_r, n_e = full['psi0'].shape
+    assert (n_ray, n_r, n_e) == (4096, 540, 20)
+    st = M.Stepper(full, M.MGFLD_MIXED, tol=1e-10, max_iter=60)
+    psi, ye, T = st.state_to_device(full['psi0'], full['ye0'], full['T0'])
+    rc = st.step(psi, ye, T)
+    torch.cuda.synchronize()
+    rep = {k: v.cpu().numpy() for k, v in st.report.items()}
+    assert rc == M.MGFLD_OK and np.all(rep['ray_status'] == 0)
+    assert len(np.unique(rep['iters'])) >= 2          # uneven per-ray iteration counts
+    L = rep['ledger']
+    assert np.all(np.abs(L[:, 3]) <= 1e-12 * np.abs(L[:, 1]))
+    rays = [0, 2079, 4095]
+    sub = problems.subset_rays(full, rays)
+    out = O.step(sub['problem'], sub['psi0'], sub['ye0'], sub['T0'])
+    got = psi[rays].cpu().numpy()
+    fwd = float(np.max(O.rel_change(got - out['psi'], out['psi'])))
+    print(f'4096 x 540 x 20 mixed: sampled forward {fwd:.2e}; iterations {np.bincount(rep["iters"]).tolist()}, '
+          f'chunks of {st.chunk} rays')
+    assert fwd < 1e-10
+    assert np.max(np.abs(T[rays].cpu().numpy() / out['T'] - 1.0)) < 1e-10
+
+
+def test_adjoint_workload_full_size_against_central_differences():
+    inp = problems.make_problem(5)
+    n_ray, _, n_r, n_e = inp['psi0'].shape
+    assert (n_ray, n_r, n_e) == (512, 512, 20)
+    n_steps = 20
+    runner = ADJ.AdjointRunner(inp, checkpoint_every=5)
+    s_np = np.ones((4, n_e)) * (1.0 + 0.1 * np.arange(4 * n_e).reshape(4, n_e) / (4 * n_e))
+    scale = _dev(s_np).requires_grad_()
+    psi0, ye0, T0 = _dev(inp['psi0']), _dev(inp['ye0']), _dev(inp['T0'])
+    J = ADJ.heating_objective(scale, psi0, ye0, T0, runner, n_steps)
+    (gs,) = torch.autograd.grad(J, [scale])
+    gs = gs.cpu().numpy()
+
+    def J_of(sc):
+        with torch.no_grad():
+            v, _ = runner.forward(_dev(sc), psi0, ye0, T0, n_steps)
+        return float(v)
+
+    gmax = np.max(np.abs(gs))
+    assert gmax > 0.0 and float(J) > 0.0
+    for q, k in [(0, 4), (1, 12)]:
+        h = 1e-4 * s_np[q, k]
+        sp, sm = s_np.copy(), s_np.copy()
+        sp[q, k] += h
+        sm[q, k] -= h
+        fd = (J_of(sp) - J_of(sm)) / (2 * h)
+        print(f'dJ/dscale[{q},{k}]: adjoint {gs[q, k]:.6e}, central differences {fd:.6e}')
+        assert abs(fd - gs[q, k]) <= 1e-6 * gmax + 1e-6 * abs(fd)
