@@ -82,3 +82,12 @@ def test_full_launch_mixed_sampled():
     print(f'256-ray launch, n+1 coefficients (mixed): sampled forward {fwd:.2e}, iterations {rep["iters"].max()}')
     assert fwd < 1e-10
 
+
+
+@pytest.mark.parametrize('n_e,bc', [(7, 1), (3, 0)])
+def test_coefficients_at_the_iterate_ragged_and_reflecting(n_e, bc):
+    inp = SP.strong(n_ray=3, n_r=9, n_e=n_e, kabs=1e13, kscat=1e14, nes=5.0, bc=bc)
+    psi, ye, T, codes, rep = run_gpu(inp, tol=1e-11, coef_iterate=True)
+    out = O.step(inp['problem'], inp['psi0'], inp['ye0'], inp['T0'], coef_iterate=True)
+    assert codes == [M.MGFLD_OK]
+    assert normwise(psi, out['psi']) < max(1e-11, SP.fp64_tolerance(inp))

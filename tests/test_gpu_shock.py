@@ -131,3 +131,30 @@ def test_adjoint_rejects_shock_terms_before_touching_the_device():
     rc = M.lib().mgfld_adjoint(ctypes.byref(dims), ctypes.byref(prob), ctypes.byref(st), ctypes.byref(st),
                                ctypes.byref(io), ctypes.c_void_p(0x100000), 16, None)
     assert rc == M.MGFLD_ENOMEM
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize('case', ['jump at the last interior edge', 'reflecting edge, 7 groups', 'one zone'])
+def test_shock_edge_cases(case):
+    """Shock terms where the roll-in weight sits at the grid's ends, with a reflecting outer edge and
+    ragged groups, and on one-zone rays (no interior edge: the terms vanish)."""
+    _gpu()
+    if case == 'jump at the last interior edge':
+        inp = SP.strong(n_ray=2, n_r=12, n_e=5, kabs=1e15, kscat=1e15, nes=10.0, lapse=True)
+        u = np.zeros_like(inp['problem']['rho'])
+        u[:, -1] = -0.05 * O.C_LIGHT
+        u[:, 0] = 0.015 * O.C_LIGHT                   # half rolled in at the innermost edge
+    elif case == 'reflecting edge, 7 groups':
+        inp = SP.strong(n_ray=2, n_r=10, n_e=7, kabs=1e15, kscat=1e15, nes=10.0, bc=M.MGFLD_BC_REFLECT)
+        u = -0.03 * O.C_LIGHT * (np.arange(10)[None, :] >= 5) * np.ones((2, 1))
+    else:
+        inp = SP.strong(n_ray=2, n_r=1, n_e=4)
+        u = np.full_like(inp['problem']['rho'], -0.1 * O.C_LIGHT)
+    eta1 = np.broadcast_to(np.linspace(0.1, 0.9, inp['psi0'].shape[3]), inp['psi0'].shape).copy()
+    inp = dict(inp, problem=dict(inp['problem'], u=u, eta1=eta1))
+    psi, ye, T, codes, rep = run_gpu(inp, tol=1e-11)
+    out = O.step(inp['problem'], inp['psi0'], inp['ye0'], inp['T0'])
+    assert codes == [M.MGFLD_OK]
+    assert normwise(psi, out['psi']) < SP.fp64_tolerance(inp)
+    L = rep['ledger']
+    assert np.all(np.abs(L[:, 3]) <= 1e-12 * np.abs(L[:, 1]))

@@ -120,3 +120,10 @@ def test_reflecting_edge_and_bad_arguments():
     lap = torch.empty(n_ray, n_r, dtype=torch.float64, device='cuda')
     assert M.mgfld_stress_lapse(dims, dp.struct, psi, ye, T, ws, lapse=lap) == M.MGFLD_EINVAL     # no p
     assert M.mgfld_stress_lapse(dims, dp.struct, psi, ye, T, ws[:1024], p=_dev(p), lapse=lap) == M.MGFLD_ENOMEM
+
+
+def test_one_zone_rays():
+    inp = SP.strong(n_ray=2, n_r=1, n_e=4)
+    p, m = problems.stress_inputs(inp)
+    got, _ = check(inp['problem'], inp['psi0'], inp['ye0'], inp['T0'], p, m)
+    assert np.all(got['lapse'] > 0.0)
