@@ -53,6 +53,13 @@ identically here and documented with the project's design notes):
       (Eq. d12 with the pair energy eps + eps' given to the e-e+ pair); partners nu_e/nubar_e and
       nu_mu,tau/nubar_mu,tau.  It enters the sources (hence Eq. a62b) but not lambda^(t) (a1) and,
       being symmetric in the pair, leaves the lepton number and Eq. a62a unchanged.
+  P2  Optional angular correction of the pair annihilation kernel (Eqs. d16-d22, prob['pair_chi']):
+      chi = min(chi_1, chi_2) per (zone, eps, eps') formed at the start of the step from the flux
+      factors eta1 (the same input as S2; absent, 0) and the neutrinospheres of the step's
+      coefficients at psi^n, with the cone edges of Eqs. d17-d18 extended by Eq. d22 at the zone
+      centre R_i.  Eq. d14 puts chi on the annihilation kernel only.  Eq. d16 is kept as printed,
+      1 - eta etabar / 6, which is the average for distributions psi0 (1 + eta mu); Eq. d15's
+      psi0 + 3 mu psi1 would give 1 - 3 eta etabar / 2 (negative for forward-peaked radiation).
   R12 (optional, the paper-literal form of Eq. a59) lambda^(t) and F at n+1: the flux
       coefficients (mean free path with j at the iterate's Ye and the NES rates at its psi,
       neutrinosphere, ghost factor, limiter) are formed again at every outer iterate with
@@ -263,14 +270,50 @@ def pair_kernels(eps, T, coef):
     return cb, cb * np.exp(-e / T[:, :, None, None])
 
 
-def pair_source(psi, w, phi_a, phi_p):
-    """Zeroth-moment pair source per unit length, Eq. d14 with Phi_1 = 0 and chi = 1 (reading P1),
-    divided by c like the NES source:
-    S_k = C [(1 - psi_k) sum_k' w_k' Phi^p[k,k'] (1 - psibar_k') - psi_k sum_k' w_k' Phi^a[k,k'] psibar_k'],
-    psibar the partner species' occupation."""
+def chi_isotropic(eta, eta_bar):
+    """chi_1 of Eq. d16 as printed, 1 - eta etabar / 6: the annihilation factor (1 - n.nbar)^2
+    averaged over the near-isotropic distributions psi0 (1 + eta mu), relative to isotropic ones
+    (reading P2: Eq. d15's psi0 + 3 mu psi1 would give 1 - 3 eta etabar / 2); eta = psi1/psi0 of the
+    neutrino at eps, eta_bar of the antineutrino at eps'."""
+    return 1.0 - eta * eta_bar / 6.0
+
+
+def pair_mu(r_nu, R):
+    """The cone edge of Eqs. d17-d18 extended to any radius by Eq. d22:
+    max(sign(1 - (R_nu/R)^2) sqrt(|1 - (R_nu/R)^2|), -1)."""
+    x = 1.0 - (np.asarray(r_nu, dtype=np.float64) / R) ** 2
+    return np.maximum(np.sign(x) * np.sqrt(np.abs(x)), -1.0)
+
+
+def chi_beamed(mu, mu_bar):
+    """chi_2 of Eq. d19 for radiation emitted isotropically by the neutrinospheres and seen inside
+    the cones mu >= mu_i, mu' >= mu_i' (Eqs. d17-d18), relative to isotropic radiation."""
+    return (8.0 + (mu * mu_bar - 3.0) * (1.0 + mu) * (1.0 + mu_bar)) / 8.0
+
+
+def pair_chi(eta, r_nu, rc):
+    """chi = min(chi_1, chi_2) (Eq. d21) per (ray, species q, zone, k, k') for species q at eps_k
+    against its partner at eps_k': eta [n_ray, 4, n_r, n_e] flux factors, r_nu [n_ray, 4, n_e]
+    neutrinosphere radii, rc [n_ray, n_r] zone centres (reading P2)."""
+    mu = pair_mu(r_nu[:, :, None, :], rc[:, None, :, None])           # [ray, q, zone, k]
+    bar = PAIR_PARTNER
+    c1 = chi_isotropic(eta[..., :, None], eta[:, bar][..., None, :])
+    c2 = chi_beamed(mu[..., :, None], mu[:, bar][..., None, :])
+    return np.minimum(c1, c2)
+
+
+def pair_source(psi, w, phi_a, phi_p, chi=None):
+    """Zeroth-moment pair source per unit length, Eq. d14 with Phi_1 = 0 (reading P1), divided by c
+    like the NES source:
+    S_k = C [(1 - psi_k) sum_k' w_k' Phi^p[k,k'] (1 - psibar_k') - psi_k sum_k' w_k' chi Phi^a[k,k'] psibar_k'],
+    psibar the partner species' occupation; chi [n_ray, 4, n_r, n_e, n_e] the angular correction of
+    the annihilation kernel (Eqs. d16-d22), or None for 1."""
     bar = psi[:, PAIR_PARTNER]
     make = np.einsum('rikm,rim,rqim->rqik', phi_p, w, 1.0 - bar)
-    kill = np.einsum('rikm,rim,rqim->rqik', phi_a, w, bar)
+    if chi is None:
+        kill = np.einsum('rikm,rim,rqim->rqik', phi_a, w, bar)
+    else:
+        kill = np.einsum('rikm,rqikm,rim,rqim->rqik', phi_a, chi, w, bar)
     return C_NES * ((1.0 - psi) * make - psi * kill)
 
 
@@ -334,6 +377,10 @@ def setup_step(prob, psi_n, ye_n, T_n):
     f.e_edge = np.asarray(prob['e_edge'], dtype=np.float64)
     f.u, f.eta1 = prob.get('u'), prob.get('eta1')
     flux_coefficients(f, f.psi_n, f.ye_n)                     # at psi^n, Ye^n: reading R2
+    f.chi = None
+    if f.pair_a is not None and prob.get('pair_chi'):
+        eta = np.zeros_like(f.psi_n) if f.eta1 is None else np.clip(np.asarray(f.eta1, dtype=np.float64), 0.0, 1.0)
+        f.chi = pair_chi(eta, f.r_nu, f.rc)                   # reading P2
     return f
 
 
@@ -514,7 +561,7 @@ def sources(f, psi, ye):
     s_ae = absem_source(psi, j, f.kappa_abs)
     s_nes = nes_source(psi, f.w, f.phi_out, f.phi_in)
     if f.pair_a is not None:
-        s_nes = s_nes + pair_source(psi, f.w, f.pair_a, f.pair_p)
+        s_nes = s_nes + pair_source(psi, f.w, f.pair_a, f.pair_p, f.chi)
     return s_ae + s_nes, s_ae, j, dmu_q, live
 
 
@@ -585,10 +632,12 @@ def jacobian(f, psi, ye):
     if f.pair_a is not None:
         # d S_pair,k / d psi_k (own species, diagonal) and d S_pair,k / d psibar_k' (partner)
         bar = psi[:, PAIR_PARTNER]
+        pa = f.pair_a[:, None] if f.chi is None else f.pair_a[:, None] * f.chi   # [ray, q|1, zone, k, k']
         diag = diag + C_NES * (np.einsum('rikm,rim,rqim->rqik', f.pair_p, w, 1.0 - bar)
-                               + np.einsum('rikm,rim,rqim->rqik', f.pair_a, w, bar))
+                               + np.einsum('rqikm,rim,rqim->rqik', np.broadcast_to(pa, psi.shape + psi.shape[-1:]),
+                                           w, bar))
         dP = -C_NES * (np.einsum('rikm,rim,rqik->rqikm', f.pair_p, w, 1.0 - psi)
-                       + np.einsum('rikm,rim,rqik->rqikm', f.pair_a, w, psi))
+                       + np.einsum('rqikm,rim,rqik->rqikm', np.broadcast_to(pa, psi.shape + psi.shape[-1:]), w, psi))
     A = np.zeros((n_ray, n_r, M, M))
     for q in range(N_SPECIES):
         sl = slice(q * n_e, (q + 1) * n_e)

@@ -133,3 +133,106 @@ def test_gpu_step_refuses_the_pair_process():
     rc = M.lib().mgfld_assemble(ctypes.byref(dims), ctypes.byref(prob), ctypes.byref(st), ctypes.byref(sys_),
                                 ctypes.c_void_p(0x100000), 1 << 30, None)
     assert rc == M.MGFLD_EINVAL
+
+
+# ------------------------------------------------------------------ angular correction (Eqs. d16-d22)
+
+MU_GL, W_GL = np.polynomial.legendre.leggauss(24)
+PHI = np.linspace(0.0, 2.0 * np.pi, 64, endpoint=False)        # exact for trigonometric degree < 64
+
+
+def _pair_average(f_nu, f_bar, lo=-1.0, lo_bar=-1.0):
+    """(4 pi)^-2 int dOmega dOmega' f_nu(mu) f_bar(mu') (1 - n.nbar)^2 by quadrature: Gauss-Legendre
+    in mu on [lo, 1] and mu' on [lo_bar, 1], the rectangle rule in the relative azimuth (the
+    integrand is a trigonometric polynomial of degree 2 in it)."""
+    m = lo + (1.0 - lo) * 0.5 * (MU_GL + 1.0)
+    wm = 0.5 * (1.0 - lo) * W_GL
+    mb = lo_bar + (1.0 - lo_bar) * 0.5 * (MU_GL + 1.0)
+    wb = 0.5 * (1.0 - lo_bar) * W_GL
+    M, MB, P = np.meshgrid(m, mb, PHI, indexing='ij')
+    dot = M * MB + np.sqrt(1.0 - M * M) * np.sqrt(1.0 - MB * MB) * np.cos(P)
+    g = f_nu(M) * f_bar(MB) * (1.0 - dot) ** 2
+    # dOmega = dmu dphi and the azimuth of the first direction integrates to 2 pi
+    return np.einsum('i,j,ijk->', wm, wb, g) * (2.0 * np.pi) * (2.0 * np.pi / len(PHI)) / (4.0 * np.pi) ** 2
+
+
+@pytest.mark.parametrize('eta,eta_bar', [(0.1, 0.3), (0.25, 0.25), (0.0, 0.4), (0.33, 0.05)])
+def test_chi1_is_the_near_isotropic_angular_average(eta, eta_bar):
+    """Eq. d16 as printed is the average for the distributions psi0 (1 + eta mu), relative to
+    isotropic radiation of the same number.  Eq. d15 writes psi0 + 3 mu psi1, for which the same
+    average is 1 - 3 eta etabar / 2 (shown here too): the paper is at odds with itself, and the
+    oracle keeps the printed Eq. d16 (reading P2), which stays positive for any flux factors."""
+    den = _pair_average(lambda m: np.ones_like(m), lambda m: np.ones_like(m))
+    num = _pair_average(lambda m: 1.0 + m * eta, lambda m: 1.0 + m * eta_bar)
+    assert abs(num / den - O.chi_isotropic(eta, eta_bar)) < 1e-13
+    num3 = _pair_average(lambda m: 1.0 + 3.0 * m * eta, lambda m: 1.0 + 3.0 * m * eta_bar)
+    assert abs(num3 / den - (1.0 - 1.5 * eta * eta_bar)) < 1e-13
+
+
+@pytest.mark.parametrize('mu,mu_bar', [(0.3, 0.6), (0.8, 0.8), (-0.5, 0.2), (0.95, 0.1)])
+def test_chi2_is_the_beamed_angular_average(mu, mu_bar):
+    """Eq. d19 against the average over radiation confined to the cones mu >= mu_i with the
+    occupation 2/(1 - mu_i) psi0 there (Eqs. d17-d18); Eq. d20 at equal cones."""
+    num = _pair_average(lambda m: np.full_like(m, 2.0 / (1.0 - mu)), lambda m: np.full_like(m, 2.0 / (1.0 - mu_bar)),
+                        lo=mu, lo_bar=mu_bar)
+    den = _pair_average(lambda m: np.ones_like(m), lambda m: np.ones_like(m))
+    assert abs(num / den - O.chi_beamed(mu, mu_bar)) < 1e-13
+    if mu == mu_bar:
+        assert abs(O.chi_beamed(mu, mu) - (1.0 - mu) ** 2 * (mu * mu + 4.0 * mu + 5.0) / 8.0) < 1e-15
+
+
+def test_cone_extension_inside_the_neutrinosphere():
+    """Eq. d22: outside R_nu the cone edge of Eq. d17; inside it falls to -1 (chi_2 = 1, isotropic),
+    so chi = chi_1 there (Eq. d21)."""
+    R_nu = 5e6
+    assert abs(O.pair_mu(R_nu, 1e7) - np.sqrt(1.0 - 0.25)) < 1e-15
+    assert O.pair_mu(R_nu, 4.9e6) < -0.04 and O.pair_mu(R_nu, 1e6) == -1.0
+    assert O.chi_beamed(-1.0, -1.0) == 1.0
+    eta = np.full((1, 4, 2, 3), 0.3)
+    r_nu = np.full((1, 4, 3), R_nu)
+    chi = O.pair_chi(eta, r_nu, np.array([[1e6, 5e7]]))
+    assert np.allclose(chi[0, :, 0], O.chi_isotropic(0.3, 0.3), rtol=0, atol=1e-15)
+    assert np.all(chi[0, :, 1] < O.chi_isotropic(0.3, 0.3))
+
+
+def _with_chi(pair=30.0):
+    inp = SP.strong(n_ray=2, n_r=12, n_e=5, kabs=3e16, kscat=1e15, nes=30.0, lapse=True, pair=pair)
+    p = dict(inp['problem'], pair_chi=True)
+    rc = 0.5 * (p['r_edge'][:, 1:] + p['r_edge'][:, :-1])
+    p['eta1'] = np.broadcast_to(np.clip(rc / rc[:, -1:], 0.0, 1.0)[:, None, :, None], inp['psi0'].shape).copy()
+    return dict(inp, problem=p)
+
+
+def test_step_with_the_angular_correction():
+    inp = _with_chi()
+    out = O.step(inp['problem'], inp['psi0'], inp['ye0'], inp['T0'])
+    plain = O.step(dict(inp['problem'], pair_chi=False), inp['psi0'], inp['ye0'], inp['T0'])
+    L = out['ledger']
+    assert np.all(np.abs(L[:, 3]) <= 1e-13 * np.abs(L[:, 1]))
+    assert np.all(np.abs(L[:, 7]) <= 1e-12 * np.abs(L[:, 5]))
+    assert np.max(O.rel_change(out['psi'] - plain['psi'], plain['psi'])) > 1e-6
+    f = O.setup_step(inp['problem'], inp['psi0'], inp['ye0'], inp['T0'])
+    assert f.chi is not None and np.all(f.chi <= 1.0) and np.all(f.chi > 0.0)
+
+
+def test_jacobian_with_the_angular_correction():
+    inp = _with_chi()
+    f = O.setup_step(inp['problem'], inp['psi0'], inp['ye0'], inp['T0'])
+    rng = np.random.default_rng(2)
+    psi = np.clip(f.psi_n * (1 + 0.3 * rng.uniform(-1, 1, f.psi_n.shape)), 0, 1)
+    ye = f.ye_n.copy()
+    A, Bm, Bp = O.jacobian(f, psi, ye)
+    r = 0
+    J = O.dense_matrix(A[r], Bm[r], Bp[r])
+    u0 = O.pack(psi, ye)
+    M = u0.shape[-1]
+    cols = range(0, u0[r].size, 7)
+    for c in cols:
+        h = 1e-6 * abs(u0[r].flat[c]) if c % M == M - 1 else 1e-2
+        up = u0.copy(); up[r].flat[c] += h
+        um = u0.copy(); um[r].flat[c] -= h
+        gp = O.pack(*O.residual(f, *O.unpack(up, f.n_e)))[r]
+        gm = O.pack(*O.residual(f, *O.unpack(um, f.n_e)))[r]
+        col = ((gp - gm) / (2 * h)).reshape(-1)
+        scale = np.maximum(np.abs(J[:, c]).max(), np.abs(col).max())
+        assert np.max(np.abs(J[:, c] - col)) < 1e-6 * scale
