@@ -297,7 +297,14 @@ extern "C" mgfld_status mgfld_energy_advect(const mgfld_dims *dims, const mgfld_
   g.n_ray = dims->n_ray;
   g.n_r = dims->n_r;
   g.n = dims->n_e;
+  // systems per block: the most that fill whole warps (spb n a multiple of 32; every FP64 warp
+  // instruction costs the pipe the same however many of its lanes work), else as many as fit
   g.spb = kEadvThreads / g.n;
+  for (int sp = kEadvThreads / g.n; sp >= 1; --sp)
+    if ((sp * g.n) % 32 == 0) {
+      g.spb = sp;
+      break;
+    }
   g.limit = prob->limit != 0;
   g.r_n = prob->r_edge_n;
   g.r_np1 = prob->r_edge_np1;
