@@ -516,8 +516,9 @@ def reference_arm(args, n_gpus, rank):
 
 def profile_step(path, n_rays):
     """One implicit step of the first n_rays rays of the benchmark workload (FP64 Newton, the
-    mixed path, or the mixed path with the shock terms), or two energy-advection steps, for ncu
-    captures of single launches; exits non-zero on a failed step."""
+    mixed path, the mixed path with the shock terms or with the flux coefficients formed at every
+    outer iterate), two energy-advection steps, or one stress-and-lapse call, for ncu captures of
+    single launches; exits non-zero on a failed step."""
     import torch
     from paper_1809_05608_gb300 import build as B
     if not os.path.exists(B.LIB):
@@ -544,7 +545,7 @@ def profile_step(path, n_rays):
     else:
         inp = problems.make_problem(CONFIG_ID, rays=slice(0, n_rays))
     prec = M.MGFLD_FP64 if path == 'fp64' else M.MGFLD_MIXED
-    st = M.Stepper(inp, prec, tol=TOL, max_iter=60)
+    st = M.Stepper(inp, prec, tol=TOL, max_iter=60, coef_iterate=path == 'coef')
     psi, ye, T = st.state_to_device(inp['psi0'], inp['ye0'], inp['T0'])
     rc = st.step(psi, ye, T)
     torch.cuda.synchronize()
@@ -561,9 +562,10 @@ def main():
     ap.add_argument('--impl', default='mgfld', choices=['mgfld', 'reference'])
     ap.add_argument('--oracle-rays', type=int, default=12)
     ap.add_argument('--no-cpu-baseline', action='store_true')
-    ap.add_argument('--profile-step', choices=['mixed', 'fp64', 'shock', 'eadv', 'stress'],
+    ap.add_argument('--profile-step', choices=['mixed', 'fp64', 'shock', 'coef', 'eadv', 'stress'],
                     help='profiling target: one implicit step of this path (shock: the mixed path with '
-                         'the shock terms; eadv: two energy-advection steps; stress: two stress-and-lapse '
+                         'the shock terms; coef: the mixed path with the flux coefficients formed at '
+                         'every outer iterate; eadv: two energy-advection steps; stress: two stress-and-lapse '
                          'calls) on --rays rays, no timing')
     ap.add_argument('--rays', type=int, default=64)
     args = ap.parse_args()

@@ -204,6 +204,26 @@ __global__ void k_phi(Prob p, Ws w, const double *__restrict__ T, int zpb) {
   }
 }
 
+// The NES sums of one (zone, group) row for the four species, sum_k' phin_k' psi_k' and
+// sum_k' phout_k' psi_k' (psi of species q at ps0 + q qs), each row entry loaded once for all
+// species; every sum runs over k' in ascending order.  The kernels that call it are bound by
+// these 8N FP64 FMAs per thread, not by the row reads.
+__device__ inline void nes_sums(const double *__restrict__ fin, const double *__restrict__ fout,
+                                const double *__restrict__ ps0, size_t qs, int n, double gain[NS],
+                                double lp[NS]) {
+#pragma unroll
+  for (int q = 0; q < NS; ++q) gain[q] = lp[q] = 0.0;
+  for (int kp = 0; kp < n; ++kp) {
+    const double a = fin[kp], b = fout[kp];
+#pragma unroll
+    for (int q = 0; q < NS; ++q) {
+      const double v = ps0[q * qs + kp];
+      gain[q] += a * v;
+      lp[q] += b * v;
+    }
+  }
+}
+
 // Emissivity at Ye^n and the transport mean free path at psi^n, one thread per (ray, zone,
 // group) for the four species (which share the zone's NES rows and, for nu_mu/tau and their
 // antiparticles with mu = 0, the exponential):
@@ -229,6 +249,8 @@ __global__ void k_jlam(Prob p, Ws w, const double *__restrict__ psi, const doubl
   // direct form.
   const double emu = w.phin32 ? z[ZC_EMU] : -1.0;
   const double ex = emu > 0.0 ? exp(-eps * z[ZC_INV_T]) : 0.0;
+  double gain[NS], lp[NS];
+  nes_sums(fin, fout, psi + (((size_t)ray * NS) * p.n_r + i) * n, (size_t)p.n_r * n, n, gain, lp);
   double e_mu0 = 0.0;
   for (int q = 0; q < NS; ++q) {
     const size_t g = (((size_t)ray * NS + q) * p.n_r + i) * n + k;
@@ -246,19 +268,13 @@ __global__ void k_jlam(Prob p, Ws w, const double *__restrict__ psi, const doubl
     }
     const double j = kap * e1;
     w.jbuf[g] = j;
-    const double *ps = psi + (g - k);
-    double gain = 0.0, lp = 0.0;
-    for (int kp = 0; kp < n; ++kp) {
-      gain += fin[kp] * ps[kp];
-      lp += fout[kp] * ps[kp];
-    }
-    const double kt = kap + j + ksc + gain + (rs - lp);
+    const double kt = kap + j + ksc + gain[q] + (rs - lp[q]);
     const double y = rsqrt(kt);            // sqrt(lambda): the edge mean free path is a product
     w.kinv[g] = kt;
     w.slam[g] = y;
     w.lam[g] = y * y;
-    w.g0[g] = gain;                        // reused by the first outer iteration's residual
-    w.l0[g] = lp;
+    w.g0[g] = gain[q];                        // reused by the first outer iteration's residual
+    w.l0[g] = lp[q];
     w.psi_n[g] = psi[g];
   }
 }
@@ -384,20 +400,25 @@ __global__ void k_edges(Prob p, Ws w, const double *__restrict__ psi_src) {
       geom = m2 * (sp * sp) < df * df;
     }
     // one quotient for both branches: numerator and denominator selected first
-    double num = psi_e, den = sp;
+    double num = psi_e, den = sp, h = 1.0;
     if (geom) {
-      num = 0.5 * (1.0 + sqrt(m2)) * psi_e;
+      h = 0.5 * (1.0 + sqrt(m2));
+      num = h * psi_e;
       den = x;
     }
-    F = num / den;
-    if (w.jl) {
-      const double s = dpsi > 0.0 ? 1.0 : -1.0;
-      if (geom) {                       // Phi = (h / b) psi_e s
-        dl = dr = 0.25 * (1.0 + sqrt(m2)) / b * s;
-      } else {                          // Phi = psi_e d / (psi_e + b |d|)
-        const double phi = psi_e * dpsi / sp;
-        dl = ((0.5 * dpsi - psi_e) - phi * (0.5 - b * s)) / sp;
-        dr = ((0.5 * dpsi + psi_e) - phi * (0.5 + b * s)) / sp;
+    if (!w.jl) {
+      F = num / den;
+    } else {
+      // the derivatives need 1/den as well: one division for F and both of them
+      const double r = 1.0 / den;
+      F = num * r;
+      if (geom) {                       // Phi = (h / b) psi_e s with 1/b = |d| / x
+        dl = dr = 0.5 * h * dpsi * r;
+      } else {                          // Phi = psi_e d / (psi_e + b |d|) = F d
+        const double s = dpsi > 0.0 ? 1.0 : -1.0;
+        const double phi = F * dpsi;
+        dl = ((0.5 * dpsi - psi_e) - phi * (0.5 - b * s)) * r;
+        dr = ((0.5 * dpsi + psi_e) - phi * (0.5 + b * s)) * r;
       }
     }
   }
@@ -424,17 +445,13 @@ __global__ void k_lam_iter(Prob p, Ws w, const double *__restrict__ psi) {
   const double *fin = w.phin + (zi * n + k) * n;
   const double *fout = w.phout + (zi * n + k) * n;
   const double rs = w.rsum[zi * n + k];
+  double gain[NS], lp[NS];
+  nes_sums(fin, fout, psi + (((size_t)ray * NS) * p.n_r + i) * n, (size_t)p.n_r * n, n, gain, lp);
   for (int q = 0; q < NS; ++q) {
     const size_t g = (((size_t)ray * NS + q) * p.n_r + i) * n + k;
     const double sc = p.scale ? p.scale[q * n + k] : 1.0;
     const double kap = p.kabs[g] * sc, ksc = p.kscat[g] * sc;
-    const double *ps = psi + (g - k);
-    double gain = 0.0, lp = 0.0;
-    for (int kp = 0; kp < n; ++kp) {
-      gain += fin[kp] * ps[kp];
-      lp += fout[kp] * ps[kp];
-    }
-    const double kt = kap + w.jbuf[g] + ksc + gain + (rs - lp);
+    const double kt = kap + w.jbuf[g] + ksc + gain[q] + (rs - lp[q]);
     const double y = rsqrt(kt);
     w.kinv[g] = kt;
     w.slam[g] = y;
