@@ -7,7 +7,6 @@ its rounding is relative to the size of the terms, not of the difference: per ed
 1e-13 x scale, scale = (4 pi/(hc)^3)/3 sum_q N_q sum_k F (|X_{i+1}| + |X_i|) A / Delta M.  The
 lapse is a product of n_r exponentials (the GPU forms one exponential of a suffix sum): relative
 1e-12."""
-import ctypes
 
 import numpy as np
 import pytest
