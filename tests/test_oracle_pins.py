@@ -191,6 +191,41 @@ def test_neutrinosphere_is_at_two_thirds_optical_depth():
             assert abs(tau - 2.0 / 3.0) < 1e-12
 
 
+def test_outer_ghost_follows_constant_luminosity_from_the_neutrinosphere():
+    """Eq. a62af comes from two premises stated beside it: constant luminosity at the surface,
+    psi1_{I+1} R_{I+1}^2 = psi1_I R_I^2, and the geometric relation psi1 = (1 + mu) psi0 / 2 with
+    mu = sqrt(1 - (R_nu/R)^2) the cosine subtended by the neutrinosphere.  Together they give the
+    exact ratio psi0_{I+1}/psi0_I = R_I^2 (1 + mu_I) / (R_{I+1}^2 (1 + mu_{I+1})), whose expansion
+    R^2 (1 + mu)/2 = R^2 - R_nu^2/4 - R_nu^4/(16 R^2) - ... the printed factor truncates after
+    the R_nu^2 term: the oracle's ghost factor must match the exact ratio to fourth order in
+    R_nu/R_I (a wrong coefficient, sign or edge would show at second order), equal the free-space
+    R_I^2/R_{I+1}^2 at R_nu = 0, and hold R_nu at R_I beyond it."""
+    r_edge = np.array([[1.0e6, 2.0e6, 3.0e6, 4.0e6]])
+    rc = 0.5 * (r_edge[:, 1:] + r_edge[:, :-1])
+    r_i = rc[0, -1]
+    r_g = 2.0 * r_edge[0, -1] - r_i
+
+    def exact(rn):
+        mu = lambda r: np.sqrt(1.0 - (rn / r)**2)
+        return r_i**2 * (1.0 + mu(r_i)) / (r_g**2 * (1.0 + mu(r_g)))
+
+    errs = []
+    for x in (0.4, 0.2, 0.1, 0.05):
+        rn = x * r_i
+        got = O.ghost_factor(rc, r_edge, np.full((1, 4, 3), rn))
+        assert got.shape == (1, 4, 3) and np.all(got == got[0, 0, 0])
+        err = abs(got[0, 0, 0] / exact(rn) - 1.0)
+        assert err <= 0.1 * x**4
+        errs.append(err)
+    # fourth order: halving R_nu/R_I divides the error by ~16
+    assert all(8.0 < a / b < 32.0 for a, b in zip(errs[:-1], errs[1:]) if b > 1e-15)
+    free = O.ghost_factor(rc, r_edge, np.zeros((1, 4, 3)))
+    assert np.allclose(free, r_i**2 / r_g**2, rtol=1e-15, atol=0)
+    clamp = O.ghost_factor(rc, r_edge, np.full((1, 4, 3), 2.0 * r_i))
+    at_ri = O.ghost_factor(rc, r_edge, np.full((1, 4, 3), r_i))
+    assert np.array_equal(clamp, at_ri)
+
+
 # ---------------------------------------------------------------- Jacobian and linear algebra
 
 def test_jacobian_matches_central_differences():
