@@ -98,3 +98,61 @@ def test_status_strings(L):
     assert M.status_str(M.MGFLD_OK) == 'ok'
     assert 'converge' in M.status_str(M.MGFLD_ENOCONV)
     assert M.status_str(99) == 'unknown status'
+
+
+def _fake(n):
+    return ctypes.c_void_p(0x7e0000000000 + 0x100000 * n)
+
+
+def test_other_entry_points_check_their_arguments_before_any_launch(L):
+    """mgfld_assemble, mgfld_factor, mgfld_solve, mgfld_stress_lapse and mgfld_energy_advect refuse
+    missing buffers, bad sizes, precisions and workspaces with a status code, on the host, before
+    any CUDA call (the fake pointers are never dereferenced)."""
+    d = M.Dims(2, 8, 5, 4)
+    need = M.mgfld_workspace_bytes(d, M.MGFLD_FP64)
+    ws = 0x7f0000000000
+    st = M.State(_fake(1), _fake(2), _fake(3))
+    sysm = M.System(_fake(4), _fake(5), _fake(6), _fake(7))
+    R = ctypes.byref
+
+    def assemble(dims=d, prob=None, system=sysm, w=ws, nbytes=need):
+        return L.mgfld_assemble(R(dims), R(prob or _prob()), R(st), R(system), ctypes.c_void_p(w), nbytes, None)
+
+    assert assemble(nbytes=need - 1) == M.MGFLD_ENOMEM
+    assert assemble(w=ws + 16) == M.MGFLD_EINVAL
+    assert assemble(dims=M.Dims(2, 8, 33, 4)) == M.MGFLD_EINVAL
+    assert assemble(prob=_prob(null_rho=True)) == M.MGFLD_EINVAL
+    assert assemble(system=M.System(_fake(4), None, _fake(6), _fake(7))) == M.MGFLD_EINVAL
+    paired = _prob()
+    paired.pair_coef = _fake(9)
+    assert assemble(prob=paired) == M.MGFLD_EINVAL            # species-pair blocks are not built
+
+    for prec in (-1, 2):
+        assert L.mgfld_factor(R(d), R(sysm), prec, _fake(8), None) == M.MGFLD_EINVAL
+        assert L.mgfld_solve(R(d), R(sysm), prec, _fake(8), _fake(9), _fake(10), None) == M.MGFLD_EINVAL
+    assert L.mgfld_factor(R(d), R(sysm), M.MGFLD_FP64, None, None) == M.MGFLD_EINVAL
+    assert L.mgfld_factor(R(M.Dims(2, 8, 5, 3)), R(sysm), M.MGFLD_FP64, _fake(8), None) == M.MGFLD_EINVAL
+    assert L.mgfld_solve(R(d), R(sysm), M.MGFLD_MIXED, _fake(8), None, _fake(10), None) == M.MGFLD_EINVAL
+    assert L.mgfld_solve(R(d), R(sysm), M.MGFLD_MIXED, _fake(8), _fake(9), None, None) == M.MGFLD_EINVAL
+
+    def stress(io, w=ws, nbytes=need, state=st):
+        return L.mgfld_stress_lapse(R(d), R(_prob()), R(state), R(io), ctypes.c_void_p(w), nbytes, None)
+
+    io = M.StressIO(_fake(11), None, _fake(12), None, _fake(13))
+    assert stress(io, nbytes=need - 1) == M.MGFLD_ENOMEM
+    assert stress(io, w=ws + 8) == M.MGFLD_EINVAL
+    assert stress(M.StressIO(None, None, _fake(12), None, _fake(13))) == M.MGFLD_EINVAL   # lapse needs p
+    assert stress(io, state=M.State(_fake(1), None, _fake(3))) == M.MGFLD_EINVAL
+
+    def eadv(prob, dims=d, psi=_fake(14)):
+        return L.mgfld_energy_advect(R(dims), R(prob), psi, None, None)
+
+    full = [_fake(20 + i) for i in range(8)]
+    ok = M.EadvProblem(*full, 1, None)
+    assert eadv(ok, dims=M.Dims(2, 8, 2, 4)) == M.MGFLD_EINVAL        # the PPM stencil needs 3 groups
+    assert eadv(ok, dims=M.Dims(2, 8, 5, 2)) == M.MGFLD_EINVAL
+    assert eadv(ok, psi=None) == M.MGFLD_EINVAL
+    for field in ('r_edge_n', 'r_edge_np1', 'rho_n', 'rho_np1', 'e_edge'):
+        bad = M.EadvProblem(*full, 1, None)
+        setattr(bad, field, None)
+        assert eadv(bad) == M.MGFLD_EINVAL, field
