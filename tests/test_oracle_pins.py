@@ -342,6 +342,75 @@ def test_constant_opacity_diffusion_converges_to_green_function():
     assert 1.6 < errs[0] / errs[1] < 2.4 and 1.6 < errs[1] / errs[2] < 2.4
 
 
+
+def test_pure_diffusion_step_is_the_scalar_tridiagonal_solve():
+    """With scattering only (no absorption, emission or NES) each (species, group) of Eq. a58 is an
+    independent linear tridiagonal system once the flux coefficients are frozen at psi^n:
+    (1/(a c dt) + (a^2/V)(alpha_+ + alpha_-)) psi_i - (a^2/V)(alpha_+ psi_{i+1} + alpha_- psi_{i-1})
+    = psi^n_i/(a c dt), zero flux at the centre and, here, at a reflecting outer edge.  The oracle's
+    Newton on the coupled (species x group + Ye) blocks must reproduce LAPACK's dgtsv on it to
+    rounding, and leave Ye and T unchanged (no lepton or energy source)."""
+    lapack = pytest.importorskip('scipy.linalg.lapack')
+    n_r, n_e = 48, 3
+    r_edge = np.geomspace(1e6, 3e7, n_r + 1)[None, :]
+    rc = 0.5 * (r_edge[0, 1:] + r_edge[0, :-1])
+    lapse = np.sqrt(1.0 - 2.04e5 / rc)[None, :]
+    rng = np.random.default_rng(11)
+    ksc = 10.0 ** rng.uniform(-6, -4, size=(1, 4, n_r, n_e))
+    prob = dict(r_edge=r_edge, lapse=lapse, e_edge=np.array([4.0, 9.0, 20.0, 45.0]), rho=np.full((1, n_r), 1e11),
+                kappa_abs=np.zeros((1, 4, n_r, n_e)), kappa_scat=ksc, nes_coef=None, dt=2e-5,
+                outer_bc=O.BC_REFLECT)
+    psi_n = 0.5 * np.exp(-((rc / 8e6) ** 2))[None, None, :, None] * (1.0 + 0.3 * rng.random((1, 4, n_r, n_e)))
+    ye, T = np.full((1, n_r), 0.3), np.full((1, n_r), 4.0)
+    out = O.step(prob, psi_n, ye, T)
+    f = out['frozen']
+    vol = 4.0 * np.pi * (r_edge[0, 1:] ** 3 - r_edge[0, :-1] ** 3) / 3.0
+    pre = lapse[0] ** 2 / vol
+    inv = 1.0 / (lapse[0] * O.C_LIGHT * prob['dt'])
+    worst = 0.0
+    for q in range(4):
+        for k in range(n_e):
+            ap = f.alpha[0, q, :, k].copy()              # outer edge of each zone
+            ap[-1] = 0.0                                 # reflecting outer edge
+            am = np.concatenate([[0.0], ap[:-1]])        # inner edge; zero flux at the centre
+            d = inv + pre * (ap + am)
+            dl = -pre[1:] * am[1:]
+            du = -pre[:-1] * ap[:-1]
+            x = lapack.dgtsv(dl, d, du, (inv * psi_n[0, q, :, k])[:, None])[3][:, 0]
+            worst = max(worst, np.max(np.abs(out['psi'][0, q, :, k] - x) / np.abs(x)))
+    assert worst < 1e-13
+    assert np.max(np.abs(out['ye'] / ye - 1)) < 1e-15
+    assert np.max(np.abs(out['T'] / T - 1)) < 1e-14
+
+
+def test_equal_electron_neutrino_and_antineutrino_sources_leave_ye_fixed():
+    """Eq. a62a changes Ye by the difference of the nu_e and nubar_e absorption/emission sources.
+    At mu_nue = 0 the two species have the same equilibrium occupation and emissivity; started
+    from the same psi they stay equal, so Ye must not move, while the heavy-lepton neutrinos
+    (started elsewhere, with their own sources) do not enter Ye at all."""
+    from scipy.optimize import brentq
+    n_r, n_e = 16, 5
+    r_edge = np.geomspace(1e6, 1e7, n_r + 1)[None, :]
+    rho, T = np.full((1, n_r), 3e12), np.full((1, n_r), 6.0)
+    eos = O.EosParams()
+    y0 = brentq(lambda y: float(O.mu_nue(rho[:, :1], T[:, :1], np.array([[y]]), eos)[0, 0]), 1e-3, 0.6, xtol=1e-15)
+    ye = np.full((1, n_r), y0)
+    assert abs(float(O.mu_nue(rho[:, :1], T[:, :1], ye[:, :1], eos)[0, 0])) < 1e-9
+    e_edge = np.geomspace(2.0, 80.0, n_e + 1)
+    rng = np.random.default_rng(5)
+    kap = np.broadcast_to(10.0 ** rng.uniform(-7, -5, size=(1, 1, n_r, n_e)), (1, 4, n_r, n_e)).copy()
+    psi = np.empty((1, 4, n_r, n_e))
+    psi[:, 0] = psi[:, 1] = 0.2 * rng.random((1, n_r, n_e))
+    psi[:, 2] = psi[:, 3] = 0.6 * rng.random((1, n_r, n_e))
+    prob = dict(r_edge=r_edge, lapse=None, e_edge=e_edge, rho=rho, kappa_abs=kap, kappa_scat=kap, nes_coef=None,
+                dt=1e-6, outer_bc=O.BC_GHOST, eos=eos)
+    out = O.step(prob, psi, ye, T)
+    assert np.max(np.abs(out['ye'] / ye - 1)) < 1e-14
+    assert np.max(np.abs(out['psi'][:, 0] - out['psi'][:, 1])) <= 1e-14 * np.max(np.abs(out['psi'][:, 0]))
+    assert np.max(np.abs(out['psi'][:, 0] - psi[:, 0])) > 1e-6       # the sources did act
+    S, _, _, _, _ = O.sources(out['frozen'], out['psi'], out['ye'])
+    assert np.max(np.abs(S[:, 2] - S[:, 0])) > 1e3 * np.max(np.abs(S[:, 1] - S[:, 0]))
+
 def _redshift_problem(lapse_on):
     """Opaque isothermal source (r < 20 km) radiating into a transparent static medium
     with the lapse a(R) = sqrt(1 - R0/R), R0 = 2.04 km (Eq. t1), in steady state."""
