@@ -435,7 +435,8 @@ def _redshift_problem(lapse_on):
 @pytest.mark.parametrize("lapse_on", [False, True])
 def test_stationary_free_streaming_luminosity(lapse_on):
     """Outside the source the stationary solution carries A psi1 / a^2 = const exactly
-    (Eq. t2, t3); the luminosity falls as a^-2 (Eq. t4) and psi1 as R^-2 when a = 1."""
+    (Eq. t2, t3); the luminosity falls as a^-2 (Eq. t4), the local mean energy as a^-1 (Eq. t7)
+    and psi1 as R^-2 when a = 1."""
     prob, psi, ye, T, rc = _redshift_problem(lapse_on)
     out = O.step(prob, psi, ye, T, max_iter=20)
     f = out['frozen']
@@ -452,6 +453,12 @@ def test_stationary_free_streaming_luminosity(lapse_on):
     Lum = Re[outside, None] ** 2 * np.einsum('k,eqk->eq', E**3 * dE, psi1) / a_e[outside, None] ** 4
     La2 = Lum * a_e[outside, None] ** 2
     assert np.max(np.abs(La2 / La2[:1] - 1)) < 1e-9
+    # Eq. t7: the mean energy of the flux in the local frame (eps = E/a) falls as 1/a
+    mean = np.einsum('k,eqk->eq', E**3 * dE, psi1) / np.einsum('k,eqk->eq', E**2 * dE, psi1) / a_e[outside, None]
+    ma = mean * a_e[outside, None]
+    assert np.max(np.abs(ma / ma[:1] - 1)) < 1e-9
+    if lapse_on:
+        assert mean[0, 0] / mean[-1, 0] > 1.02            # blue-shifted deep in the well
     if not lapse_on:
         assert np.max(np.abs(psi1 * Re[outside, None, None] ** 2 / (psi1[:1] * Re[outside][0] ** 2) - 1)) < 1e-9
 
