@@ -128,3 +128,17 @@ def heating_objective(scale, psi0, ye0, T0, runner: AdjointRunner, n_steps: int)
     if _FN is None:
         _FN = _heating_function()
     return _FN.apply(scale, psi0, ye0, T0, runner, n_steps)
+
+
+def reduce_over_ranks(J, scale_grad, group=None):
+    """Ray-sharded runs (contiguous ray blocks per rank): J is a sum over rays, so the whole-job
+    objective and its gradient with respect to the shared [4, n_e] opacity scales are sums over
+    the ranks' values, formed by one all-reduce of 1 + 4 n_e doubles (NCCL for device tensors,
+    gloo for host ones).  The gradients with respect to psi^0, Ye^0 and T^0 belong to the rank's
+    own rays and are not reduced.  Returns the summed (J, scale_grad)."""
+    import torch
+    import torch.distributed as dist
+    g = torch.as_tensor(scale_grad, dtype=torch.float64)
+    buf = torch.cat([torch.as_tensor(J, dtype=torch.float64, device=g.device).reshape(1), g.reshape(-1)])
+    dist.all_reduce(buf, op=dist.ReduceOp.SUM, group=group)
+    return buf[0], buf[1:].reshape(g.shape)
