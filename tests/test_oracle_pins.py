@@ -68,6 +68,46 @@ def test_f2_equalises_pressures_at_nuclear_density():
     assert abs(p1 / p2 - 1) < 1e-13
 
 
+
+def test_cold_electron_terms_are_the_degenerate_relativistic_fermi_gas():
+    """Eq. e4's F1 with gamma1 = 4/3 must be the energy coefficient of a zero-temperature,
+    ultra-relativistic electron gas with two spin states, u = F1 n^{4/3}, and mu_e (Eq. e13) its
+    Fermi energy: both from the Fermi sea n = 8 pi p_F^3 / (3 h^3), u = int 8 pi p^2 (pc) dp / h^3,
+    integrated numerically here (MeV, cm)."""
+    from scipy.integrate import quad
+    p = O.EosParams()
+    for n in (1e30, 3.7e35, 2e38):
+        pf = O.HC * (3.0 * n / (8.0 * np.pi)) ** (1.0 / 3.0)         # p_F c in MeV
+        n_sea = quad(lambda x: 8.0 * np.pi * x * x / O.HC**3, 0.0, pf)[0]
+        u_sea = quad(lambda x: 8.0 * np.pi * x**3 / O.HC**3, 0.0, pf)[0]
+        assert abs(n_sea / n - 1) < 1e-12
+        assert abs(p.f1 * n ** (4.0 / 3.0) / u_sea - 1) < 1e-12
+        rho = n * p.m_b / 0.5
+        mu_e, _, _ = O.eos_chemical_potentials(np.array(rho), np.array(1.0), np.array(0.5), p)
+        assert abs(mu_e / pf - 1) < 1e-12
+
+
+def test_nucleon_terms_are_the_dilute_limit_of_the_ideal_fermi_gas():
+    """The thermal parts of mu_n and mu_p (Eqs. e11, e12) are the Maxwell-Boltzmann limit of a
+    non-relativistic ideal Fermi gas of statistical weight 2: for a chemical potential mu (rest
+    mass excluded) the exact density n = 2 int 4 pi p^2 dp / h^3 / (1 + exp((p^2/2m - mu)/T)) fed
+    to the oracle must give back mu up to the leading degeneracy correction, -T z / 2^{3/2} with
+    z = e^{mu/T}, which halves when z halves."""
+    from scipy.integrate import quad
+    p = O.EosParams()
+    T = 2.0
+    errs = []
+    for mu in (-16.0, -16.0 - T * np.log(2.0), -16.0 - 2 * T * np.log(2.0)):
+        occ = lambda x: 2.0 * 4.0 * np.pi * x * x / O.HC**3 / (1.0 + np.exp((x * x / (2 * p.mb_c2) - mu) / T))
+        n = quad(occ, 0.0, np.sqrt(2 * p.mb_c2 * 80 * T), epsabs=0, epsrel=1e-13, limit=200)[0]
+        rho = n * p.m_b / 0.5                                          # Ye = 0.5: n_p = n_n = n
+        _, _, mu_p = O.eos_chemical_potentials(np.array(rho), np.array(T), np.array(0.5), p)
+        z = np.exp(mu / T)
+        err = float(mu_p) - mu
+        assert abs(err + T * z / 2**1.5) < 0.02 * T * z, (mu, err, T * z / 2**1.5)
+        errs.append(err)
+    assert 1.9 < errs[0] / errs[1] < 2.1 and 1.9 < errs[1] / errs[2] < 2.1
+
 def test_dmu_dye_matches_complex_step():
     p = O.EosParams()
     rho = np.array([3e14, 1e10, 1e6]); T = np.array([30.0, 2.0, 0.1]); ye = np.array([0.1, 0.3, 0.5])
