@@ -240,8 +240,10 @@ mgfld_status mgfld_solve(const mgfld_dims *dims, const mgfld_system *sys, int pr
  *     opts->precision) exceeds MGFLD_NOALLOC_SCRATCH_BYTES (e.g. 4 rays of 512 zones x
  *     20 groups in FP64); split the rays into several calls.
  *   - Returns MGFLD_EINVAL if opts->profile is set (timing would create CUDA events).
- *   - The first call on each device looks up the array's device address with that
- *     device current; make that first call before any stream capture begins.
+ *   - Every call looks up the array's device address on the current device (nothing is
+ *     cached, so a context reset between calls is harmless); the first call on a device
+ *     also loads the library's device code there, so make it before any stream capture
+ *     begins.
  *   - All calls on a device share the one array: calls that may overlap on the GPU
  *     (other streams, other host threads) race and must be serialised by the caller.
  *     Each call rewrites every part of the scratch it reads, so the contents left by

@@ -8,35 +8,23 @@
 // them this entry point takes no workspace and calls no allocating routine: the scratch
 // lives in `g_scratch` below, which every GPU that loads this library keeps for the
 // lifetime of the process.
-#include <mutex>
-
 #include "mgfld_internal.cuh"
 
 namespace {
 
 constexpr size_t kScratchBytes = MGFLD_NOALLOC_SCRATCH_BYTES;
-constexpr int kMaxDevices = 64;
 
 // The scratch itself.  In host code `g_scratch` names a host-side shadow, not device
-// memory, so its device address is looked up once per device below.
+// memory, so its device address is looked up below.
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
-std::mutex g_lock;
-void *g_addr[kMaxDevices] = {};
-
-// Device address of g_scratch on the current device; the first call on a device does
-// the lookup (cudaGetSymbolAddress) with that device current.
+// Device address of g_scratch on the current device, looked up on every call with that
+// device current (cheap, and it allocates nothing).  Not cached: a context torn down and
+// created again (cudaDeviceReset) reloads the module at another address.
 mgfld_status scratch_address(void **out) {
-  int dev = -1;
-  if (cudaGetDevice(&dev) != cudaSuccess) return MGFLD_ECUDA;
-  if (dev < 0 || dev >= kMaxDevices) return MGFLD_ECUDA;
-  std::lock_guard<std::mutex> guard(g_lock);
-  if (!g_addr[dev]) {
-    void *p = nullptr;
-    if (cudaGetSymbolAddress(&p, g_scratch) != cudaSuccess || p == nullptr) return MGFLD_ECUDA;
-    g_addr[dev] = p;
-  }
-  *out = g_addr[dev];
+  void *p = nullptr;
+  if (cudaGetSymbolAddress(&p, g_scratch) != cudaSuccess || p == nullptr) return MGFLD_ECUDA;
+  *out = p;
   return MGFLD_OK;
 }
 

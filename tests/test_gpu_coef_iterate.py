@@ -3,13 +3,14 @@ oracle's reading R12.
 
 The root of this reading is fixed only to the level at which the limiter's branch choice and the
 neutrinosphere crossing, which move with the iterate, stop changing: both programs stall within
-~1e-11 of it on the stiff problems, so the FP64 gate is max(1e-11, the problem's FP64 floor); the
-mixed path keeps its 1e-10."""
+~1e-11 of it on the stiff problems, so their FP64 gate is max(1e-11, the problem's FP64 floor); the
+single ray and the benchmark-family rays keep 1e-12 in FP64, the mixed path its 1e-10."""
 import numpy as np
 import pytest
 
 from oracle import mgfld_oracle as O
 from paper_1809_05608_gb300 import problems
+from tests import parity_measures as PM
 from tests import small_problems as SP
 
 torch = pytest.importorskip('torch')
@@ -44,26 +45,25 @@ def normwise(a, b):
 
 
 CASES = [
-    ('single ray 64 x 12', lambda: problems.make_problem(1), 0, 1e-12),
+    ('single ray 64 x 12', lambda: problems.make_problem(1), 0, 1e-12, False),
     ('strong with lapse', lambda: SP.strong(n_ray=2, n_r=16, n_e=5, kabs=3e16, kscat=1e15, nes=30.0, lapse=True),
-     0, 1e-11),
-    ('3 full rays, fp64', lambda: problems.make_problem(2, rays=[0, 101, 255]), 0, 1e-12),
-    ('3 full rays, mixed', lambda: problems.make_problem(2, rays=[0, 101, 255]), 1, 1e-10),
+     0, 1e-11, True),
+    ('3 full rays, fp64', lambda: problems.make_problem(3, rays=[0, 511, 1023]), 0, 1e-12, False),
+    ('3 full rays, mixed', lambda: problems.make_problem(3, rays=[0, 511, 1023]), 1, 1e-10, False),
 ]
 
 
-@pytest.mark.parametrize('name,make,precision,tol', CASES, ids=[c[0] for c in CASES])
-def test_coefficients_at_the_iterate_match_oracle(name, make, precision, tol):
+@pytest.mark.parametrize('name,make,precision,tol,stiff', CASES, ids=[c[0] for c in CASES])
+def test_coefficients_at_the_iterate_match_oracle(name, make, precision, tol, stiff):
     inp = make()
     psi, ye, T, codes, rep = run_gpu(inp, precision=precision, tol=tol, coef_iterate=True)
     frozen, _, _, _, rep0 = run_gpu(inp, precision=precision, tol=tol)
     out = O.step(inp['problem'], inp['psi0'], inp['ye0'], inp['T0'], coef_iterate=True)
     assert codes == [M.MGFLD_OK]
-    fwd = normwise(psi, out['psi'])
-    gate = 1e-10 if precision == 1 else max(1e-11, SP.fp64_tolerance(inp))
-    print(f'{name}: forward {fwd:.2e} (gate {gate:.1e}); n+1 against frozen {normwise(frozen, psi):.1e}; '
+    gate = 1e-10 if precision == 1 else (max(1e-11, SP.fp64_tolerance(inp)) if stiff else 1e-12)
+    PM.report(name, psi, out['psi'], gate)
+    print(f'  n+1 against frozen {normwise(frozen, psi):.1e}; '
           f'iterations {rep["iters"].max()} (frozen {rep0["iters"].max()}), oracle {out["iters"]}')
-    assert fwd < gate
     assert np.max(np.abs(T / out['T'] - 1.0)) < gate
     assert normwise(frozen, psi) > 1e-7                 # the reading changes the result
     assert rep['iters'].max() <= rep0['iters'].max() + 3
@@ -72,15 +72,14 @@ def test_coefficients_at_the_iterate_match_oracle(name, make, precision, tol):
 
 
 def test_full_launch_mixed_sampled():
-    full = problems.make_problem(2)
+    full = problems.make_problem(3)
     psi, ye, T, codes, rep = run_gpu(full, precision=1, tol=1e-10, coef_iterate=True)
     assert codes == [M.MGFLD_OK] and np.all(rep['ray_status'] == 0)
-    rays = [9, 140, 230]
+    rays = [9, 540, 1000]
     sub = problems.subset_rays(full, rays)
     out = O.step(sub['problem'], sub['psi0'], sub['ye0'], sub['T0'], coef_iterate=True)
-    fwd = normwise(psi[rays], out['psi'])
-    print(f'256-ray launch, n+1 coefficients (mixed): sampled forward {fwd:.2e}, iterations {rep["iters"].max()}')
-    assert fwd < 1e-10
+    PM.report('1024-ray launch, n+1 coefficients (mixed), sampled rays', psi[rays], out['psi'], 1e-10)
+    print(f'  iterations {rep["iters"].max()}')
 
 
 

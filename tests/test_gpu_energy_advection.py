@@ -148,9 +148,9 @@ def test_rollout_at_the_imposed_shock():
 
 
 def test_full_size_conservation_and_sampled_parity():
-    """The 256-ray workload in the launch configuration the benchmark times: neutrino number per
+    """The 1024-ray workload in the launch configuration the benchmark times: neutrino number per
     comoving mass conserved by every system, and three rays against the oracle."""
-    inp = problems.make_energy_advection(config=2)
+    inp = problems.make_energy_advection(config=3)
     psi, xi = run_gpu(inp)
     n0, _ = E.number_energy(inp['psi'], inp['e_edge'], np.broadcast_to(inp['lapse_n'][:, None], psi.shape[:-1]))
     n1, _ = E.number_energy(psi, inp['e_edge'], np.broadcast_to(inp['lapse_np1'][:, None], psi.shape[:-1]))
@@ -160,7 +160,7 @@ def test_full_size_conservation_and_sampled_parity():
     # (floored far below every system that holds neutrinos)
     ref0 = n0 / rho0
     assert np.max(np.abs(n1 / rho1 - ref0) / (ref0 + 1e-30 * ref0.max())) < 1e-12
-    rays = [0, 128, 255]
+    rays = [0, 511, 1023]
     sub = dict(inp)
     for key in ('r_edge_n', 'r_edge_np1', 'rho_n', 'rho_np1', 'lapse_n', 'lapse_np1', 'psi', 'eta1'):
         sub[key] = np.ascontiguousarray(inp[key][rays])

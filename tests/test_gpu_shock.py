@@ -69,15 +69,15 @@ def test_single_ray_shock_fp64_matches_oracle():
 @pytest.mark.gpu
 @pytest.mark.parametrize('precision', [0, 1])
 def test_full_size_shock_rays(precision):
-    """Three 512 x 20 rays of the 256-ray profile family with the shock, two steps; FP64 at the
-    problem's FP64 floor, mixed at 1e-10."""
+    """Three 512 x 20 rays of the 1024-ray benchmark workload with the shock, two steps; FP64 at
+    1e-12, mixed at 1e-10."""
     _gpu()
-    inp = problems.make_shock_problem(2, rays=[0, 101, 255])
+    inp = problems.make_shock_problem(3, rays=[0, 511, 1023])
     psi, ye, T, codes, rep = run_gpu(inp, precision=precision, steps=2, tol=1e-12 if precision == 0 else 1e-10)
     psi_o, ye_o, T_o, _ = O.run_steps(inp['problem'], inp['psi0'], inp['ye0'], inp['T0'], 2)
     assert codes == [M.MGFLD_OK] * 2
     fwd = normwise(psi, psi_o)
-    gate = SP.fp64_tolerance(inp) if precision == 0 else 1e-10
+    gate = 1e-12 if precision == 0 else 1e-10
     print(f'3 shock rays, precision {precision}, 2 steps: forward {fwd:.2e} (gate {gate:.1e})')
     assert fwd < gate
     assert np.max(np.abs(T / T_o - 1)) < gate
@@ -86,17 +86,17 @@ def test_full_size_shock_rays(precision):
 
 @pytest.mark.gpu
 def test_full_launch_with_shock_sampled():
-    """The 256-ray launch with the shock in the mixed path (the benchmark's shock line):
+    """The 1024-ray launch with the shock in the mixed path (the benchmark's shock line):
     sampled rays vs the oracle, every ray converged, lepton number balanced."""
     _gpu()
-    full = problems.make_shock_problem(2)
+    full = problems.make_shock_problem(3)
     psi, ye, T, codes, rep = run_gpu(full, precision=1, tol=1e-10)
     assert codes == [M.MGFLD_OK]
-    rays = [7, 128, 251]
+    rays = [7, 512, 1020]
     sub = problems.subset_rays(full, rays)
     psi_o, _, T_o, _ = O.run_steps(sub['problem'], sub['psi0'], sub['ye0'], sub['T0'], 1)
     fwd = normwise(psi[rays], psi_o)
-    print(f'256-ray shock launch (mixed), sampled rays: forward {fwd:.2e}')
+    print(f'1024-ray shock launch (mixed), sampled rays: forward {fwd:.2e}')
     assert fwd < 1e-10
     assert np.all(rep['ray_status'] == 0)
     L = rep['ledger']

@@ -91,11 +91,11 @@ def test_full_size_rays_after_a_step_with_lapse():
 
 
 def test_full_launch_sampled():
-    full = problems.make_problem(2)
+    full = problems.make_problem(3)
     p, m = problems.stress_inputs(full)
     pr = full['problem']
     got = run_gpu(pr, full['psi0'], full['ye0'], full['T0'], p, m)
-    rays = [0, 77, 255]
+    rays = [0, 300, 1023]
     sub = problems.subset_rays(full, rays)
     ref = S.stress_and_lapse(sub['problem'], sub['psi0'], sub['ye0'], sub['T0'], p[rays], m[rays])
     scale = stress_scale(sub['problem'], sub['psi0'], sub['ye0'], sub['T0'])
