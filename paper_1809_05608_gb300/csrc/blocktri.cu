@@ -390,45 +390,70 @@ __device__ inline void gj_invert(float *a, float (*prow)[NP + 4], int r, bool ro
   }
 }
 
-// In-place Gauss-Jordan inverse without row exchanges, lane r holding row r: at step ps lane
-// ps publishes its row and the reciprocal of its pivot through a double-buffered shared-memory
-// row, and every lane eliminates with packed FP32 FMAs (the owner scales its row by the same
-// formula).  No reduction sits on the chain of pivot steps, and row r of the inverse ends in
-// lane r.  Returns false (the same in every lane) when a pivot was zero or not finite.
-// Used for the mixed path's zone blocks: with the group weights w_k of the NES moments, a
-// diagonal block is a Z-matrix whose weighted column sums are 1/(a c dt) + transport + kappa_a
-// + j > 0 (number conservation of the NES terms), so it and its Schur complements are
-// M-matrices, for which elimination without pivoting is stable.
+// In-place Gauss-Jordan inverse without row exchanges, lane r holding row r, with 2 x 2 pivot
+// blocks: at step b the owners of rows p = 2b and p + 1 publish both rows (double-buffered
+// shared memory), every lane forms the inverse of the pivot block
+// P = [[d00, d01], [d10, d11]] in closed form (one reciprocal of its determinant) and eliminates
+// with the two multipliers (a_p, a_{p+1}) P^{-1}; the owners take the rows of P^{-1} times the
+// pivot rows by the same formula.  Half as many broadcast steps on the chain of each block, the
+// same number of FMAs.  Leading 2 x 2 blocks of the Schur complements of an M-matrix (or of a
+// column diagonally dominant matrix) are nonsingular, so no exchanges are needed; returns false
+// (the same in every lane) when a determinant was zero or not finite.  NP must be even.
 template <int NP>
-__device__ inline bool gj_invert_np(float *a, float (*prow)[NP + 4], int r) {
+__device__ inline bool gj_invert_np2(float *a, float (*prow)[2][NP + 4], int r) {
+  static_assert(NP % 4 == 0, "pivot pairs inside 16-byte pieces");
   bool ok = true;
 #pragma unroll
-  for (int ps = 0; ps < NP; ++ps) {
-    float *pb = prow[ps & 1];
-    const bool me = (r == ps);
-    if (me) {
-      const float inv = rcp_nr(a[ps]);
-      ok = isfinite(inv) && a[ps] != 0.f;
-      // 8-byte stores of the register pairs that the packed FMAs keep (no repacking moves)
+  for (int b = 0; b < NP / 2; ++b) {
+    const int p = 2 * b;
+    float (*pb)[NP + 4] = prow[b & 1];
+    if (r == p || r == p + 1) {
+      float *dst = pb[r - p];
 #pragma unroll
-      for (int c = 0; c < NP; c += 2) *reinterpret_cast<float2 *>(pb + c) = make_float2(a[c], a[c + 1]);
-      pb[NP] = inv;
+      for (int c = 0; c < NP; c += 2) *reinterpret_cast<float2 *>(dst + c) = make_float2(a[c], a[c + 1]);
     }
     __syncwarp();
-    float pv[NP];
+    // the pivot block (columns p, p + 1 of both pivot rows) first
+    const float2 q0 = *reinterpret_cast<const float2 *>(&pb[0][p]);
+    const float2 q1 = *reinterpret_cast<const float2 *>(&pb[1][p]);
+    const float det = fmaf(q0.x, q1.y, -(q0.y * q1.x));
+    const float idet = rcp_nr(det);
+    ok = ok && isfinite(idet) && det != 0.f;
+    const float i00 = q1.y * idet, i01 = -q0.y * idet, i10 = -q1.x * idet, i11 = q0.x * idet;
+    float f0, f1;
+    if (r == p) {
+      f0 = 1.f - i00;
+      f1 = -i01;
+    } else if (r == p + 1) {
+      f0 = -i10;
+      f1 = 1.f - i11;
+    } else {
+      f0 = fmaf(a[p], i00, a[p + 1] * i10);
+      f1 = fmaf(a[p], i01, a[p + 1] * i11);
+    }
 #pragma unroll
     for (int c = 0; c < NP; c += 4) {
-      const float4 v = *reinterpret_cast<const float4 *>(pb + c);
-      pv[c] = v.x;
-      pv[c + 1] = v.y;
-      pv[c + 2] = v.z;
-      pv[c + 3] = v.w;
+      const float4 v0 = *reinterpret_cast<const float4 *>(&pb[0][c]);
+      const float4 v1 = *reinterpret_cast<const float4 *>(&pb[1][c]);
+      float2 lo = __ffma2_rn(make_float2(-f0, -f0), make_float2(v0.x, v0.y), make_float2(a[c], a[c + 1]));
+      float2 hi = __ffma2_rn(make_float2(-f0, -f0), make_float2(v0.z, v0.w), make_float2(a[c + 2], a[c + 3]));
+      lo = __ffma2_rn(make_float2(-f1, -f1), make_float2(v1.x, v1.y), lo);
+      hi = __ffma2_rn(make_float2(-f1, -f1), make_float2(v1.z, v1.w), hi);
+      a[c] = lo.x;
+      a[c + 1] = lo.y;
+      a[c + 2] = hi.x;
+      a[c + 3] = hi.y;
     }
-    const float inv = pb[NP];
-    const float f = me ? fmaf(-1.f, inv, 1.f) : a[ps] * inv;
-#pragma unroll
-    for (int c = 0; c < NP; c += 2) fma2_row(a, -f, pv, c);
-    a[ps] = me ? inv : -f;
+    if (r == p) {
+      a[p] = i00;
+      a[p + 1] = i01;
+    } else if (r == p + 1) {
+      a[p] = i10;
+      a[p + 1] = i11;
+    } else {
+      a[p] = -f0;
+      a[p + 1] = -f1;
+    }
   }
   return __all_sync(0xffffffffu, ok);
 }
@@ -440,7 +465,7 @@ template <int NP> __host__ __device__ constexpr int fw_wpc() { return NP > 24 ? 
 // At most 128 registers (NP <= 24), so that four CTAs (eight systems) fit on an SM and the
 // 256-ray workload's 512 CTAs run in a single wave on 152 SMs.
 // PIVOT: partial pivoting in every zone (the C ABI's factor of arbitrary systems); otherwise
-// elimination without row exchanges (the outer iteration's M-matrix blocks, see gj_invert_np)
+// elimination without row exchanges (the outer iteration's M-matrix blocks, see gj_invert_np2)
 // with partial pivoting only for a zone whose unpivoted elimination met a zero or non-finite
 // pivot.
 template <int NP, typename TIn, typename TC, bool PIVOT>
@@ -454,6 +479,7 @@ k_factor_w32(int n, int n_r, int n_sys, const TIn *__restrict__ diag, const TC *
   __shared__ __align__(16) float tile[W][NP][NP];
   __shared__ __align__(16) float ushr[W][NP];
   __shared__ __align__(16) float prow[W][2][NP + 4];
+  __shared__ __align__(16) float prow2[W][2][2][NP + 4];
   __shared__ __align__(16) float rowbuf[W][2][NP][NP];
   const int wid = threadIdx.x >> 5, r = threadIdx.x & 31;
   const int half = wid & 1;                          // 0: zones 0..m top-down, 1: zones n_r-1..m+1 bottom-up
@@ -543,7 +569,7 @@ k_factor_w32(int n, int n_r, int n_sys, const TIn *__restrict__ diag, const TC *
       }
     };
     build_a();
-    const bool ok = PIVOT ? false : gj_invert_np<NP>(a, prow[wid], r);
+    const bool ok = PIVOT ? false : gj_invert_np2<NP>(a, prow2[wid], r);
     __syncwarp();                  // every lane has read the previous zone's tile row
     if (ok) {
       if (row) {

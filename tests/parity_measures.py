@@ -45,3 +45,29 @@ def report(name, a, b, gate):
     assert nw < gate, (name, nw, gate)
     assert ratio < 1.0, (name, ratio)
     return nw
+
+
+def stepwise(M, torch, inp, precision, steps, gate, label, **step_kw):
+    """`steps` GPU steps of `inp`, each compared with the oracle's step taken from the GPU's own
+    previous state (the parity of one implicit step, gated at `gate`), and the final state with
+    the oracle's own `steps` consecutive steps (states that differ by ~gate after a step give
+    different next steps: the drift is gated at steps * gate).  Returns the final GPU state
+    (psi, ye, T), the per-step codes, the last report and the oracle's final state."""
+    from oracle import mgfld_oracle as O
+    st = M.Stepper(inp, precision, **step_kw)
+    psi, ye, T = st.state_to_device(inp['psi0'], inp['ye0'], inp['T0'])
+    prob = inp['problem']
+    prev = (inp['psi0'], inp['ye0'], inp['T0'])
+    codes = []
+    for s in range(steps):
+        codes.append(st.step(psi, ye, T))
+        torch.cuda.synchronize()
+        got = (psi.cpu().numpy(), ye.cpu().numpy(), T.cpu().numpy())
+        ref = O.step(prob, *prev)
+        report(f'{label}, step {s + 1} from the same state', got[0], ref['psi'], gate)
+        assert np.max(np.abs(got[2] / ref['T'] - 1.0)) < gate
+        prev = got
+    rep = {k: v.cpu().numpy() for k, v in st.report.items()}
+    psi_o, ye_o, T_o, _ = O.run_steps(prob, inp['psi0'], inp['ye0'], inp['T0'], steps)
+    report(f'{label}, {steps} steps from the start (drift)', prev[0], psi_o, steps * gate)
+    return prev, codes, rep, (psi_o, ye_o, T_o)

@@ -170,6 +170,13 @@ def test_multistep_gradients_match_oracle_and_checkpointing_is_exact():
 
 
 def test_autograd_function_and_central_differences():
+    """Gradients through the autograd function against central differences of the GPU forward
+    map, 1e-6 relative per entry.  Checked: every opacity scale with s |dJ/ds| >= 1e-3 |J| and five
+    psi^0 entries with psi |dJ/dpsi| >= 1e-2 |J|, at h = 1e-3 of the entry.  At that h the
+    truncation error is ~1e-10 (measured with the oracle) and the forward map's convergence noise
+    (~1e-13 |J|) contributes 1e-13 |J| / (h |g|) <= 1e-7 of |g|; entries carrying less of J are
+    below what central differences of a forward map at that accuracy resolve to 1e-6, and are
+    checked against the oracle adjoint instead (test_multistep_gradients_match_oracle...)."""
     inp = CASES['odd_groups']()
     n_e = inp['psi0'].shape[3]
     n_steps = 3
@@ -180,6 +187,7 @@ def test_autograd_function_and_central_differences():
     J = ADJ.heating_objective(scale, psi0, ye0, T0, r, n_steps)
     gs, gp = torch.autograd.grad(2.0 * J, [scale, psi0])
     gs, gp = gs.cpu().numpy() / 2.0, gp.cpu().numpy() / 2.0
+    J = float(J)
 
     def J_of(sc, ps):
         with torch.no_grad():
@@ -187,22 +195,29 @@ def test_autograd_function_and_central_differences():
         return float(v)
 
     s_np = _scale(n_e)
-    gmax = np.max(np.abs(gs))
-    for q, k in [(0, 0), (0, n_e - 1), (1, 3), (2, 2), (3, 5)]:
-        h = 1e-4 * s_np[q, k]
+    big = np.argwhere(s_np * np.abs(gs) >= 1e-3 * abs(J))
+    assert len(big) >= 4
+    worst = 0.0
+    for q, k in big:
+        h = 1e-3 * s_np[q, k]
         sp, sm = s_np.copy(), s_np.copy()
         sp[q, k] += h
         sm[q, k] -= h
         fd = (J_of(sp, inp['psi0']) - J_of(sm, inp['psi0'])) / (2 * h)
-        assert abs(fd - gs[q, k]) <= 1e-6 * gmax + 1e-6 * abs(fd), (q, k, fd, gs[q, k])
-    big = np.argwhere(inp['psi0'] > 1e-3)
+        worst = max(worst, abs(fd - gs[q, k]) / abs(gs[q, k]))
+        assert abs(fd - gs[q, k]) <= 1e-6 * abs(gs[q, k]), (q, k, fd, gs[q, k])
+    wp = np.abs(gp * inp['psi0'])
+    cand = np.argwhere(wp >= 1e-2 * abs(J))
     rng = np.random.default_rng(3)
-    gpmax = np.max(np.abs(gp))
-    for idx in big[rng.choice(len(big), size=5, replace=False)]:
+    worst_p = 0.0
+    for idx in cand[rng.choice(len(cand), size=min(5, len(cand)), replace=False)]:
         idx = tuple(idx)
-        h = 1e-5 * inp['psi0'][idx]
+        h = 1e-3 * inp['psi0'][idx]
         pp, pm = inp['psi0'].copy(), inp['psi0'].copy()
         pp[idx] += h
         pm[idx] -= h
         fd = (J_of(s_np, pp) - J_of(s_np, pm)) / (2 * h)
-        assert abs(fd - gp[idx]) <= 1e-5 * gpmax + 1e-5 * abs(fd), (idx, fd, gp[idx])
+        worst_p = max(worst_p, abs(fd - gp[idx]) / abs(gp[idx]))
+        assert abs(fd - gp[idx]) <= 1e-6 * abs(gp[idx]), (idx, fd, gp[idx])
+    print(f'central differences: {len(big)} scale entries, worst {worst:.1e}; 5 psi0 entries, worst {worst_p:.1e} '
+          f'(per entry, relative)')
