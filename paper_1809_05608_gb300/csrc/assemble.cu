@@ -74,40 +74,63 @@ __global__ void k_assemble(Prob p, Ws w, const double *__restrict__ psi, TD *__r
       w.l0[g] = lp;
     }
   }
-  const double loss = w.rsum[zi * n + k] - lp;          // sum_k' phout (1 - psi_k')
-  const double sc = p.scale ? p.scale[q * n + k] : 1.0;
-  const double kap = p.kabs[g] * sc;
   const double j = w.jbuf[g];
-  const double S = j * (1.0 - pk) - kap * pk + ((1.0 - pk) * gain - pk * loss);
-  if (src_out) {               // converged sources for Eq. a62b and the ledgers
-    src_out[g] = S;
-    return;
-  }
+  double G, dg, c_low, c_up;
+  if (!first && !src_out && !w.jl) {
+    // Later iterations with the coefficients frozen for the step: the constants the first pass
+    // stored, G = psi (D0 + j + gain - lp) - c_r psi_{i+1} - c_l psi_{i-1} - (b0 + j + gain), which
+    // is Eq. a58 with the flux of Eq. a59 and S regrouped (the terms in psi collected).
+    dg = ((w.cdiag[g] + j) + gain) - lp;
+    G = fma(pk, dg, -((w.cb[g] + j) + gain));
+    c_up = w.cup[g];
+    c_low = w.clow[g];
+    if (i < last) G = fma(-c_up, ps[k + n], G);
+    if (i > 0) G = fma(-c_low, ps[k - (ptrdiff_t)n], G);
+  } else {
+    const double loss = w.rsum[zi * n + k] - lp;          // sum_k' phout (1 - psi_k')
+    const double sc = p.scale ? p.scale[q * n + k] : 1.0;
+    const double kap = p.kabs[g] * sc;
+    const double S = j * (1.0 - pk) - kap * pk + ((1.0 - pk) * gain - pk * loss);
+    if (src_out) {               // converged sources for Eq. a62b and the ledgers
+      src_out[g] = S;
+      return;
+    }
 
-  const double al_out = w.alpha[g];
-  const double al_in = i > 0 ? w.alpha[g - n] : 0.0;
-  const double gh = (i == last) ? w.ghost[((size_t)ray * NS + q) * n + k] : 0.0;
-  const double p_right = i < last ? ps[k + n] : gh * pk;
-  const double p_left = i > 0 ? ps[k - (ptrdiff_t)n] : pk;
-  const double flux_out = -al_out * (p_right - pk);
-  const double flux_in = -al_in * (pk - p_left);
-  // shock transport: the step-constant frame terms of Eqs. a93 and a99 (formed at psi^n)
-  const double sh = p.u ? w.shock[g] : 0.0;
-  const double G = (pk - w.psi_n[g]) * inv_acdt + pre * (flux_out - flux_in + sh) - S;
+    const double al_out = w.alpha[g];
+    const double al_in = i > 0 ? w.alpha[g - n] : 0.0;
+    const double gh = (i == last) ? w.ghost[((size_t)ray * NS + q) * n + k] : 0.0;
+    const double p_right = i < last ? ps[k + n] : gh * pk;
+    const double p_left = i > 0 ? ps[k - (ptrdiff_t)n] : pk;
+    const double flux_out = -al_out * (p_right - pk);
+    const double flux_in = -al_in * (pk - p_left);
+    // shock transport: the step-constant frame terms of Eqs. a93 and a99 (formed at psi^n)
+    const double sh = p.u ? w.shock[g] : 0.0;
+    G = (pk - w.psi_n[g]) * inv_acdt + pre * (flux_out - flux_in + sh) - S;
+    // flux parts of the row: d(flux at i+1/2)/d psi_i = jl, d/d psi_{i+1} = jr; alpha and -alpha with
+    // the frozen coefficients, with the limiter's own derivative when they follow the iterate
+    double jdiag = al_out * (1.0 - gh) + al_in, jlow = al_in, jup = al_out;
+    if (w.jl) {
+      const double jl_out = w.jl[g], jr_out = w.jr[g];
+      const double jl_in = i > 0 ? w.jl[g - n] : 0.0, jr_in = i > 0 ? w.jr[g - n] : 0.0;
+      jdiag = jl_out + gh * jr_out - jr_in;
+      jlow = jl_in;
+      jup = -jr_out;
+    }
+    dg = inv_acdt + pre * jdiag + j + kap + (gain + loss);
+    c_low = pre * jlow;
+    c_up = i < last ? pre * jup : 0.0;
+    if (first && !w.jl) {
+      // the step constants of the later iterations (frozen coefficients): D0 with the ghost of
+      // the outer edge folded in, the couplings, and the psi-independent part b0
+      w.cdiag[g] = inv_acdt + pre * jdiag + kap + w.rsum[zi * n + k];
+      w.cup[g] = c_up;
+      w.clow[g] = c_low;
+      w.cb[g] = w.psi_n[g] * inv_acdt - pre * sh;
+    }
+  }
   rhs[g] = -G;
 
   if (jac_flag && !jac_flag[ray]) return;
-  // flux parts of the row: d(flux at i+1/2)/d psi_i = jl, d/d psi_{i+1} = jr; alpha and -alpha with
-  // the frozen coefficients, with the limiter's own derivative when they follow the iterate
-  double jdiag = al_out * (1.0 - gh) + al_in, jlow = al_in, jup = al_out;
-  if (w.jl) {
-    const double jl_out = w.jl[g], jr_out = w.jr[g];
-    const double jl_in = i > 0 ? w.jl[g - n] : 0.0, jr_in = i > 0 ? w.jr[g - n] : 0.0;
-    jdiag = jl_out + gh * jr_out - jr_in;
-    jlow = jl_in;
-    jup = -jr_out;
-  }
-  const double dg = inv_acdt + pre * jdiag + j + kap + (gain + loss);
   TD *row = diag + g * n;
   // dS_k/dpsi_k' = (1 - psi_k) phin + psi_k phout = phin - psi_k phd, entered with a minus;
   // dg joins the diagonal entry in FP64.  Rows are written 16 bytes at a time where n allows
@@ -151,8 +174,8 @@ __global__ void k_assemble(Prob p, Ws w, const double *__restrict__ psi, TD *__r
       for (int kp = 0; kp < n; ++kp) row[kp] = TD(kp == k ? dk : fma(pk, fd[kp], -fin[kp]));
     }
   }
-  lower[g] = -pre * jlow;
-  upper[g] = i < last ? -pre * jup : 0.0;
+  lower[g] = -c_low;
+  upper[g] = -c_up;
   if (w.lower32) {
     w.lower32[g] = (float)lower[g];
     w.upper32[g] = (float)upper[g];

@@ -48,7 +48,7 @@ struct Prob {
 struct Layout {
   int mixed;
   size_t groups, phout, phin, phd, rsum, phin32, phd32, lam, slam, g0, l0, alpha, ghost, rnu, jbuf, psi_n, ye_n, e_n,
-      zone, src, shock;
+      zone, src, shock, cdiag, cup, clow, cb;
   size_t diag, lower, upper, rhs, x, dinv, zled, sscale, kinv, lower32, upper32, g32, rhs32;
   size_t viol, vprev, active, iters, status, refac, nfact, nanflag, list_act, list_ref, counters;
   size_t total;
@@ -90,6 +90,7 @@ __device__ inline double minerbo_eta2(double eta1) {
 // Pointers resolved from a layout.
 struct Ws {
   double *E, *W;            // group centre energy at infinity E_k and E_k^2 dE_k (Eq. a01b)
+  double *WE;               // E_k^3 dE_k
   // Weighted NES kernels of each zone, [ray][zone][k][k'] (row k contiguous), with the moment
   // constant C = 2 pi / (c (hc)^3) and the group weight w_k' = eps_k'^2 d eps_k' folded in:
   //   phout[k][k'] = C w_k' Phi_out(eps_k, eps_k'),  phin[k][k'] = C w_k' Phi_in(eps_k, eps_k').
@@ -103,6 +104,12 @@ struct Ws {
   double *zone;             // per zone [n_ray][n_r][ZC_N]: see ZC_* below
   double *src;              // per (ray, q, i, k): total source S at the converged state
   double *shock;            // per (ray, q, i, k): the step-constant shock term of Eq. a99's bracket
+  // Per (ray, q, i, k), written by the first residual pass when the flux coefficients are frozen
+  // for the step: the psi coefficient of Eq. a58 without the iterate-dependent j and NES terms,
+  // D0 = 1/(a c dt) + (a^2/V)(alpha_out (1 - ghost) + alpha_in) + kappa_a + sum_k' phout; the
+  // couplings c_r = (a^2/V) alpha_out (0 in the last zone: the ghost is in D0) and c_l = (a^2/V)
+  // alpha_in; and b0 = psi^n/(a c dt) - (a^2/V) shock.
+  double *cdiag, *cup, *clow, *cb;
   double *lim;              // per (ray, q, i, k), or null: the flux limiter at the outer edge (kept
                             // by the setup for the neutrino stress)
   double *jl, *jr;          // per (ray, q, i, k), or null: d(edge flux A psi1/a^2)/d psi_i and

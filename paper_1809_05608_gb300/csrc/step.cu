@@ -27,7 +27,7 @@ Layout make_layout(int n_ray, int n_r, int n, int precision) {
   const size_t R = (size_t)n_ray, Z = R * n_r, F = Z * NS * n, B = F * n;
   size_t off = 0;
   auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes); return o; };
-  L.groups = take(sizeof(double) * 2 * MAX_NE);
+  L.groups = take(sizeof(double) * 3 * MAX_NE);
   L.phout = take(sizeof(double) * Z * n * n);
   L.phin = take(sizeof(double) * Z * n * n);
   L.phd = take(precision == MGFLD_MIXED ? 0 : sizeof(double) * Z * n * n);
@@ -45,6 +45,10 @@ Layout make_layout(int n_ray, int n_r, int n, int precision) {
   L.zone = take(sizeof(double) * Z * ZC_N);
   L.src = take(sizeof(double) * F);
   L.shock = take(sizeof(double) * F);
+  L.cdiag = take(sizeof(double) * F);
+  L.cup = take(sizeof(double) * F);
+  L.clow = take(sizeof(double) * F);
+  L.cb = take(sizeof(double) * F);
   L.diag = take((precision == MGFLD_MIXED ? sizeof(float) : sizeof(double)) * B);
   L.lower = take(sizeof(double) * F);
   L.upper = take(sizeof(double) * F);
@@ -91,6 +95,7 @@ Ws resolve(void *base, const Layout &L) {
   Ws w;
   w.E = (double *)(b + L.groups);
   w.W = w.E + MAX_NE;
+  w.WE = w.W + MAX_NE;
   w.phout = (double *)(b + L.phout);
   w.phin = (double *)(b + L.phin);
   w.phd = L.mixed ? nullptr : (double *)(b + L.phd);
@@ -111,6 +116,10 @@ Ws resolve(void *base, const Layout &L) {
   w.zone = (double *)(b + L.zone);
   w.src = (double *)(b + L.src);
   w.shock = (double *)(b + L.shock);
+  w.cdiag = (double *)(b + L.cdiag);
+  w.cup = (double *)(b + L.cup);
+  w.clow = (double *)(b + L.clow);
+  w.cb = (double *)(b + L.cb);
   w.lim = nullptr;
   w.jl = w.jr = nullptr;       // set by mgfld_step when the coefficients follow the iterate
   w.diag = (double *)(b + L.diag);
@@ -237,7 +246,10 @@ __global__ void k_update_psi(Prob p, Ws w, Tol tl, double *__restrict__ psi, con
 // One Newton step of the zone-local Ye equation (Eq. a62a) at the updated psi, with T held at
 // T^n (Sec. "Lagrangian Transport Step"), then the nu_e / nubar_e emissivities at the new Ye.
 // A change dmu of the chemical potential rescales j = kappa_a e^{(mu - eps)/T} by e^{dmu/T},
-// one exponential per species (direct evaluation where the exponent cap is involved).
+// one exponential per species (direct evaluation where the exponent cap is involved).  The cap
+// is tested once per species at the lowest group energy, where mu - eps is largest: in the
+// usual case no group reaches it and the per-group sums share their products,
+//   sum w j (1 - psi) - sum w kappa psi  and  sum w j (1 - psi)  (the Ye derivative).
 __global__ void k_update_ye(Prob p, Ws w, Tol tl, const double *__restrict__ psi, double *__restrict__ ye,
                             const double *__restrict__ T, const int *__restrict__ list, int n_list) {
   const int n = p.n;
@@ -256,6 +268,7 @@ __global__ void k_update_ye(Prob p, Ws w, Tol tl, const double *__restrict__ psi
     const double Ti = T[zi], rho = p.rho[zi];
     const double cy = kFourPiHC3 * p.eos.mb / rho;
     const double capT = kExpCap * Ti;
+    const double eps0 = w.E[0] * inv_a;
     double Y = ye[zi];
     double mu, dmu;
     mu_nue_zone(p.eos, z[ZC_MUA], z[ZC_MUB], Ti, Y, mu, dmu);
@@ -264,15 +277,28 @@ __global__ void k_update_ye(Prob p, Ws w, Tol tl, const double *__restrict__ psi
       const double sg = lepton_sign(q);
       const double muq = species_mu(q, mu), dmuq_T = sg * dmu / Ti;
       const size_t g0 = (((size_t)ray * NS + q) * p.n_r + i) * n;
-      double a0 = 0.0, a1 = 0.0;
-      for (int k = 0; k < n; ++k) {
-        const double wk = w.W[k];
-        const double sc = p.scale ? p.scale[q * n + k] : 1.0;
-        const double kap = p.kabs[g0 + k] * sc;
-        const double j = w.jbuf[g0 + k];
-        const double pk = psi[g0 + k];
-        a0 += wk * (j * (1.0 - pk) - kap * pk);
-        if (muq - w.E[k] * inv_a < capT) a1 += wk * (1.0 - pk) * j;
+      double a0, a1 = 0.0, c = 0.0;
+      if (muq - eps0 < capT) {                    // no group at the cap
+        for (int k = 0; k < n; ++k) {
+          const double wk = w.W[k];
+          const double kap = p.scale ? p.kabs[g0 + k] * p.scale[q * n + k] : p.kabs[g0 + k];
+          const double pk = psi[g0 + k];
+          const double wj = wk * w.jbuf[g0 + k];
+          a1 += fma(-wj, pk, wj);                 // w j (1 - psi)
+          c = fma(wk * kap, pk, c);               // w kappa psi
+        }
+        a0 = a1 - c;
+      } else {
+        a0 = 0.0;
+        for (int k = 0; k < n; ++k) {
+          const double wk = w.W[k];
+          const double kap = p.scale ? p.kabs[g0 + k] * p.scale[q * n + k] : p.kabs[g0 + k];
+          const double pk = psi[g0 + k];
+          const double wj = wk * w.jbuf[g0 + k];
+          const double tj = fma(-wj, pk, wj);
+          a0 += tj - wk * kap * pk;
+          if (muq - w.E[k] * inv_a < capT) a1 += tj;
+        }
       }
       sG += sg * a0 * inv_a3;
       sdG += sg * a1 * inv_a3 * dmuq_T;
@@ -289,14 +315,18 @@ __global__ void k_update_ye(Prob p, Ws w, Tol tl, const double *__restrict__ psi
       const double m0 = species_mu(q, mu), m1 = species_mu(q, mu1);
       const double ratio = exp((m1 - m0) / Ti);
       const size_t g0 = (((size_t)ray * NS + q) * p.n_r + i) * n;
-      for (int k = 0; k < n; ++k) {
-        const double eps = w.E[k] * inv_a;
-        if (m0 - eps < capT && m1 - eps < capT) {
-          w.jbuf[g0 + k] *= ratio;
-        } else {
-          const double sc = p.scale ? p.scale[q * n + k] : 1.0;
-          bool live;
-          w.jbuf[g0 + k] = emissivity(p.kabs[g0 + k] * sc, m1, eps, Ti, live);
+      if (m0 - eps0 < capT && m1 - eps0 < capT) {
+        for (int k = 0; k < n; ++k) w.jbuf[g0 + k] *= ratio;
+      } else {
+        for (int k = 0; k < n; ++k) {
+          const double eps = w.E[k] * inv_a;
+          if (m0 - eps < capT && m1 - eps < capT) {
+            w.jbuf[g0 + k] *= ratio;
+          } else {
+            const double sc = p.scale ? p.scale[q * n + k] : 1.0;
+            bool live;
+            w.jbuf[g0 + k] = emissivity(p.kabs[g0 + k] * sc, m1, eps, Ti, live);
+          }
         }
       }
     }
@@ -341,6 +371,8 @@ __global__ void k_check(int n_ray, Ws w, Tol tl) {
 // Eq. a62b with the converged sources (w.src), T from the EoS, and per-zone ledger terms:
 // [0] lepton number before, [1] after, [2] lepton number lost at R_{I+1/2} (last zone only),
 // [3] energy at infinity before, [4] after, [5] energy lost, [6] gain-region heating.
+// The group sums run over the grid at infinity (W_k = E_k^2 dE_k, W_k E_k) and take the zone's
+// lapse factors once: eps^2 d eps = W / a^3 and eps^3 d eps = W E / a^4 on the comoving grid.
 __global__ void k_finish(Prob p, Ws w, const double *__restrict__ psi, const double *__restrict__ ye,
                          double *__restrict__ T) {
   const int n = p.n;
@@ -350,7 +382,7 @@ __global__ void k_finish(Prob p, Ws w, const double *__restrict__ psi, const dou
   const int last = p.n_r - 1;
   const double *z = w.zone + zi * ZC_N;
   const double inv_a = z[ZC_INV_A], a = z[ZC_A];
-  const double inv_a3 = inv_a * inv_a * inv_a;
+  const double inv_a3 = inv_a * inv_a * inv_a, inv_a4 = inv_a3 * inv_a;
   const double vol = z[ZC_VOL];
   const double rho = p.rho[zi], Y = ye[zi], Yn = w.ye_n[zi];
   const double acdt = z[ZC_ACDT];
@@ -358,25 +390,43 @@ __global__ void k_finish(Prob p, Ws w, const double *__restrict__ psi, const dou
   double lep_loss = 0.0, en_loss = 0.0;
   for (int q = 0; q < NS; ++q) {
     const size_t g0 = (((size_t)ray * NS + q) * p.n_r + i) * n;
+    double sS = 0.0, eA = 0.0, eB = 0.0, nA = 0.0, nB = 0.0;
     for (int k = 0; k < n; ++k) {
-      const double wk = w.W[k] * inv_a3;
-      const double eps = w.E[k] * inv_a;
-      const double S = w.src[g0 + k];
-      const double pk = psi[g0 + k];
-      sum_e += stat_weight(q) * wk * eps * S;
-      if (q < 2) heat += wk * eps * S;
-      nu_lep_a += lepton_sign(q) * wk * pk;
-      nu_lep_b += lepton_sign(q) * wk * w.psi_n[g0 + k];
-      nu_en_a += stat_weight(q) * wk * eps * pk;
-      nu_en_b += stat_weight(q) * wk * eps * w.psi_n[g0 + k];
-      if (i == last) {
+      const double we = w.WE[k];
+      const double pk = psi[g0 + k], pn = w.psi_n[g0 + k];
+      sS = fma(we, w.src[g0 + k], sS);
+      eA = fma(we, pk, eA);
+      eB = fma(we, pn, eB);
+      if (q < 2) {
+        nA = fma(w.W[k], pk, nA);
+        nB = fma(w.W[k], pn, nB);
+      }
+    }
+    const double sw = stat_weight(q), sl = lepton_sign(q);
+    sum_e += sw * sS;
+    if (q < 2) {
+      heat += sS;
+      nu_lep_a += sl * nA;
+      nu_lep_b += sl * nB;
+    }
+    nu_en_a += sw * eA;
+    nu_en_b += sw * eB;
+    if (i == last) {
+      for (int k = 0; k < n; ++k) {
+        const double pk = psi[g0 + k];
         const double gh = w.ghost[((size_t)ray * NS + q) * n + k];
         const double fb = -w.alpha[g0 + k] * (gh * pk - pk);       // A psi1 / a^2 at R_{I+1/2}
         lep_loss += lepton_sign(q) * w.W[k] * fb;
-        en_loss += stat_weight(q) * w.W[k] * w.E[k] * fb;
+        en_loss += stat_weight(q) * w.WE[k] * fb;
       }
     }
   }
+  sum_e *= inv_a4;
+  heat *= inv_a4;
+  nu_lep_a *= inv_a3;
+  nu_lep_b *= inv_a3;
+  nu_en_a *= inv_a4;
+  nu_en_b *= inv_a4;
   const double e_new = w.e_n[zi] - acdt * kFourPiHC3 * (p.eos.mb / rho) * sum_e;
   T[zi] = (e_new - eos_e_cold(p.eos, rho, Y)) / p.eos.ec;
   double *zl = w.zled + zi * 8;
