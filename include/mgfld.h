@@ -85,14 +85,23 @@ typedef struct {
    * The shock terms are not differentiated: mgfld_adjoint returns MGFLD_EINVAL when u is set. */
   const double *u;
   const double *eta1;
-  /* Synthetic pair process (Eq. d14, zeroth moment, Legendre order 0): pair_coef [n_ray][n_r] the
-   * annihilation kernel (cm^3/s), the creation kernel exp(-(eps + eps')/T^n) times it (Eq. d12),
-   * nu_e paired with nubar_e and nu_mu,tau with nubar_mu,tau.  Must be NULL: mgfld_step,
-   * mgfld_assemble and mgfld_adjoint return MGFLD_EINVAL when it is set.  The process couples
-   * each species to its partner group by group, which the per-species blocks of this library do
-   * not hold; with the partner's derivative left to the outer iteration the pair mode does not
-   * converge (it needs coupled 2 n_e x 2 n_e species-pair blocks). */
+  /* Synthetic pair process (Eq. d14, zeroth moment, Legendre order 0), optional:
+   * pair_coef [n_ray][n_r] the annihilation kernel Phi^a (cm^3/s), or NULL for no pair process;
+   *       the creation kernel is e^{-(eps + eps')/T^n} Phi^a (Eq. d12, the pair energy eps + eps'
+   *       given to the e-e+ pair), nu_e paired with nubar_e and nu_mu,tau with nubar_mu,tau.  The
+   *       process enters the sources (and so Eq. a62b) but not the transport mean free path, and
+   *       leaves the lepton number (Eq. a62a) unchanged.  It couples each species to its partner
+   *       group by group: mgfld_step then solves per (ray, pair) with coupled 2 n_e x 2 n_e zone
+   *       blocks (n_e <= 24; FP64 or FP32 factors as opts->precision), and needs the workspace
+   *       of mgfld_workspace_bytes_pair.  Not combined with opts->coef_iterate (EINVAL);
+   *       mgfld_assemble and mgfld_adjoint return MGFLD_EINVAL when it is set.
+   * pair_chi nonzero: the angular correction chi = min(chi_1, chi_2) of the annihilation kernel
+   *       (Eqs. d16-d22) per (zone, eps, eps'): chi_1 = 1 - eta eta' / 6 with the flux factors of
+   *       `eta1` (zero where eta1 is NULL), chi_2 from the cones of radiation emitted by each
+   *       species' neutrinosphere at psi^n (Eqs. d17-d19), extended inside it by Eq. d22.  Read
+   *       only when pair_coef is set. */
   const double *pair_coef;
+  int pair_chi;
 } mgfld_problem;
 
 /* State at t^n on entry, t^{n+1} on exit (in place). */
@@ -149,6 +158,11 @@ typedef struct {
 
 /* Bytes of workspace mgfld_step needs for these dimensions and precision. */
 size_t mgfld_workspace_bytes(const mgfld_dims *dims, int precision);
+
+/* Bytes of workspace mgfld_step needs when the problem carries the pair process (pair_coef set):
+ * the coupled 2 n_e x 2 n_e blocks and the pair kernels of every zone.  0 for invalid dims or
+ * n_e > 24. */
+size_t mgfld_workspace_bytes_pair(const mgfld_dims *dims, int precision);
 
 /*
  * mgfld_step -- one implicit transport step for all rays (Eqs. a58, a59, a62a
@@ -237,8 +251,8 @@ mgfld_status mgfld_solve(const mgfld_dims *dims, const mgfld_system *sys, int pr
  * allocated or freed by this call.  Inputs and outputs are the caller's, as for
  * mgfld_step.
  *   - Returns MGFLD_ENOMEM, before touching the GPU, when mgfld_workspace_bytes(dims,
- *     opts->precision) exceeds MGFLD_NOALLOC_SCRATCH_BYTES (e.g. 4 rays of 512 zones x
- *     20 groups in FP64); split the rays into several calls.
+ *     opts->precision) exceeds MGFLD_NOALLOC_SCRATCH_BYTES (at 512 zones x 20 groups: more
+ *     than 2 rays in FP64, more than 3 in MIXED); split the rays into several calls.
  *   - Returns MGFLD_EINVAL if opts->profile is set (timing would create CUDA events).
  *   - Every call looks up the array's device address on the current device (nothing is
  *     cached, so a context reset between calls is harmless); the first call on a device

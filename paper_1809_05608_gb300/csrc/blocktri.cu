@@ -299,6 +299,243 @@ k_solve(int n, int n_r, int n_sys, const double *__restrict__ dinv, const double
 }
 
 // ---------------------------------------------------------------------------------------
+// Thread-per-row elimination and substitution for systems of any block width up to 64 rows
+// (the coupled nu / antinu blocks of the pair process: 2 n_e rows), in FP64 or FP32, with
+// `spr` systems per ray (the launch's j-th system is system j % spr of ray ray_list[j / spr]).
+// Same algorithm and thread mapping as k_factor / k_solve above: partial pivoting through integer
+// keys (6 row bits for blocks wider than 32), the next zone's rows fetched one zone ahead, the
+// pivot row read from shared memory where it is used; shared memory sized at launch.
+template <int NP, typename T>
+struct RowCta {
+  static constexpr int gcd(int a, int b) { return b == 0 ? a : gcd(b, a % b); }
+  static constexpr int SPC0 = 32 / gcd(NP, 32);
+  static constexpr int SPC = SPC0 % 2 == 0 ? SPC0 : 2 * SPC0;   // half-systems per CTA (even)
+  static constexpr int THREADS = SPC * NP;
+  static constexpr int KB = NP > 32 ? 6 : 5;                     // row bits of a pivot key
+  static constexpr size_t TILE = sizeof(T) * SPC * NP * (NP + 1); // natural-order inverse of the previous zone
+  static constexpr size_t PROW = sizeof(T) * SPC * NP;           // pivot row of the current step
+  static constexpr size_t USHR = sizeof(T) * SPC * NP;           // column scaling of the next zone's Schur term
+  static constexpr size_t PINV = 16 * SPC;                       // 1 / pivot (16-byte slots)
+  static constexpr size_t CAND = sizeof(int) * SPC * NP;         // pivot-search keys
+  static constexpr size_t PIVR = sizeof(int) * SPC * NP;         // row chosen at each step
+  static constexpr size_t BYTES = TILE + PROW + USHR + PINV + CAND + PIVR;
+};
+
+__device__ inline long system_of_spr(long j, const int *ray_list, int spr) {
+  return ray_list ? (long)ray_list[j / spr] * spr + (j % spr) : j;
+}
+
+template <int KB> __device__ inline int row_key(double x, int r) {
+  const unsigned hi = (unsigned)((unsigned long long)__double_as_longlong(x) >> 32) & 0x7fffffffu;
+  return (int)((hi & ~((1u << KB) - 1u)) | (unsigned)((1 << KB) - 1 - r));
+}
+template <int KB> __device__ inline int row_key(float x, int r) {
+  const unsigned b = (unsigned)__float_as_int(x) & 0x7fffffffu;
+  return (int)((b & ~((1u << KB) - 1u)) | (unsigned)((1 << KB) - 1 - r));
+}
+__device__ inline double recip_t(double d) { return recip(d); }
+__device__ inline float recip_t(float d) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(d));
+  const float e = fmaf(-d, r, 1.f);
+  return isfinite(r) ? fmaf(r, e, r) : r;
+}
+
+template <int NP, typename TIn, typename T>
+__global__ void __launch_bounds__(RowCta<NP, T>::THREADS)
+k_factor_rows(int n, int n_r, int n_sys, int spr, const TIn *__restrict__ diag, const T *__restrict__ lower,
+              const T *__restrict__ upper, T *__restrict__ dinv, const int *__restrict__ ray_list) {
+  using C = RowCta<NP, T>;
+  constexpr int SPC = C::SPC, KB = C::KB;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T (*tile)[NP][NP + 1] = reinterpret_cast<T (*)[NP][NP + 1]>(smem_raw);
+  T (*prow)[NP] = reinterpret_cast<T (*)[NP]>(smem_raw + C::TILE);
+  T (*ushr)[NP] = reinterpret_cast<T (*)[NP]>(smem_raw + C::TILE + C::PROW);
+  T *pinv = reinterpret_cast<T *>(smem_raw + C::TILE + C::PROW + C::USHR);          // stride 16 bytes
+  int (*cand)[NP] = reinterpret_cast<int (*)[NP]>(smem_raw + C::TILE + C::PROW + C::USHR + C::PINV);
+  int (*pivrow)[NP] = reinterpret_cast<int (*)[NP]>(smem_raw + C::TILE + C::PROW + C::USHR + C::PINV + C::CAND);
+  constexpr int PS = 16 / sizeof(T);                 // pinv slot stride in elements
+
+  const int s = threadIdx.x / NP, r = threadIdx.x % NP;
+  const int half = s & 1;                            // 0: zones 0..m top-down, 1: zones n_r-1..m+1 bottom-up
+  const long jsys = (long)blockIdx.x * (SPC / 2) + (s >> 1);
+  const bool valid = jsys < n_sys;
+  const long sys = valid ? system_of_spr(jsys, ray_list, spr) : 0;
+  const int m = n_r / 2;
+  const int len = half == 0 ? m + 1 : n_r - 1 - m;   // zones of this half; all threads step m + 1 times
+  const T one = T(1), zero = T(0);
+
+  T nxt[NP];
+  T nl = zero;
+  auto load_row = [&](int j) {
+    const bool act = valid && j < len && r < n;
+    const int z = half == 0 ? j : n_r - 1 - j;
+    const size_t zr = ((size_t)sys * n_r + (act ? z : 0)) * n + r;
+#pragma unroll
+    for (int c = 0; c < NP; ++c) {
+      if (act && c < n) nxt[c] = (T)diag[zr * n + c];
+      else nxt[c] = (c == r) ? one : zero;
+    }
+    nl = (act && j > 0) ? (half == 0 ? lower[zr] : upper[zr]) : zero;
+  };
+  load_row(0);
+  for (int j = 0; j <= m; ++j) {
+    const bool active = j < len;
+    const int i = half == 0 ? j : n_r - 1 - j;
+    const bool real = valid && active && r < n;
+    const size_t zrow = ((size_t)sys * n_r + (real ? i : 0)) * n + r;
+    T a[NP];
+#pragma unroll
+    for (int c = 0; c < NP; ++c) a[c] = nxt[c];
+    const T lr = nl;
+    if (j + 1 <= m) load_row(j + 1);
+    if (j > 0 && active) {
+#pragma unroll
+      for (int c = 0; c < NP; ++c) a[c] = fma(-(lr * tile[s][r][c]), ushr[s][c], a[c]);
+    }
+    if (half == 0 && j == m && n_r - 1 > m) {
+      const T um = real ? upper[zrow] : zero;
+#pragma unroll
+      for (int c = 0; c < NP; ++c) a[c] = fma(-(um * tile[s + 1][r][c]), ushr[s + 1][c], a[c]);
+    }
+    bool used = false;
+    int my_step = 0;
+    cand[s][r] = row_key<KB>(a[0], r);
+#pragma unroll
+    for (int pstep = 0; pstep < NP; ++pstep) {
+      __syncthreads();
+      int best_key = cand[s][0];
+#pragma unroll
+      for (int c = 1; c < NP; ++c) best_key = max(best_key, cand[s][c]);
+      const int best = (1 << KB) - 1 - (best_key & ((1 << KB) - 1));
+      const bool me = (r == best);
+      if (me) {
+        pinv[s * PS] = recip_t(a[pstep]);
+#pragma unroll
+        for (int c = 0; c < NP; ++c) prow[s][c] = a[c];
+        pivrow[s][pstep] = r;
+        used = true;
+        my_step = pstep;
+      }
+      __syncthreads();
+      const T inv = pinv[s * PS];
+      const T f = fma(me ? -one : a[pstep], inv, me ? one : zero);
+      if (pstep + 1 < NP) {
+        a[pstep + 1] = fma(-f, prow[s][pstep + 1], a[pstep + 1]);
+        cand[s][r] = used ? -1 : row_key<KB>(a[pstep + 1], r);
+      }
+#pragma unroll
+      for (int c = 0; c < NP; ++c)
+        if (c != pstep + 1 && c != pstep) a[c] = fma(-f, prow[s][c], a[c]);
+      a[pstep] = me ? inv : -f;
+    }
+    __syncthreads();
+    if (active) {
+#pragma unroll
+      for (int c = 0; c < NP; ++c) tile[s][my_step][pivrow[s][c]] = a[c];
+      ushr[s][r] = real ? (half == 0 ? upper[zrow] : lower[zrow]) : zero;
+    }
+    __syncthreads();
+    if (real) {
+      T *out = dinv + zrow * n;
+#pragma unroll
+      for (int c = 0; c < NP; ++c)
+        if (c < n) out[c] = tile[s][r][c];
+    }
+  }
+}
+
+// Substitution with those factors (twisted, as k_solve).  FP64: rhs and x as given.  FP32: the
+// right-hand side arrives scaled by 2^k per system and rounded to FP32 (rhs32, k in sys_exp, from
+// k_sysmax), the sweeps run in FP32 and x is scaled back by an exact multiplication by 2^-k; the
+// forward results are kept in x (in the scaled units) until the backward sweep replaces them.
+template <int NP, typename T>
+__global__ void __launch_bounds__(RowCta<NP, T>::THREADS)
+k_solve_rows(int n, int n_r, int n_sys, int spr, const T *__restrict__ dinv, const T *__restrict__ lower,
+             const T *__restrict__ upper, const double *rhs, const float *__restrict__ rhs32,
+             const int *__restrict__ sys_exp, double *x, const int *__restrict__ ray_list) {
+  constexpr int SPC = RowCta<NP, T>::SPC;
+  __shared__ T v[SPC][NP];
+  __shared__ T mid[SPC / 2][NP];
+  const int s = threadIdx.x / NP, r = threadIdx.x % NP;
+  const int half = s & 1, sl = s >> 1;
+  const long jsys = (long)blockIdx.x * (SPC / 2) + sl;
+  const bool valid = jsys < n_sys;
+  const long sys = valid ? system_of_spr(jsys, ray_list, spr) : 0;
+  const bool realr = valid && r < n;
+  const size_t base = (size_t)sys * n_r * n;
+  const int m = n_r / 2, B = n_r - 1 - m;
+  const int F = half == 0 ? m : B;
+  const bool f32 = sizeof(T) == 4;
+  const double unscale = (f32 && valid) ? ldexp(1.0, -sys_exp[jsys]) : 1.0;
+  const T zero = T(0);
+  auto b_at = [&](size_t zr) -> T { return f32 ? (T)rhs32[zr] : (T)rhs[zr]; };
+  auto rowdot = [&](int z, bool real) {
+    const T *src = dinv + (base + (size_t)z * n + r) * n;
+    T acc0 = zero, acc1 = zero;
+    if (real) {
+#pragma unroll
+      for (int c = 0; c < NP; c += 2) {
+        if (c < n) acc0 = fma(src[c], v[s][c], acc0);
+        if (c + 1 < n) acc1 = fma(src[c + 1], v[s][c + 1], acc1);
+      }
+    }
+    return acc0 + acc1;
+  };
+  T prev = zero;
+  for (int j = 0; j < m; ++j) {
+    const bool act = j < F;
+    const bool real = realr && act;
+    const int z = half == 0 ? j : n_r - 1 - j;
+    const size_t zr = base + (size_t)(real ? z : 0) * n + r;
+    const T c = (real && j > 0) ? (half == 0 ? lower[zr] : upper[zr]) : zero;
+    const T b = real ? b_at(zr) : zero;
+    v[s][r] = real ? b - c * prev : zero;
+    __syncthreads();
+    const T g = rowdot(z, real);
+    if (real) {
+      x[zr] = (double)g;
+      prev = g;
+    }
+    __syncthreads();
+  }
+  if (half == 1) mid[sl][r] = B > 0 ? prev : zero;
+  __syncthreads();
+  if (half == 0) {
+    const size_t zr = base + (size_t)m * n + r;
+    const T l = (realr && m > 0) ? lower[zr] : zero;
+    const T u = (realr && m < n_r - 1) ? upper[zr] : zero;
+    v[s][r] = realr ? b_at(zr) - l * prev - u * mid[sl][r] : zero;
+  }
+  __syncthreads();
+  if (half == 0) {
+    const T xm = rowdot(m, realr);
+    if (realr) x[base + (size_t)m * n + r] = (double)xm * unscale;
+    prev = xm;
+  }
+  __syncthreads();
+  if (half == 0) mid[sl][r] = prev;
+  __syncthreads();
+  if (half == 1) prev = mid[sl][r];
+  for (int j = 0; j < m; ++j) {
+    const bool act = j < F;
+    const bool real = realr && act;
+    const int z = half == 0 ? m - 1 - j : m + 1 + j;
+    const size_t zr = base + (size_t)(real ? z : 0) * n + r;
+    const T c = real ? (half == 0 ? upper[zr] : lower[zr]) : zero;
+    v[s][r] = real ? c * prev : zero;
+    __syncthreads();
+    const T acc = rowdot(z, real);
+    if (real) {
+      const T xi = (T)x[zr] - acc;
+      x[zr] = (double)xi * unscale;
+      prev = xi;
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------------------
 // Warp-synchronous FP32 variants (MIXED precision): one warp per half of a (ray, species)
 // system, lane r owns block row r (NP <= 32), no CTA-wide barriers.  FP32 arithmetic is 63x
 // cheaper than FP64 on this GPU, so these kernels are bound by the dependency chain along the
@@ -313,6 +550,15 @@ __device__ inline void cp_async16(void *dst, const void *src) {
 __device__ inline void cp_async4(void *dst, const void *src) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((unsigned)__cvta_generic_to_shared(dst)), "l"(src)
                : "memory");
+}
+__device__ inline void cp_async8(void *dst, const void *src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((unsigned)__cvta_generic_to_shared(dst)), "l"(src)
+               : "memory");
+}
+// one element of 4 or 8 bytes
+template <typename TE> __device__ inline void cp_async_elem(TE *dst, const TE *src) {
+  if constexpr (sizeof(TE) == 4) cp_async4(dst, src);
+  else cp_async8(dst, src);
 }
 __device__ inline void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ inline void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
@@ -458,6 +704,12 @@ __device__ inline bool gj_invert_np2(float *a, float (*prow)[2][NP + 4], int r) 
   return __all_sync(0xffffffffu, ok);
 }
 
+// CTAs per SM the FP32 factor is compiled for (its register budget): the kernel is bound by the
+// latency of its pivot chain, so resident warps matter more than a few spilled registers.
+#ifndef MGFLD_FW32_MINB
+#define MGFLD_FW32_MINB 4
+#endif
+
 // Warps per CTA of the factor: four (two systems), two for the widest blocks so that the
 // static shared memory (two row buffers and the inverse tile per warp) stays under 48 KB.
 template <int NP> __host__ __device__ constexpr int fw_wpc() { return NP > 24 ? 2 : 4; }
@@ -469,7 +721,7 @@ template <int NP> __host__ __device__ constexpr int fw_wpc() { return NP > 24 ? 
 // with partial pivoting only for a zone whose unpivoted elimination met a zero or non-finite
 // pivot.
 template <int NP, typename TIn, typename TC, bool PIVOT>
-__global__ void __launch_bounds__(fw_wpc<NP>() * 32, 4)
+__global__ void __launch_bounds__(fw_wpc<NP>() * 32, MGFLD_FW32_MINB)
 k_factor_w32(int n, int n_r, int n_sys, const TIn *__restrict__ diag, const TC *__restrict__ lower,
              const TC *__restrict__ upper, float *__restrict__ dinv, const int *__restrict__ ray_list) {
   static_assert(NP % 4 == 0, "rows of NP floats in 16-byte pieces");
@@ -481,6 +733,7 @@ k_factor_w32(int n, int n_r, int n_sys, const TIn *__restrict__ diag, const TC *
   __shared__ __align__(16) float prow[W][2][NP + 4];
   __shared__ __align__(16) float prow2[W][2][2][NP + 4];
   __shared__ __align__(16) float rowbuf[W][2][NP][NP];
+  __shared__ __align__(16) TC cplb[W][2][2][32];      // per lane: the next zone's couplings (rows path)
   const int wid = threadIdx.x >> 5, r = threadIdx.x & 31;
   const int half = wid & 1;                          // 0: zones 0..m top-down, 1: zones n_r-1..m+1 bottom-up
   const long jsys = (long)blockIdx.x * (W / 2) + (wid >> 1);
@@ -508,21 +761,29 @@ k_factor_w32(int n, int n_r, int n_sys, const TIn *__restrict__ diag, const TC *
 #pragma unroll
         for (int c = 0; c < NP; c += 4) cp_async16(dst + c, diag + zr * n + c);
       }
+      // couplings to the previous zone of this half's sequence (row scaling of its Schur term)
+      // and to the next one (column scaling of this zone's Schur term), in the same copy group
+      cp_async_elem(&cplb[wid][j & 1][0][r], (half == 0 ? lower : upper) + zr);
+      cp_async_elem(&cplb[wid][j & 1][1][r], (half == 0 ? upper : lower) + zr);
       cp_async_commit();
-    } else if (row) {
+    } else {
+      if (row) {
 #pragma unroll
-      for (int c = 0; c < NP; ++c) dst[c] = (real && c < n) ? (float)diag[zr * n + c] : ((c == r) ? 1.f : 0.f);
+        for (int c = 0; c < NP; ++c) dst[c] = (real && c < n) ? (float)diag[zr * n + c] : ((c == r) ? 1.f : 0.f);
+      }
+      nl_raw = half == 0 ? lower[zr] : upper[zr];
+      nu_raw = half == 0 ? upper[zr] : lower[zr];
     }
-    // couplings to the previous zone of this half's sequence (row scaling of its Schur term)
-    // and to the next one (column scaling of this zone's Schur term)
-    nl_raw = half == 0 ? lower[zr] : upper[zr];
-    nu_raw = half == 0 ? upper[zr] : lower[zr];
   };
   if (len > 0) load_row(0);
   for (int j = 0; j < len; ++j) {
     const int z = zone(j);
     const size_t zrow = ((size_t)sys * n_r + z) * n + r;
-    if (vec) cp_async_wait_all();
+    if (vec) {
+      cp_async_wait_all();
+      nl_raw = cplb[wid][j & 1][0][r];
+      nu_raw = cplb[wid][j & 1][1][r];
+    }
     const float lr = (real && j > 0) ? (float)nl_raw : 0.f;
     const float ur = real ? (float)nu_raw : 0.f;
     if (j + 1 < len) load_row(j + 1);
@@ -754,6 +1015,35 @@ __global__ void k_sysmax(int n, int n_r, const double *__restrict__ rhs, const i
   __shared__ double red[256];
   __shared__ int kexp_s;
   const long sys = system_of(blockIdx.x, ray_list);
+  const size_t base = (size_t)sys * n_r * n;
+  const unsigned cnt = (unsigned)(n_r * n);
+  double m = 0.0;
+  for (unsigned e = threadIdx.x; e < cnt; e += blockDim.x) m = fmax(m, fabs(rhs[base + e]));
+  red[threadIdx.x] = m;
+  __syncthreads();
+  for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+    if (threadIdx.x < h) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + h]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    m = red[0];
+    const long long b = __double_as_longlong(m);
+    const int e = (int)((b >> 52) & 0x7ff);
+    const int k = (m > 0.0 && e < 0x7ff) ? 1022 - e : 0;
+    sys_exp[blockIdx.x] = k;
+    kexp_s = k;
+  }
+  __syncthreads();
+  const int k = kexp_s;
+  for (unsigned e = threadIdx.x; e < cnt; e += blockDim.x) rhs32[base + e] = d2f_exp2(rhs[base + e], k);
+}
+
+// k_sysmax for systems listed with `spr` systems per ray.
+__global__ void k_sysmax_spr(int n, int n_r, const double *__restrict__ rhs, const int *__restrict__ ray_list, int spr,
+                             int *__restrict__ sys_exp, float *__restrict__ rhs32) {
+  __shared__ double red[256];
+  __shared__ int kexp_s;
+  const long sys = system_of_spr(blockIdx.x, ray_list, spr);
   const size_t base = (size_t)sys * n_r * n;
   const unsigned cnt = (unsigned)(n_r * n);
   double m = 0.0;
@@ -1042,6 +1332,65 @@ cudaError_t launch_factor(int n, int n_r, int n_sys, const void *diag, int diag_
   } else {
     MGFLD_DISPATCH_NP(n, return (run_factor<NP>(n, n_r, n_sys, diag, diag_fp32, lower, upper, dinv,
                                                         ray_list, s)))
+  }
+}
+
+#define MGFLD_DISPATCH_NPW(n, ...)                          \
+  if (n <= 8) { constexpr int NP = 8; __VA_ARGS__; }          \
+  else if (n <= 16) { constexpr int NP = 16; __VA_ARGS__; }   \
+  else if (n <= 24) { constexpr int NP = 24; __VA_ARGS__; }   \
+  else if (n <= 32) { constexpr int NP = 32; __VA_ARGS__; }   \
+  else if (n <= 40) { constexpr int NP = 40; __VA_ARGS__; }   \
+  else { constexpr int NP = 48; __VA_ARGS__; }
+
+template <int NP, typename TIn, typename T>
+static cudaError_t run_factor_rows(int nb, int n_r, int n_sys, int spr, const TIn *diag, const T *lower,
+                                   const T *upper, T *dinv, const int *ray_list, cudaStream_t s) {
+  using C = RowCta<NP, T>;
+  const unsigned grid = (unsigned)((n_sys + C::SPC / 2 - 1) / (C::SPC / 2));
+  if (C::BYTES > 48 * 1024) {
+    const cudaError_t e = cudaFuncSetAttribute(k_factor_rows<NP, TIn, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)C::BYTES);
+    if (e != cudaSuccess) return e;
+  }
+  k_factor_rows<NP, TIn, T><<<grid, C::THREADS, C::BYTES, s>>>(nb, n_r, n_sys, spr, diag, lower, upper, dinv, ray_list);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_factor_rows(int nb, int n_r, int n_sys, int spr, const void *diag, const void *lower,
+                               const void *upper, void *dinv, int fp32, const int *ray_list, cudaStream_t s) {
+  if (n_sys == 0) return cudaSuccess;
+  if (nb > 48) return cudaErrorInvalidValue;
+  if (fp32) {
+    MGFLD_DISPATCH_NPW(nb, return (run_factor_rows<NP, float, float>(nb, n_r, n_sys, spr, (const float *)diag,
+                                                                        (const float *)lower, (const float *)upper,
+                                                                        (float *)dinv, ray_list, s)))
+  } else {
+    MGFLD_DISPATCH_NPW(nb, return (run_factor_rows<NP, double, double>(nb, n_r, n_sys, spr, (const double *)diag,
+                                                                          (const double *)lower, (const double *)upper,
+                                                                          (double *)dinv, ray_list, s)))
+  }
+}
+
+cudaError_t launch_solve_rows(int nb, int n_r, int n_sys, int spr, const void *dinv, const void *lower,
+                              const void *upper, const double *rhs, float *rhs32, int *sys_exp, double *x, int fp32,
+                              const int *ray_list, cudaStream_t s) {
+  if (n_sys == 0) return cudaSuccess;
+  if (nb > 48) return cudaErrorInvalidValue;
+  if (fp32) {
+    // per-system power-of-two scaling of the right-hand side for the FP32 sweeps
+    k_sysmax_spr<<<n_sys, 256, 0, s>>>(nb, n_r, rhs, ray_list, spr, sys_exp, rhs32);
+    MGFLD_DISPATCH_NPW(nb, using C = RowCta<NP, float>;
+                       k_solve_rows<NP, float><<<(unsigned)((n_sys + C::SPC / 2 - 1) / (C::SPC / 2)), C::THREADS, 0, s>>>(
+                           nb, n_r, n_sys, spr, (const float *)dinv, (const float *)lower, (const float *)upper, rhs,
+                           rhs32, sys_exp, x, ray_list);
+                       return cudaGetLastError())
+  } else {
+    MGFLD_DISPATCH_NPW(nb, using C = RowCta<NP, double>;
+                       k_solve_rows<NP, double><<<(unsigned)((n_sys + C::SPC / 2 - 1) / (C::SPC / 2)), C::THREADS, 0, s>>>(
+                           nb, n_r, n_sys, spr, (const double *)dinv, (const double *)lower, (const double *)upper, rhs,
+                           nullptr, nullptr, x, ray_list);
+                       return cudaGetLastError())
   }
 }
 

@@ -41,20 +41,23 @@ struct Prob {
   double dt;
   const double *r_edge, *lapse, *e_edge, *rho, *kabs, *kscat, *nes, *scale;
   const double *u, *eta1;   // shock transport (Eqs. a90-a99): zone velocity and flux factor, or NULL
+  const double *pair;       // synthetic pair process (Eq. d14): annihilation kernel per zone, or NULL
+  int pair_chi;             // its angular correction (Eqs. d16-d22) on
   Eos eos;
 };
 
 // Workspace regions (byte offsets from the workspace base).
 struct Layout {
-  int mixed;
+  int mixed, pair;
   size_t groups, phout, phin, phd, rsum, phin32, phd32, lam, slam, g0, l0, alpha, ghost, rnu, jbuf, psi_n, ye_n, e_n,
-      zone, src, shock, cdiag, cup, clow, cb;
+      zone, src, shock, cdiag, cup, clow, cb, pmake, pmsum, pkill;
   size_t diag, lower, upper, rhs, x, dinv, zled, sscale, kinv, lower32, upper32, g32, rhs32;
   size_t viol, vprev, active, iters, status, refac, nfact, nanflag, list_act, list_ref, counters;
   size_t total;
 };
 
-Layout make_layout(int n_ray, int n_r, int n, int precision);
+// pair: the coupled nu / antinu systems of the pair process (wider blocks and the pair kernels).
+Layout make_layout(int n_ray, int n_r, int n, int precision, int pair = 0);
 
 // Argument checks and the device view of a caller's problem (shared by the C entry points).
 bool dims_ok(const mgfld_dims *d);
@@ -110,6 +113,10 @@ struct Ws {
   // couplings c_r = (a^2/V) alpha_out (0 in the last zone: the ghost is in D0) and c_l = (a^2/V)
   // alpha_in; and b0 = psi^n/(a c dt) - (a^2/V) shock.
   double *cdiag, *cup, *clow, *cb;
+  // Pair process, or null: per zone the weighted creation kernel pmake[k][k'] = C w_k' Phi^p
+  // ([ray][zone][k][k']) with its row sums pmsum, and per species the weighted annihilation kernel
+  // pkill[q][k][k'] = C w_k' chi_q Phi^a ([ray][zone][q][k][k']).
+  double *pmake, *pmsum, *pkill;
   double *lim;              // per (ray, q, i, k), or null: the flux limiter at the outer edge (kept
                             // by the setup for the neutrino stress)
   double *jl, *jr;          // per (ray, q, i, k), or null: d(edge flux A psi1/a^2)/d psi_i and
@@ -251,6 +258,23 @@ __device__ inline double f2d_exp2(float v, int k) {
 // MIXED-precision factor with FP32 diagonal blocks and FP32 coupling coefficients.
 cudaError_t launch_factor_f32(int n, int n_r, int n_sys, const float *diag, const float *lower32,
                               const float *upper32, float *dinv, const int *ray_list, cudaStream_t s);
+// Pair process (pair.cu): the weighted kernels of every zone (after the neutrinosphere scan),
+// and the residual / Jacobian of the coupled pair systems (blocks of 2 n rows, vectors
+// [ray][pair][zone][2 n]; src_out in the psi layout).
+cudaError_t launch_pair(const Prob &p, const Ws &w, const double *T, cudaStream_t s);
+cudaError_t launch_assemble_pair(const Prob &p, const Ws &w, const double *psi, void *diag, int diag_fp32,
+                                 double *lower, double *upper, double *rhs, const int *list, int n_list,
+                                 const int *jac_flag, cudaStream_t s, double *src_out, int first);
+
+// Thread-per-row factor and substitution of systems of block width nb <= 48 with spr systems per
+// ray (the coupled nu / antinu pair systems: nb = 2 n, spr = 2), FP64 or FP32 (fp32: float blocks,
+// couplings and factors; the substitution scales each system's right-hand side by a power of two
+// into rhs32 / sys_exp first).
+cudaError_t launch_factor_rows(int nb, int n_r, int n_sys, int spr, const void *diag, const void *lower,
+                               const void *upper, void *dinv, int fp32, const int *ray_list, cudaStream_t s);
+cudaError_t launch_solve_rows(int nb, int n_r, int n_sys, int spr, const void *dinv, const void *lower,
+                              const void *upper, const double *rhs, float *rhs32, int *sys_exp, double *x, int fp32,
+                              const int *ray_list, cudaStream_t s);
 cudaError_t launch_solve(int n, int n_r, int n_sys, const void *dinv, const double *lower,
                          const double *upper, const double *rhs, double *x, int precision,
                          const int *ray_list, cudaStream_t s);

@@ -35,7 +35,8 @@ extern "C" mgfld_status mgfld_step_noalloc(const mgfld_dims *dims, const mgfld_p
                                            mgfld_step_report *report, void *stream) {
   if (!dims || !opts) return MGFLD_EINVAL;
   if (opts->profile) return MGFLD_EINVAL;       // timing would create CUDA events
-  const size_t need = mgfld_workspace_bytes(dims, opts->precision);
+  const size_t need = (prob && prob->pair_coef) ? mgfld_workspace_bytes_pair(dims, opts->precision)
+                                                 : mgfld_workspace_bytes(dims, opts->precision);
   if (need == 0) return MGFLD_EINVAL;
   if (need > kScratchBytes) return MGFLD_ENOMEM;
   void *ws = nullptr;

@@ -513,6 +513,10 @@ cudaError_t launch_setup(const Prob &p, const Ws &w, const double *psi, const do
   k_nusphere<<<nblk((size_t)p.n_ray * NS * p.n * 32, B), B, 0, s>>>(p, w);   // a warp per (ray, q, k)
   k_edges<<<nblk(nall, B), B, 0, s>>>(p, w, w.psi_n);
   if (p.u) k_shock<<<nblk(nall, B), B, 0, s>>>(p, w, w.psi_n);
+  if (p.pair && w.pmake) {
+    const cudaError_t e = launch_pair(p, w, T, s);
+    if (e != cudaSuccess) return e;
+  }
   return cudaGetLastError();
 }
 

@@ -21,9 +21,10 @@ namespace mgfld {
 
 static size_t align_up(size_t v) { return (v + 255) & ~(size_t)255; }
 
-Layout make_layout(int n_ray, int n_r, int n, int precision) {
+Layout make_layout(int n_ray, int n_r, int n, int precision, int pair) {
   Layout L{};
   L.mixed = precision == MGFLD_MIXED;
+  L.pair = pair != 0;
   const size_t R = (size_t)n_ray, Z = R * n_r, F = Z * NS * n, B = F * n;
   size_t off = 0;
   auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes); return o; };
@@ -49,12 +50,14 @@ Layout make_layout(int n_ray, int n_r, int n, int precision) {
   L.cup = take(sizeof(double) * F);
   L.clow = take(sizeof(double) * F);
   L.cb = take(sizeof(double) * F);
-  L.diag = take((precision == MGFLD_MIXED ? sizeof(float) : sizeof(double)) * B);
+  // pair systems: per ray two (2n x 2n) blocks per zone, twice the four species' n x n blocks
+  const size_t Bs = pair ? 2 * B : B;
+  L.diag = take((precision == MGFLD_MIXED ? sizeof(float) : sizeof(double)) * Bs);
   L.lower = take(sizeof(double) * F);
   L.upper = take(sizeof(double) * F);
   L.rhs = take(sizeof(double) * F);
   L.x = take(sizeof(double) * F);
-  L.dinv = take((precision == MGFLD_MIXED ? sizeof(float) : sizeof(double)) * B);
+  L.dinv = take((precision == MGFLD_MIXED ? sizeof(float) : sizeof(double)) * Bs);
   L.zled = take(sizeof(double) * Z * 8);
   L.sscale = take(sizeof(int) * R * NS);
   L.lower32 = take(precision == MGFLD_MIXED ? sizeof(float) * F : 0);
@@ -73,6 +76,9 @@ Layout make_layout(int n_ray, int n_r, int n, int precision) {
   L.list_act = take(sizeof(int) * R);
   L.list_ref = take(sizeof(int) * R);
   L.counters = take(sizeof(int) * 8);
+  L.pmake = take(pair ? sizeof(double) * Z * n * n : 0);
+  L.pmsum = take(pair ? sizeof(double) * Z * n : 0);
+  L.pkill = take(pair ? sizeof(double) * Z * NS * n * n : 0);
   // Setup-only arrays share storage with buffers that are first written after the setup has
   // consumed them: sqrt(lambda) (read by the limiter kernel) lives in rhs, and (FP64) the NES
   // sums at psi^n (read by the first residual, before the first solve or the final sources) in
@@ -120,6 +126,9 @@ Ws resolve(void *base, const Layout &L) {
   w.cup = (double *)(b + L.cup);
   w.clow = (double *)(b + L.clow);
   w.cb = (double *)(b + L.cb);
+  w.pmake = L.pair ? (double *)(b + L.pmake) : nullptr;
+  w.pmsum = L.pair ? (double *)(b + L.pmsum) : nullptr;
+  w.pkill = L.pair ? (double *)(b + L.pkill) : nullptr;
   w.lim = nullptr;
   w.jl = w.jr = nullptr;       // set by mgfld_step when the coefficients follow the iterate
   w.diag = (double *)(b + L.diag);
@@ -230,8 +239,16 @@ __global__ void k_update_psi(Prob p, Ws w, Tol tl, double *__restrict__ psi, con
   const int ray = in ? list[rl] : list[0];
   float viol = 0.f;
   if (in) {
-    const size_t g = (size_t)ray * per_ray + (t - rl * per_ray);
-    const double d = w.x[g];
+    const unsigned local = t - rl * per_ray;
+    const size_t g = (size_t)ray * per_ray + local;
+    size_t gx = g;
+    if (p.pair) {
+      // the correction of the coupled pair systems, [ray][pair][zone][2 n]
+      const unsigned zq = local / (unsigned)p.n, k = local - zq * p.n;
+      const unsigned q = zq / (unsigned)p.n_r, i = zq - q * p.n_r;
+      gx = (((size_t)ray * 2 + (q >> 1)) * p.n_r + i) * (2 * p.n) + (q & 1) * p.n + k;
+    }
+    const double d = w.x[gx];
     const double v = psi[g] + d;
     psi[g] = v;
     viol = tol_ratio(fabs(d), fmax(fabs(v), tl.tolmin), tl.tolm, tl.tole);
@@ -558,6 +575,7 @@ Prob make_prob(const mgfld_dims *d, const mgfld_problem *p) {
   q.r_edge = p->r_edge; q.lapse = p->lapse; q.e_edge = p->e_edge; q.rho = p->rho;
   q.kabs = p->kappa_abs; q.kscat = p->kappa_scat; q.nes = p->nes_coef; q.scale = p->scale;
   q.u = p->u; q.eta1 = p->eta1;
+  q.pair = p->pair_coef; q.pair_chi = p->pair_chi;
   q.eos = make_eos(p->eos);
   return q;
 }
@@ -587,6 +605,11 @@ size_t mgfld_workspace_bytes(const mgfld_dims *dims, int precision) {
   return make_layout(dims->n_ray, dims->n_r, dims->n_e, precision).total;
 }
 
+size_t mgfld_workspace_bytes_pair(const mgfld_dims *dims, int precision) {
+  if (!dims_ok(dims) || 2 * dims->n_e > 48) return 0;
+  return make_layout(dims->n_ray, dims->n_r, dims->n_e, precision, 1).total;
+}
+
 size_t mgfld_factor_bytes(const mgfld_dims *dims, int precision) {
   if (!dims_ok(dims)) return 0;
   const size_t blocks = (size_t)dims->n_ray * NS * dims->n_r * dims->n_e * dims->n_e;
@@ -614,9 +637,11 @@ mgfld_status mgfld_step(const mgfld_dims *dims, const mgfld_problem *prob, mgfld
       !(opts->tol > 0.0) || !(opts->tol_ye > 0.0) || !(opts->tolmin_psi >= 0.0) || !(opts->tolmin_ye >= 0.0))
     return MGFLD_EINVAL;
   if (opts->coef_iterate && prob->u) return MGFLD_EINVAL;
-  if (prob->pair_coef) return MGFLD_EINVAL;       // species-pair blocks are not built
+  const int pair = prob->pair_coef != nullptr;
+  // the pair process: coupled blocks of 2 n_e <= 48 rows, with the coefficients frozen for the step
+  if (pair && (2 * dims->n_e > 48 || opts->coef_iterate)) return MGFLD_EINVAL;
   if (((uintptr_t)ws & 255u) != 0) return MGFLD_EINVAL;
-  const Layout L = make_layout(dims->n_ray, dims->n_r, dims->n_e, opts->precision);
+  const Layout L = make_layout(dims->n_ray, dims->n_r, dims->n_e, opts->precision, pair);
   if (ws_bytes < L.total) return MGFLD_ENOMEM;
   cudaStream_t s = (cudaStream_t)stream;
   Ws w = resolve(ws, L);
@@ -642,7 +667,7 @@ mgfld_status mgfld_step(const mgfld_dims *dims, const mgfld_problem *prob, mgfld
   k_init<<<nblk(R, 128), 128, 0, s>>>(R, w);
   MGFLD_CUDA(cudaGetLastError());
   MGFLD_CUDA(cudaMemsetAsync(w.counters, 0, sizeof(int) * 8, s));
-  prof.end(MGFLD_PROF_SETUP, p.u ? 8 : 7);
+  prof.end(MGFLD_PROF_SETUP, 7 + (p.u ? 1 : 0) + (pair ? 1 : 0));
   int n_act = R, n_ref = R;
   int host_counters[8];
   for (int it = 0; it < opts->max_iter && n_act > 0; ++it) {
@@ -654,14 +679,21 @@ mgfld_status mgfld_step(const mgfld_dims *dims, const mgfld_problem *prob, mgfld
       prof.end(MGFLD_PROF_SETUP, 3);
     }
     prof.begin(MGFLD_PROF_ASSEMBLE);
-    MGFLD_CUDA(launch_assemble(p, w, state->psi, w.diag, tl.mixed, w.lower, w.upper, w.rhs, w.list_act, n_act,
-                               jac, s, nullptr, it == 0));
+    if (pair)
+      MGFLD_CUDA(launch_assemble_pair(p, w, state->psi, w.diag, tl.mixed, w.lower, w.upper, w.rhs, w.list_act, n_act,
+                                      jac, s, nullptr, it == 0));
+    else
+      MGFLD_CUDA(launch_assemble(p, w, state->psi, w.diag, tl.mixed, w.lower, w.upper, w.rhs, w.list_act, n_act,
+                                 jac, s, nullptr, it == 0));
     prof.end(MGFLD_PROF_ASSEMBLE, 1);
     const int *flist = tl.chord ? w.list_ref : w.list_act;
     const int nf = tl.chord ? n_ref : n_act;
     if (nf > 0) {
       prof.begin(MGFLD_PROF_FACTOR);
-      if (tl.mixed)
+      if (pair)
+        MGFLD_CUDA(launch_factor_rows(2 * n, NR, nf * 2, 2, w.diag, tl.mixed ? (const void *)w.lower32 : w.lower,
+                                      tl.mixed ? (const void *)w.upper32 : w.upper, w.dinv, tl.mixed, flist, s));
+      else if (tl.mixed)
         MGFLD_CUDA(launch_factor_f32(n, NR, nf * NS, (const float *)w.diag, w.lower32, w.upper32, (float *)w.dinv,
                                      flist, s));
       else
@@ -669,7 +701,11 @@ mgfld_status mgfld_step(const mgfld_dims *dims, const mgfld_problem *prob, mgfld
       prof.end(MGFLD_PROF_FACTOR, 1);
     }
     prof.begin(MGFLD_PROF_SOLVE);
-    if (tl.mixed && n % 2 == 0)
+    if (pair)
+      MGFLD_CUDA(launch_solve_rows(2 * n, NR, n_act * 2, 2, w.dinv, tl.mixed ? (const void *)w.lower32 : w.lower,
+                                   tl.mixed ? (const void *)w.upper32 : w.upper, w.rhs, w.rhs32, w.sscale, w.x,
+                                   tl.mixed, w.list_act, s));
+    else if (tl.mixed && n % 2 == 0)
       MGFLD_CUDA(launch_solve_tma(n, NR, n_act * NS, w.dinv, w.lower32, w.upper32, w.rhs, w.rhs32, w.x, w.g32,
                                   w.list_act, w.sscale, w.counters + 3, s));
     else
@@ -694,8 +730,12 @@ mgfld_status mgfld_step(const mgfld_dims *dims, const mgfld_problem *prob, mgfld
     n_ref = host_counters[1];
   }
   prof.begin(MGFLD_PROF_FINISH);
-  MGFLD_CUDA(launch_assemble(p, w, state->psi, w.diag, tl.mixed, w.lower, w.upper, w.rhs, nullptr, R, nullptr,
-                             s, w.src));
+  if (pair)
+    MGFLD_CUDA(launch_assemble_pair(p, w, state->psi, w.diag, tl.mixed, w.lower, w.upper, w.rhs, nullptr, R, nullptr,
+                                    s, w.src, 0));
+  else
+    MGFLD_CUDA(launch_assemble(p, w, state->psi, w.diag, tl.mixed, w.lower, w.upper, w.rhs, nullptr, R, nullptr,
+                               s, w.src));
   k_finish<<<nblk((size_t)R * NR, 128), 128, 0, s>>>(p, w, state->psi, state->ye, state->T);
   MGFLD_CUDA(cudaGetLastError());
   MGFLD_CUDA(cudaMemsetAsync(w.counters + 2, 0, sizeof(int), s));

@@ -20,7 +20,7 @@ MGFLD_FP64, MGFLD_MIXED = 0, 1
 MGFLD_BC_GHOST, MGFLD_BC_REFLECT = 0, 1
 N_SPECIES = 4
 
-EXPORTED = ('mgfld_eos_default', 'mgfld_workspace_bytes', 'mgfld_step', 'mgfld_assemble',
+EXPORTED = ('mgfld_eos_default', 'mgfld_workspace_bytes', 'mgfld_workspace_bytes_pair', 'mgfld_step', 'mgfld_assemble',
             'mgfld_factor_bytes', 'mgfld_factor', 'mgfld_solve', 'mgfld_status_str', 'mgfld_step_noalloc',
             'mgfld_adjoint_workspace_bytes', 'mgfld_adjoint', 'mgfld_energy_advect', 'mgfld_stress_lapse')
 NOALLOC_SCRATCH_BYTES = 64 << 20
@@ -40,7 +40,7 @@ class Problem(ctypes.Structure):
                 ('rho', ctypes.c_void_p), ('kappa_abs', ctypes.c_void_p), ('kappa_scat', ctypes.c_void_p),
                 ('nes_coef', ctypes.c_void_p), ('scale', ctypes.c_void_p), ('eos', EosParams),
                 ('dt', ctypes.c_double), ('outer_bc', ctypes.c_int), ('u', ctypes.c_void_p),
-                ('eta1', ctypes.c_void_p), ('pair_coef', ctypes.c_void_p)]
+                ('eta1', ctypes.c_void_p), ('pair_coef', ctypes.c_void_p), ('pair_chi', ctypes.c_int)]
 
 
 class State(ctypes.Structure):
@@ -100,6 +100,8 @@ def lib():
     L.mgfld_eos_default.argtypes = []
     L.mgfld_workspace_bytes.restype = ctypes.c_size_t
     L.mgfld_workspace_bytes.argtypes = [P(Dims), ctypes.c_int]
+    L.mgfld_workspace_bytes_pair.restype = ctypes.c_size_t
+    L.mgfld_workspace_bytes_pair.argtypes = [P(Dims), ctypes.c_int]
     L.mgfld_factor_bytes.restype = ctypes.c_size_t
     L.mgfld_factor_bytes.argtypes = [P(Dims), ctypes.c_int]
     L.mgfld_step.restype = ctypes.c_int
@@ -174,9 +176,10 @@ class DeviceProblem:
                 np.array(v, dtype=np.float64, order='C'), device=device)
         self.dt = float(prob['dt'])
         self.outer_bc = int(prob.get('outer_bc', MGFLD_BC_GHOST))
+        self.pair_chi = 1 if prob.get('pair_chi') else 0
         self.eos = lib().mgfld_eos_default()
         self.struct = Problem(*[_ptr(self.t[f]) for f in self.FIELDS], self.eos, self.dt, self.outer_bc,
-                              *[_ptr(self.t[f]) for f in self.OPTIONAL_FIELDS])
+                              *[_ptr(self.t[f]) for f in self.OPTIONAL_FIELDS], self.pair_chi)
 
     def rays(self, lo, hi, n_r, n_e):
         """C struct viewing rays [lo, hi) only (rays are independent; used for chunking)."""
@@ -186,7 +189,7 @@ class DeviceProblem:
         return Problem(off('r_edge', n_r + 1), off('lapse', n_r), _ptr(self.t['e_edge']), off('rho', n_r),
                        off('kappa_abs', N_SPECIES * n_r * n_e), off('kappa_scat', N_SPECIES * n_r * n_e),
                        off('nes_coef', n_r), _ptr(self.t['scale']), self.eos, self.dt, self.outer_bc,
-                       off('u', n_r), off('eta1', N_SPECIES * n_r * n_e), off('pair_coef', n_r))
+                       off('u', n_r), off('eta1', N_SPECIES * n_r * n_e), off('pair_coef', n_r), self.pair_chi)
 
 
 PROF_NAMES = ('setup', 'assemble', 'factor', 'solve', 'update', 'finish')
@@ -209,6 +212,10 @@ def step_opts(precision=MGFLD_FP64, tol=1e-10, tolmin_psi=1.0, tol_ye=None, tolm
 
 def mgfld_workspace_bytes(dims: Dims, precision: int) -> int:
     return int(lib().mgfld_workspace_bytes(ctypes.byref(dims), int(precision)))
+
+
+def mgfld_workspace_bytes_pair(dims: Dims, precision: int) -> int:
+    return int(lib().mgfld_workspace_bytes_pair(ctypes.byref(dims), int(precision)))
 
 
 def mgfld_factor_bytes(dims: Dims, precision: int) -> int:
@@ -298,12 +305,13 @@ class Stepper:
         self.prob = DeviceProblem(prob, device)
         self.precision = precision
         self.opts = step_opts(precision, **opt_kw)
-        per_ray = mgfld_workspace_bytes(Dims(1, self.n_r, self.n_e, N_SPECIES), precision)
+        wsb = mgfld_workspace_bytes_pair if prob.get('pair_coef') is not None else mgfld_workspace_bytes
+        per_ray = wsb(Dims(1, self.n_r, self.n_e, N_SPECIES), precision)
         if max_ws_bytes is None:
             free, _ = torch.cuda.mem_get_info()
             max_ws_bytes = free // 2
         self.chunk = max(1, min(self.n_ray, int(max_ws_bytes // max(per_ray, 1))))
-        nbytes = mgfld_workspace_bytes(Dims(self.chunk, self.n_r, self.n_e, N_SPECIES), precision)
+        nbytes = wsb(Dims(self.chunk, self.n_r, self.n_e, N_SPECIES), precision)
         self.ws = torch.empty(nbytes, dtype=torch.uint8, device=device)
         self.report = dict(iters=torch.zeros(self.n_ray, dtype=torch.int32, device=device),
                            ray_status=torch.zeros(self.n_ray, dtype=torch.int32, device=device),

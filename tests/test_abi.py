@@ -94,6 +94,26 @@ def test_argument_errors_are_reported_before_any_launch(L):
     assert _call_step(L, d, _prob(), M.step_opts(tol=0.0), base, need) == M.MGFLD_EINVAL
 
 
+def test_pair_process_arguments(L):
+    """The pair process: coupled (nu, antinu) blocks need the pair workspace, at most 24 groups, and
+    the frozen flux coefficients; refused on the host before any launch otherwise."""
+    d = M.Dims(2, 8, 5, 4)
+    base = 0x7f0000000000
+    for prec in (M.MGFLD_FP64, M.MGFLD_MIXED):
+        plain, paired = M.mgfld_workspace_bytes(d, prec), M.mgfld_workspace_bytes_pair(d, prec)
+        # twice the dense blocks and factors, plus the creation and four annihilation kernels per zone
+        blk = (8 if prec == M.MGFLD_FP64 else 4) * 2 * 4 * 8 * 5 * 5
+        assert paired >= plain + 2 * blk + 8 * 2 * 8 * 5 * 5 * 5
+    assert M.mgfld_workspace_bytes_pair(M.Dims(1, 4, 25, 4), 0) == 0
+    assert M.mgfld_workspace_bytes_pair(M.Dims(1, 4, 24, 4), 0) > 0
+    p = _prob()
+    p.pair_coef = ctypes.c_void_p(0x90000)
+    need = M.mgfld_workspace_bytes_pair(d, 0)
+    assert _call_step(L, d, p, M.step_opts(), base, need - 1) == M.MGFLD_ENOMEM
+    assert _call_step(L, d, p, M.step_opts(coef_iterate=True), base, need) == M.MGFLD_EINVAL
+    assert _call_step(L, M.Dims(2, 8, 25, 4), p, M.step_opts(), base, 1 << 40) == M.MGFLD_EINVAL
+
+
 def test_status_strings(L):
     assert M.status_str(M.MGFLD_OK) == 'ok'
     assert 'converge' in M.status_str(M.MGFLD_ENOCONV)
@@ -125,7 +145,7 @@ def test_other_entry_points_check_their_arguments_before_any_launch(L):
     assert assemble(system=M.System(_fake(4), None, _fake(6), _fake(7))) == M.MGFLD_EINVAL
     paired = _prob()
     paired.pair_coef = _fake(9)
-    assert assemble(prob=paired) == M.MGFLD_EINVAL            # species-pair blocks are not built
+    assert assemble(prob=paired) == M.MGFLD_EINVAL            # its system is per species: use mgfld_step
 
     for prec in (-1, 2):
         assert L.mgfld_factor(R(d), R(sysm), prec, _fake(8), None) == M.MGFLD_EINVAL

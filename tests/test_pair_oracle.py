@@ -7,7 +7,8 @@
 * The process makes and destroys neutrinos in pairs: each flavour's lepton number is untouched
   for any occupations, so a full step conserves lepton number (and energy with matter) exactly.
 * The Jacobian, now coupling the partner species, equals central differences of the residual.
-* Switching the process on changes the result (it is not inert in the cases below)."""
+* Switching the process on changes the result (it is not inert in the cases below).
+The GPU's coupled pair systems are checked against this oracle in tests/test_gpu_pair.py."""
 import numpy as np
 import pytest
 
@@ -117,18 +118,16 @@ def test_adjoint_refuses_pairs_before_touching_the_device():
     assert rc == M.MGFLD_EINVAL
 
 
-def test_gpu_step_refuses_the_pair_process():
-    """The library's per-species blocks do not hold the partner coupling: mgfld_step and
-    mgfld_assemble refuse a problem with pair_coef in their argument checks (host only)."""
+def test_gpu_assemble_refuses_the_pair_process():
+    """mgfld_assemble writes the per-species system, which has no partner coupling: it refuses a
+    problem with pair_coef in its argument checks (host only); mgfld_step takes the process with
+    its coupled pair systems (tests/test_gpu_pair.py)."""
     import ctypes
     from paper_1809_05608_gb300 import mgfld as M
     fake = ctypes.c_void_p(0x10000)
     prob = M.Problem(*[fake] * 8, M.lib().mgfld_eos_default(), 1e-6, 0, None, None, fake)
     st = M.State(fake, fake, fake)
     dims = M.Dims(1, 8, 4, 4)
-    rc = M.lib().mgfld_step(ctypes.byref(dims), ctypes.byref(prob), ctypes.byref(st),
-                            ctypes.byref(M.step_opts()), None, ctypes.c_void_p(0x100000), 1 << 30, None)
-    assert rc == M.MGFLD_EINVAL
     sys_ = M.System(fake, fake, fake, fake)
     rc = M.lib().mgfld_assemble(ctypes.byref(dims), ctypes.byref(prob), ctypes.byref(st), ctypes.byref(sys_),
                                 ctypes.c_void_p(0x100000), 1 << 30, None)
