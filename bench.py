@@ -217,31 +217,25 @@ def traffic_record(kernel):
 
 def run_path(M, torch, inp, precision, steps, warmup, barrier, clocks=None, refactor_ratio=None,
              coef_iterate=False, keep=False):
-    """Time `steps` implicit steps of one path after `warmup` untimed ones.  The timed loop runs
-    with per-category CUDA events (mgfld_step_opts.profile) so that each kernel category's device
-    time inside the timed region is known.  The stepper (workspace) is released unless `keep`."""
+    """Time `steps` implicit steps of one path after `warmup` untimed ones.  The timed loop calls
+    mgfld_step as a user does: asynchronous on the stream (the whole step one CUDA graph, its outer
+    iteration a device-side loop), no host synchronisation between steps, CUDA events on the
+    stream around the loop.  A second pass of `steps` steps then runs with per-category CUDA events
+    (mgfld_step_opts.profile, which drives the outer iteration from the host) for the kernel times
+    of the rooflines.  The stepper (workspace) is released unless `keep`."""
     st = M.Stepper(inp, precision, tol=TOL, max_iter=60, refactor_ratio=refactor_ratio, coef_iterate=coef_iterate)
     if clocks:
         clocks.start()
     psi, ye, T = st.state_to_device(inp['psi0'], inp['ye0'], inp['T0'])
     stream = torch.cuda.current_stream()
-    prof = (ctypes.c_double * 12)()
     nfact = torch.zeros_like(st.report['factorizations'])
     iters = torch.zeros_like(st.report['iters'])
-    for wi in range(warmup):
-        # The warm-up runs exactly what the timed loop runs (profiling events, report sums),
-        # so that one-time costs (lazy module loading, event creation) stay outside the timing.
-        st.opts.profile = ctypes.cast(prof, ctypes.c_void_p) if wi == warmup - 1 else None
-        rc = st.step(psi, ye, T)
+    for _ in range(warmup):
+        # the same call as the timed loop (the first builds and caches the step's graph)
+        rc = st.step(psi, ye, T, wait=False)
         assert rc == M.MGFLD_OK, M.status_str(rc)
-        nfact += st.report['factorizations']
-        iters += st.report['iters']
+    assert st.worst_status() == M.MGFLD_OK
     torch.cuda.synchronize()
-    for c in range(12):
-        prof[c] = 0.0
-    nfact.zero_()
-    iters.zero_()
-    st.opts.profile = ctypes.cast(prof, ctypes.c_void_p)
     barrier()
     torch.cuda.synchronize()
     t_start = time.time()
@@ -249,7 +243,7 @@ def run_path(M, torch, inp, precision, steps, warmup, barrier, clocks=None, refa
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(steps):
-        rc = st.step(psi, ye, T)
+        rc = st.step(psi, ye, T, wait=False)
         assert rc == M.MGFLD_OK, M.status_str(rc)
         nfact += st.report['factorizations']
         iters += st.report['iters']
@@ -262,12 +256,32 @@ def run_path(M, torch, inp, precision, steps, warmup, barrier, clocks=None, refa
         clk = clocks.stop()
     barrier()
     ms = e0.elapsed_time(e1)
+    assert st.worst_status() == M.MGFLD_OK
+    # the profiled pass: per-category kernel times (and the unit counts they belong to)
+    prof = (ctypes.c_double * 12)()
+    st.opts.profile = ctypes.cast(prof, ctypes.c_void_p)
+    rc = st.step(psi, ye, T)                      # event creation outside the counted pass
+    assert rc == M.MGFLD_OK, M.status_str(rc)
+    for c in range(12):
+        prof[c] = 0.0
+    pfact = torch.zeros_like(nfact)
+    piters = torch.zeros_like(iters)
+    torch.cuda.synchronize()
+    p0 = time.perf_counter()
+    for _ in range(steps):
+        rc = st.step(psi, ye, T)
+        assert rc == M.MGFLD_OK, M.status_str(rc)
+        pfact += st.report['factorizations']
+        piters += st.report['iters']
+    torch.cuda.synchronize()
+    p_ms = (time.perf_counter() - p0) * 1e3
     st.opts.profile = None
     prof = {name: dict(ms=prof[2 * c], launches=int(prof[2 * c + 1])) for c, name in enumerate(M.PROF_NAMES)}
     ws_gb = (st.ws.numel() + sum(t.numel() * 8 for t in st.prob.t.values() if t is not None)) / 1e9
-    out = dict(ms=ms, steps=steps, prof=prof, nfact=int(nfact.sum()), iters=int(iters.sum()),
+    out = dict(ms=ms, steps=steps, prof=prof, nfact=int(pfact.sum()), iters=int(piters.sum()),
+               timed_nfact=int(nfact.sum()), timed_iters=int(iters.sum()),
                max_iters=int(st.report['iters'].max()), iters_hist=np.bincount(iters.cpu().numpy()).tolist(),
-               clocks=clk, chunk=st.chunk, ws_gb=ws_gb, n_ray=st.n_ray)
+               clocks=clk, chunk=st.chunk, ws_gb=ws_gb, n_ray=st.n_ray, profiled_ms=p_ms)
     if keep:
         out['stepper'] = st
         out['state'] = (psi, ye, T)
@@ -432,6 +446,7 @@ def step_roofline(res, inp, precision):
         tot32 += F32
         totb += B
     steps = res['steps']
+    # per-step scale of the profiled pass's units (the timed pass ran the same workload)
     for base, c in cats.items():
         bound = max(('fp64', c['t64']), ('fp32', c['t32']), ('hbm', c['tb']), key=lambda v: v[1])
         c['bound'] = bound[0]
@@ -498,7 +513,7 @@ def e2e_run(M, torch, inp, precision, steps):
         src = hs if s == 0 else out
         for d, h in zip(dev, src):
             d.copy_(h, non_blocking=True)
-        rc = st.step(*dev)
+        rc = st.step(*dev, wait=False)            # asynchronous: the next uploads overlap it
         assert rc == M.MGFLD_OK, M.status_str(rc)
         free[b].record(stream)
         for o, d in zip(out, dev):
@@ -506,6 +521,7 @@ def e2e_run(M, torch, inp, precision, steps):
     e1.record(stream)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
+    assert st.worst_status() == M.MGFLD_OK
     st.prob = bufs[0]
     del st, bufs, dev
     torch.cuda.empty_cache()
@@ -859,7 +875,9 @@ def main():
     e2e = e2e_run(M, torch, inp, M.MGFLD_MIXED, args.steps)
     e2e_ms = max_over_ranks(e2e['ms']) / args.steps
     roof = roofline_for(mixed, inp, M.MGFLD_MIXED)
-    launches = sum(v['launches'] for v in mixed['prof'].values())
+    # library kernels in the timed region: those of the profiled pass (the same kernels per
+    # iteration), plus the graph's loop-condition kernel per iteration and its status kernel per step
+    launches = sum(v['launches'] for v in mixed['prof'].values()) + args.steps * (mixed['max_iters'] + 1)
     extra = {}
     if not args.no_extra:
         # the 3D-scale configuration: 4096 rays x 540 x 20, its rays sharded over the ranks
@@ -945,6 +963,10 @@ def main():
         e2e=dict(value=job_throughput(ups, ws, e2e_ms), unit=UNIT, h2d_bytes_per_step=e2e['h2d'],
                  d2h_bytes_per_step=e2e['d2h']),
         gpu_launches=launches,
+        timing='mgfld_step as a user calls it: asynchronous on the stream (one CUDA graph per step, its outer '
+               'iteration a device-side while loop), no host synchronisation inside the timed loop; kernel_ms and '
+               'the rooflines from a second pass of the same number of steps with per-category CUDA events',
+        profiled_ms_per_step=mixed['profiled_ms'] / args.steps,
         kernel_ms={k: v['ms'] for k, v in mixed['prof'].items()},
         iterations_histogram=mixed['iters_hist'],
         fp64_path=path_summary(fp64, inp, M.MGFLD_FP64, ws, ms_fp64, ups, n_rays_rank, dtype='f64',

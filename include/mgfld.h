@@ -22,7 +22,8 @@
  *     n_ray * n_s * n_r * n_e < 2^31 (EINVAL otherwise; split the rays).
  *   - Units: cm, s, g/cm^3, MeV (T is kT in MeV).
  *   - Every call is asynchronous on `stream` (a cudaStream_t passed as void*;
- *     NULL is the legacy default stream) except where stated.
+ *     NULL is the legacy default stream) except where stated (mgfld_step with
+ *     profiling, mgfld_step_noalloc and mgfld_adjoint synchronise it).
  *   - Errors are returned as mgfld_status; nothing aborts, throws or traps.
  *     Argument errors are detected on the host before any launch.
  */
@@ -154,6 +155,10 @@ typedef struct {
                           after, lost, residual (Eqs. a60-a62 with a62a, a62b) */
   double *heating;     /* [n_ray] MeV deposited in matter by nu_e + nubar_e between 100 and 300 km */
   int *factorizations; /* [n_ray] number of block factorisations performed */
+  int *status;         /* [1] the step's status once it has run on the stream: the worst ray status
+                          (ENAN before ENOCONV), ECUDA if a bounded wait of the substitution gave
+                          up, else OK.  mgfld_step returns before the step has run, so this is
+                          where a caller reads non-convergence (after synchronising the stream) */
 } mgfld_step_report;
 
 /* Bytes of workspace mgfld_step needs for these dimensions and precision. */
@@ -170,12 +175,24 @@ size_t mgfld_workspace_bytes_pair(const mgfld_dims *dims, int precision);
  *   dims, prob, opts: as above (host structs holding device pointers).
  *   state: psi^n, Ye^n, T^n on entry; psi^{n+1}, Ye^{n+1}, T^{n+1} on exit.
  *   report: optional per-ray outputs (device); may be NULL.
- *   ws, ws_bytes: device workspace of at least mgfld_workspace_bytes() bytes,
- *   256-byte aligned; its contents are scratch.
- * The outer iteration tests convergence on the host once per iteration, so
- * this call synchronises `stream` once per outer iteration.
- * Returns OK, EINVAL, ENOMEM, ECUDA, or the worst ray status (ENAN before
- * ENOCONV).  Rays that fail keep their last iterate.
+ *   ws, ws_bytes: device workspace of at least mgfld_workspace_bytes() bytes
+ *   (mgfld_workspace_bytes_pair() with the pair process), 256-byte aligned; its
+ *   contents are scratch.
+ * Asynchronous on `stream`: the whole step (set-up, outer iteration, finish) is
+ * one CUDA graph launched on the stream, its outer iteration a device-side loop
+ * (a while-conditional node whose condition the convergence test sets after each
+ * iteration), so nothing waits on the host and the call returns before the step
+ * has run.  The graph of each distinct set of arguments (pointers, sizes,
+ * options) is built on its first call, with a CUDA graph capture on streams of
+ * the library's own, and kept for the life of the process; that first call must
+ * not be made while the calling thread is capturing.  The call returns OK,
+ * EINVAL, ENOMEM or ECUDA (argument and launch errors); the per-ray statuses,
+ * iteration counts and ledgers, and the step's worst status (report->status:
+ * ENAN before ENOCONV, ECUDA if a bounded wait gave up) are written on the
+ * stream.  Rays that fail keep their last iterate.
+ * With opts->profile set the outer iteration runs from the host instead (one
+ * stream synchronisation per iteration, for the per-category events) and the
+ * call returns the worst ray status as well.
  */
 mgfld_status mgfld_step(const mgfld_dims *dims, const mgfld_problem *prob, mgfld_state *state,
                         const mgfld_step_opts *opts, mgfld_step_report *report,
@@ -248,11 +265,14 @@ mgfld_status mgfld_solve(const mgfld_dims *dims, const mgfld_system *sys, int pr
  * that cannot afford the device synchronisation of cudaMalloc/cudaFree.  The step's
  * scratch is a fixed array of MGFLD_NOALLOC_SCRATCH_BYTES in the library's device
  * image, kept by every GPU that loads the library until the process exits; nothing is
- * allocated or freed by this call.  Inputs and outputs are the caller's, as for
- * mgfld_step.
- *   - Returns MGFLD_ENOMEM, before touching the GPU, when mgfld_workspace_bytes(dims,
- *     opts->precision) exceeds MGFLD_NOALLOC_SCRATCH_BYTES (at 512 zones x 20 groups: more
- *     than 2 rays in FP64, more than 3 in MIXED); split the rays into several calls.
+ * allocated or freed by this call, and no CUDA graph is created: the outer iteration runs
+ * from the host (one stream synchronisation per iteration) and the call returns the worst
+ * ray status, as mgfld_step does with profiling.  Inputs and outputs are the caller's, as
+ * for mgfld_step.
+ *   - Returns MGFLD_ENOMEM, before touching the GPU, when the step's workspace
+ *     (mgfld_workspace_bytes, or mgfld_workspace_bytes_pair with the pair process) exceeds
+ *     MGFLD_NOALLOC_SCRATCH_BYTES (at 512 zones x 20 groups: more than 2 rays in FP64, more
+ *     than 3 in MIXED); split the rays into several calls.
  *   - Returns MGFLD_EINVAL if opts->profile is set (timing would create CUDA events).
  *   - Every call looks up the array's device address on the current device (nothing is
  *     cached, so a context reset between calls is harmless); the first call on a device

@@ -37,6 +37,7 @@ class AdjointRunner:
         self.ws = torch.empty(nbytes, dtype=torch.uint8, device=device)
         self.heating = torch.zeros(self.n_ray, dtype=torch.float64, device=device)
         self.ray_status = torch.zeros(self.n_ray, dtype=torch.int32, device=device)
+        self.status = torch.zeros(1, dtype=torch.int32, device=device)
         self.checkpoint_every = max(1, int(checkpoint_every))
         self.max_sweeps, self.sweep_tol = int(max_sweeps), float(sweep_tol)
         self.sweeps = []
@@ -48,7 +49,9 @@ class AdjointRunner:
 
     def _step(self, ps, psi, ye, T):
         rc = M.mgfld_step(self.dims, ps, psi, ye, T, self.opts, self.ws,
-                          dict(heating=self.heating, ray_status=self.ray_status))
+                          dict(heating=self.heating, ray_status=self.ray_status, status=self.status))
+        if rc == M.MGFLD_OK:
+            rc = int(self.status.item())          # the step's own status (waits for it)
         if rc != M.MGFLD_OK:
             raise M.MgfldError(rc, 'mgfld_step')
         return self.heating.sum()

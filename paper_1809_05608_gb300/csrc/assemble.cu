@@ -17,12 +17,12 @@ template <typename TD>
 __global__ void k_assemble(Prob p, Ws w, const double *__restrict__ psi, TD *__restrict__ diag,
                            double *__restrict__ lower, double *__restrict__ upper, double *__restrict__ rhs,
                            const int *__restrict__ list, int n_list, const int *__restrict__ jac_flag,
-                           double *__restrict__ src_out, int first) {
+                           double *__restrict__ src_out, int first, const int *__restrict__ n_dev) {
   const int n = p.n;
   // 32-bit index arithmetic (element counts are below 2^31, checked on the host).
   const unsigned per_ray = (unsigned)(NS * p.n_r * n);
   const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= (unsigned)n_list * per_ray) return;
+  if (t >= (unsigned)listed(n_list, n_dev) * per_ray) return;
   const unsigned rl = t / per_ray;
   const int ray = list ? list[rl] : (int)rl;
   // Thread order (zone, species, group) inside a ray: the four species of a zone share the
@@ -184,17 +184,17 @@ __global__ void k_assemble(Prob p, Ws w, const double *__restrict__ psi, TD *__r
 
 cudaError_t launch_assemble(const Prob &p, const Ws &w, const double *psi, void *diag, int diag_fp32,
                             double *lower, double *upper, double *rhs, const int *list, int n_list,
-                            const int *jac_flag, cudaStream_t s, double *src_out, int first) {
+                            const int *jac_flag, cudaStream_t s, double *src_out, int first, const int *n_dev) {
   const size_t total = (size_t)n_list * NS * p.n_r * p.n;
   if (total == 0) return cudaSuccess;
   const unsigned B = 256;
   const unsigned grid = (unsigned)((total + B - 1) / B);
   if (diag_fp32)
     k_assemble<float><<<grid, B, 0, s>>>(p, w, psi, (float *)diag, lower, upper, rhs, list, n_list, jac_flag,
-                                         src_out, first);
+                                         src_out, first, n_dev);
   else
     k_assemble<double><<<grid, B, 0, s>>>(p, w, psi, (double *)diag, lower, upper, rhs, list, n_list,
-                                          jac_flag, src_out, first);
+                                          jac_flag, src_out, first, n_dev);
   return cudaGetLastError();
 }
 

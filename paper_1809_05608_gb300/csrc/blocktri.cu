@@ -96,7 +96,8 @@ template <> __device__ inline float to_t<float>(double v) { return (float)v; }
 template <int NP, typename TIn>
 __global__ void __launch_bounds__(Pack<NP>::THREADS)
 k_factor(int n, int n_r, int n_sys, const TIn *__restrict__ diag, const double *__restrict__ lower,
-         const double *__restrict__ upper, double *__restrict__ dinv, const int *__restrict__ ray_list) {
+         const double *__restrict__ upper, double *__restrict__ dinv, const int *__restrict__ ray_list,
+         const int *__restrict__ n_dev) {
   constexpr int SPC = Pack<NP>::SPC;
   __shared__ double tile[SPC][NP][NP + 1];           // natural-order inverse of the previous zone
   __shared__ __align__(16) double prow[SPC][NP];     // pivot row of the current step
@@ -107,8 +108,10 @@ k_factor(int n, int n_r, int n_sys, const TIn *__restrict__ diag, const double *
 
   const int s = threadIdx.x / NP, r = threadIdx.x % NP;
   const int half = s & 1;                            // 0: zones 0..m top-down, 1: zones n_r-1..m+1 bottom-up
+  const int n_sys_e = listed_sys(n_sys, n_dev, NS);
+  if ((long)blockIdx.x * (SPC / 2) >= n_sys_e) return;   // the whole CTA
   const long jsys = (long)blockIdx.x * (SPC / 2) + (s >> 1);
-  const bool valid = jsys < n_sys;
+  const bool valid = jsys < n_sys_e;
   const long sys = valid ? system_of(jsys, ray_list) : 0;
   const int m = n_r / 2;
   const int len = half == 0 ? m + 1 : n_r - 1 - m;   // zones of this half; all threads step m + 1 times
@@ -217,14 +220,17 @@ k_factor(int n, int n_r, int n_sys, const TIn *__restrict__ diag, const double *
 template <int NP>
 __global__ void __launch_bounds__(Pack<NP>::THREADS)
 k_solve(int n, int n_r, int n_sys, const double *__restrict__ dinv, const double *__restrict__ lower,
-        const double *__restrict__ upper, const double *rhs, double *x, const int *__restrict__ ray_list) {
+        const double *__restrict__ upper, const double *rhs, double *x, const int *__restrict__ ray_list,
+        const int *__restrict__ n_dev) {
   constexpr int SPC = Pack<NP>::SPC;
   __shared__ double v[SPC][NP];
   __shared__ double mid[SPC / 2][NP];               // h_{m+1}, then x_m
   const int s = threadIdx.x / NP, r = threadIdx.x % NP;
   const int half = s & 1, sl = s >> 1;
+  const int n_sys_e = listed_sys(n_sys, n_dev, NS);
+  if ((long)blockIdx.x * (SPC / 2) >= n_sys_e) return;   // the whole CTA
   const long jsys = (long)blockIdx.x * (SPC / 2) + sl;
-  const bool valid = jsys < n_sys;
+  const bool valid = jsys < n_sys_e;
   const long sys = valid ? system_of(jsys, ray_list) : 0;
   const bool realr = valid && r < n;
   const size_t base = (size_t)sys * n_r * n;
@@ -344,7 +350,8 @@ __device__ inline float recip_t(float d) {
 template <int NP, typename TIn, typename T>
 __global__ void __launch_bounds__(RowCta<NP, T>::THREADS)
 k_factor_rows(int n, int n_r, int n_sys, int spr, const TIn *__restrict__ diag, const T *__restrict__ lower,
-              const T *__restrict__ upper, T *__restrict__ dinv, const int *__restrict__ ray_list) {
+              const T *__restrict__ upper, T *__restrict__ dinv, const int *__restrict__ ray_list,
+              const int *__restrict__ n_dev) {
   using C = RowCta<NP, T>;
   constexpr int SPC = C::SPC, KB = C::KB;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -358,8 +365,10 @@ k_factor_rows(int n, int n_r, int n_sys, int spr, const TIn *__restrict__ diag, 
 
   const int s = threadIdx.x / NP, r = threadIdx.x % NP;
   const int half = s & 1;                            // 0: zones 0..m top-down, 1: zones n_r-1..m+1 bottom-up
+  const int n_sys_e = listed_sys(n_sys, n_dev, spr);
+  if ((long)blockIdx.x * (SPC / 2) >= n_sys_e) return;   // the whole CTA
   const long jsys = (long)blockIdx.x * (SPC / 2) + (s >> 1);
-  const bool valid = jsys < n_sys;
+  const bool valid = jsys < n_sys_e;
   const long sys = valid ? system_of_spr(jsys, ray_list, spr) : 0;
   const int m = n_r / 2;
   const int len = half == 0 ? m + 1 : n_r - 1 - m;   // zones of this half; all threads step m + 1 times
@@ -453,14 +462,17 @@ template <int NP, typename T>
 __global__ void __launch_bounds__(RowCta<NP, T>::THREADS)
 k_solve_rows(int n, int n_r, int n_sys, int spr, const T *__restrict__ dinv, const T *__restrict__ lower,
              const T *__restrict__ upper, const double *rhs, const float *__restrict__ rhs32,
-             const int *__restrict__ sys_exp, double *x, const int *__restrict__ ray_list) {
+             const int *__restrict__ sys_exp, double *x, const int *__restrict__ ray_list,
+             const int *__restrict__ n_dev) {
   constexpr int SPC = RowCta<NP, T>::SPC;
   __shared__ T v[SPC][NP];
   __shared__ T mid[SPC / 2][NP];
   const int s = threadIdx.x / NP, r = threadIdx.x % NP;
   const int half = s & 1, sl = s >> 1;
+  const int n_sys_e = listed_sys(n_sys, n_dev, spr);
+  if ((long)blockIdx.x * (SPC / 2) >= n_sys_e) return;   // the whole CTA
   const long jsys = (long)blockIdx.x * (SPC / 2) + sl;
-  const bool valid = jsys < n_sys;
+  const bool valid = jsys < n_sys_e;
   const long sys = valid ? system_of_spr(jsys, ray_list, spr) : 0;
   const bool realr = valid && r < n;
   const size_t base = (size_t)sys * n_r * n;
@@ -723,7 +735,8 @@ template <int NP> __host__ __device__ constexpr int fw_wpc() { return NP > 24 ? 
 template <int NP, typename TIn, typename TC, bool PIVOT>
 __global__ void __launch_bounds__(fw_wpc<NP>() * 32, MGFLD_FW32_MINB)
 k_factor_w32(int n, int n_r, int n_sys, const TIn *__restrict__ diag, const TC *__restrict__ lower,
-             const TC *__restrict__ upper, float *__restrict__ dinv, const int *__restrict__ ray_list) {
+             const TC *__restrict__ upper, float *__restrict__ dinv, const int *__restrict__ ray_list,
+             const int *__restrict__ n_dev) {
   static_assert(NP % 4 == 0, "rows of NP floats in 16-byte pieces");
   // tile: the natural-order inverse of each warp's last zone (read by the other half at the
   // middle zone); ushr: that zone's coupling to the next zone of the sequence; prow: pivot rows.
@@ -737,7 +750,7 @@ k_factor_w32(int n, int n_r, int n_sys, const TIn *__restrict__ diag, const TC *
   const int wid = threadIdx.x >> 5, r = threadIdx.x & 31;
   const int half = wid & 1;                          // 0: zones 0..m top-down, 1: zones n_r-1..m+1 bottom-up
   const long jsys = (long)blockIdx.x * (W / 2) + (wid >> 1);
-  if (jsys >= n_sys) return;                        // both warps of the system leave; no barrier below
+  if (jsys >= listed_sys(n_sys, n_dev, NS)) return;  // both warps of the system leave; no barrier below
   const long sys = system_of(jsys, ray_list);
   const bool real = r < n;
   const bool row = r < NP;
@@ -875,13 +888,13 @@ template <int NP>
 __global__ void __launch_bounds__(kWarpsPerCta * 32)
 k_solve_w32(int n, int n_r, int n_sys, const float *__restrict__ dinv, const double *__restrict__ lower,
             const double *__restrict__ upper, const double *__restrict__ rhs, double *__restrict__ x,
-            const int *__restrict__ ray_list) {
+            const int *__restrict__ ray_list, const int *__restrict__ n_dev) {
   __shared__ float hbuf[kWarpsPerCta / 2][32], xbuf[kWarpsPerCta / 2][32];
   const unsigned full = 0xffffffffu;
   const int wid = threadIdx.x >> 5, r = threadIdx.x & 31;
   const int half = wid & 1, slot = wid >> 1;
   const long jsys = (long)blockIdx.x * (kWarpsPerCta / 2) + slot;
-  if (jsys >= n_sys) return;
+  if (jsys >= listed_sys(n_sys, n_dev, NS)) return;
   const long sys = system_of(jsys, ray_list);
   const bool real = r < n;
   const size_t base = (size_t)sys * n_r * n;
@@ -1011,9 +1024,10 @@ __device__ inline bool mbar_wait_bounded(unsigned long long *bar, unsigned parit
 // the substitution reads FP32 values.  One CTA per listed system; its n_r x n right-hand side is
 // contiguous (coalesced loads; the second pass reads it from L2).
 __global__ void k_sysmax(int n, int n_r, const double *__restrict__ rhs, const int *__restrict__ ray_list,
-                         int *__restrict__ sys_exp, float *__restrict__ rhs32) {
+                         int *__restrict__ sys_exp, float *__restrict__ rhs32, const int *__restrict__ n_dev) {
   __shared__ double red[256];
   __shared__ int kexp_s;
+  if ((int)blockIdx.x >= listed_sys(gridDim.x, n_dev, NS)) return;    // the whole block
   const long sys = system_of(blockIdx.x, ray_list);
   const size_t base = (size_t)sys * n_r * n;
   const unsigned cnt = (unsigned)(n_r * n);
@@ -1040,9 +1054,10 @@ __global__ void k_sysmax(int n, int n_r, const double *__restrict__ rhs, const i
 
 // k_sysmax for systems listed with `spr` systems per ray.
 __global__ void k_sysmax_spr(int n, int n_r, const double *__restrict__ rhs, const int *__restrict__ ray_list, int spr,
-                             int *__restrict__ sys_exp, float *__restrict__ rhs32) {
+                             int *__restrict__ sys_exp, float *__restrict__ rhs32, const int *__restrict__ n_dev) {
   __shared__ double red[256];
   __shared__ int kexp_s;
+  if ((int)blockIdx.x >= listed_sys(gridDim.x, n_dev, spr)) return;   // the whole block
   const long sys = system_of_spr(blockIdx.x, ray_list, spr);
   const size_t base = (size_t)sys * n_r * n;
   const unsigned cnt = (unsigned)(n_r * n);
@@ -1106,7 +1121,8 @@ template <int NP, bool VEC>
 __global__ void __launch_bounds__(SolveRing<NP>::WPC * 32)
 k_solve_tma(int n, int n_r, int n_sys, const float *__restrict__ dinv, const float *__restrict__ lower,
             const float *__restrict__ upper, const float *__restrict__ rhs32, double *__restrict__ x,
-            float *__restrict__ g32, const int *__restrict__ ray_list, const int *__restrict__ sys_exp, int *err) {
+            float *__restrict__ g32, const int *__restrict__ ray_list, const int *__restrict__ sys_exp, int *err,
+            const int *__restrict__ n_dev) {
   using R = SolveRing<NP>;
   static_assert(R::WPC == 2, "one system per CTA: two warps, one per half");
   constexpr int S = R::STAGES;
@@ -1120,7 +1136,7 @@ k_solve_tma(int n, int n_r, int n_sys, const float *__restrict__ dinv, const flo
   const unsigned full = 0xffffffffu;
   const int half = threadIdx.x >> 5, r = threadIdx.x & 31;
   const long jsys = blockIdx.x;
-  if (jsys >= n_sys) return;                                // whole CTA
+  if (jsys >= listed_sys(n_sys, n_dev, NS)) return;         // whole CTA
   const long sys = system_of(jsys, ray_list);
   const bool real = r < n;
   const int rr = real ? r : 0;                              // lanes without a row use row 0 (unused)
@@ -1270,68 +1286,69 @@ k_solve_tma(int n, int n_r, int n_sys, const float *__restrict__ dinv, const flo
 
 cudaError_t launch_solve_tma(int n, int n_r, int n_sys, const void *dinv, const float *lower32,
                              const float *upper32, const double *rhs, float *rhs32, double *x, float *g32,
-                             const int *ray_list, int *sys_exp, int *err, cudaStream_t s) {
+                             const int *ray_list, int *sys_exp, int *err, cudaStream_t s, const int *n_dev) {
   if (n_sys == 0) return cudaSuccess;
-  k_sysmax<<<n_sys, 256, 0, s>>>(n, n_r, rhs, ray_list, sys_exp, rhs32);
+  k_sysmax<<<n_sys, 256, 0, s>>>(n, n_r, rhs, ray_list, sys_exp, rhs32, n_dev);
   MGFLD_DISPATCH_NP(n, {
     using R = SolveRing<NP>;
     const unsigned grid = (unsigned)n_sys;                 // one system (two warps) per CTA
     if (n == NP)
       k_solve_tma<NP, true><<<grid, R::WPC * 32, 0, s>>>(n, n_r, n_sys, (const float *)dinv, lower32, upper32, rhs32,
-                                                         x, g32, ray_list, sys_exp, err);
+                                                         x, g32, ray_list, sys_exp, err, n_dev);
     else
       k_solve_tma<NP, false><<<grid, R::WPC * 32, 0, s>>>(n, n_r, n_sys, (const float *)dinv, lower32, upper32,
-                                                          rhs32, x, g32, ray_list, sys_exp, err);
+                                                          rhs32, x, g32, ray_list, sys_exp, err, n_dev);
     return cudaGetLastError();
   })
 }
 
 template <int NP>
 static cudaError_t run_factor(int n, int n_r, int n_sys, const void *diag, int diag_fp32, const double *lower,
-                              const double *upper, void *dinv, const int *ray_list, cudaStream_t s) {
+                              const double *upper, void *dinv, const int *ray_list, cudaStream_t s,
+                              const int *n_dev) {
   constexpr int SPS = Pack<NP>::SPC / 2;             // systems per CTA
   const unsigned grid = (unsigned)((n_sys + SPS - 1) / SPS);
   if (diag_fp32)
     k_factor<NP, float><<<grid, Pack<NP>::THREADS, 0, s>>>(n, n_r, n_sys, (const float *)diag, lower, upper,
-                                                           (double *)dinv, ray_list);
+                                                           (double *)dinv, ray_list, n_dev);
   else
     k_factor<NP, double><<<grid, Pack<NP>::THREADS, 0, s>>>(n, n_r, n_sys, (const double *)diag, lower, upper,
-                                                            (double *)dinv, ray_list);
+                                                            (double *)dinv, ray_list, n_dev);
   return cudaGetLastError();
 }
 
 template <int NP>
 static cudaError_t run_solve(int n, int n_r, int n_sys, const void *dinv, const double *lower,
                              const double *upper, const double *rhs, double *x, const int *ray_list,
-                             cudaStream_t s) {
+                             cudaStream_t s, const int *n_dev) {
   constexpr int SPS = Pack<NP>::SPC / 2;             // systems per CTA
   const unsigned grid = (unsigned)((n_sys + SPS - 1) / SPS);
   k_solve<NP><<<grid, Pack<NP>::THREADS, 0, s>>>(n, n_r, n_sys, (const double *)dinv, lower, upper, rhs, x,
-                                                 ray_list);
+                                                 ray_list, n_dev);
   return cudaGetLastError();
 }
 
 cudaError_t launch_factor(int n, int n_r, int n_sys, const void *diag, int diag_fp32, const double *lower,
                           const double *upper, void *dinv, int precision, const int *ray_list,
-                          cudaStream_t s) {
+                          cudaStream_t s, const int *n_dev) {
   if (n_sys == 0) return cudaSuccess;
   if (precision == MGFLD_MIXED) {
     if (diag_fp32) {
       MGFLD_DISPATCH_NP(n, constexpr int W = fw_wpc<NP>();
                         const unsigned grid = (unsigned)((n_sys + W / 2 - 1) / (W / 2));
                         k_factor_w32<NP, float, double, true><<<grid, W * 32, 0, s>>>(
-                            n, n_r, n_sys, (const float *)diag, lower, upper, (float *)dinv, ray_list);
+                            n, n_r, n_sys, (const float *)diag, lower, upper, (float *)dinv, ray_list, n_dev);
                         return cudaGetLastError())
     } else {
       MGFLD_DISPATCH_NP(n, constexpr int W = fw_wpc<NP>();
                         const unsigned grid = (unsigned)((n_sys + W / 2 - 1) / (W / 2));
                         k_factor_w32<NP, double, double, true><<<grid, W * 32, 0, s>>>(
-                            n, n_r, n_sys, (const double *)diag, lower, upper, (float *)dinv, ray_list);
+                            n, n_r, n_sys, (const double *)diag, lower, upper, (float *)dinv, ray_list, n_dev);
                         return cudaGetLastError())
     }
   } else {
     MGFLD_DISPATCH_NP(n, return (run_factor<NP>(n, n_r, n_sys, diag, diag_fp32, lower, upper, dinv,
-                                                        ray_list, s)))
+                                                        ray_list, s, n_dev)))
   }
 }
 
@@ -1345,7 +1362,8 @@ cudaError_t launch_factor(int n, int n_r, int n_sys, const void *diag, int diag_
 
 template <int NP, typename TIn, typename T>
 static cudaError_t run_factor_rows(int nb, int n_r, int n_sys, int spr, const TIn *diag, const T *lower,
-                                   const T *upper, T *dinv, const int *ray_list, cudaStream_t s) {
+                                   const T *upper, T *dinv, const int *ray_list, cudaStream_t s,
+                                   const int *n_dev) {
   using C = RowCta<NP, T>;
   const unsigned grid = (unsigned)((n_sys + C::SPC / 2 - 1) / (C::SPC / 2));
   if (C::BYTES > 48 * 1024) {
@@ -1353,68 +1371,71 @@ static cudaError_t run_factor_rows(int nb, int n_r, int n_sys, int spr, const TI
                                                (int)C::BYTES);
     if (e != cudaSuccess) return e;
   }
-  k_factor_rows<NP, TIn, T><<<grid, C::THREADS, C::BYTES, s>>>(nb, n_r, n_sys, spr, diag, lower, upper, dinv, ray_list);
+  k_factor_rows<NP, TIn, T><<<grid, C::THREADS, C::BYTES, s>>>(nb, n_r, n_sys, spr, diag, lower, upper, dinv, ray_list,
+                                                               n_dev);
   return cudaGetLastError();
 }
 
 cudaError_t launch_factor_rows(int nb, int n_r, int n_sys, int spr, const void *diag, const void *lower,
-                               const void *upper, void *dinv, int fp32, const int *ray_list, cudaStream_t s) {
+                               const void *upper, void *dinv, int fp32, const int *ray_list, cudaStream_t s,
+                               const int *n_dev) {
   if (n_sys == 0) return cudaSuccess;
   if (nb > 48) return cudaErrorInvalidValue;
   if (fp32) {
     MGFLD_DISPATCH_NPW(nb, return (run_factor_rows<NP, float, float>(nb, n_r, n_sys, spr, (const float *)diag,
                                                                         (const float *)lower, (const float *)upper,
-                                                                        (float *)dinv, ray_list, s)))
+                                                                        (float *)dinv, ray_list, s, n_dev)))
   } else {
     MGFLD_DISPATCH_NPW(nb, return (run_factor_rows<NP, double, double>(nb, n_r, n_sys, spr, (const double *)diag,
                                                                           (const double *)lower, (const double *)upper,
-                                                                          (double *)dinv, ray_list, s)))
+                                                                          (double *)dinv, ray_list, s, n_dev)))
   }
 }
 
 cudaError_t launch_solve_rows(int nb, int n_r, int n_sys, int spr, const void *dinv, const void *lower,
                               const void *upper, const double *rhs, float *rhs32, int *sys_exp, double *x, int fp32,
-                              const int *ray_list, cudaStream_t s) {
+                              const int *ray_list, cudaStream_t s, const int *n_dev) {
   if (n_sys == 0) return cudaSuccess;
   if (nb > 48) return cudaErrorInvalidValue;
   if (fp32) {
     // per-system power-of-two scaling of the right-hand side for the FP32 sweeps
-    k_sysmax_spr<<<n_sys, 256, 0, s>>>(nb, n_r, rhs, ray_list, spr, sys_exp, rhs32);
+    k_sysmax_spr<<<n_sys, 256, 0, s>>>(nb, n_r, rhs, ray_list, spr, sys_exp, rhs32, n_dev);
     MGFLD_DISPATCH_NPW(nb, using C = RowCta<NP, float>;
                        k_solve_rows<NP, float><<<(unsigned)((n_sys + C::SPC / 2 - 1) / (C::SPC / 2)), C::THREADS, 0, s>>>(
                            nb, n_r, n_sys, spr, (const float *)dinv, (const float *)lower, (const float *)upper, rhs,
-                           rhs32, sys_exp, x, ray_list);
+                           rhs32, sys_exp, x, ray_list, n_dev);
                        return cudaGetLastError())
   } else {
     MGFLD_DISPATCH_NPW(nb, using C = RowCta<NP, double>;
                        k_solve_rows<NP, double><<<(unsigned)((n_sys + C::SPC / 2 - 1) / (C::SPC / 2)), C::THREADS, 0, s>>>(
                            nb, n_r, n_sys, spr, (const double *)dinv, (const double *)lower, (const double *)upper, rhs,
-                           nullptr, nullptr, x, ray_list);
+                           nullptr, nullptr, x, ray_list, n_dev);
                        return cudaGetLastError())
   }
 }
 
 cudaError_t launch_factor_f32(int n, int n_r, int n_sys, const float *diag, const float *lower32,
-                              const float *upper32, float *dinv, const int *ray_list, cudaStream_t s) {
+                              const float *upper32, float *dinv, const int *ray_list, cudaStream_t s,
+                              const int *n_dev) {
   if (n_sys == 0) return cudaSuccess;
   MGFLD_DISPATCH_NP(n, constexpr int W = fw_wpc<NP>();
                     const unsigned grid = (unsigned)((n_sys + W / 2 - 1) / (W / 2));
                     k_factor_w32<NP, float, float, false><<<grid, W * 32, 0, s>>>(n, n_r, n_sys, diag, lower32, upper32,
-                                                                            dinv, ray_list);
+                                                                            dinv, ray_list, n_dev);
                     return cudaGetLastError())
 }
 
 cudaError_t launch_solve(int n, int n_r, int n_sys, const void *dinv, const double *lower,
                          const double *upper, const double *rhs, double *x, int precision,
-                         const int *ray_list, cudaStream_t s) {
+                         const int *ray_list, cudaStream_t s, const int *n_dev) {
   if (n_sys == 0) return cudaSuccess;
   if (precision == MGFLD_MIXED) {
     const unsigned grid = (unsigned)((n_sys + kWarpsPerCta / 2 - 1) / (kWarpsPerCta / 2));
     MGFLD_DISPATCH_NP(n, k_solve_w32<NP><<<grid, kWarpsPerCta * 32, 0, s>>>(n, n_r, n_sys, (const float *)dinv,
-                                                                          lower, upper, rhs, x, ray_list);
+                                                                          lower, upper, rhs, x, ray_list, n_dev);
                          return cudaGetLastError())
   } else {
-    MGFLD_DISPATCH_NP(n, return (run_solve<NP>(n, n_r, n_sys, dinv, lower, upper, rhs, x, ray_list, s)))
+    MGFLD_DISPATCH_NP(n, return (run_solve<NP>(n, n_r, n_sys, dinv, lower, upper, rhs, x, ray_list, s, n_dev)))
   }
 }
 

@@ -59,6 +59,13 @@ struct Layout {
 // pair: the coupled nu / antinu systems of the pair process (wider blocks and the pair kernels).
 Layout make_layout(int n_ray, int n_r, int n, int precision, int pair = 0);
 
+// mgfld_step with the outer iteration driven from the host (one stream synchronisation per
+// iteration; returns the worst ray status): what mgfld_step does when profiling is requested,
+// and the path of the no-allocation entry point, which creates no graph.
+mgfld_status step_host_synchronised(const mgfld_dims *dims, const mgfld_problem *prob, mgfld_state *state,
+                                    const mgfld_step_opts *opts, mgfld_step_report *report, void *ws,
+                                    size_t ws_bytes, void *stream);
+
 // Argument checks and the device view of a caller's problem (shared by the C entry points).
 bool dims_ok(const mgfld_dims *d);
 bool prob_ok(const mgfld_problem *p);
@@ -220,15 +227,24 @@ cudaError_t launch_setup(const Prob &p, const Ws &w, const double *psi, const do
 // first: psi is still psi^n (first outer iteration), so the NES sums come from the setup (g0, l0).
 cudaError_t launch_assemble(const Prob &p, const Ws &w, const double *psi, void *diag, int diag_fp32,
                             double *lower, double *upper, double *rhs, const int *list, int n_list,
-                            const int *jac_flag, cudaStream_t s, double *src_out = nullptr, int first = 0);
+                            const int *jac_flag, cudaStream_t s, double *src_out = nullptr, int first = 0,
+                            const int *n_dev = nullptr);
 cudaError_t launch_factor(int n, int n_r, int n_sys, const void *diag, int diag_fp32, const double *lower,
                           const double *upper, void *dinv, int precision, const int *ray_list,
-                          cudaStream_t s);
+                          cudaStream_t s, const int *n_dev = nullptr);
 // MIXED-precision solve fed by bulk asynchronous copies; requires even n, 16-byte aligned
 // arrays and rhs != x.  Sets *err on a bounded-wait timeout.
 cudaError_t launch_solve_tma(int n, int n_r, int n_sys, const void *dinv, const float *lower32,
                              const float *upper32, const double *rhs, float *rhs32, double *x, float *g32,
-                             const int *ray_list, int *sys_exp, int *err, cudaStream_t s);
+                             const int *ray_list, int *sys_exp, int *err, cudaStream_t s,
+                             const int *n_dev = nullptr);
+
+// Count of a launch's listed rays: the host's n (the grid is sized for it) or, when the launch
+// belongs to an outer iteration that runs without the host, the device-resident count n_dev
+// (<= n; blocks past it return at once).
+__device__ inline int listed(int n, const int *n_dev) { return n_dev ? *n_dev : n; }
+// The same for a launch over systems, spr systems per listed ray.
+__device__ inline int listed_sys(int n_sys, const int *n_dev, int spr) { return n_dev ? *n_dev * spr : n_sys; }
 
 // Exact power-of-two rescaling between FP64 and FP32 by exponent arithmetic on the bit
 // patterns (integer pipe only; mantissa truncated to 24 bits; results below the FP32 normal
@@ -257,26 +273,29 @@ __device__ inline double f2d_exp2(float v, int k) {
 }
 // MIXED-precision factor with FP32 diagonal blocks and FP32 coupling coefficients.
 cudaError_t launch_factor_f32(int n, int n_r, int n_sys, const float *diag, const float *lower32,
-                              const float *upper32, float *dinv, const int *ray_list, cudaStream_t s);
+                              const float *upper32, float *dinv, const int *ray_list, cudaStream_t s,
+                              const int *n_dev = nullptr);
 // Pair process (pair.cu): the weighted kernels of every zone (after the neutrinosphere scan),
 // and the residual / Jacobian of the coupled pair systems (blocks of 2 n rows, vectors
 // [ray][pair][zone][2 n]; src_out in the psi layout).
 cudaError_t launch_pair(const Prob &p, const Ws &w, const double *T, cudaStream_t s);
 cudaError_t launch_assemble_pair(const Prob &p, const Ws &w, const double *psi, void *diag, int diag_fp32,
                                  double *lower, double *upper, double *rhs, const int *list, int n_list,
-                                 const int *jac_flag, cudaStream_t s, double *src_out, int first);
+                                 const int *jac_flag, cudaStream_t s, double *src_out, int first,
+                                 const int *n_dev = nullptr);
 
 // Thread-per-row factor and substitution of systems of block width nb <= 48 with spr systems per
 // ray (the coupled nu / antinu pair systems: nb = 2 n, spr = 2), FP64 or FP32 (fp32: float blocks,
 // couplings and factors; the substitution scales each system's right-hand side by a power of two
 // into rhs32 / sys_exp first).
 cudaError_t launch_factor_rows(int nb, int n_r, int n_sys, int spr, const void *diag, const void *lower,
-                               const void *upper, void *dinv, int fp32, const int *ray_list, cudaStream_t s);
+                               const void *upper, void *dinv, int fp32, const int *ray_list, cudaStream_t s,
+                               const int *n_dev = nullptr);
 cudaError_t launch_solve_rows(int nb, int n_r, int n_sys, int spr, const void *dinv, const void *lower,
                               const void *upper, const double *rhs, float *rhs32, int *sys_exp, double *x, int fp32,
-                              const int *ray_list, cudaStream_t s);
+                              const int *ray_list, cudaStream_t s, const int *n_dev = nullptr);
 cudaError_t launch_solve(int n, int n_r, int n_sys, const void *dinv, const double *lower,
                          const double *upper, const double *rhs, double *x, int precision,
-                         const int *ray_list, cudaStream_t s);
+                         const int *ray_list, cudaStream_t s, const int *n_dev = nullptr);
 
 }  // namespace mgfld

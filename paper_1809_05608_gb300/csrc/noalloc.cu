@@ -45,5 +45,7 @@ extern "C" mgfld_status mgfld_step_noalloc(const mgfld_dims *dims, const mgfld_p
   // Every buffer of the step is written before it is read (k_init resets the per-ray
   // bookkeeping, the counters are cleared on the stream), so the previous call's
   // contents need no clearing here.
-  return mgfld_step(dims, prob, state, opts, report, ws, kScratchBytes, stream);
+  // The outer iteration runs from the host (one stream synchronisation per iteration): the graph
+  // path of mgfld_step would instantiate a CUDA graph, which allocates.
+  return mgfld::step_host_synchronised(dims, prob, state, opts, report, ws, kScratchBytes, stream);
 }

@@ -106,11 +106,11 @@ template <typename TD>
 __global__ void k_assemble_pair(Prob p, Ws w, const double *__restrict__ psi, TD *__restrict__ diag,
                                 double *__restrict__ lower, double *__restrict__ upper, double *__restrict__ rhs,
                                 const int *__restrict__ list, int n_list, const int *__restrict__ jac_flag,
-                                double *__restrict__ src_out, int first) {
+                                double *__restrict__ src_out, int first, const int *__restrict__ n_dev) {
   const int n = p.n, n2 = 2 * n;
   const unsigned per_ray = (unsigned)(NS * p.n_r * n);
   const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= (unsigned)n_list * per_ray) return;
+  if (t >= (unsigned)listed(n_list, n_dev) * per_ray) return;
   const unsigned rl = t / per_ray;
   const int ray = list ? list[rl] : (int)rl;
   const unsigned local = t - rl * per_ray;
@@ -201,17 +201,17 @@ __global__ void k_assemble_pair(Prob p, Ws w, const double *__restrict__ psi, TD
 
 cudaError_t launch_assemble_pair(const Prob &p, const Ws &w, const double *psi, void *diag, int diag_fp32,
                                  double *lower, double *upper, double *rhs, const int *list, int n_list,
-                                 const int *jac_flag, cudaStream_t s, double *src_out, int first) {
+                                 const int *jac_flag, cudaStream_t s, double *src_out, int first, const int *n_dev) {
   const size_t total = (size_t)n_list * NS * p.n_r * p.n;
   if (total == 0) return cudaSuccess;
   const unsigned B = 256;
   const unsigned grid = (unsigned)((total + B - 1) / B);
   if (diag_fp32)
     k_assemble_pair<float><<<grid, B, 0, s>>>(p, w, psi, (float *)diag, lower, upper, rhs, list, n_list, jac_flag,
-                                              src_out, first);
+                                              src_out, first, n_dev);
   else
     k_assemble_pair<double><<<grid, B, 0, s>>>(p, w, psi, (double *)diag, lower, upper, rhs, list, n_list, jac_flag,
-                                               src_out, first);
+                                               src_out, first, n_dev);
   return cudaGetLastError();
 }
 

@@ -83,56 +83,90 @@ __global__ void k_zone(Prob p, Ws w, const double *__restrict__ ye, const double
 // g_m = e^{-(eps_m - eps_{m-1})/T} of consecutive groups (one exponential each, shared by the
 // zone through shared memory) as a running product along the row; up-scattering is its square
 // (coef e^{-2(eps_k' - eps_k)/T}) and Phi_in(eps_k, eps_k') = Phi_out(eps_k', eps_k).
-// One thread per row: every row runs the same n-1 steps (its k down-scattering entries, then its
-// n-1-k up-scattering entries).  Rows are staged in shared memory with a padded stride (n + 1)
-// and copied out coalesced.
+// Rows k and n-1-k share a thread, so that every thread runs the same n-1 steps of the
+// down-scattering chains and n-1 of the up-scattering chains (no divergent loop lengths).
+// Rows are staged in shared memory with a padded stride (n + 1) and copied out coalesced.
+static inline int phi_threads_per_zone(int n) { return (n + 1) / 2; }
 static inline size_t phi_zone_bytes(int n) { return sizeof(double) * (2 * (size_t)n * (n + 1) + 2 * (size_t)n); }
-// Zones per block: about 160 threads, at most 8 zones (56 KB of staging at n = 20, four blocks per SM).
+// Zones per block: zones * threads per zone a multiple of 32 where the staging fits in 113 KB
+// (two blocks per SM), else as many zones as fit.
 static inline int phi_zones_per_block(int n) {
-  int z = 160 / n;
-  if (z > 8) z = 8;
-  return z < 1 ? 1 : z;
+  const int h = phi_threads_per_zone(n);
+  int g = h, b = 32;
+  while (b) { const int t = g % b; g = b; b = t; }
+  const int full = 32 / g;
+  const int fit = (int)((size_t)113 * 1024 / phi_zone_bytes(n));
+  return full <= fit ? full : (fit < 1 ? 1 : fit);
 }
 static inline size_t phi_smem_bytes(int n) { return (size_t)phi_zones_per_block(n) * phi_zone_bytes(n); }
 
-// Row k of one zone's kernels into the staged tiles so (out) and si (in) (row stride ld), from
-// the zone's consecutive-group ratios gap[m] and weights cw[m]; returns the row sum of the
-// out-kernel (the diagonal, then the down-scattering entries, then the up-scattering ones).
-// Down-scattering entries run along the row as P = prod gap (one multiply per step) with the
+// Rows ka = t and kb = n-1-t of one zone's kernels into the staged tiles so (out) and si (in)
+// (row stride ld), from the zone's consecutive-group ratios gap[m] and weights cw[m]; returns
+// the two rows' sums of the out-kernel (equal rows of odd n: the middle row, both chains).
+// Down-scattering entries run along a row as P = prod gap (one multiply per step) with the
 // up-scattering partner o P = cw P^2; up-scattering entries likewise from Q = prod gap.
-__device__ inline double phi_row(int n, int k, const double *gap, const double *cw, double *so, double *si, int ld) {
-  double *o_row = so + (size_t)k * ld, *i_row = si + (size_t)k * ld;
-  double rs = cw[k];
-  o_row[k] = cw[k];
-  i_row[k] = cw[k];
+__device__ inline void phi_chains(int n, int t, const double *gap, const double *cw, double *so, double *si, int ld,
+                                  double &rs_a, double &rs_b) {
+  const int ka = t, kb = n - 1 - t;                     // ka <= kb; equal for the middle row of odd n
+  double *oa = so + (size_t)ka * ld, *ia = si + (size_t)ka * ld;
+  double *ob = so + (size_t)kb * ld, *ib = si + (size_t)kb * ld;
+  double rsa = cw[ka], rsb = (ka == kb) ? 0.0 : cw[kb];
+  oa[ka] = cw[ka];
+  ia[ka] = cw[ka];
+  ob[kb] = cw[kb];
+  ib[kb] = cw[kb];
+  // Down-scattering (k' < k): row ka's ka entries, then row kb's kb entries (n - 1 steps).
   double P = 1.0;
-  for (int kp = k - 1; kp >= 0; --kp) {
+  for (int j = 0; j < n - 1; ++j) {
+    const bool first = j < ka;
+    if (!first && ka == kb) break;                      // middle row: its chain is already done
+    const int kp = first ? ka - 1 - j : kb - 1 - (j - ka);
+    if (j == ka) P = 1.0;
     P *= gap[kp + 1];                                   // e^{-(eps_k - eps_kp)/T}
     const double o = cw[kp] * P;                        // down-scattering k -> kp
-    o_row[kp] = o;
-    i_row[kp] = o * P;                                  // up-scattering kp -> k: cw e^{-2(eps_k - eps_kp)/T}
-    rs += o;
+    const double v = o * P;                             // up-scattering kp -> k: cw e^{-2(eps_k - eps_kp)/T}
+    if (first) { oa[kp] = o; ia[kp] = v; rsa += o; } else { ob[kp] = o; ib[kp] = v; rsb += o; }
   }
+  // Up-scattering (k' > k): row kb's n-1-kb entries, then row ka's n-1-ka entries.
+  const int nb = n - 1 - kb;
   double Q = 1.0;
-  for (int kp = k + 1; kp < n; ++kp) {
+  for (int j = 0; j < n - 1; ++j) {
+    const bool first = j < nb;
+    if (!first && ka == kb) break;
+    const int kp = first ? kb + 1 + j : ka + 1 + (j - nb);
+    if (j == nb) Q = 1.0;
     Q *= gap[kp];                                       // e^{-(eps_kp - eps_k)/T}
     const double v = cw[kp] * Q;                        // down-scattering kp -> k
     const double o = v * Q;                             // up-scattering k -> kp
-    o_row[kp] = o;
-    i_row[kp] = v;
-    rs += o;
+    if (first) { ob[kp] = o; ib[kp] = v; rsb += o; } else { oa[kp] = o; ia[kp] = v; rsa += o; }
   }
-  return rs;
+  if (kb != ka) {
+    rs_a = rsa;
+    rs_b = rsb;
+  } else {
+    rs_a = rs_b = rsa + rsb;
+  }
+}
+
+// The consecutive-group ratios e^{-(eps_m - eps_{m-1})/T} and weights C w_m = C W_m / a^3 of one
+// zone into shared memory, the zone's H threads striding over the groups.
+__device__ inline void phi_zone_consts(const Ws &w, int n, int t, int H, double inv_a, double Ti, double nes,
+                                       double *gap, double *cw) {
+  const double cc = kCNes * inv_a * inv_a * inv_a * nes;
+  for (int k = t; k < n; k += H) {
+    if (k > 0) gap[k] = exp(-(w.E[k] - w.E[k - 1]) * inv_a / Ti);
+    cw[k] = cc * w.W[k];
+  }
 }
 
 __global__ void k_phi(Prob p, Ws w, const double *__restrict__ T, int zpb) {
   extern __shared__ double smem[];
-  const int n = p.n, ld = n + 1;
+  const int n = p.n, H = (n + 1) / 2, ld = n + 1;
   double *gapm = smem;                                   // [zpb][n]  e^{-(eps_m - eps_{m-1})/T}
   double *cwm = gapm + (size_t)zpb * n;                   // [zpb][n]  C w_m = C W_m / a^3
   double *sout = cwm + (size_t)zpb * n;                   // [zpb][n][n + 1]
   double *sin_ = sout + (size_t)zpb * n * ld;             // [zpb][n][n + 1]
-  const int zl = threadIdx.x / n, k = threadIdx.x % n;
+  const int zl = threadIdx.x / H, t = threadIdx.x % H;
   const unsigned nz = (unsigned)(p.n_ray * p.n_r);
   const unsigned z0 = blockIdx.x * (unsigned)zpb;
   const unsigned zi = z0 + zl;
@@ -141,13 +175,15 @@ __global__ void k_phi(Prob p, Ws w, const double *__restrict__ T, int zpb) {
   double *cw = cwm + (size_t)(live ? zl : 0) * n;
   if (live) {
     const int ray = (int)(zi / (unsigned)p.n_r), i = (int)(zi - (unsigned)ray * p.n_r);
-    const double inv_a = 1.0 / lapse_at(p, ray, i);
-    const double cc = kCNes * inv_a * inv_a * inv_a * (p.nes ? p.nes[zi] : 0.0);
-    if (k > 0) gap[k] = exp(-(w.E[k] - w.E[k - 1]) * inv_a / T[zi]);
-    cw[k] = cc * w.W[k];
+    phi_zone_consts(w, n, t, H, 1.0 / lapse_at(p, ray, i), T[zi], p.nes ? p.nes[zi] : 0.0, gap, cw);
   }
   __syncthreads();
-  if (live) w.rsum[(size_t)zi * n + k] = phi_row(n, k, gap, cw, sout + (size_t)zl * n * ld, sin_ + (size_t)zl * n * ld, ld);
+  if (live) {
+    double rsa, rsb;
+    phi_chains(n, t, gap, cw, sout + (size_t)zl * n * ld, sin_ + (size_t)zl * n * ld, ld, rsa, rsb);
+    w.rsum[(size_t)zi * n + t] = rsa;
+    if (n - 1 - t != t) w.rsum[(size_t)zi * n + (n - 1 - t)] = rsb;
+  }
   __syncthreads();
   // Coalesced copy of the block's zones (contiguous in [ray][zone][k][k'] order).
   const unsigned nzb = (z0 + zpb <= nz) ? (unsigned)zpb : nz - z0;
@@ -507,7 +543,7 @@ cudaError_t launch_setup(const Prob &p, const Ws &w, const double *psi, const do
       const cudaError_t e = cudaFuncSetAttribute(k_phi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
       if (e != cudaSuccess) return e;
     }
-    k_phi<<<nblk(nz, zpb), zpb * p.n, sm, s>>>(p, w, T, zpb);
+    k_phi<<<nblk(nz, zpb), zpb * phi_threads_per_zone(p.n), sm, s>>>(p, w, T, zpb);
   }
   k_jlam<<<nblk(nzk, B), B, 0, s>>>(p, w, psi, T);
   k_nusphere<<<nblk((size_t)p.n_ray * NS * p.n * 32, B), B, 0, s>>>(p, w);   // a warp per (ray, q, k)

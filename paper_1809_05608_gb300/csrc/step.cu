@@ -14,6 +14,8 @@
 #include <cmath>
 #include <cstring>
 #include <mutex>
+#include <string>
+#include <unordered_map>
 
 #include "mgfld_internal.cuh"
 
@@ -231,10 +233,12 @@ __device__ inline void report_violation_block(Ws &w, int ray, float viol) {
 // of Eq. a62ab, one thread per (ray, q, i, k) of the active rays.  All 32 lanes of a warp reach
 // the reduction (out-of-range lanes carry ratio 0).
 __global__ void k_update_psi(Prob p, Ws w, Tol tl, double *__restrict__ psi, const int *__restrict__ list,
-                             int n_list) {
+                             int n_list, const int *__restrict__ n_dev) {
   const unsigned per_ray = (unsigned)(NS * p.n_r * p.n);
+  const unsigned total = (unsigned)listed(n_list, n_dev) * per_ray;
+  if (blockIdx.x * blockDim.x >= total) return;          // the whole block
   const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
-  const bool in = t < (unsigned)n_list * per_ray;
+  const bool in = t < total;
   const unsigned rl = t / per_ray;
   const int ray = in ? list[rl] : list[0];
   float viol = 0.f;
@@ -268,10 +272,13 @@ __global__ void k_update_psi(Prob p, Ws w, Tol tl, double *__restrict__ psi, con
 // usual case no group reaches it and the per-group sums share their products,
 //   sum w j (1 - psi) - sum w kappa psi  and  sum w j (1 - psi)  (the Ye derivative).
 __global__ void k_update_ye(Prob p, Ws w, Tol tl, const double *__restrict__ psi, double *__restrict__ ye,
-                            const double *__restrict__ T, const int *__restrict__ list, int n_list) {
+                            const double *__restrict__ T, const int *__restrict__ list, int n_list,
+                            const int *__restrict__ n_dev) {
   const int n = p.n;
+  const unsigned total = (unsigned)(listed(n_list, n_dev) * p.n_r);
+  if (blockIdx.x * blockDim.x >= total) return;          // the whole block
   const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
-  const bool in = t < (unsigned)(n_list * p.n_r);
+  const bool in = t < total;
   const unsigned rl = t / (unsigned)p.n_r;
   const int ray = in ? list[rl] : list[0];
   float viol = 0.f;
@@ -494,6 +501,19 @@ __global__ void k_ledger(int n_r, Ws w, double *ledger, double *heating, int *st
   }
 }
 
+// Outer loop of the graph path: continue while some ray is still active and no bounded wait of
+// the substitution gave up (counters[0]: active rays, counters[3]: the wait flag).
+__global__ void k_loop_cond(cudaGraphConditionalHandle h, const int *__restrict__ counters) {
+  cudaGraphSetConditional(h, (counters[0] > 0 && counters[3] == 0) ? 1u : 0u);
+}
+
+// The step's status for the caller's report: ECUDA if a bounded wait gave up, else the worst ray
+// status (ENAN before ENOCONV), else OK.
+__global__ void k_status(const int *__restrict__ counters, int *__restrict__ status) {
+  *status = counters[3] != 0 ? MGFLD_ECUDA
+                             : (counters[2] == 2 ? MGFLD_ENAN : (counters[2] == 1 ? MGFLD_ENOCONV : MGFLD_OK));
+}
+
 // Optional per-category timing: a pair of CUDA events per category, read back after the host
 // synchronisations the outer iteration already performs.  The events are created on the
 // first profiled call on each device and kept for the life of the process (creating and
@@ -628,131 +648,335 @@ const char *mgfld_status_str(mgfld_status s) {
   return "unknown status";
 }
 
-mgfld_status mgfld_step(const mgfld_dims *dims, const mgfld_problem *prob, mgfld_state *state,
-                        const mgfld_step_opts *opts, mgfld_step_report *report, void *ws, size_t ws_bytes,
-                        void *stream) {
+}  // extern "C"
+
+namespace mgfld {
+
+// Everything one call of the step needs, resolved from its arguments.
+struct StepCall {
+  Layout L;
+  Ws w;
+  Prob p;
+  Tol tl;
+  int pair, R, n, NR, coef_iterate, precision;
+  mgfld_state st;
+  mgfld_step_report rep;
+};
+
+static mgfld_status step_prepare(const mgfld_dims *dims, const mgfld_problem *prob, mgfld_state *state,
+                                 const mgfld_step_opts *opts, mgfld_step_report *report, void *ws, size_t ws_bytes,
+                                 StepCall &c) {
   if (!dims_ok(dims) || !prob_ok(prob) || !state || !state->psi || !state->ye || !state->T || !opts || !ws)
     return MGFLD_EINVAL;
   if ((opts->precision != MGFLD_FP64 && opts->precision != MGFLD_MIXED) || opts->max_iter < 1 ||
       !(opts->tol > 0.0) || !(opts->tol_ye > 0.0) || !(opts->tolmin_psi >= 0.0) || !(opts->tolmin_ye >= 0.0))
     return MGFLD_EINVAL;
   if (opts->coef_iterate && prob->u) return MGFLD_EINVAL;
-  const int pair = prob->pair_coef != nullptr;
+  c.pair = prob->pair_coef != nullptr;
   // the pair process: coupled blocks of 2 n_e <= 48 rows, with the coefficients frozen for the step
-  if (pair && (2 * dims->n_e > 48 || opts->coef_iterate)) return MGFLD_EINVAL;
+  if (c.pair && (2 * dims->n_e > 48 || opts->coef_iterate)) return MGFLD_EINVAL;
   if (((uintptr_t)ws & 255u) != 0) return MGFLD_EINVAL;
-  const Layout L = make_layout(dims->n_ray, dims->n_r, dims->n_e, opts->precision, pair);
-  if (ws_bytes < L.total) return MGFLD_ENOMEM;
-  cudaStream_t s = (cudaStream_t)stream;
-  Ws w = resolve(ws, L);
+  c.L = make_layout(dims->n_ray, dims->n_r, dims->n_e, opts->precision, c.pair);
+  if (ws_bytes < c.L.total) return MGFLD_ENOMEM;
+  c.w = resolve(ws, c.L);
   if (opts->coef_iterate) {
     // the limiter's derivatives take the storage of 1/lambda and lambda, which the neutrinosphere
     // scan has consumed before the limiter kernel writes them (setup and every iteration)
-    w.jl = w.kinv;
-    w.jr = w.lam;
+    c.w.jl = c.w.kinv;
+    c.w.jr = c.w.lam;
   }
-  const Prob p = make_prob(dims, prob);
-  Tol tl;
+  c.p = make_prob(dims, prob);
+  Tol &tl = c.tl;
   tl.tol = opts->tol; tl.tolmin = opts->tolmin_psi; tl.tol_ye = opts->tol_ye; tl.tolmin_ye = opts->tolmin_ye;
   tl.refactor_ratio = opts->refactor_ratio > 0.0 ? opts->refactor_ratio : 0.1;
   tl.max_iter = opts->max_iter; tl.mixed = opts->precision == MGFLD_MIXED;
   tl.chord = tl.mixed || opts->refactor_ratio > 0.0;
   tl.tolm = (float)std::frexp(opts->tol, &tl.tole);
   tl.tolm_ye = (float)std::frexp(opts->tol_ye, &tl.tole_ye);
-  const int R = dims->n_ray, n = dims->n_e, NR = dims->n_r;
+  c.R = dims->n_ray; c.n = dims->n_e; c.NR = dims->n_r;
+  c.coef_iterate = opts->coef_iterate;
+  c.precision = opts->precision;
+  c.st = *state;
+  c.rep = report ? *report : mgfld_step_report{};
+  return MGFLD_OK;
+}
 
-  Prof prof(opts->profile, s);
-  prof.begin(MGFLD_PROF_SETUP);
-  MGFLD_CUDA(launch_setup(p, w, state->psi, state->ye, state->T, s));
-  k_init<<<nblk(R, 128), 128, 0, s>>>(R, w);
-  MGFLD_CUDA(cudaGetLastError());
-  MGFLD_CUDA(cudaMemsetAsync(w.counters, 0, sizeof(int) * 8, s));
-  prof.end(MGFLD_PROF_SETUP, 7 + (p.u ? 1 : 0) + (pair ? 1 : 0));
-  int n_act = R, n_ref = R;
+// The set-up of the step: frozen coefficients, per-ray bookkeeping, cleared counters.
+static cudaError_t enqueue_setup(const StepCall &c, cudaStream_t s) {
+  cudaError_t e = launch_setup(c.p, c.w, c.st.psi, c.st.ye, c.st.T, s);
+  if (e != cudaSuccess) return e;
+  k_init<<<nblk(c.R, 128), 128, 0, s>>>(c.R, c.w);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  return cudaMemsetAsync(c.w.counters, 0, sizeof(int) * 8, s);
+}
+
+// One outer iteration (Eq. a62aa): residual / Jacobian of the listed rays, factorisation of the
+// rays that need it, substitution, psi and Ye updates, convergence test and the next lists.  The
+// listed counts are the host's (n_act, n_ref) or, with device_counts, counters[0] and [1] on the
+// device (the grids then cover all rays and blocks past the counts return at once).
+static cudaError_t enqueue_iteration(const StepCall &c, int it, int n_act, int n_ref, bool device_counts, Prof *prof,
+                                     cudaStream_t s) {
+  const Prob &p = c.p;
+  const Ws &w = c.w;
+  const Tol &tl = c.tl;
+  const int n = c.n, NR = c.NR, R = c.R, pair = c.pair;
+  const int *cnt_act = device_counts ? w.counters : nullptr;
+  const int *cnt_ref = device_counts ? (tl.chord ? w.counters + 1 : w.counters) : nullptr;
+  const int *jac = tl.chord ? w.refac : nullptr;
+  cudaError_t e = cudaSuccess;
+#define MGFLD_ENQ(x)                          \
+  do {                                        \
+    if ((e = (x)) != cudaSuccess) return e;   \
+  } while (0)
+  if (c.coef_iterate && it > 0) {
+    // the flux coefficients of Eq. a59 at the current iterate (psi and Ye updated in place)
+    if (prof) prof->begin(MGFLD_PROF_SETUP);
+    MGFLD_ENQ(launch_coef_iterate(p, w, c.st.psi, s));
+    if (prof) prof->end(MGFLD_PROF_SETUP, 3);
+  }
+  if (prof) prof->begin(MGFLD_PROF_ASSEMBLE);
+  if (pair)
+    MGFLD_ENQ(launch_assemble_pair(p, w, c.st.psi, w.diag, tl.mixed, w.lower, w.upper, w.rhs, w.list_act, n_act, jac,
+                                   s, nullptr, it == 0, cnt_act));
+  else
+    MGFLD_ENQ(launch_assemble(p, w, c.st.psi, w.diag, tl.mixed, w.lower, w.upper, w.rhs, w.list_act, n_act, jac, s,
+                              nullptr, it == 0, cnt_act));
+  if (prof) prof->end(MGFLD_PROF_ASSEMBLE, 1);
+  const int *flist = tl.chord ? w.list_ref : w.list_act;
+  const int nf = tl.chord ? n_ref : n_act;
+  if (nf > 0) {
+    if (prof) prof->begin(MGFLD_PROF_FACTOR);
+    if (pair)
+      MGFLD_ENQ(launch_factor_rows(2 * n, NR, nf * 2, 2, w.diag, tl.mixed ? (const void *)w.lower32 : w.lower,
+                                   tl.mixed ? (const void *)w.upper32 : w.upper, w.dinv, tl.mixed, flist, s, cnt_ref));
+    else if (tl.mixed)
+      MGFLD_ENQ(launch_factor_f32(n, NR, nf * NS, (const float *)w.diag, w.lower32, w.upper32, (float *)w.dinv, flist,
+                                  s, cnt_ref));
+    else
+      MGFLD_ENQ(launch_factor(n, NR, nf * NS, w.diag, 0, w.lower, w.upper, w.dinv, c.precision, flist, s, cnt_ref));
+    if (prof) prof->end(MGFLD_PROF_FACTOR, 1);
+  }
+  if (prof) prof->begin(MGFLD_PROF_SOLVE);
+  if (pair)
+    MGFLD_ENQ(launch_solve_rows(2 * n, NR, n_act * 2, 2, w.dinv, tl.mixed ? (const void *)w.lower32 : w.lower,
+                                tl.mixed ? (const void *)w.upper32 : w.upper, w.rhs, w.rhs32, w.sscale, w.x, tl.mixed,
+                                w.list_act, s, cnt_act));
+  else if (tl.mixed && n % 2 == 0)
+    MGFLD_ENQ(launch_solve_tma(n, NR, n_act * NS, w.dinv, w.lower32, w.upper32, w.rhs, w.rhs32, w.x, w.g32,
+                               w.list_act, w.sscale, w.counters + 3, s, cnt_act));
+  else
+    MGFLD_ENQ(launch_solve(n, NR, n_act * NS, w.dinv, w.lower, w.upper, w.rhs, w.x, c.precision, w.list_act, s,
+                           cnt_act));
+  if (prof) prof->end(MGFLD_PROF_SOLVE, 1);
+  if (prof) prof->begin(MGFLD_PROF_UPDATE);
+  k_update_psi<<<nblk((size_t)n_act * NS * NR * n, 256), 256, 0, s>>>(p, w, tl, c.st.psi, w.list_act, n_act, cnt_act);
+  MGFLD_ENQ(cudaGetLastError());
+  k_update_ye<<<nblk((size_t)n_act * NR, 128), 128, 0, s>>>(p, w, tl, c.st.psi, c.st.ye, c.st.T, w.list_act, n_act,
+                                                            cnt_act);
+  MGFLD_ENQ(cudaGetLastError());
+  MGFLD_ENQ(cudaMemsetAsync(w.counters, 0, sizeof(int) * 2, s));
+  k_check<<<nblk(R, 128), 128, 0, s>>>(R, w, tl);
+  MGFLD_ENQ(cudaGetLastError());
+  if (prof) prof->end(MGFLD_PROF_UPDATE, 3);
+  return cudaSuccess;
+}
+
+// After the iteration: Eq. a62b with the converged sources, T, the ledgers, the report.
+static cudaError_t enqueue_finish(const StepCall &c, Prof *prof, cudaStream_t s) {
+  const Ws &w = c.w;
+  const int R = c.R, NR = c.NR;
+  cudaError_t e = cudaSuccess;
+  if (prof) prof->begin(MGFLD_PROF_FINISH);
+  if (c.pair)
+    MGFLD_ENQ(launch_assemble_pair(c.p, w, c.st.psi, w.diag, c.tl.mixed, w.lower, w.upper, w.rhs, nullptr, R, nullptr,
+                                   s, w.src, 0));
+  else
+    MGFLD_ENQ(launch_assemble(c.p, w, c.st.psi, w.diag, c.tl.mixed, w.lower, w.upper, w.rhs, nullptr, R, nullptr, s,
+                              w.src));
+  k_finish<<<nblk((size_t)R * NR, 128), 128, 0, s>>>(c.p, w, c.st.psi, c.st.ye, c.st.T);
+  MGFLD_ENQ(cudaGetLastError());
+  MGFLD_ENQ(cudaMemsetAsync(w.counters + 2, 0, sizeof(int), s));
+  k_ledger<<<R, 128, 0, s>>>(NR, w, c.rep.ledger, c.rep.heating, c.rep.ray_status);
+  MGFLD_ENQ(cudaGetLastError());
+  if (prof) prof->end(MGFLD_PROF_FINISH, 3);
+  if (c.rep.iters)
+    MGFLD_ENQ(cudaMemcpyAsync(c.rep.iters, w.iters, sizeof(int) * R, cudaMemcpyDeviceToDevice, s));
+  if (c.rep.factorizations)
+    MGFLD_ENQ(cudaMemcpyAsync(c.rep.factorizations, w.nfact, sizeof(int) * R, cudaMemcpyDeviceToDevice, s));
+  if (c.rep.status) {
+    k_status<<<1, 1, 0, s>>>(w.counters, c.rep.status);
+    MGFLD_ENQ(cudaGetLastError());
+  }
+  return cudaSuccess;
+#undef MGFLD_ENQ
+}
+
+// The step with the outer iteration driven from the host: one stream synchronisation per
+// iteration (the convergence counters), per-category timing when requested.
+static mgfld_status step_host_loop(const StepCall &c, double *profile, cudaStream_t s) {
+  Prof prof(profile, s);
+  Prof *pp = profile ? &prof : nullptr;
+  if (pp) prof.begin(MGFLD_PROF_SETUP);
+  MGFLD_CUDA(enqueue_setup(c, s));
+  if (pp) prof.end(MGFLD_PROF_SETUP, 7 + (c.p.u ? 1 : 0) + (c.pair ? 1 : 0));
+  int n_act = c.R, n_ref = c.R;
   int host_counters[8];
-  for (int it = 0; it < opts->max_iter && n_act > 0; ++it) {
-    const int *jac = tl.chord ? w.refac : nullptr;
-    if (opts->coef_iterate && it > 0) {
-      // the flux coefficients of Eq. a59 at the current iterate (psi and Ye updated in place)
-      prof.begin(MGFLD_PROF_SETUP);
-      MGFLD_CUDA(launch_coef_iterate(p, w, state->psi, s));
-      prof.end(MGFLD_PROF_SETUP, 3);
-    }
-    prof.begin(MGFLD_PROF_ASSEMBLE);
-    if (pair)
-      MGFLD_CUDA(launch_assemble_pair(p, w, state->psi, w.diag, tl.mixed, w.lower, w.upper, w.rhs, w.list_act, n_act,
-                                      jac, s, nullptr, it == 0));
-    else
-      MGFLD_CUDA(launch_assemble(p, w, state->psi, w.diag, tl.mixed, w.lower, w.upper, w.rhs, w.list_act, n_act,
-                                 jac, s, nullptr, it == 0));
-    prof.end(MGFLD_PROF_ASSEMBLE, 1);
-    const int *flist = tl.chord ? w.list_ref : w.list_act;
-    const int nf = tl.chord ? n_ref : n_act;
-    if (nf > 0) {
-      prof.begin(MGFLD_PROF_FACTOR);
-      if (pair)
-        MGFLD_CUDA(launch_factor_rows(2 * n, NR, nf * 2, 2, w.diag, tl.mixed ? (const void *)w.lower32 : w.lower,
-                                      tl.mixed ? (const void *)w.upper32 : w.upper, w.dinv, tl.mixed, flist, s));
-      else if (tl.mixed)
-        MGFLD_CUDA(launch_factor_f32(n, NR, nf * NS, (const float *)w.diag, w.lower32, w.upper32, (float *)w.dinv,
-                                     flist, s));
-      else
-        MGFLD_CUDA(launch_factor(n, NR, nf * NS, w.diag, 0, w.lower, w.upper, w.dinv, opts->precision, flist, s));
-      prof.end(MGFLD_PROF_FACTOR, 1);
-    }
-    prof.begin(MGFLD_PROF_SOLVE);
-    if (pair)
-      MGFLD_CUDA(launch_solve_rows(2 * n, NR, n_act * 2, 2, w.dinv, tl.mixed ? (const void *)w.lower32 : w.lower,
-                                   tl.mixed ? (const void *)w.upper32 : w.upper, w.rhs, w.rhs32, w.sscale, w.x,
-                                   tl.mixed, w.list_act, s));
-    else if (tl.mixed && n % 2 == 0)
-      MGFLD_CUDA(launch_solve_tma(n, NR, n_act * NS, w.dinv, w.lower32, w.upper32, w.rhs, w.rhs32, w.x, w.g32,
-                                  w.list_act, w.sscale, w.counters + 3, s));
-    else
-      MGFLD_CUDA(launch_solve(n, NR, n_act * NS, w.dinv, w.lower, w.upper, w.rhs, w.x, opts->precision,
-                              w.list_act, s));
-    prof.end(MGFLD_PROF_SOLVE, 1);
-    prof.begin(MGFLD_PROF_UPDATE);
-    k_update_psi<<<nblk((size_t)n_act * NS * NR * n, 256), 256, 0, s>>>(p, w, tl, state->psi, w.list_act, n_act);
-    MGFLD_CUDA(cudaGetLastError());
-    k_update_ye<<<nblk((size_t)n_act * NR, 128), 128, 0, s>>>(p, w, tl, state->psi, state->ye, state->T,
-                                                              w.list_act, n_act);
-    MGFLD_CUDA(cudaGetLastError());
-    MGFLD_CUDA(cudaMemsetAsync(w.counters, 0, sizeof(int) * 2, s));
-    k_check<<<nblk(R, 128), 128, 0, s>>>(R, w, tl);
-    MGFLD_CUDA(cudaGetLastError());
-    prof.end(MGFLD_PROF_UPDATE, 3);
-    MGFLD_CUDA(cudaMemcpyAsync(host_counters, w.counters, sizeof(int) * 4, cudaMemcpyDeviceToHost, s));
+  for (int it = 0; it < c.tl.max_iter && n_act > 0; ++it) {
+    MGFLD_CUDA(enqueue_iteration(c, it, n_act, n_ref, false, pp, s));
+    MGFLD_CUDA(cudaMemcpyAsync(host_counters, c.w.counters, sizeof(int) * 4, cudaMemcpyDeviceToHost, s));
     MGFLD_CUDA(cudaStreamSynchronize(s));
     prof.collect();
     if (host_counters[3] != 0) return MGFLD_ECUDA;      // a bounded wait in the solve gave up
     n_act = host_counters[0];
     n_ref = host_counters[1];
   }
-  prof.begin(MGFLD_PROF_FINISH);
-  if (pair)
-    MGFLD_CUDA(launch_assemble_pair(p, w, state->psi, w.diag, tl.mixed, w.lower, w.upper, w.rhs, nullptr, R, nullptr,
-                                    s, w.src, 0));
-  else
-    MGFLD_CUDA(launch_assemble(p, w, state->psi, w.diag, tl.mixed, w.lower, w.upper, w.rhs, nullptr, R, nullptr,
-                               s, w.src));
-  k_finish<<<nblk((size_t)R * NR, 128), 128, 0, s>>>(p, w, state->psi, state->ye, state->T);
-  MGFLD_CUDA(cudaGetLastError());
-  MGFLD_CUDA(cudaMemsetAsync(w.counters + 2, 0, sizeof(int), s));
-  k_ledger<<<R, 128, 0, s>>>(NR, w, report ? report->ledger : nullptr, report ? report->heating : nullptr,
-                             report ? report->ray_status : nullptr);
-  MGFLD_CUDA(cudaGetLastError());
-  prof.end(MGFLD_PROF_FINISH, 3);
-  if (report && report->iters)
-    MGFLD_CUDA(cudaMemcpyAsync(report->iters, w.iters, sizeof(int) * R, cudaMemcpyDeviceToDevice, s));
-  if (report && report->factorizations)
-    MGFLD_CUDA(cudaMemcpyAsync(report->factorizations, w.nfact, sizeof(int) * R, cudaMemcpyDeviceToDevice, s));
-  MGFLD_CUDA(cudaMemcpyAsync(host_counters + 2, w.counters + 2, sizeof(int), cudaMemcpyDeviceToHost, s));
+  MGFLD_CUDA(enqueue_finish(c, pp, s));
+  MGFLD_CUDA(cudaMemcpyAsync(host_counters + 2, c.w.counters + 2, sizeof(int), cudaMemcpyDeviceToHost, s));
   MGFLD_CUDA(cudaStreamSynchronize(s));
   prof.collect();
   if (host_counters[2] == 2) return MGFLD_ENAN;
   if (host_counters[2] == 1) return MGFLD_ENOCONV;
   return MGFLD_OK;
+}
+
+// ------------------------------------------------------------------ the graph path
+//
+// The whole step as one CUDA graph: the set-up and the first iteration, then a while-conditional
+// node whose body is one iteration with device-resident counts, its condition set on the device
+// by k_loop_cond after every convergence test, then the finish.  Nothing waits on the host, so the
+// call is asynchronous on the caller's stream.  The instantiated graph of each distinct set of
+// arguments (pointers, sizes, options) is kept for the life of the process and launched again
+// when the same arguments come back.
+
+static void key_put(std::string &k, const void *v, size_t n) { k.append((const char *)v, n); }
+template <typename T> static void key_put(std::string &k, const T &v) { key_put(k, &v, sizeof(T)); }
+
+static std::string graph_key(int dev, const mgfld_dims *d, const mgfld_problem *pr, const mgfld_state *st,
+                             const mgfld_step_opts *o, const mgfld_step_report &rep, const void *ws, size_t ws_bytes) {
+  std::string k;
+  key_put(k, dev);
+  key_put(k, d->n_ray); key_put(k, d->n_r); key_put(k, d->n_e); key_put(k, d->n_s);
+  const void *ptrs[] = {pr->r_edge, pr->lapse, pr->e_edge, pr->rho, pr->kappa_abs, pr->kappa_scat, pr->nes_coef,
+                        pr->scale, pr->u, pr->eta1, pr->pair_coef, st->psi, st->ye, st->T, rep.iters, rep.ray_status,
+                        rep.ledger, rep.heating, rep.factorizations, rep.status, ws};
+  key_put(k, ptrs, sizeof(ptrs));
+  const double eos[] = {pr->eos.gamma1, pr->eos.gamma2, pr->eos.e_coef, pr->eos.g_n, pr->eos.g_p, pr->eos.rho_nuc,
+                        pr->eos.rho_0, pr->eos.mb_c2, pr->eos.m_b, pr->dt, o->tol, o->tolmin_psi, o->tol_ye,
+                        o->tolmin_ye, o->refactor_ratio};
+  key_put(k, eos, sizeof(eos));
+  const int ints[] = {pr->outer_bc, pr->pair_chi, o->precision, o->max_iter, o->coef_iterate};
+  key_put(k, ints, sizeof(ints));
+  key_put(k, ws_bytes);
+  return k;
+}
+
+struct GraphCache {
+  std::mutex lock;
+  std::unordered_map<std::string, cudaGraphExec_t> execs;
+  cudaStream_t cap[64][2] = {};      // per device: the streams the graphs are captured on
+};
+static GraphCache &graph_cache() {
+  static GraphCache *c = new GraphCache();     // kept for the life of the process
+  return *c;
+}
+
+static cudaError_t build_step_graph(const StepCall &c, cudaStream_t cs, cudaStream_t bs, cudaGraphExec_t *out) {
+  cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed);
+  if (e != cudaSuccess) return e;
+  cudaGraph_t g = nullptr, body = nullptr, done = nullptr;
+  cudaStreamCaptureStatus cst;
+  const cudaGraphNode_t *deps = nullptr;
+  size_t nd = 0;
+  cudaGraphConditionalHandle h{};
+  cudaGraphNodeParams cp{};
+  cudaGraphNode_t cn{};
+  bool body_open = false;
+  auto fail = [&](cudaError_t err) {
+    if (body_open) {
+      cudaGraph_t tmp = nullptr;
+      cudaStreamEndCapture(bs, &tmp);
+    }
+    cudaGraph_t tmp = nullptr;
+    cudaStreamEndCapture(cs, &tmp);
+    if (tmp) cudaGraphDestroy(tmp);
+    return err;
+  };
+  if ((e = cudaStreamGetCaptureInfo(cs, &cst, nullptr, &g)) != cudaSuccess) return fail(e);
+  if ((e = cudaGraphConditionalHandleCreate(&h, g, 0, cudaGraphCondAssignDefault)) != cudaSuccess) return fail(e);
+  if ((e = enqueue_setup(c, cs)) != cudaSuccess) return fail(e);
+  if ((e = enqueue_iteration(c, 0, c.R, c.R, false, nullptr, cs)) != cudaSuccess) return fail(e);
+  k_loop_cond<<<1, 1, 0, cs>>>(h, c.w.counters);
+  if ((e = cudaGetLastError()) != cudaSuccess) return fail(e);
+  if ((e = cudaStreamGetCaptureInfo(cs, &cst, nullptr, &g, &deps, nullptr, &nd)) != cudaSuccess) return fail(e);
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = h;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  if ((e = cudaGraphAddNode(&cn, g, deps, nullptr, nd, &cp)) != cudaSuccess) return fail(e);
+  if ((e = cudaStreamUpdateCaptureDependencies(cs, &cn, nullptr, 1, cudaStreamSetCaptureDependencies)) != cudaSuccess)
+    return fail(e);
+  body = cp.conditional.phGraph_out[0];
+  if ((e = cudaStreamBeginCaptureToGraph(bs, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed)) != cudaSuccess)
+    return fail(e);
+  body_open = true;
+  if ((e = enqueue_iteration(c, 1, c.R, c.R, true, nullptr, bs)) != cudaSuccess) return fail(e);
+  k_loop_cond<<<1, 1, 0, bs>>>(h, c.w.counters);
+  if ((e = cudaGetLastError()) != cudaSuccess) return fail(e);
+  if ((e = cudaStreamEndCapture(bs, &body)) != cudaSuccess) return fail(e);
+  body_open = false;
+  if ((e = enqueue_finish(c, nullptr, cs)) != cudaSuccess) return fail(e);
+  if ((e = cudaStreamEndCapture(cs, &done)) != cudaSuccess) return e;
+  e = cudaGraphInstantiate(out, done, 0);
+  cudaGraphDestroy(done);
+  return e;
+}
+
+static mgfld_status step_graph(const StepCall &c, const mgfld_dims *dims, const mgfld_problem *prob,
+                               const mgfld_step_opts *opts, void *ws, size_t ws_bytes, cudaStream_t s) {
+  int dev = 0;
+  MGFLD_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return MGFLD_ECUDA;
+  const std::string key = graph_key(dev, dims, prob, &c.st, opts, c.rep, ws, ws_bytes);
+  GraphCache &gc = graph_cache();
+  cudaGraphExec_t exec = nullptr;
+  {
+    std::lock_guard<std::mutex> guard(gc.lock);
+    auto it = gc.execs.find(key);
+    if (it != gc.execs.end()) {
+      exec = it->second;
+    } else {
+      for (int k = 0; k < 2; ++k)
+        if (!gc.cap[dev][k]) MGFLD_CUDA(cudaStreamCreateWithFlags(&gc.cap[dev][k], cudaStreamNonBlocking));
+      MGFLD_CUDA(build_step_graph(c, gc.cap[dev][0], gc.cap[dev][1], &exec));
+      gc.execs.emplace(key, exec);
+    }
+  }
+  MGFLD_CUDA(cudaGraphLaunch(exec, s));
+  return MGFLD_OK;
+}
+
+mgfld_status step_host_synchronised(const mgfld_dims *dims, const mgfld_problem *prob, mgfld_state *state,
+                                    const mgfld_step_opts *opts, mgfld_step_report *report, void *ws,
+                                    size_t ws_bytes, void *stream) {
+  StepCall c;
+  const mgfld_status st = step_prepare(dims, prob, state, opts, report, ws, ws_bytes, c);
+  if (st != MGFLD_OK) return st;
+  return step_host_loop(c, opts->profile, (cudaStream_t)stream);
+}
+
+}  // namespace mgfld
+
+extern "C" {
+
+mgfld_status mgfld_step(const mgfld_dims *dims, const mgfld_problem *prob, mgfld_state *state,
+                        const mgfld_step_opts *opts, mgfld_step_report *report, void *ws, size_t ws_bytes,
+                        void *stream) {
+  StepCall c;
+  const mgfld_status st = step_prepare(dims, prob, state, opts, report, ws, ws_bytes, c);
+  if (st != MGFLD_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (opts->profile) return step_host_loop(c, opts->profile, s);
+  return step_graph(c, dims, prob, opts, ws, ws_bytes, s);
 }
 
 mgfld_status mgfld_assemble(const mgfld_dims *dims, const mgfld_problem *prob, const mgfld_state *state,

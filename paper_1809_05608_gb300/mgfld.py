@@ -55,7 +55,7 @@ class StepOpts(ctypes.Structure):
 
 class StepReport(ctypes.Structure):
     _fields_ = [('iters', ctypes.c_void_p), ('ray_status', ctypes.c_void_p), ('ledger', ctypes.c_void_p),
-                ('heating', ctypes.c_void_p), ('factorizations', ctypes.c_void_p)]
+                ('heating', ctypes.c_void_p), ('factorizations', ctypes.c_void_p), ('status', ctypes.c_void_p)]
 
 
 class System(ctypes.Structure):
@@ -223,14 +223,15 @@ def mgfld_factor_bytes(dims: Dims, precision: int) -> int:
 
 
 def mgfld_step(dims, problem_struct, psi, ye, T, opts, ws, report=None, stream=None):
-    """One implicit step in place on (psi, ye, T) (torch CUDA FP64 tensors).
-    `report` is a dict of optional device tensors: iters, ray_status (int32),
-    ledger [n_ray, 8], heating [n_ray] (float64), factorizations (int32)."""
+    """One implicit step in place on (psi, ye, T) (torch CUDA FP64 tensors), asynchronous on the
+    stream unless opts.profile is set.  `report` is a dict of optional device tensors: iters,
+    ray_status (int32), ledger [n_ray, 8], heating [n_ray] (float64), factorizations (int32),
+    status [1] (int32, the step's worst status once it has run)."""
     rep = None
     if report is not None:
         rep = StepReport(_ptr(report.get('iters')), _ptr(report.get('ray_status')),
                          _ptr(report.get('ledger')), _ptr(report.get('heating')),
-                         _ptr(report.get('factorizations')))
+                         _ptr(report.get('factorizations')), _ptr(report.get('status')))
     st = State(_ptr(psi), _ptr(ye), _ptr(T))
     return lib().mgfld_step(ctypes.byref(dims), ctypes.byref(problem_struct), ctypes.byref(st),
                             ctypes.byref(opts), ctypes.byref(rep) if rep is not None else None,
@@ -244,7 +245,7 @@ def mgfld_step_noalloc(dims, problem_struct, psi, ye, T, opts, report=None, stre
     if report is not None:
         rep = StepReport(_ptr(report.get('iters')), _ptr(report.get('ray_status')),
                          _ptr(report.get('ledger')), _ptr(report.get('heating')),
-                         _ptr(report.get('factorizations')))
+                         _ptr(report.get('factorizations')), _ptr(report.get('status')))
     st = State(_ptr(psi), _ptr(ye), _ptr(T))
     return lib().mgfld_step_noalloc(ctypes.byref(dims), ctypes.byref(problem_struct), ctypes.byref(st),
                                     ctypes.byref(opts), ctypes.byref(rep) if rep is not None else None,
@@ -318,26 +319,42 @@ class Stepper:
                            ledger=torch.zeros(self.n_ray, 8, dtype=torch.float64, device=device),
                            heating=torch.zeros(self.n_ray, dtype=torch.float64, device=device),
                            factorizations=torch.zeros(self.n_ray, dtype=torch.int32, device=device))
+        self.n_chunks = (self.n_ray + self.chunk - 1) // self.chunk
+        self.status = torch.zeros(self.n_chunks, dtype=torch.int32, device=device)
 
     def state_to_device(self, psi, ye, T, device='cuda'):
         import torch
         return tuple(torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64), device=device)
                      for a in (psi, ye, T))
 
-    def step(self, psi, ye, T, stream=None):
-        """Advance (psi, ye, T) in place by one step; returns the worst mgfld status."""
-        worst = MGFLD_OK
-        for lo in range(0, self.n_ray, self.chunk):
+    def step(self, psi, ye, T, stream=None, wait=True):
+        """Advance (psi, ye, T) in place by one step.  The step runs asynchronously on the stream;
+        with wait (default) the call then reads the step's status back (one synchronisation) and
+        returns the worst mgfld status, without it it returns at once (MGFLD_OK: launched) and the
+        status stays in self.status (one entry per chunk of rays) for the caller to read."""
+        for c, lo in enumerate(range(0, self.n_ray, self.chunk)):
             hi = min(self.n_ray, lo + self.chunk)
             d = Dims(hi - lo, self.n_r, self.n_e, N_SPECIES)
             ps = self.prob.struct if (lo == 0 and hi == self.n_ray) else self.prob.rays(lo, hi, self.n_r, self.n_e)
             rep = {k: v[lo:hi] for k, v in self.report.items()}
+            rep['status'] = self.status[c:c + 1]
             rc = mgfld_step(d, ps, psi[lo:hi], ye[lo:hi], T[lo:hi], self.opts, self.ws, rep, stream)
             if rc in (MGFLD_EINVAL, MGFLD_ENOMEM, MGFLD_ECUDA):
                 raise MgfldError(rc, 'mgfld_step')
-            if rc == MGFLD_ENAN or (rc == MGFLD_ENOCONV and worst != MGFLD_ENAN):
-                worst = rc
-        return worst
+            if self.opts.profile:                  # the host-driven loop: rc is the step's status
+                self.status[c] = rc
+        if not wait:
+            return MGFLD_OK
+        return self.worst_status()
+
+    def worst_status(self):
+        """The worst status of the last step over its chunks (synchronises)."""
+        codes = self.status.cpu().tolist()
+        if MGFLD_ECUDA in codes:
+            raise MgfldError(MGFLD_ECUDA, 'mgfld_step (bounded wait)')
+        if MGFLD_ENAN in codes:
+            return MGFLD_ENAN
+        return MGFLD_ENOCONV if MGFLD_ENOCONV in codes else MGFLD_OK
 
 
 def eadv_problem(t, limit=True):

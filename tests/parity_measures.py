@@ -65,7 +65,9 @@ def stepwise(M, torch, inp, precision, steps, gate, label, **step_kw):
         got = (psi.cpu().numpy(), ye.cpu().numpy(), T.cpu().numpy())
         ref = O.step(prob, *prev)
         report(f'{label}, step {s + 1} from the same state', got[0], ref['psi'], gate)
-        assert np.max(np.abs(got[2] / ref['T'] - 1.0)) < gate
+        t_err = float(np.max(np.abs(got[2] / ref['T'] - 1.0)))
+        print(f'  T relative {t_err:.2e}')
+        assert t_err < gate
         prev = got
     rep = {k: v.cpu().numpy() for k, v in st.report.items()}
     psi_o, ye_o, T_o, _ = O.run_steps(prob, inp['psi0'], inp['ye0'], inp['T0'], steps)

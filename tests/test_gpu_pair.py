@@ -67,13 +67,16 @@ def test_strong_coupling_with_pairs(precision, pair, chi):
     print(f'  iterations {rep["iters"].tolist()}, factorisations {rep["factorizations"].tolist()}')
 
 
-@pytest.mark.parametrize('precision,gate', [(0, 1e-12), (1, 1e-10)])
-def test_benchmark_rays_with_pairs(precision, gate):
+@pytest.mark.parametrize('precision,gate,tol', [(0, 1e-12, 1e-12), (1, 1e-10, 1e-11)])
+def test_benchmark_rays_with_pairs(precision, gate, tol):
+    """The pair process moves much energy between the neutrinos and the matter on these rays, so T
+    (from the sources of every group, weighted by eps^3) follows the convergence of psi less
+    tightly than psi does: the mixed path iterates to 1e-11 here to hold T at its 1e-10."""
     inp = _benchmark_rays()
     _, codes, rep, _ = PM.stepwise(M, torch, inp, precision, 2, gate, f'3 benchmark rays with pairs, {precision}',
-                                   tol=1e-12 if precision == 0 else 1e-10, max_iter=40)
+                                   tol=tol, max_iter=40)
     assert codes == [M.MGFLD_OK] * 2
-    _ledgers_balanced(rep)
+    _ledgers_balanced(rep, en=1e-12 if precision == 0 else 1e-10)
     # the process is not inert on these rays
     plain = problems.make_problem(3, rays=[0, 511, 1023])
     st = M.Stepper(plain, precision, tol=1e-12 if precision == 0 else 1e-10, max_iter=40)
@@ -96,7 +99,9 @@ def test_full_launch_with_pairs_sampled():
     torch.cuda.synchronize()
     rep = {k: v.cpu().numpy() for k, v in st.report.items()}
     assert rc == M.MGFLD_OK and np.all(rep['ray_status'] == 0)
-    _ledgers_balanced(rep, lep=1e-12)
+    # lepton number balances to rounding; the energy to the iteration's tolerance (the sources of
+    # Eq. a62b are those of the last iterate, whose residual is set by tol)
+    _ledgers_balanced(rep, lep=1e-12, en=1e-10)
     rays = [5, 600, 1000]
     sub = problems.subset_rays(full, rays)
     out = O.step(sub['problem'], sub['psi0'], sub['ye0'], sub['T0'])
