@@ -320,8 +320,8 @@ def roofline_for(res, inp, precision):
     per_clk = FP32_FLOP_PER_CLK_SM if fp32 else FP64_FLOP_PER_CLK_SM
     peak = per_clk * N_SM * SM_HZ / 1e12
     launches = max(prof[dom]['launches'], 1)
-    kname = {'factor': 'k_factor_w32' if fp32 else 'k_factor', 'assemble': 'k_assemble'}[dom]
-    tr = traffic_record({'k_factor_w32': 'k_factor_f32'}.get(kname, kname))
+    kname = {'factor': 'k_factor_row2' if fp32 else 'k_factor', 'assemble': 'k_assemble'}[dom]
+    tr = traffic_record(kname)
     traffic = None
     if tr is not None:
         units_per_launch = (res['nfact'] if dom == 'factor' else res['iters']) * inp['psi0'].shape[1] / launches
@@ -332,7 +332,7 @@ def roofline_for(res, inp, precision):
 
 
 def factor_roofline(res, inp):
-    """HBM roofline of the mixed path's FP32 block factorisation (k_factor_w32), the kernel that
+    """HBM roofline of the mixed path's FP32 block factorisation (k_factor_row2), the kernel that
     moves the FP32 blocks: per (zone, system) factorisation the N x N Jacobian block read and its
     N x N inverse written (2 x 4 N^2 B) plus the two FP32 couplings (8 N B).  Its FP32 flops
     (2 N^3 + 2 N^2) are reported beside it as a fraction of the derived FP32 peak."""
@@ -343,9 +343,9 @@ def factor_roofline(res, inp):
     per_unit = 8 * n * n + 8 * n
     gbs = per_unit * units / (prof['ms'] * 1e-3) / 1e9
     tfs = (2.0 * n**3 + 2.0 * n**2) * units / (prof['ms'] * 1e-3) / 1e12
-    tr = traffic_record('k_factor_f32')
+    tr = traffic_record('k_factor_row2')
     traffic = None if tr is None else tr['bytes'] / tr['units'] * (units / n_r / launches)
-    return dict(bound='hbm', kernel='k_factor_w32', achieved=gbs, peak=PEAK_HBM_GBS, unit='GB/s',
+    return dict(bound='hbm', kernel='k_factor_row2', achieved=gbs, peak=PEAK_HBM_GBS, unit='GB/s',
                 frac=gbs / PEAK_HBM_GBS, traffic=traffic, peak_source=HBM_SOURCE, bytes_per_zone_system=per_unit,
                 fp32_tflops=tfs, fp32_frac=tfs / PEAK_FP32_TFS, fp32_peak_source=PEAK_SOURCE % FP32_FLOP_PER_CLK_SM,
                 kernel_ms_per_launch=prof['ms'] / launches, kernel_share=prof['ms'] / res['ms'])

@@ -881,6 +881,195 @@ k_factor_w32(int n, int n_r, int n_sys, const TIn *__restrict__ diag, const TC *
   if (half == 1) asm volatile("bar.sync %0, 64;" ::"r"(1 + (wid >> 1)) : "memory");
 }
 
+// ---------------------------------------------------------------------------------------
+// FP32 factor of the outer iteration with two block rows per lane (the mixed path's zone blocks,
+// M-matrices: no row exchanges).  L = NP/2 lanes hold a half-system, lane m rows m and m + L, and a
+// warp holds S = 32 / L half-systems (three at NP = 20); warp 0 of a CTA takes the top-down halves
+// and warp 1 the bottom-up halves of the same S systems.  Every pivot row is read from shared memory
+// once per lane for its two rows, so a broadcast serves twice the rows and S systems at once: the
+// shared-memory traffic per system, which bounds the one-row-per-lane kernel, drops about threefold.
+// Gauss-Jordan with 2 x 2 pivot blocks as gj_invert_np2; the Schur term of the next zone is formed
+// from the lane's own rows of the inverse, still in registers (row r of the inverse stays with the
+// lane of row r); the next zone's rows and couplings arrive by asynchronous copies issued one zone
+// ahead.  A zone whose 2 x 2 pivot block is singular or not finite leaves its inverse non-finite
+// (the outer iteration then reports ENAN for the ray); the ABI's factor of arbitrary systems uses
+// the pivoting kernel above.
+template <int NP>
+struct Row2 {
+  static constexpr int L = NP / 2;                 // lanes per half-system
+  static constexpr int S = 32 / L;                 // half-systems per warp
+  static constexpr int PAD = NP + 4;               // row stride of the shared-memory rows (floats)
+};
+
+template <int NP>
+__global__ void __launch_bounds__(64, 8)
+k_factor_row2(int n_r, int n_sys, const float *__restrict__ diag, const float *__restrict__ lower,
+              const float *__restrict__ upper, float *__restrict__ dinv, const int *__restrict__ ray_list,
+              const int *__restrict__ n_dev) {
+  using C = Row2<NP>;
+  constexpr int L = C::L, S = C::S, PD = C::PAD;
+  static_assert(NP % 4 == 0 && L % 2 == 0, "pivot pairs in one lane pair, rows in 16-byte pieces");
+  __shared__ __align__(16) float rows[2][S][NP][PD];       // the next zone's rows, per warp
+  __shared__ __align__(16) float cpl[2][S][2][NP];         // its couplings (to the previous / next zone)
+  __shared__ __align__(16) float prow[2][2][S][2][PD];     // per warp, double-buffered pivot row pairs
+  __shared__ __align__(16) float ucol[2][S][NP];           // column scaling of the next zone's Schur term
+  __shared__ __align__(16) float midt[S][NP][PD];          // bottom-up half's last inverse (middle zone)
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int half = wid;                                    // 0: zones 0..m top-down, 1: n_r-1..m+1 bottom-up
+  const int g = lane / L, mm = lane % L;                   // half-system of the warp, lane in it
+  const int n_sys_e = listed_sys(n_sys, n_dev, NS);
+  const long j0 = (long)blockIdx.x * S;
+  if (j0 >= n_sys_e) return;                               // the whole CTA
+  const long jsys = j0 + g;
+  const bool valid = g < S && jsys < n_sys_e;
+  const long sys = valid ? system_of(jsys, ray_list) : 0;
+  const int gs = g < S ? g : 0;                            // shared-memory slot (idle lanes use 0)
+  const int m = n_r / 2;
+  const int len = half == 0 ? m + 1 : n_r - 1 - m;
+  auto zone = [&](int j) { return half == 0 ? j : n_r - 1 - j; };
+  const int r0 = mm, r1 = mm + L;                          // this lane's two rows
+  auto issue = [&](int j) {                                // rows and couplings of zone j
+    if (valid && j < len) {
+      const size_t zb = ((size_t)sys * n_r + zone(j)) * NP;
+#pragma unroll
+      for (int c = 0; c < NP; c += 4) {
+        cp_async16(&rows[wid][gs][r0][c], diag + (zb + r0) * NP + c);
+        cp_async16(&rows[wid][gs][r1][c], diag + (zb + r1) * NP + c);
+      }
+      const float *lin = half == 0 ? lower : upper, *lout = half == 0 ? upper : lower;
+      cp_async4(&cpl[wid][gs][0][r0], lin + zb + r0);
+      cp_async4(&cpl[wid][gs][0][r1], lin + zb + r1);
+      cp_async4(&cpl[wid][gs][1][r0], lout + zb + r0);
+      cp_async4(&cpl[wid][gs][1][r1], lout + zb + r1);
+    }
+    cp_async_commit();
+  };
+  float a0[NP], a1[NP];
+  issue(0);
+  for (int j = 0; j < len; ++j) {
+    cp_async_wait_all();
+    __syncwarp();
+    // the zone's rows minus the Schur term of the previous zone: row r gets
+    // -l_r (row r of the previous inverse, this lane's registers) * u_prev (column scaling)
+    const float l0 = (valid && j > 0) ? cpl[wid][gs][0][r0] : 0.f;
+    const float l1 = (valid && j > 0) ? cpl[wid][gs][0][r1] : 0.f;
+    const float u0 = valid ? cpl[wid][gs][1][r0] : 0.f, u1 = valid ? cpl[wid][gs][1][r1] : 0.f;
+#pragma unroll
+    for (int c = 0; c < NP; c += 4) {
+      float4 x0 = valid ? *reinterpret_cast<const float4 *>(&rows[wid][gs][r0][c]) : make_float4(0.f, 0.f, 0.f, 0.f);
+      float4 x1 = valid ? *reinterpret_cast<const float4 *>(&rows[wid][gs][r1][c]) : make_float4(0.f, 0.f, 0.f, 0.f);
+      if (!valid) {                                        // identity blocks for lanes without a system
+        x0 = make_float4(c == r0 ? 1.f : 0.f, c + 1 == r0 ? 1.f : 0.f, c + 2 == r0 ? 1.f : 0.f, c + 3 == r0 ? 1.f : 0.f);
+        x1 = make_float4(c == r1 ? 1.f : 0.f, c + 1 == r1 ? 1.f : 0.f, c + 2 == r1 ? 1.f : 0.f, c + 3 == r1 ? 1.f : 0.f);
+      }
+      if (j > 0) {
+        const float4 u = *reinterpret_cast<const float4 *>(&ucol[wid][gs][c]);
+        x0.x = fmaf(-(l0 * a0[c]), u.x, x0.x);
+        x0.y = fmaf(-(l0 * a0[c + 1]), u.y, x0.y);
+        x0.z = fmaf(-(l0 * a0[c + 2]), u.z, x0.z);
+        x0.w = fmaf(-(l0 * a0[c + 3]), u.w, x0.w);
+        x1.x = fmaf(-(l1 * a1[c]), u.x, x1.x);
+        x1.y = fmaf(-(l1 * a1[c + 1]), u.y, x1.y);
+        x1.z = fmaf(-(l1 * a1[c + 2]), u.z, x1.z);
+        x1.w = fmaf(-(l1 * a1[c + 3]), u.w, x1.w);
+      }
+      a0[c] = x0.x; a0[c + 1] = x0.y; a0[c + 2] = x0.z; a0[c + 3] = x0.w;
+      a1[c] = x1.x; a1[c + 1] = x1.y; a1[c + 2] = x1.z; a1[c + 3] = x1.w;
+    }
+    __syncwarp();                                          // every lane has read the rows and ucol
+    issue(j + 1);
+    if (half == 0 && j == m) {
+      // middle zone: wait for the bottom-up half (which arrives once, after its last zone, whatever
+      // its length) and subtract its term diag(u_m) D''^{-1}_{m+1} diag(l_{m+1}) as well
+      asm volatile("bar.sync 1, 64;" ::: "memory");
+      if (n_r - 1 > m) {
+#pragma unroll
+        for (int c = 0; c < NP; ++c) {
+          const float lc = ucol[1][gs][c];
+          a0[c] = fmaf(-(u0 * midt[gs][r0][c]), lc, a0[c]);
+          a1[c] = fmaf(-(u1 * midt[gs][r1][c]), lc, a1[c]);
+        }
+      }
+    }
+    // Gauss-Jordan inversion with 2 x 2 pivot blocks (rows p, p + 1: lanes p % L and p % L + 1 of
+    // slot p / L, known at compile time)
+#pragma unroll
+    for (int b = 0; b < NP / 2; ++b) {
+      const int p = 2 * b, sl = p / L, pl = p % L;
+      float (*pb)[2][PD] = prow[wid][b & 1];
+      if (g < S && (mm == pl || mm == pl + 1)) {          // lanes beyond the S half-systems publish nothing
+        float *dst = pb[gs][mm - pl];
+#pragma unroll
+        for (int c = 0; c < NP; c += 2) {
+          if (sl == 0) *reinterpret_cast<float2 *>(dst + c) = make_float2(a0[c], a0[c + 1]);
+          else *reinterpret_cast<float2 *>(dst + c) = make_float2(a1[c], a1[c + 1]);
+        }
+      }
+      __syncwarp();
+      const float2 q0 = *reinterpret_cast<const float2 *>(&pb[gs][0][p]);
+      const float2 q1 = *reinterpret_cast<const float2 *>(&pb[gs][1][p]);
+      const float det = fmaf(q0.x, q1.y, -(q0.y * q1.x));
+      const float idet = rcp_nr(det);
+      const float i00 = q1.y * idet, i01 = -q0.y * idet, i10 = -q1.x * idet, i11 = q0.x * idet;
+      // multipliers of the two rows: owners take the rows of P^{-1} times the pivot rows
+      float f00, f01, f10, f11;
+      if (sl == 0 && mm == pl) { f00 = 1.f - i00; f01 = -i01; }
+      else if (sl == 0 && mm == pl + 1) { f00 = -i10; f01 = 1.f - i11; }
+      else { f00 = fmaf(a0[p], i00, a0[p + 1] * i10); f01 = fmaf(a0[p], i01, a0[p + 1] * i11); }
+      if (sl == 1 && mm == pl) { f10 = 1.f - i00; f11 = -i01; }
+      else if (sl == 1 && mm == pl + 1) { f10 = -i10; f11 = 1.f - i11; }
+      else { f10 = fmaf(a1[p], i00, a1[p + 1] * i10); f11 = fmaf(a1[p], i01, a1[p + 1] * i11); }
+#pragma unroll
+      for (int c = 0; c < NP; c += 4) {
+        const float4 v0 = *reinterpret_cast<const float4 *>(&pb[gs][0][c]);
+        const float4 v1 = *reinterpret_cast<const float4 *>(&pb[gs][1][c]);
+        float2 lo = __ffma2_rn(make_float2(-f00, -f00), make_float2(v0.x, v0.y), make_float2(a0[c], a0[c + 1]));
+        float2 hi = __ffma2_rn(make_float2(-f00, -f00), make_float2(v0.z, v0.w), make_float2(a0[c + 2], a0[c + 3]));
+        lo = __ffma2_rn(make_float2(-f01, -f01), make_float2(v1.x, v1.y), lo);
+        hi = __ffma2_rn(make_float2(-f01, -f01), make_float2(v1.z, v1.w), hi);
+        a0[c] = lo.x; a0[c + 1] = lo.y; a0[c + 2] = hi.x; a0[c + 3] = hi.y;
+        lo = __ffma2_rn(make_float2(-f10, -f10), make_float2(v0.x, v0.y), make_float2(a1[c], a1[c + 1]));
+        hi = __ffma2_rn(make_float2(-f10, -f10), make_float2(v0.z, v0.w), make_float2(a1[c + 2], a1[c + 3]));
+        lo = __ffma2_rn(make_float2(-f11, -f11), make_float2(v1.x, v1.y), lo);
+        hi = __ffma2_rn(make_float2(-f11, -f11), make_float2(v1.z, v1.w), hi);
+        a1[c] = lo.x; a1[c + 1] = lo.y; a1[c + 2] = hi.x; a1[c + 3] = hi.y;
+      }
+      if (sl == 0 && mm == pl) { a0[p] = i00; a0[p + 1] = i01; }
+      else if (sl == 0 && mm == pl + 1) { a0[p] = i10; a0[p + 1] = i11; }
+      else { a0[p] = -f00; a0[p + 1] = -f01; }
+      if (sl == 1 && mm == pl) { a1[p] = i00; a1[p + 1] = i01; }
+      else if (sl == 1 && mm == pl + 1) { a1[p] = i10; a1[p + 1] = i11; }
+      else { a1[p] = -f10; a1[p + 1] = -f11; }
+    }
+    // the inverse rows to the factor buffer, and this zone's coupling to the next zone of the
+    // sequence (column scaling of the next Schur term) to the warp's shared row
+    if (valid) {
+      float *o0 = dinv + (((size_t)sys * n_r + zone(j)) * NP + r0) * NP;
+      float *o1 = dinv + (((size_t)sys * n_r + zone(j)) * NP + r1) * NP;
+#pragma unroll
+      for (int c = 0; c < NP; c += 4) {
+        *reinterpret_cast<float4 *>(o0 + c) = make_float4(a0[c], a0[c + 1], a0[c + 2], a0[c + 3]);
+        *reinterpret_cast<float4 *>(o1 + c) = make_float4(a1[c], a1[c + 1], a1[c + 2], a1[c + 3]);
+      }
+    }
+    if (g < S) {
+      ucol[wid][gs][r0] = u0;
+      ucol[wid][gs][r1] = u1;
+    }
+    if (half == 1 && j == len - 1 && g < S) {
+      // the bottom-up half's last inverse for the middle zone of the top-down half
+#pragma unroll
+      for (int c = 0; c < NP; ++c) {
+        midt[gs][r0][c] = a0[c];
+        midt[gs][r1][c] = a1[c];
+      }
+    }
+    __syncwarp();
+  }
+  cp_async_wait_all();
+  if (half == 1) asm volatile("bar.sync 1, 64;" ::: "memory");
+}
+
 // Forward/back substitution with the twisted FP32 factors, two warps per system (the top-down
 // and bottom-up halves), lane r owning block row r; the halves meet at the middle zone m through
 // shared memory and a two-warp named barrier.
@@ -1418,6 +1607,14 @@ cudaError_t launch_factor_f32(int n, int n_r, int n_sys, const float *diag, cons
                               const float *upper32, float *dinv, const int *ray_list, cudaStream_t s,
                               const int *n_dev) {
   if (n_sys == 0) return cudaSuccess;
+  if (n % 4 == 0) {
+    // blocks of a multiple of 4 rows: two rows per lane
+    MGFLD_DISPATCH_NP(n, constexpr int S = Row2<NP>::S;
+                      k_factor_row2<NP><<<(unsigned)((n_sys + S - 1) / S), 64, 0, s>>>(n_r, n_sys, diag, lower32,
+                                                                                         upper32, dinv, ray_list,
+                                                                                         n_dev);
+                      return cudaGetLastError())
+  }
   MGFLD_DISPATCH_NP(n, constexpr int W = fw_wpc<NP>();
                     const unsigned grid = (unsigned)((n_sys + W / 2 - 1) / (W / 2));
                     k_factor_w32<NP, float, float, false><<<grid, W * 32, 0, s>>>(n, n_r, n_sys, diag, lower32, upper32,
