@@ -759,7 +759,8 @@ def reference_arm(args, n_gpus, rank):
 def profile_step(path, n_rays, config):
     """One implicit step of the first n_rays rays of a workload (FP64 Newton, the mixed path, the
     mixed path with the shock terms or with the flux coefficients formed at every outer iterate),
-    two energy-advection steps, or one stress-and-lapse call, for ncu captures of single launches;
+    two energy-advection steps, or one stress-and-lapse call, for ncu captures of single launches
+    (the step with its outer iteration driven from the host, whose kernels are ordinary launches);
     exits non-zero on a failed step."""
     import torch
     from paper_1809_05608_gb300 import build as B
@@ -789,6 +790,10 @@ def profile_step(path, n_rays, config):
     prec = M.MGFLD_FP64 if path == 'fp64' else M.MGFLD_MIXED
     st = M.Stepper(inp, prec, tol=TOL, max_iter=60, coef_iterate=path == 'coef')
     psi, ye, T = st.state_to_device(inp['psi0'], inp['ye0'], inp['T0'])
+    # the host-driven outer iteration (per-category events): ncu profiles the kernels of ordinary
+    # launches, not those inside a graph with a conditional node
+    prof = (ctypes.c_double * 12)()
+    st.opts.profile = ctypes.cast(prof, ctypes.c_void_p)
     rc = st.step(psi, ye, T)
     torch.cuda.synchronize()
     print(f'profile step {path}: {n_rays} rays, status {M.status_str(rc)}, '

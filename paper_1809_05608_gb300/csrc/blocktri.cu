@@ -93,8 +93,13 @@ template <> __device__ inline float to_t<float>(double v) { return (float)v; }
 // with one FMA and updates its NP entries.  The entry of the next pivot column is updated
 // first and its key published at once, so that the next search only waits for that one FMA
 // while the other NP - 1 drain through the FP64 pipe.
+// CTAs per SM the FP64 factor is compiled for (its register budget).
+#ifndef MGFLD_FP64_MINB
+#define MGFLD_FP64_MINB 4
+#endif
+
 template <int NP, typename TIn>
-__global__ void __launch_bounds__(Pack<NP>::THREADS)
+__global__ void __launch_bounds__(Pack<NP>::THREADS, NP <= 20 ? MGFLD_FP64_MINB : 1)
 k_factor(int n, int n_r, int n_sys, const TIn *__restrict__ diag, const double *__restrict__ lower,
          const double *__restrict__ upper, double *__restrict__ dinv, const int *__restrict__ ray_list,
          const int *__restrict__ n_dev) {
@@ -116,21 +121,8 @@ k_factor(int n, int n_r, int n_sys, const TIn *__restrict__ diag, const double *
   const int m = n_r / 2;
   const int len = half == 0 ? m + 1 : n_r - 1 - m;   // zones of this half; all threads step m + 1 times
 
-  // Rows of the next zone are fetched one zone ahead (registers) to hide memory latency.
-  double nxt[NP];
-  double nl = 0.0;
-  auto load_row = [&](int j) {
-    const bool act = valid && j < len && r < n;
-    const int z = half == 0 ? j : n_r - 1 - j;
-    const size_t zr = ((size_t)sys * n_r + (act ? z : 0)) * n + r;
-#pragma unroll
-    for (int c = 0; c < NP; ++c) {
-      if (act && c < n) nxt[c] = (double)diag[zr * n + c];
-      else nxt[c] = (c == r) ? 1.0 : 0.0;
-    }
-    nl = (act && j > 0) ? (half == 0 ? lower[zr] : upper[zr]) : 0.0;
-  };
-  load_row(0);
+  // Each zone's rows are loaded when the zone starts: an FP64 zone step holds the pipe for far
+  // longer than a memory round trip, and the registers of a prefetch would cost resident CTAs.
   for (int j = 0; j <= m; ++j) {
     const bool active = j < len;                     // inactive (bottom half, j >= len): dummy identity
     const int i = half == 0 ? j : n_r - 1 - j;
@@ -138,9 +130,8 @@ k_factor(int n, int n_r, int n_sys, const TIn *__restrict__ diag, const double *
     const size_t zrow = ((size_t)sys * n_r + (real ? i : 0)) * n + r;   // (sys, i, r)
     double a[NP];
 #pragma unroll
-    for (int c = 0; c < NP; ++c) a[c] = nxt[c];
-    const double lr = nl;
-    if (j + 1 <= m) load_row(j + 1);
+    for (int c = 0; c < NP; ++c) a[c] = (real && c < n) ? (double)diag[zrow * n + c] : ((c == r) ? 1.0 : 0.0);
+    const double lr = (real && j > 0) ? (half == 0 ? lower[zrow] : upper[zrow]) : 0.0;
     if (j > 0 && active) {
 #pragma unroll
       for (int c = 0; c < NP; ++c) a[c] = fma(-(lr * tile[s][r][c]), ushr[s][c], a[c]);
@@ -174,25 +165,22 @@ k_factor(int n, int n_r, int n_sys, const TIn *__restrict__ diag, const double *
         my_step = pstep;
       }
       __syncthreads();
-      double pr[NP];
-#pragma unroll
-      for (int c = 0; c < NP; c += 2) {
-        const double2 v = *reinterpret_cast<const double2 *>(&prow[s][c]);
-        pr[c] = v.x;
-        pr[c + 1] = v.y;
-      }
       const double inv = pinv[s];
       // Uniform update for every row: a -= f * pivot_row, with f chosen so that the pivot row
       // itself becomes pivot_row / pivot (f = 1 - 1/pivot): one FMA either way.  The pivot
       // column itself is overwritten below, so its update is skipped.
       const double f = fma(me ? -1.0 : a[pstep], inv, me ? 1.0 : 0.0);
       if (pstep + 1 < NP) {
-        a[pstep + 1] = fma(-f, pr[pstep + 1], a[pstep + 1]);
+        a[pstep + 1] = fma(-f, prow[s][pstep + 1], a[pstep + 1]);
         cand[s][r] = used ? -1 : pivot_key(a[pstep + 1], r);
       }
+      // the rest of the pivot row read from shared memory as it is used (16-byte pieces)
 #pragma unroll
-      for (int c = 0; c < NP; ++c)
-        if (c != pstep + 1 && c != pstep) a[c] = fma(-f, pr[c], a[c]);
+      for (int c = 0; c < NP; c += 2) {
+        const double2 v = *reinterpret_cast<const double2 *>(&prow[s][c]);
+        if (c != pstep + 1 && c != pstep) a[c] = fma(-f, v.x, a[c]);
+        if (c + 1 != pstep + 1 && c + 1 != pstep) a[c + 1] = fma(-f, v.y, a[c + 1]);
+      }
       a[pstep] = me ? inv : -f;
     }
     // Row r now holds row my_step of the inverse, with column c belonging to input row pivrow[c].
@@ -901,8 +889,13 @@ struct Row2 {
   static constexpr int PAD = NP + 4;               // row stride of the shared-memory rows (floats)
 };
 
+// CTAs per SM the two-rows-per-lane factor is compiled for (its register budget).
+#ifndef MGFLD_ROW2_MINB
+#define MGFLD_ROW2_MINB 8
+#endif
+
 template <int NP>
-__global__ void __launch_bounds__(64, 8)
+__global__ void __launch_bounds__(64, MGFLD_ROW2_MINB)
 k_factor_row2(int n_r, int n_sys, const float *__restrict__ diag, const float *__restrict__ lower,
               const float *__restrict__ upper, float *__restrict__ dinv, const int *__restrict__ ray_list,
               const int *__restrict__ n_dev) {
