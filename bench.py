@@ -231,10 +231,15 @@ def run_path(M, torch, inp, precision, steps, warmup, barrier, clocks=None, refa
     nfact = torch.zeros_like(st.report['factorizations'])
     iters = torch.zeros_like(st.report['iters'])
     for _ in range(warmup):
-        # the same call as the timed loop (the first builds and caches the step's graph)
+        # the same calls as the timed loop (the first builds and caches the step's graph; the
+        # counters' first additions load their kernels, which a cold page cache makes slow)
         rc = st.step(psi, ye, T, wait=False)
         assert rc == M.MGFLD_OK, M.status_str(rc)
+        nfact += st.report['factorizations']
+        iters += st.report['iters']
     assert st.worst_status() == M.MGFLD_OK
+    nfact.zero_()
+    iters.zero_()
     torch.cuda.synchronize()
     barrier()
     torch.cuda.synchronize()
@@ -266,6 +271,9 @@ def run_path(M, torch, inp, precision, steps, warmup, barrier, clocks=None, refa
         prof[c] = 0.0
     pfact = torch.zeros_like(nfact)
     piters = torch.zeros_like(iters)
+    hist = torch.zeros(61, dtype=torch.int64, device=iters.device)
+    hist += torch.bincount(st.report['iters'].long(), minlength=61)[:61]   # its kernels loaded, then reset
+    hist.zero_()
     torch.cuda.synchronize()
     p0 = time.perf_counter()
     for _ in range(steps):
@@ -273,6 +281,7 @@ def run_path(M, torch, inp, precision, steps, warmup, barrier, clocks=None, refa
         assert rc == M.MGFLD_OK, M.status_str(rc)
         pfact += st.report['factorizations']
         piters += st.report['iters']
+        hist += torch.bincount(st.report['iters'].long(), minlength=61)[:61]
     torch.cuda.synchronize()
     p_ms = (time.perf_counter() - p0) * 1e3
     st.opts.profile = None
@@ -280,8 +289,8 @@ def run_path(M, torch, inp, precision, steps, warmup, barrier, clocks=None, refa
     ws_gb = (st.ws.numel() + sum(t.numel() * 8 for t in st.prob.t.values() if t is not None)) / 1e9
     out = dict(ms=ms, steps=steps, prof=prof, nfact=int(pfact.sum()), iters=int(piters.sum()),
                timed_nfact=int(nfact.sum()), timed_iters=int(iters.sum()),
-               max_iters=int(st.report['iters'].max()), iters_hist=np.bincount(iters.cpu().numpy()).tolist(),
-               clocks=clk, chunk=st.chunk, ws_gb=ws_gb, n_ray=st.n_ray, profiled_ms=p_ms)
+               max_iters=int(st.report['iters'].max()), iters_hist=np.trim_zeros(hist.cpu().numpy(), 'b').tolist(),
+               clocks=clk, chunk=st.chunk, ws_gb=ws_gb, n_ray=st.n_ray, profiled_ms=p_ms, coef=coef_iterate)
     if keep:
         out['stepper'] = st
         out['state'] = (psi, ye, T)
@@ -291,20 +300,23 @@ def run_path(M, torch, inp, precision, steps, warmup, barrier, clocks=None, refa
     return out
 
 
-def algorithmic_work(inp, kernel, nfact, iters, precision):
+def algorithmic_work(inp, kernel, nfact, iters, precision, coef=False):
     """Algorithmic flop count over the timed steps for one kernel category.
 
     factor: per (zone, system) factorisation, N^3 FMAs of in-place Gauss-Jordan plus
     2 N^2 for the diagonal Schur scaling: 2 N^3 + 2 N^2 flops (FP64 or FP32).
     assemble (FP64 pipe only): per (zone, system, iteration) residual, two length-N NES sums
     per row (4 N^2) + 16 N of transport/absorption terms; with a fresh FP64 Jacobian one FMA
-    per entry (2 N^2).  The mixed path's Jacobian rows are FP32 and are not counted."""
+    per entry (2 N^2).  The mixed path's Jacobian rows are FP32 and are not counted.  With the
+    flux coefficients formed at every iterate (coef) the NES sums arrive from the coefficient
+    pass and the residual forms its rows from the coefficients and the limiter's derivatives
+    (32 N)."""
     n_ray, n_s, n_r, n = inp['psi0'].shape
     if kernel == 'factor':
         per = 2.0 * n**3 + 2.0 * n**2
         return per * n_s * n_r * nfact
     if kernel == 'assemble':
-        per_res = 4.0 * n**2 + 16.0 * n
+        per_res = 32.0 * n if coef else 4.0 * n**2 + 16.0 * n
         per_jac = 2.0 * n**2 if precision == 0 else 0.0
         return n_s * n_r * (per_res * iters + per_jac * nfact)
     raise ValueError(kernel)
@@ -314,7 +326,7 @@ def roofline_for(res, inp, precision):
     """Roofline of the dominant kernel of the residual/Jacobian and factor categories."""
     prof = res['prof']
     dom = max(('assemble', 'factor'), key=lambda k: prof[k]['ms'])
-    flops = algorithmic_work(inp, dom, res['nfact'], res['iters'], precision)
+    flops = algorithmic_work(inp, dom, res['nfact'], res['iters'], precision, coef=res.get('coef', False))
     achieved = flops / (prof[dom]['ms'] * 1e-3) / 1e12
     fp32 = dom == 'factor' and precision == 1
     per_clk = FP32_FLOP_PER_CLK_SM if fp32 else FP64_FLOP_PER_CLK_SM
@@ -375,16 +387,18 @@ def solve_roofline(res, inp):
                 kernel_share=prof['ms'] / res['ms'])
 
 
-def category_work(n, precision):
+def category_work(n, precision, coef=False):
     """Algorithmic work of each kernel category, per unit, for N = n groups.
 
     Returns {category: (unit, fp64 flop, fp32 flop, HBM bytes)} with units:
       'step'  per (zone, system) and step;
       'iter'  per (zone, system) and outer iteration of its ray;
+      'citer' per (zone, system) and outer iteration after the first (coef only);
       'fact'  per (zone, system) and factorisation;
-    and a second entry '<category>_fact' for the per-factorisation part of a category that has one.
-    FP64 (precision 0) vs mixed (1) as the two paths compute.  Counted from the formulas (not from
-    the instructions the kernels issue): see the work table of the design notes."""
+    and a second entry '<category>_<unit>' for a further part of a category.
+    FP64 (precision 0) vs mixed (1) as the two paths compute; coef: the flux coefficients formed
+    again at every outer iterate.  Counted from the formulas (not from the instructions the
+    kernels issue): see the work table of the design notes."""
     N = float(n)
     mixed = precision == 1
     blk = 4.0 if mixed else 8.0
@@ -415,6 +429,13 @@ def category_work(n, precision):
         'finish': ('step', 16 * N + (0.0 if mixed else 4 * N * N), 2 * N * N if mixed else 0.0,
                    (2 if mixed else 4) * N * N + 40 * N),
     }
+    if coef:
+        # the coefficients at the iterate: the NES sums (4 N^2, handed on to the residual), the
+        # mean free path, the neutrinosphere scan and the limiter with its two derivatives (~50 N);
+        # NES kernels read (4 N^2 B), psi and sqrt(lambda) read, seven coefficient arrays written
+        w['setup_citer'] = ('citer', 4 * N * N + 50 * N, 0.0, 4 * N * N + 96 * N)
+        # the residual rows from the kept sums, the coefficients and the limiter's derivatives
+        w['assemble'] = ('iter', 32 * N, 0.0, 88 * N)
     return w
 
 
@@ -425,10 +446,11 @@ def step_roofline(res, inp, precision):
     per-ray iteration and factorisation counts."""
     n_ray, n_s, n_r, n = inp['psi0'].shape
     zs = n_s * n_r                               # (zone, system) pairs per ray
-    units = dict(step=zs * n_ray * res['steps'], iter=zs * res['iters'], fact=zs * res['nfact'])
+    units = dict(step=zs * n_ray * res['steps'], iter=zs * res['iters'], fact=zs * res['nfact'],
+                 citer=zs * (res['iters'] - n_ray * res['steps']))
     cats = {}
     tot64 = tot32 = totb = t_roof = 0.0
-    for name, (unit, f64, f32, b) in category_work(n, precision).items():
+    for name, (unit, f64, f32, b) in category_work(n, precision, coef=res.get('coef', False)).items():
         u = units[unit]
         F64, F32, B = f64 * u, f32 * u, b * u
         t64 = F64 / (PEAK_FP64_TFS * 1e12)
@@ -545,26 +567,36 @@ def _oracle_worker(job):
     return 0
 
 
-def _warm_worker(_):
+def _init_worker(barrier):
+    """Pool start-up: the oracle's imports, then a wait until every worker has done them, so that
+    no worker is still starting (and taking host cores) once the pool is handed over."""
     from oracle import mgfld_oracle  # noqa: F401
+    try:
+        barrier.wait(timeout=600)
+    except Exception:
+        pass
+
+
+def _warm_worker(_):
     return os.getpid()
 
 
 class OraclePool:
     """A process pool over rays for the CPU oracle (rays are independent), started with `spawn`
-    and with one BLAS thread per process, so that each worker is one host core."""
+    and with one BLAS thread per process, so that each worker is one host core.  Every worker is
+    started and has imported the oracle before the constructor returns."""
 
     def __init__(self, cores=None):
-        import concurrent.futures
         import multiprocessing
         self.cores = cores or host_cores()
         saved = {k: os.environ.get(k) for k in ('OMP_NUM_THREADS', 'OPENBLAS_NUM_THREADS', 'MKL_NUM_THREADS')}
         for k in saved:
             os.environ[k] = '1'
         try:
-            self.ex = concurrent.futures.ProcessPoolExecutor(self.cores,
-                                                             mp_context=multiprocessing.get_context('spawn'))
-            list(self.ex.map(_warm_worker, range(self.cores)))      # start-up outside any timing
+            ctx = multiprocessing.get_context('spawn')
+            barrier = ctx.Barrier(self.cores)
+            self.ex = ctx.Pool(self.cores, initializer=_init_worker, initargs=(barrier,))
+            self.ex.map(_warm_worker, range(self.cores), chunksize=1)   # start-up outside any timing
         finally:
             for k, v in saved.items():
                 if v is None:
@@ -576,11 +608,12 @@ class OraclePool:
         """Wall time of the oracle on the given rays, one pool task per ray."""
         jobs = [(problems.subset_rays(inp, slice(r, r + 1)), n_steps, kw) for r in rays]
         w0 = time.perf_counter()
-        list(self.ex.map(_oracle_worker, jobs))
+        self.ex.map(_oracle_worker, jobs, chunksize=1)
         return time.perf_counter() - w0
 
     def close(self):
-        self.ex.shutdown()
+        self.ex.close()
+        self.ex.join()
 
 
 def oracle_sample(inp, n_rays, n_steps=1, **step_kw):

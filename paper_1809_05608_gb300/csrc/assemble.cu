@@ -45,7 +45,7 @@ __global__ void k_assemble(Prob p, Ws w, const double *__restrict__ psi, TD *__r
   const double *fin = w.phin + (zi * n + k) * n;
   const double *fout = w.phout + (zi * n + k) * n;
   double gain = 0.0, lp = 0.0;
-  if (first) {                 // psi = psi^n: the setup already formed these sums
+  if (first) {                 // formed at this psi already: by the setup (psi^n) or with the n+1 coefficients
     gain = w.g0[g];
     lp = w.l0[g];
   } else if (src_out && w.phin32) {
@@ -88,8 +88,7 @@ __global__ void k_assemble(Prob p, Ws w, const double *__restrict__ psi, TD *__r
     if (i > 0) G = fma(-c_low, ps[k - (ptrdiff_t)n], G);
   } else {
     const double loss = w.rsum[zi * n + k] - lp;          // sum_k' phout (1 - psi_k')
-    const double sc = p.scale ? p.scale[q * n + k] : 1.0;
-    const double kap = p.kabs[g] * sc;
+    const double kap = scaled(p, p.kabs, g, q, k);
     const double S = j * (1.0 - pk) - kap * pk + ((1.0 - pk) * gain - pk * loss);
     if (src_out) {               // converged sources for Eq. a62b and the ledgers
       src_out[g] = S;
@@ -133,12 +132,14 @@ __global__ void k_assemble(Prob p, Ws w, const double *__restrict__ psi, TD *__r
   if (jac_flag && !jac_flag[ray]) return;
   TD *row = diag + g * n;
   // dS_k/dpsi_k' = (1 - psi_k) phin + psi_k phout = phin - psi_k phd, entered with a minus;
-  // dg joins the diagonal entry in FP64.  Rows are written 16 bytes at a time where n allows
+  // dg joins the diagonal entry in the rows' precision.  Rows are written 16 bytes at a time where n allows
   // (the rows of one warp's threads are 16-byte aligned and contiguous per species).
   if (sizeof(TD) == 4 && w.phin32) {
     const float *fi = w.phin32 + (zi * n + k) * n, *fd = w.phd32 + (zi * n + k) * n;
-    const float pf = (float)pk;
-    const float dk = (float)((double)fmaf(pf, fd[k], -fi[k]) + dg);
+    // FP32 operands from the integer pipe (truncated; the FP32 Jacobian is the preconditioner of
+    // the FP64 refinement), dg joining the diagonal in FP32
+    const float pf = d2f_exp2(pk, 0);
+    const float dk = fmaf(pf, fd[k], -fi[k]) + (float)dg;
     if ((n & 3) == 0) {
       for (int c = 0; c < n; c += 4) {
         const float4 a = *reinterpret_cast<const float4 *>(fi + c);
@@ -177,8 +178,8 @@ __global__ void k_assemble(Prob p, Ws w, const double *__restrict__ psi, TD *__r
   lower[g] = -c_low;
   upper[g] = -c_up;
   if (w.lower32) {
-    w.lower32[g] = (float)lower[g];
-    w.upper32[g] = (float)upper[g];
+    w.lower32[g] = d2f_exp2(-c_low, 0);
+    w.upper32[g] = d2f_exp2(-c_up, 0);
   }
 }
 
@@ -195,6 +196,70 @@ cudaError_t launch_assemble(const Prob &p, const Ws &w, const double *psi, void 
   else
     k_assemble<double><<<grid, B, 0, s>>>(p, w, psi, (double *)diag, lower, upper, rhs, list, n_list,
                                           jac_flag, src_out, first, n_dev);
+  return cudaGetLastError();
+}
+
+// The converged sources of the mixed path for Eq. a62b and the ledgers, one thread per (ray, q, i,
+// k) of every ray:
+//   S = j (1 - psi) - kappa_a psi + (1 - psi) gain - psi loss          (Eqs. a55, d8)
+// at psi = psi_m + dpsi (dpsi the ray's last, sub-tolerance correction w.x): gain and
+// loss = rsum - lp from the sums of the ray's last residual at psi_m (g0, l0) plus phin.dpsi and
+// (phin - phd).dpsi taken in FP32 (|dpsi| is below the tolerance, so their FP32 rounding stays far
+// below the FP64 rounding of the sums), the two corrections joined in FP32 before one conversion.
+// The block stages the corrections of the rows it covers in shared memory as FP32, one conversion
+// per value instead of one per product.
+constexpr int kSrcThreads = 256;
+__global__ void __launch_bounds__(kSrcThreads)
+k_src_mixed(Prob p, Ws w, const double *__restrict__ psi, double *__restrict__ src) {
+  __shared__ float xs[kSrcThreads + 2 * MAX_NE];
+  const int n = p.n;
+  const unsigned per_ray = (unsigned)(NS * p.n_r * n);
+  const unsigned total = (unsigned)p.n_ray * per_ray;
+  const unsigned b0 = blockIdx.x * kSrcThreads;
+  const unsigned last = min(b0 + kSrcThreads, total) - 1;
+  const unsigned gq0 = b0 / (unsigned)n;                    // first (ray, zone, species) row group
+  const unsigned cnt = (last / (unsigned)n - gq0 + 1) * (unsigned)n;
+  for (unsigned j = threadIdx.x; j < cnt; j += kSrcThreads) {
+    const unsigned gq = gq0 + j / (unsigned)n, kk = j % (unsigned)n;
+    const unsigned ray = gq / (unsigned)(NS * p.n_r), rem = gq - ray * (unsigned)(NS * p.n_r);
+    const unsigned i = rem / NS, q = rem - i * NS;
+    xs[j] = (float)w.x[(((size_t)ray * NS + q) * p.n_r + i) * n + kk];
+  }
+  __syncthreads();
+  const unsigned t = b0 + threadIdx.x;
+  if (t >= total) return;
+  const unsigned ray = t / per_ray;
+  const unsigned local = t - ray * per_ray;
+  const unsigned kq = local / (unsigned)n;
+  const int k = (int)(local - kq * n);
+  const int q = (int)(kq % NS);
+  const int i = (int)(kq / NS);
+  const size_t g = (((size_t)ray * NS + q) * p.n_r + i) * n + k;
+  const size_t zi = (size_t)ray * p.n_r + i;
+  const float *fi = w.phin32 + (zi * n + k) * n, *fd = w.phd32 + (zi * n + k) * n;
+  const float *dx = xs + (t / (unsigned)n - gq0) * (unsigned)n;
+  float dg = 0.f, dl = 0.f;
+  for (int kp = 0; kp < n; ++kp) {
+    const float d = dx[kp], a = fi[kp];
+    dg = fmaf(a, d, dg);
+    dl = fmaf(a - fd[kp], d, dl);
+  }
+  const double pk = psi[g];
+  const double q1 = 1.0 - pk;
+  const float pf = d2f_exp2(pk, 0);
+  // (1 - psi) dgain + psi dlp: the FP32 part of (1 - psi) gain - psi loss
+  const float corr = fmaf(1.f - pf, dg, pf * dl);
+  const double kap = scaled(p, p.kabs, g, q, k);
+  const double loss0 = w.rsum[zi * n + k] - w.l0[g];
+  double S = fma(q1, w.g0[g], fma(-pk, loss0, (double)corr));
+  S = fma(w.jbuf[g], q1, fma(-kap, pk, S));
+  src[g] = S;
+}
+
+cudaError_t launch_src_mixed(const Prob &p, const Ws &w, const double *psi, double *src, cudaStream_t s) {
+  const size_t total = (size_t)p.n_ray * NS * p.n_r * p.n;
+  if (total == 0) return cudaSuccess;
+  k_src_mixed<<<(unsigned)((total + kSrcThreads - 1) / kSrcThreads), kSrcThreads, 0, s>>>(p, w, psi, src);
   return cudaGetLastError();
 }
 

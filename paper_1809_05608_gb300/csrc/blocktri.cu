@@ -891,7 +891,7 @@ struct Row2 {
 
 // CTAs per SM the two-rows-per-lane factor is compiled for (its register budget).
 #ifndef MGFLD_ROW2_MINB
-#define MGFLD_ROW2_MINB 8
+#define MGFLD_ROW2_MINB 9
 #endif
 
 template <int NP>
@@ -1201,67 +1201,51 @@ __device__ inline bool mbar_wait_bounded(unsigned long long *bar, unsigned parit
   return false;
 }
 
+// The power-of-two scaling of one system's right-hand side for the FP32 substitution: k such that
+// max |rhs| 2^k lies in [1/2, 1) (from the largest exponent, so the maximum is taken over the
+// upper words of the bit patterns: integer pipe only), and the FP32 copy rhs 2^k.  All threads of
+// the block call it.
+__device__ inline void sysmax_scale(const double *__restrict__ rhs, int cnt, int *__restrict__ sys_exp,
+                                    float *__restrict__ rhs32) {
+  __shared__ unsigned red[256];
+  __shared__ int kexp_s;
+  unsigned m = 0u;
+  for (int e = threadIdx.x; e < cnt; e += blockDim.x)
+    m = max(m, (unsigned)(__double_as_longlong(rhs[e]) >> 32) & 0x7fffffffu);
+  red[threadIdx.x] = m;
+  __syncthreads();
+  for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+    if (threadIdx.x < h) red[threadIdx.x] = max(red[threadIdx.x], red[threadIdx.x + h]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const int e = (int)(red[0] >> 20);
+    const int k = (e > 0 && e < 0x7ff) ? 1022 - e : 0;
+    *sys_exp = k;
+    kexp_s = k;
+  }
+  __syncthreads();
+  const int k = kexp_s;
+  for (int e = threadIdx.x; e < cnt; e += blockDim.x) rhs32[e] = d2f_exp2(rhs[e], k);
+}
+
 // Per-system power-of-two scaling of the FP32 solve: k with max |rhs| 2^k in [0.5, 1) (the
 // exponent field of the maximum), then the scaled right-hand side rounded to FP32 once, so that
 // the substitution reads FP32 values.  One CTA per listed system; its n_r x n right-hand side is
 // contiguous (coalesced loads; the second pass reads it from L2).
 __global__ void k_sysmax(int n, int n_r, const double *__restrict__ rhs, const int *__restrict__ ray_list,
                          int *__restrict__ sys_exp, float *__restrict__ rhs32, const int *__restrict__ n_dev) {
-  __shared__ double red[256];
-  __shared__ int kexp_s;
   if ((int)blockIdx.x >= listed_sys(gridDim.x, n_dev, NS)) return;    // the whole block
-  const long sys = system_of(blockIdx.x, ray_list);
-  const size_t base = (size_t)sys * n_r * n;
-  const unsigned cnt = (unsigned)(n_r * n);
-  double m = 0.0;
-  for (unsigned e = threadIdx.x; e < cnt; e += blockDim.x) m = fmax(m, fabs(rhs[base + e]));
-  red[threadIdx.x] = m;
-  __syncthreads();
-  for (int h = blockDim.x / 2; h > 0; h >>= 1) {
-    if (threadIdx.x < h) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + h]);
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) {
-    m = red[0];
-    const long long b = __double_as_longlong(m);
-    const int e = (int)((b >> 52) & 0x7ff);
-    const int k = (m > 0.0 && e < 0x7ff) ? 1022 - e : 0;
-    sys_exp[blockIdx.x] = k;
-    kexp_s = k;
-  }
-  __syncthreads();
-  const int k = kexp_s;
-  for (unsigned e = threadIdx.x; e < cnt; e += blockDim.x) rhs32[base + e] = d2f_exp2(rhs[base + e], k);
+  const size_t base = (size_t)system_of(blockIdx.x, ray_list) * n_r * n;
+  sysmax_scale(rhs + base, n_r * n, sys_exp + blockIdx.x, rhs32 + base);
 }
 
 // k_sysmax for systems listed with `spr` systems per ray.
 __global__ void k_sysmax_spr(int n, int n_r, const double *__restrict__ rhs, const int *__restrict__ ray_list, int spr,
                              int *__restrict__ sys_exp, float *__restrict__ rhs32, const int *__restrict__ n_dev) {
-  __shared__ double red[256];
-  __shared__ int kexp_s;
   if ((int)blockIdx.x >= listed_sys(gridDim.x, n_dev, spr)) return;   // the whole block
-  const long sys = system_of_spr(blockIdx.x, ray_list, spr);
-  const size_t base = (size_t)sys * n_r * n;
-  const unsigned cnt = (unsigned)(n_r * n);
-  double m = 0.0;
-  for (unsigned e = threadIdx.x; e < cnt; e += blockDim.x) m = fmax(m, fabs(rhs[base + e]));
-  red[threadIdx.x] = m;
-  __syncthreads();
-  for (int h = blockDim.x / 2; h > 0; h >>= 1) {
-    if (threadIdx.x < h) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + h]);
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) {
-    m = red[0];
-    const long long b = __double_as_longlong(m);
-    const int e = (int)((b >> 52) & 0x7ff);
-    const int k = (m > 0.0 && e < 0x7ff) ? 1022 - e : 0;
-    sys_exp[blockIdx.x] = k;
-    kexp_s = k;
-  }
-  __syncthreads();
-  const int k = kexp_s;
-  for (unsigned e = threadIdx.x; e < cnt; e += blockDim.x) rhs32[base + e] = d2f_exp2(rhs[base + e], k);
+  const size_t base = (size_t)system_of_spr(blockIdx.x, ray_list, spr) * n_r * n;
+  sysmax_scale(rhs + base, n_r * n, sys_exp + blockIdx.x, rhs32 + base);
 }
 
 // Row r of a zone's inverse times the zone vector held in shared memory (vb).  VEC: n == NP,

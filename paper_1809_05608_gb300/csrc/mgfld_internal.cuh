@@ -176,8 +176,12 @@ __device__ inline void mu_nue_zone(const Eos &e, double A, double B, double T, d
 // a / (tol b) for a, b >= 0 as a float, without an FP64 division: exponents by integer
 // arithmetic, mantissas (the leading 23 bits) divided in FP32.  tol = tolm * 2^tole.
 // Enough for convergence tests (ratio <= 1) and contraction ratios; +inf for non-finite a.
+__device__ inline float tol_ratio_bits(long long ba, long long bb, float tolm, int tole);
 __device__ inline float tol_ratio(double a, double b, float tolm, int tole) {
-  const long long ba = __double_as_longlong(a), bb = __double_as_longlong(b);
+  return tol_ratio_bits(__double_as_longlong(a), __double_as_longlong(b), tolm, tole);
+}
+// The same from the bit patterns of the two non-negative values (integer and FP32 pipes only).
+__device__ inline float tol_ratio_bits(long long ba, long long bb, float tolm, int tole) {
   if (ba == 0) return 0.f;
   if (bb == 0) return INFINITY;
   const int ea = (int)(ba >> 52), eb = (int)(bb >> 52);
@@ -216,15 +220,21 @@ __device__ inline unsigned long long dbits(double v) { return (unsigned long lon
 // ---------------------------------------------------------------- launchers
 
 cudaError_t launch_groups(const Prob &p, const Ws &w, cudaStream_t s);
-// The flux coefficients again at the state psi (mean free path with the NES rates at psi and the
-// emissivity of the current Ye, neutrinosphere and ghost factor, limiter and its derivatives);
+// The flux coefficients again at the state psi for the listed rays (mean free path with the NES
+// rates at psi and the emissivity of the current Ye, neutrinosphere and ghost factor, limiter and
+// its derivatives), and the NES sums at psi for the residual pass of the same iterate (g0, l0);
 // the setup's other products (NES kernels, zone constants, psi^n) are kept.  Not combined with
 // the shock terms (refused by mgfld_step).
-cudaError_t launch_coef_iterate(const Prob &p, const Ws &w, const double *psi, cudaStream_t s);
+cudaError_t launch_coef_iterate(const Prob &p, const Ws &w, const double *psi, const int *list, int n_list,
+                                const int *n_dev, cudaStream_t s);
 cudaError_t launch_setup(const Prob &p, const Ws &w, const double *psi, const double *ye, const double *T,
                          cudaStream_t s);
 // diag is double (FP64 path, C ABI) or float (MIXED: the Jacobian feeds the FP32 factor only).
-// first: psi is still psi^n (first outer iteration), so the NES sums come from the setup (g0, l0).
+// first: the NES sums at psi are already in g0, l0 (psi^n in the first outer iteration, from the
+// setup; the iterate with the n+1 coefficients, from launch_coef_iterate).
+// The converged sources of the mixed path (all rays) from the last residual's sums and the last
+// correction, into src.
+cudaError_t launch_src_mixed(const Prob &p, const Ws &w, const double *psi, double *src, cudaStream_t s);
 cudaError_t launch_assemble(const Prob &p, const Ws &w, const double *psi, void *diag, int diag_fp32,
                             double *lower, double *upper, double *rhs, const int *list, int n_list,
                             const int *jac_flag, cudaStream_t s, double *src_out = nullptr, int first = 0,
@@ -238,6 +248,12 @@ cudaError_t launch_solve_tma(int n, int n_r, int n_sys, const void *dinv, const 
                              const float *upper32, const double *rhs, float *rhs32, double *x, float *g32,
                              const int *ray_list, int *sys_exp, int *err, cudaStream_t s,
                              const int *n_dev = nullptr);
+
+// An opacity entry of (species q, group k) times the optional per-(q, k) scale (no multiplication
+// without a scale: an FP64 operation saved per use, the same value).
+__device__ inline double scaled(const Prob &p, const double *a, size_t g, int q, int k) {
+  return p.scale ? a[g] * p.scale[q * p.n + k] : a[g];
+}
 
 // Count of a launch's listed rays: the host's n (the grid is sized for it) or, when the launch
 // belongs to an outer iteration that runs without the host, the device-resident count n_dev

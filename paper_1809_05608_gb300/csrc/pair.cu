@@ -153,8 +153,7 @@ __global__ void k_assemble_pair(Prob p, Ws w, const double *__restrict__ psi, TD
   }
   const double make = w.pmsum[zi * n + k] - mb, kill = kb;
   const double loss = w.rsum[zi * n + k] - lp;
-  const double sc = p.scale ? p.scale[q * n + k] : 1.0;
-  const double kap = p.kabs[g] * sc;
+  const double kap = scaled(p, p.kabs, g, q, k);
   const double j = w.jbuf[g];
   const double S = j * (1.0 - pk) - kap * pk + ((1.0 - pk) * gain - pk * loss) + ((1.0 - pk) * make - pk * kill);
   if (src_out) {

@@ -256,8 +256,7 @@ __global__ void k_jlam(Prob p, Ws w, const double *__restrict__ psi, const doubl
   double e_mu0 = 0.0;
   for (int q = 0; q < NS; ++q) {
     const size_t g = (((size_t)ray * NS + q) * p.n_r + i) * n + k;
-    const double sc = p.scale ? p.scale[q * n + k] : 1.0;
-    const double kap = p.kabs[g] * sc, ksc = p.kscat[g] * sc;
+    const double kap = scaled(p, p.kabs, g, q, k), ksc = scaled(p, p.kscat, g, q, k);
     double e1;
     if (emu > 0.0) {
       e1 = q == 0 ? ex * emu : (q == 1 ? ex * z[ZC_EMUI] : ex);
@@ -287,12 +286,18 @@ __global__ void k_jlam(Prob p, Ws w, const double *__restrict__ psi, const doubl
 // One warp per (ray, q, k): lane c sums the optical depth of the c-th chunk of zones counted
 // from the outer edge, an exclusive warp scan gives each chunk the depth above it, each lane
 // looks for the crossing inside its chunk, and the outermost crossing wins.
-__global__ void k_nusphere(Prob p, Ws w) {
+// With a ray list (the outer iteration at the n+1 coefficients) only the listed rays are done.
+__global__ void k_nusphere(Prob p, Ws w, const int *__restrict__ list, int n_list, const int *__restrict__ n_dev) {
   const unsigned full = 0xffffffffu;
   const int n = p.n;
-  const int t = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  const int per_ray = NS * n;
+  int t = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
   const int lane = threadIdx.x & 31;
-  if (t >= p.n_ray * NS * n) return;                // whole warps leave together
+  if (t >= (list ? listed(n_list, n_dev) : p.n_ray) * per_ray) return;   // whole warps leave together
+  if (list) {
+    const int rl = t / per_ray;
+    t = list[rl] * per_ray + (t - rl * per_ray);
+  }
   const int k = t % n, q = (t / n) % NS, ray = t / (n * NS);
   const double *re = p.r_edge + (size_t)ray * (p.n_r + 1);
   const size_t off = ((size_t)ray * NS + q) * p.n_r * n + k;
@@ -340,10 +345,17 @@ __global__ void k_nusphere(Prob p, Ws w) {
 // alpha_{i+1/2} = A_{i+1/2} D_{i+1/2} / a_{i+1/2}^2 with D = lambda_e F / (3 (R_{i+1} - R_i)),
 // lambda_e = sqrt(lambda_i lambda_{i+1}) (the product of the stored square roots),
 // F = min(F_intrp, F_geom) at psi^n.
-__global__ void k_edges(Prob p, Ws w, const double *__restrict__ psi_src) {
+// With a ray list (the outer iteration at the n+1 coefficients) only the listed rays are done.
+__global__ void k_edges(Prob p, Ws w, const double *__restrict__ psi_src, const int *__restrict__ list, int n_list,
+                        const int *__restrict__ n_dev) {
   const int n = p.n;
-  const unsigned tu = blockIdx.x * blockDim.x + threadIdx.x;
-  if (tu >= (unsigned)(p.n_ray * NS * p.n_r * n)) return;
+  const unsigned per_ray = (unsigned)(NS * p.n_r * n);
+  unsigned tu = blockIdx.x * blockDim.x + threadIdx.x;
+  if (tu >= (unsigned)(list ? listed(n_list, n_dev) : p.n_ray) * per_ray) return;
+  if (list) {
+    const unsigned rl = tu / per_ray;
+    tu = (unsigned)list[rl] * per_ray + (tu - rl * per_ray);
+  }
   const size_t t = tu;
   const unsigned u1 = tu / (unsigned)n;
   const int k = (int)(tu - u1 * n);
@@ -433,13 +445,21 @@ __global__ void k_edges(Prob p, Ws w, const double *__restrict__ psi_src) {
   }
 }
 
-// The transport mean free path at the outer iterate: as k_jlam with the NES rates at psi and the
-// emissivity the iteration keeps at the current Ye (jbuf); psi^n, the first residual's sums and
-// the emissivity are not touched.
-__global__ void k_lam_iter(Prob p, Ws w, const double *__restrict__ psi) {
+// The transport mean free path at the outer iterate of the listed rays: as k_jlam with the NES
+// rates at psi and the emissivity the iteration keeps at the current Ye (jbuf); psi^n and the
+// emissivity are not touched.  The NES sums at psi, which the residual of the same iterate needs
+// as well, are handed to it in g0 / l0 (the residual pass then reads them as it reads the setup's
+// sums at psi^n in the first iteration).
+__global__ void k_lam_iter(Prob p, Ws w, const double *__restrict__ psi, const int *__restrict__ list, int n_list,
+                           const int *__restrict__ n_dev) {
   const int n = p.n;
-  const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= (unsigned)(p.n_ray * p.n_r * n)) return;
+  const unsigned per_ray = (unsigned)(p.n_r * n);
+  unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (unsigned)listed(n_list, n_dev) * per_ray) return;
+  {
+    const unsigned rl = t / per_ray;
+    t = (unsigned)list[rl] * per_ray + (t - rl * per_ray);
+  }
   const unsigned zu = t / (unsigned)n;
   const int k = (int)(t - zu * n);
   const size_t zi = zu;
@@ -451,10 +471,11 @@ __global__ void k_lam_iter(Prob p, Ws w, const double *__restrict__ psi) {
   nes_sums(fin, fout, psi + (((size_t)ray * NS) * p.n_r + i) * n, (size_t)p.n_r * n, n, gain, lp);
   for (int q = 0; q < NS; ++q) {
     const size_t g = (((size_t)ray * NS + q) * p.n_r + i) * n + k;
-    const double sc = p.scale ? p.scale[q * n + k] : 1.0;
-    const double kap = p.kabs[g] * sc, ksc = p.kscat[g] * sc;
+    const double kap = scaled(p, p.kabs, g, q, k), ksc = scaled(p, p.kscat, g, q, k);
     const double kt = kap + w.jbuf[g] + ksc + gain[q] + (rs - lp[q]);
     const double y = rsqrt(kt);
+    w.g0[g] = gain[q];
+    w.l0[g] = lp[q];
     w.kinv[g] = kt;
     w.slam[g] = y;
     w.lam[g] = y * y;
@@ -546,8 +567,8 @@ cudaError_t launch_setup(const Prob &p, const Ws &w, const double *psi, const do
     k_phi<<<nblk(nz, zpb), zpb * phi_threads_per_zone(p.n), sm, s>>>(p, w, T, zpb);
   }
   k_jlam<<<nblk(nzk, B), B, 0, s>>>(p, w, psi, T);
-  k_nusphere<<<nblk((size_t)p.n_ray * NS * p.n * 32, B), B, 0, s>>>(p, w);   // a warp per (ray, q, k)
-  k_edges<<<nblk(nall, B), B, 0, s>>>(p, w, w.psi_n);
+  k_nusphere<<<nblk((size_t)p.n_ray * NS * p.n * 32, B), B, 0, s>>>(p, w, nullptr, 0, nullptr);   // a warp per (ray, q, k)
+  k_edges<<<nblk(nall, B), B, 0, s>>>(p, w, w.psi_n, nullptr, 0, nullptr);
   if (p.u) k_shock<<<nblk(nall, B), B, 0, s>>>(p, w, w.psi_n);
   if (p.pair && w.pmake) {
     const cudaError_t e = launch_pair(p, w, T, s);
@@ -556,13 +577,15 @@ cudaError_t launch_setup(const Prob &p, const Ws &w, const double *psi, const do
   return cudaGetLastError();
 }
 
-cudaError_t launch_coef_iterate(const Prob &p, const Ws &w, const double *psi, cudaStream_t s) {
+cudaError_t launch_coef_iterate(const Prob &p, const Ws &w, const double *psi, const int *list, int n_list,
+                                const int *n_dev, cudaStream_t s) {
+  if (n_list == 0) return cudaSuccess;
   const unsigned B = 256;
-  const size_t nzk = (size_t)p.n_ray * p.n_r * p.n;
+  const size_t nzk = (size_t)n_list * p.n_r * p.n;
   const size_t nall = nzk * NS;
-  k_lam_iter<<<nblk(nzk, B), B, 0, s>>>(p, w, psi);
-  k_nusphere<<<nblk((size_t)p.n_ray * NS * p.n * 32, B), B, 0, s>>>(p, w);
-  k_edges<<<nblk(nall, B), B, 0, s>>>(p, w, psi);
+  k_lam_iter<<<nblk(nzk, B), B, 0, s>>>(p, w, psi, list, n_list, n_dev);
+  k_nusphere<<<nblk((size_t)n_list * NS * p.n * 32, B), B, 0, s>>>(p, w, list, n_list, n_dev);
+  k_edges<<<nblk(nall, B), B, 0, s>>>(p, w, psi, list, n_list, n_dev);
   return cudaGetLastError();
 }
 

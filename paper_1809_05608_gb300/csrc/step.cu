@@ -255,8 +255,13 @@ __global__ void k_update_psi(Prob p, Ws w, Tol tl, double *__restrict__ psi, con
     const double d = w.x[gx];
     const double v = psi[g] + d;
     psi[g] = v;
-    viol = tol_ratio(fabs(d), fmax(fabs(v), tl.tolmin), tl.tolm, tl.tole);
-    if (!isfinite(v)) {
+    // |d| / max(|v|, tolmin) and the finiteness test on the bit patterns (non-negative doubles
+    // order as their integer patterns), so the FP64 pipe only takes the addition
+    const long long ad = __double_as_longlong(d) & 0x7fffffffffffffffll;
+    const long long av = __double_as_longlong(v) & 0x7fffffffffffffffll;
+    const long long tm = __double_as_longlong(tl.tolmin);
+    viol = tol_ratio_bits(ad, av > tm ? av : tm, tl.tolm, tl.tole);
+    if (av >= 0x7ff0000000000000ll) {
       atomicExch(&w.nanflag[ray], 1);
       viol = INFINITY;
     }
@@ -347,9 +352,8 @@ __global__ void k_update_ye(Prob p, Ws w, Tol tl, const double *__restrict__ psi
           if (m0 - eps < capT && m1 - eps < capT) {
             w.jbuf[g0 + k] *= ratio;
           } else {
-            const double sc = p.scale ? p.scale[q * n + k] : 1.0;
             bool live;
-            w.jbuf[g0 + k] = emissivity(p.kabs[g0 + k] * sc, m1, eps, Ti, live);
+            w.jbuf[g0 + k] = emissivity(scaled(p, p.kabs, g0 + k, q, k), m1, eps, Ti, live);
           }
         }
       }
@@ -731,7 +735,7 @@ static cudaError_t enqueue_iteration(const StepCall &c, int it, int n_act, int n
   if (c.coef_iterate && it > 0) {
     // the flux coefficients of Eq. a59 at the current iterate (psi and Ye updated in place)
     if (prof) prof->begin(MGFLD_PROF_SETUP);
-    MGFLD_ENQ(launch_coef_iterate(p, w, c.st.psi, s));
+    MGFLD_ENQ(launch_coef_iterate(p, w, c.st.psi, w.list_act, n_act, cnt_act, s));
     if (prof) prof->end(MGFLD_PROF_SETUP, 3);
   }
   if (prof) prof->begin(MGFLD_PROF_ASSEMBLE);
@@ -740,7 +744,7 @@ static cudaError_t enqueue_iteration(const StepCall &c, int it, int n_act, int n
                                    s, nullptr, it == 0, cnt_act));
   else
     MGFLD_ENQ(launch_assemble(p, w, c.st.psi, w.diag, tl.mixed, w.lower, w.upper, w.rhs, w.list_act, n_act, jac, s,
-                              nullptr, it == 0, cnt_act));
+                              nullptr, it == 0 || c.coef_iterate, cnt_act));
   if (prof) prof->end(MGFLD_PROF_ASSEMBLE, 1);
   const int *flist = tl.chord ? w.list_ref : w.list_act;
   const int nf = tl.chord ? n_ref : n_act;
@@ -790,6 +794,8 @@ static cudaError_t enqueue_finish(const StepCall &c, Prof *prof, cudaStream_t s)
   if (c.pair)
     MGFLD_ENQ(launch_assemble_pair(c.p, w, c.st.psi, w.diag, c.tl.mixed, w.lower, w.upper, w.rhs, nullptr, R, nullptr,
                                    s, w.src, 0));
+  else if (c.tl.mixed)
+    MGFLD_ENQ(launch_src_mixed(c.p, w, c.st.psi, w.src, s));
   else
     MGFLD_ENQ(launch_assemble(c.p, w, c.st.psi, w.diag, c.tl.mixed, w.lower, w.upper, w.rhs, nullptr, R, nullptr, s,
                               w.src));
