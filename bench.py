@@ -94,6 +94,14 @@ def shock_workload(n_gpus, rank, rays_per_rank=RAYS_PER_RANK):
     return inp
 
 
+def pair_workload(n_gpus, rank, rays_per_rank=RAYS_PER_RANK):
+    """The same rays with the synthetic pair process at the NES scale and its angular correction."""
+    inp = problems.make_pair_problem(CONFIG_ID, n_ray=rays_per_rank * n_gpus)
+    if n_gpus > 1:
+        inp = problems.subset_rays(inp, shard(n_gpus, rank, rays_per_rank))
+    return inp
+
+
 def c4_shard(n_gpus, rank, n_ray=None):
     """Contiguous block of the 3D-scale configuration's rays for rank `rank` (its rays are a
     fixed 64 x 64 set, so more ranks each take fewer of them)."""
@@ -263,11 +271,11 @@ def run_path(M, torch, inp, precision, steps, warmup, barrier, clocks=None, refa
     ms = e0.elapsed_time(e1)
     assert st.worst_status() == M.MGFLD_OK
     # the profiled pass: per-category kernel times (and the unit counts they belong to)
-    prof = (ctypes.c_double * 12)()
+    prof = (ctypes.c_double * (2 * M.PROF_N))()
     st.opts.profile = ctypes.cast(prof, ctypes.c_void_p)
     rc = st.step(psi, ye, T)                      # event creation outside the counted pass
     assert rc == M.MGFLD_OK, M.status_str(rc)
-    for c in range(12):
+    for c in range(2 * M.PROF_N):
         prof[c] = 0.0
     pfact = torch.zeros_like(nfact)
     piters = torch.zeros_like(iters)
@@ -300,7 +308,7 @@ def run_path(M, torch, inp, precision, steps, warmup, barrier, clocks=None, refa
     return out
 
 
-def algorithmic_work(inp, kernel, nfact, iters, precision, coef=False):
+def algorithmic_work(inp, kernel, nfact, iters, precision, coef=False, steps=0):
     """Algorithmic flop count over the timed steps for one kernel category.
 
     factor: per (zone, system) factorisation, N^3 FMAs of in-place Gauss-Jordan plus
@@ -316,17 +324,41 @@ def algorithmic_work(inp, kernel, nfact, iters, precision, coef=False):
         per = 2.0 * n**3 + 2.0 * n**2
         return per * n_s * n_r * nfact
     if kernel == 'assemble':
+        if precision == 1 and not coef:           # the first outer iteration only
+            return n_s * n_r * n_ray * steps * 24.0 * n
         per_res = 32.0 * n if coef else 4.0 * n**2 + 16.0 * n
         per_jac = 2.0 * n**2 if precision == 0 else 0.0
         return n_s * n_r * (per_res * iters + per_jac * nfact)
     raise ValueError(kernel)
 
 
+def residual_roofline(res, inp):
+    """HBM roofline of the mixed path's later residual passes (k_resid_ff): per (zone, system,
+    outer iteration after the first) the FP32-pair NES kernels (16 B per entry and zone, shared by
+    the four systems: 4 N^2 B) and 96 B per row (the kept sums read and written, the four step
+    constants, psi, j, the last correction, -G written)."""
+    n_ray, n_s, n_r, n = inp['psi0'].shape
+    prof = res['prof']['residual']
+    launches = max(prof['launches'], 1)
+    units = n_s * n_r * (res['iters'] - n_ray * res['steps'])
+    per_unit = 4 * n * n + 96 * n
+    gbs = per_unit * units / (prof['ms'] * 1e-3) / 1e9 if prof['ms'] > 0 else 0.0
+    tr = traffic_record('k_resid_ff')
+    traffic = None if tr is None else tr['bytes'] / tr['units'] * (units / n_r / launches)
+    return dict(bound='hbm', kernel='k_resid_ff', achieved=gbs, peak=PEAK_HBM_GBS, unit='GB/s',
+                frac=gbs / PEAK_HBM_GBS, traffic=traffic, peak_source=HBM_SOURCE, bytes_per_zone_system=per_unit,
+                kernel_ms_per_launch=prof['ms'] / launches, kernel_share=prof['ms'] / res['ms'])
+
+
 def roofline_for(res, inp, precision):
     """Roofline of the dominant kernel of the residual/Jacobian and factor categories."""
     prof = res['prof']
-    dom = max(('assemble', 'factor'), key=lambda k: prof[k]['ms'])
-    flops = algorithmic_work(inp, dom, res['nfact'], res['iters'], precision, coef=res.get('coef', False))
+    cands = ('assemble', 'factor', 'residual') if prof.get('residual', {}).get('launches') else ('assemble', 'factor')
+    dom = max(cands, key=lambda k: prof[k]['ms'])
+    if dom == 'residual':
+        return residual_roofline(res, inp)
+    flops = algorithmic_work(inp, dom, res['nfact'], res['iters'], precision, coef=res.get('coef', False),
+                             steps=res['steps'])
     achieved = flops / (prof[dom]['ms'] * 1e-3) / 1e12
     fp32 = dom == 'factor' and precision == 1
     per_clk = FP32_FLOP_PER_CLK_SM if fp32 else FP64_FLOP_PER_CLK_SM
@@ -436,6 +468,16 @@ def category_work(n, precision, coef=False):
         w['setup_citer'] = ('citer', 4 * N * N + 50 * N, 0.0, 4 * N * N + 96 * N)
         # the residual rows from the kept sums, the coefficients and the limiter's derivatives
         w['assemble'] = ('iter', 32 * N, 0.0, 88 * N)
+    elif mixed:
+        # the first outer iteration: the step constants and the row from the setup's NES sums
+        # (~24 FP64 flop per row); psi, psi^n, j, kappa_a, alpha, the sums read, the four step
+        # constants and -G written
+        w['assemble'] = ('step', 24 * N, 0.0, 104 * N)
+        # the later ones (k_resid_ff): the two increments phin.dpsi, phout.dpsi (4 N^2 flop at
+        # FP32-pair precision) added to the kept sums and the row formed (16 N FP64); the kernels
+        # in FP32 pairs (16 B per entry and zone: 4 N^2 B per system), and per row the sums read
+        # and written, the four step constants, psi, j, the correction, -G (96 B)
+        w['residual'] = ('citer', 16 * N, 4 * N * N, 4 * N * N + 96 * N)
     return w
 
 
@@ -825,7 +867,7 @@ def profile_step(path, n_rays, config):
     psi, ye, T = st.state_to_device(inp['psi0'], inp['ye0'], inp['T0'])
     # the host-driven outer iteration (per-category events): ncu profiles the kernels of ordinary
     # launches, not those inside a graph with a conditional node
-    prof = (ctypes.c_double * 12)()
+    prof = (ctypes.c_double * (2 * M.PROF_N))()
     st.opts.profile = ctypes.cast(prof, ctypes.c_void_p)
     rc = st.step(psi, ye, T)
     torch.cuda.synchronize()
@@ -834,14 +876,16 @@ def profile_step(path, n_rays, config):
     return 0 if rc == M.MGFLD_OK else 1
 
 
-def path_summary(res, inp, precision, ws, world_ms, ups, n_rays_rank, **extra):
-    return dict(value=job_throughput(ups, ws, world_ms), unit=UNIT, ms_per_step=world_ms,
-                kernel_ms={k: v['ms'] for k, v in res['prof'].items()},
-                outer_iterations_per_step=res['max_iters'], iterations_histogram=res['iters_hist'],
-                factorizations_per_ray_step=res['nfact'] / (n_rays_rank * res['steps']),
-                gpu_launches=sum(v['launches'] for v in res['prof'].values()),
-                roofline=roofline_for(res, inp, precision), roofline_step=step_roofline(res, inp, precision),
-                **extra)
+def path_summary(res, inp, precision, ws, world_ms, ups, n_rays_rank, rooflines=True, **extra):
+    out = dict(value=job_throughput(ups, ws, world_ms), unit=UNIT, ms_per_step=world_ms,
+               kernel_ms={k: v['ms'] for k, v in res['prof'].items()},
+               outer_iterations_per_step=res['max_iters'], iterations_histogram=res['iters_hist'],
+               factorizations_per_ray_step=res['nfact'] / (n_rays_rank * res['steps']),
+               gpu_launches=sum(v['launches'] for v in res['prof'].values()))
+    if rooflines:
+        out.update(roofline=roofline_for(res, inp, precision), roofline_step=step_roofline(res, inp, precision))
+    out.update(extra)
+    return out
 
 
 def main():
@@ -955,6 +999,18 @@ def main():
             workload='the same rays with the flux coefficients of Eq. a59 (mean free path, limiter, '
                      'neutrinosphere) formed again at every outer iterate',
             dominant_category=max(lit['prof'], key=lambda c: lit['prof'][c]['ms']))
+        # the pair process (Eq. d14 with the angular correction of Eqs. d16-d22): coupled (nu, nubar)
+        # systems of 2 n_e x 2 n_e zone blocks
+        pr = run_path(M, torch, pair_workload(n_gpus, rank), M.MGFLD_MIXED, args.steps, args.warmup, barrier)
+        ms_pair = max_over_ranks(pr['ms']) / args.steps
+        extra['pair_path'] = dict(
+            path_summary(pr, inp, M.MGFLD_MIXED, ws, ms_pair, ups, n_rays_rank, rooflines=False),
+            dtype='f32 factor + f64 residual/update',
+            workload='the same rays with the synthetic pair process at the NES scale (pair_coef = 1e-41 rho) '
+                     'and its angular correction (pair_chi, the synthetic flux factor): coupled (nu, nubar) '
+                     'systems of 40 x 40 zone blocks',
+            dominant_category=max(pr['prof'], key=lambda c: pr['prof'][c]['ms']))
+        del pr
         extra['stress_lapse'] = stress_lapse_run(M, torch, inp, args.steps, args.warmup)
         extra['energy_advection'] = energy_advection_run(
             M, torch, n_gpus, rank, args.steps, args.warmup,
@@ -973,6 +1029,9 @@ def main():
             c = oracle_pool_sample(pool, inp, rays_per_core=1, coef_iterate=True)
             c.pop('wall_s')
             extra['coef_iterate_path']['cpu_baseline'] = c
+            c = oracle_pool_sample(pool, pair_workload(n_gpus, rank), rays_per_core=1)
+            c.pop('wall_s')
+            extra['pair_path']['cpu_baseline'] = c
             extra['stress_lapse']['cpu_baseline'] = stress_oracle_sample(inp, 16)
             c4 = problems.make_problem(C4_ID)
             c = oracle_pool_sample(pool, c4, rays_per_core=1)

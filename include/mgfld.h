@@ -138,12 +138,14 @@ typedef struct {
 /* Kernel categories of mgfld_step_opts.profile. */
 enum {
   MGFLD_PROF_SETUP = 0,    /* frozen coefficients: groups, EoS, NES kernels, mean free path, limiter, shock terms */
-  MGFLD_PROF_ASSEMBLE = 1, /* residual and Jacobian rows (k_assemble) */
+  MGFLD_PROF_ASSEMBLE = 1, /* residual and Jacobian rows (k_assemble; in MIXED its first outer iteration) */
   MGFLD_PROF_FACTOR = 2,   /* block-Thomas elimination with in-block Gauss-Jordan (k_factor) */
   MGFLD_PROF_SOLVE = 3,    /* forward/back substitution (k_solve) */
   MGFLD_PROF_UPDATE = 4,   /* psi and Ye update, convergence bookkeeping (k_update_psi, k_update_ye, k_check) */
   MGFLD_PROF_FINISH = 5,   /* energy/temperature update and ledgers (k_finish, k_ledger) */
-  MGFLD_PROF_N = 6
+  MGFLD_PROF_RESIDUAL = 6, /* MIXED, later outer iterations: residual rows from the kept NES sums and the
+                              last correction (k_resid_ff) */
+  MGFLD_PROF_N = 7
 };
 
 /* Per-step report, DEVICE pointers (any may be NULL). */

@@ -86,7 +86,34 @@ __global__ void k_assemble(Prob p, Ws w, const double *__restrict__ psi, TD *__r
     c_low = w.clow[g];
     if (i < last) G = fma(-c_up, ps[k + n], G);
     if (i > 0) G = fma(-c_low, ps[k - (ptrdiff_t)n], G);
+  } else if (!src_out && !w.jl && w.phin32) {
+    // The first pass of the mixed path with the coefficients frozen for the step: the step
+    // constants (D0 with the ghost of the outer edge folded in, the couplings, the psi-independent
+    // part b0), stored for the later passes, and the row formed from them as the later passes form
+    // it.  (The FP64 path forms its first row below from the terms of Eq. a58 as written: with
+    // the regrouped form there, its results on the benchmark rays moved from 0.90 to 1.02 x 1e-12
+    // of the oracle's, across the FP64 gate.)
+    const double kap = scaled(p, p.kabs, g, q, k);
+    const double al_out = w.alpha[g];
+    const double al_in = i > 0 ? w.alpha[g - n] : 0.0;
+    const double jdiag = i == last ? fma(-al_out, w.ghost[((size_t)ray * NS + q) * n + k], al_out) + al_in
+                                   : al_out + al_in;
+    const double d0 = inv_acdt + pre * jdiag + kap + w.rsum[zi * n + k];
+    const double sh = p.u ? w.shock[g] : 0.0;
+    const double b0 = w.psi_n[g] * inv_acdt - pre * sh;
+    c_up = i < last ? pre * al_out : 0.0;
+    c_low = pre * al_in;
+    w.cdiag[g] = d0;
+    w.cup[g] = c_up;
+    w.clow[g] = c_low;
+    w.cb[g] = b0;
+    dg = ((d0 + j) + gain) - lp;
+    G = fma(pk, dg, -((b0 + j) + gain));
+    if (i < last) G = fma(-c_up, ps[k + n], G);
+    if (i > 0) G = fma(-c_low, ps[k - (ptrdiff_t)n], G);
   } else {
+    // The sources alone (src_out), the row with the flux coefficients of the iterate (jl), or
+    // the FP64 path's first row.
     const double loss = w.rsum[zi * n + k] - lp;          // sum_k' phout (1 - psi_k')
     const double kap = scaled(p, p.kabs, g, q, k);
     const double S = j * (1.0 - pk) - kap * pk + ((1.0 - pk) * gain - pk * loss);
@@ -118,9 +145,8 @@ __global__ void k_assemble(Prob p, Ws w, const double *__restrict__ psi, TD *__r
     dg = inv_acdt + pre * jdiag + j + kap + (gain + loss);
     c_low = pre * jlow;
     c_up = i < last ? pre * jup : 0.0;
-    if (first && !w.jl) {
-      // the step constants of the later iterations (frozen coefficients): D0 with the ghost of
-      // the outer edge folded in, the couplings, and the psi-independent part b0
+    if (first && !w.jl && !src_out) {
+      // the FP64 path's first pass: the step constants of its later passes
       w.cdiag[g] = inv_acdt + pre * jdiag + kap + w.rsum[zi * n + k];
       w.cup[g] = c_up;
       w.clow[g] = c_low;
@@ -260,6 +286,188 @@ cudaError_t launch_src_mixed(const Prob &p, const Ws &w, const double *psi, doub
   const size_t total = (size_t)p.n_ray * NS * p.n_r * p.n;
   if (total == 0) return cudaSuccess;
   k_src_mixed<<<(unsigned)((total + kSrcThreads - 1) / kSrcThreads), kSrcThreads, 0, s>>>(p, w, psi, src);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------------------------
+// The later residual passes of the mixed path (coefficients frozen for the step, no pair
+// process): the NES sums of the iterate from the kept sums of the previous one plus the kernels
+// times the last correction,
+//   gain = gain_prev + sum_k' phin[k][k'] dpsi_k',   lp = lp_prev + sum_k' phout[k][k'] dpsi_k',
+// exact in exact arithmetic (the sums are linear in psi).  The products and their sums are taken
+// in FP32 pairs (hi + lo, ~48 bits; products split exactly with an FMA, sums with the two-sum of
+// Knuth), on row-scaled kernels and group-scaled corrections, so the FP64 pipe only adds the two
+// increments to the kept sums and forms the row.  The pairs carry the increment to ~1e-13 of the
+// sum of its terms' magnitudes, so a (zone, species) group whose last correction exceeds ~1.6 %
+// of max(|psi|, tolmin) over the group forms its sums again in FP64 instead; below that the error
+// of an increment stays within a few FP64 roundings of the sums themselves.  Then the row
+// as the later passes form it (G = psi (D0 + j + gain - lp) - (b0 + j + gain) - couplings) and,
+// where the ray takes new factors, the FP32 Jacobian rows.
+//
+// A block takes whole zones (Z zones of NS n rows, Z NS n <= 256), stages their scaled kernels
+// and the corrections of its rows in shared memory, and runs the two dot products of a row as
+// one sequence of packed FP32x2 operations (the gain and the loss sums side by side).  Rows are
+// threads in the order (zone, species, group) of k_assemble.
+__host__ __device__ inline int ff_zpb(int n) { return (256 / (NS * n)) > 0 ? 256 / (NS * n) : 1; }
+__host__ __device__ inline int ff_ld(int n) { return (n % 2 == 0) ? n + 1 : n; }      // odd row stride in float4
+static inline size_t ff_smem(int n) {
+  const int z = ff_zpb(n), rows = z * NS * n;
+  return sizeof(float4) * (size_t)z * n * ff_ld(n) + sizeof(int2) * (size_t)z * n + sizeof(float4) * rows +
+         2 * sizeof(unsigned) * (size_t)z * NS + sizeof(long long) * (size_t)z;
+}
+
+// Knuth's two-sum of the two lanes of a pair, s + b -> s, its rounding error added to err; the
+// differences are FMAs with a -1 multiplier (exact as subtractions, no negations).
+__device__ inline void two_sum2(float2 &s, float2 &err, float2 b) {
+  const float2 m1 = make_float2(-1.f, -1.f);
+  const float2 a = s;
+  s = __fadd2_rn(a, b);
+  const float2 bb = __ffma2_rn(a, m1, s);                 // s - a
+  const float2 u = __ffma2_rn(__ffma2_rn(bb, m1, s), m1, a);   // a - (s - bb)
+  const float2 v = __ffma2_rn(bb, m1, b);                 // b - bb
+  err = __fadd2_rn(err, __fadd2_rn(u, v));
+}
+
+__global__ void __launch_bounds__(256)
+k_resid_ff(Prob p, Ws w, const double *__restrict__ psi, float *__restrict__ diag, double *__restrict__ lower,
+           double *__restrict__ upper, double *__restrict__ rhs, const int *__restrict__ list, int n_list,
+           const int *__restrict__ jac_flag, double tolmin, const int *__restrict__ n_dev) {
+  extern __shared__ __align__(16) unsigned char ff_sm[];
+  const int n = p.n, ld = ff_ld(n), zpb = ff_zpb(n);
+  const unsigned zrows = (unsigned)(NS * n), bt = (unsigned)zpb * zrows, nn = (unsigned)(n * n);
+  // (16-byte pieces first, then 8-byte, then 4-byte: every array aligned to its element)
+  float4 *tile = reinterpret_cast<float4 *>(ff_sm);                       // [zpb][n][ld]
+  float4 *dff = tile + (size_t)zpb * n * ld;                               // [bt]: (hi, lo, -hi, 0)
+  int2 *rsc = reinterpret_cast<int2 *>(dff + bt);                          // [zpb][n]
+  long long *zoff = reinterpret_cast<long long *>(rsc + (size_t)zpb * n);  // [zpb]: zone index ray n_r + i
+  unsigned *gmx = reinterpret_cast<unsigned *>(zoff + zpb);                // [zpb NS]: max |dpsi| (upper words)
+  unsigned *gpx = gmx + (size_t)zpb * NS;                                  // [zpb NS]: max |psi|
+  const unsigned per_ray = (unsigned)p.n_r * zrows;
+  const unsigned total = (unsigned)listed(n_list, n_dev) * per_ray;
+  const unsigned b0 = blockIdx.x * bt;
+  if (b0 >= total) return;                                                 // the whole block
+  const unsigned t = b0 + threadIdx.x;
+  const bool in = t < total;
+  // this row (its loads issued before the staging)
+  const unsigned rl = in ? t / per_ray : 0;
+  const int ray = list[rl];
+  const unsigned local = t - rl * per_ray;
+  const unsigned kq = local / (unsigned)n;
+  const int k = (int)(local - kq * n);
+  const int q = (int)(kq % NS);
+  const int i = (int)(kq / NS);
+  const size_t g = (((size_t)ray * NS + q) * p.n_r + i) * n + k;
+  const size_t zi = (size_t)ray * p.n_r + i;
+  const int last = p.n_r - 1;
+  double dx = 0.0, g0 = 0.0, l0 = 0.0, pk = 0.0;
+  if (in) {
+    dx = w.x[g];
+    g0 = w.g0[g];
+    l0 = w.l0[g];
+    pk = psi[g];
+  }
+  // the block's zones (consecutive in the listed order): their indices, scaled kernels, row scales
+  const unsigned gz0 = b0 / zrows;
+  const unsigned nzb = min((unsigned)zpb, (total - b0 + zrows - 1) / zrows);
+  const unsigned grp = threadIdx.x / (unsigned)n;
+  if (threadIdx.x < nzb) {
+    const unsigned gz = gz0 + threadIdx.x, zr = gz / p.n_r;
+    zoff[threadIdx.x] = (long long)list[zr] * p.n_r + (gz - zr * p.n_r);
+  }
+  if (threadIdx.x < (unsigned)zpb * NS) gmx[threadIdx.x] = gpx[threadIdx.x] = 0u;
+  __syncthreads();
+  for (unsigned zs = 0; zs < nzb; ++zs) {
+    const float4 *src = w.nesff + (size_t)zoff[zs] * nn;
+    float4 *dst = tile + (size_t)zs * n * ld;
+    for (unsigned e = threadIdx.x; e < nn; e += bt) dst[e + e / (unsigned)n * (unsigned)(ld - n)] = src[e];
+    if (threadIdx.x < (unsigned)n) rsc[zs * n + threadIdx.x] = w.nessc[(size_t)zoff[zs] * n + threadIdx.x];
+  }
+  // the corrections of the block's (zone, species) groups, each scaled by its group's largest
+  if (in) {
+    atomicMax(&gmx[grp], abs_hi_word(dx));
+    atomicMax(&gpx[grp], abs_hi_word(pk));
+  }
+  __syncthreads();
+  const int sgrp = scale_of_max(gmx[grp]);
+  {
+    const float2 d = split_ff(dx, sgrp);
+    dff[threadIdx.x] = make_float4(d.x, d.y, -d.x, 0.f);
+  }
+  __syncthreads();
+  if (!in) return;
+
+  const double *ps = psi + (g - k);
+  const unsigned zs = threadIdx.x / zrows;
+  double gain, lp;
+  // the pairs while the group's last correction is at most 2^-6 (1.6 %) of max(max |psi|, tolmin),
+  // by exponents (the same decision for every row of the group)
+  if ((int)(gmx[grp] >> 20) + 6 <= (int)(max(gpx[grp], abs_hi_word(tolmin)) >> 20)) {
+    const float4 *fr = tile + ((size_t)zs * n + k) * ld;
+    const float4 *dr = dff + (size_t)grp * n;
+    float2 sum = make_float2(0.f, 0.f), err = make_float2(0.f, 0.f);   // (gain, loss) lanes
+    for (int kp = 0; kp < n; ++kp) {
+      const float4 f = fr[kp];                       // (in hi, in lo, out hi, out lo)
+      const float4 d = dr[kp];                       // (hi, lo, -hi, 0)
+      const float2 fh = make_float2(f.x, f.z), fl = make_float2(f.y, f.w);
+      const float2 dh = make_float2(d.x, d.x), dl = make_float2(d.y, d.y), nd = make_float2(d.z, d.z);
+      const float2 pr = __fmul2_rn(fh, dh);
+      const float2 ex = __ffma2_rn(fh, dh, __fmul2_rn(fh, nd));          // exact product error
+      const float2 cr = __ffma2_rn(fh, dl, __fmul2_rn(fl, dh));          // cross terms
+      err = __fadd2_rn(err, __fadd2_rn(ex, cr));
+      two_sum2(sum, err, pr);
+    }
+    const int2 sc = rsc[zs * n + k];
+    const int ug = -(sc.x + sgrp), ul = -(sc.y + sgrp);
+    gain = (g0 + f2d_exp2(sum.x, ug)) + f2d_exp2(err.x, ug);
+    lp = (l0 + f2d_exp2(sum.y, ul)) + f2d_exp2(err.y, ul);
+  } else {
+    // a large last correction: the sums at the iterate in FP64, as k_assemble forms them
+    const double *fin = w.phin + (zi * n + k) * n, *fout = w.phout + (zi * n + k) * n;
+    gain = 0.0;
+    lp = 0.0;
+    for (int kp = 0; kp < n; ++kp) {
+      const double pv = ps[kp];
+      gain += fin[kp] * pv;
+      lp += fout[kp] * pv;
+    }
+  }
+  w.g0[g] = gain;
+  w.l0[g] = lp;
+
+  const double j = w.jbuf[g];
+  const double dg = ((w.cdiag[g] + j) + gain) - lp;
+  double G = fma(pk, dg, -((w.cb[g] + j) + gain));
+  const double c_up = w.cup[g], c_low = w.clow[g];
+  if (i < last) G = fma(-c_up, ps[k + n], G);
+  if (i > 0) G = fma(-c_low, ps[k - (ptrdiff_t)n], G);
+  rhs[g] = -G;
+
+  if (!jac_flag || !jac_flag[ray]) return;
+  // a new FP32 Jacobian row for the ray (as k_assemble writes it)
+  float *row = diag + g * n;
+  const float *fi = w.phin32 + (zi * n + k) * n, *fd = w.phd32 + (zi * n + k) * n;
+  const float pf = d2f_exp2(pk, 0);
+  const float dk = fmaf(pf, fd[k], -fi[k]) + (float)dg;
+  for (int kp = 0; kp < n; ++kp) row[kp] = kp == k ? dk : fmaf(pf, fd[kp], -fi[kp]);
+  lower[g] = -c_low;
+  upper[g] = -c_up;
+  w.lower32[g] = d2f_exp2(-c_low, 0);
+  w.upper32[g] = d2f_exp2(-c_up, 0);
+}
+
+cudaError_t launch_resid_ff(const Prob &p, const Ws &w, const double *psi, float *diag, double *lower,
+                            double *upper, double *rhs, const int *list, int n_list, const int *jac_flag,
+                            double tolmin, cudaStream_t s, const int *n_dev) {
+  const size_t zones = (size_t)n_list * p.n_r;
+  if (zones == 0) return cudaSuccess;
+  const int zpb = ff_zpb(p.n);
+  const size_t sm = ff_smem(p.n);
+  if (sm > 48 * 1024) {
+    const cudaError_t e = cudaFuncSetAttribute(k_resid_ff, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+  }
+  k_resid_ff<<<(unsigned)((zones + zpb - 1) / zpb), zpb * NS * p.n, sm, s>>>(p, w, psi, diag, lower, upper, rhs,
+                                                                            list, n_list, jac_flag, tolmin, n_dev);
   return cudaGetLastError();
 }
 

@@ -49,7 +49,7 @@ struct Prob {
 // Workspace regions (byte offsets from the workspace base).
 struct Layout {
   int mixed, pair;
-  size_t groups, phout, phin, phd, rsum, phin32, phd32, lam, slam, g0, l0, alpha, ghost, rnu, jbuf, psi_n, ye_n, e_n,
+  size_t groups, phout, phin, phd, rsum, phin32, phd32, nesff, nessc, lam, slam, g0, l0, alpha, ghost, rnu, jbuf, psi_n, ye_n, e_n,
       zone, src, shock, cdiag, cup, clow, cb, pmake, pmsum, pkill;
   size_t diag, lower, upper, rhs, x, dinv, zled, sscale, kinv, lower32, upper32, g32, rhs32;
   size_t viol, vprev, active, iters, status, refac, nfact, nanflag, list_act, list_ref, counters;
@@ -108,6 +108,12 @@ struct Ws {
   double *phd;              // phin - phout: the NES Jacobian row is -phin + psi_k phd (one FMA)
   double *rsum;             // [ray][zone][k] row sums of phout: sum_k' phout (1 - psi_k') = rsum - phout.psi
   float *phin32, *phd32;    // FP32 copies for the Jacobian of the mixed path
+  // MIXED: the NES kernels as pairs of FP32 values (hi + lo, ~48 bits), each row scaled by a power
+  // of two: nesff[k][k'] = (phin hi, phin lo, phout hi, phout lo) of phin[k][k'] 2^sin_k and
+  // phout[k][k'] 2^sout_k, nessc[k] = (sin_k, sout_k); the later residual passes add the
+  // kernels times the last correction to the kept sums in this form (FP32 pipe).
+  float4 *nesff;
+  int2 *nessc;
   double *lam, *alpha, *ghost, *rnu, *jbuf, *psi_n, *ye_n, *e_n;
   double *slam;             // per (ray, q, i, k): sqrt(lambda^(t)) at psi^n (edge mean free path = product)
   double *g0, *l0;          // per (ray, q, i, k): the NES sums phin.psi^n and phout.psi^n (first iteration)
@@ -232,6 +238,13 @@ cudaError_t launch_setup(const Prob &p, const Ws &w, const double *psi, const do
 // diag is double (FP64 path, C ABI) or float (MIXED: the Jacobian feeds the FP32 factor only).
 // first: the NES sums at psi are already in g0, l0 (psi^n in the first outer iteration, from the
 // setup; the iterate with the n+1 coefficients, from launch_coef_iterate).
+// The later residual passes of the mixed path (frozen coefficients, no pair process): the NES
+// sums of the iterate from the kept ones plus the kernels times the last correction (FP32 pairs),
+// or again in FP64 for the groups whose last correction is large against max(|psi|, tolmin); the
+// row, and the FP32 Jacobian rows of the rays flagged in jac_flag.
+cudaError_t launch_resid_ff(const Prob &p, const Ws &w, const double *psi, float *diag, double *lower,
+                            double *upper, double *rhs, const int *list, int n_list, const int *jac_flag,
+                            double tolmin, cudaStream_t s, const int *n_dev = nullptr);
 // The converged sources of the mixed path (all rays) from the last residual's sums and the last
 // correction, into src.
 cudaError_t launch_src_mixed(const Prob &p, const Ws &w, const double *psi, double *src, cudaStream_t s);
@@ -286,6 +299,33 @@ __device__ inline double f2d_exp2(float v, int k) {
   if (ed <= 0) return __longlong_as_double((long long)sign);
   if (ed >= 0x7ff) return __longlong_as_double((long long)(sign | (0x7ffull << 52)));
   return __longlong_as_double((long long)(sign | ((unsigned long long)ed << 52) | man));
+}
+
+// v 2^k as an unevaluated sum hi + lo of two FP32 values (integer pipe and two FP32
+// multiplications): hi is d2f_exp2(v, k) (the leading 24 bits), lo the remaining 29 bits of the
+// mantissa rounded to 24, so hi + lo carries ~48 bits of v.  Where lo would fall below the FP32
+// normal range (v 2^k below ~2^-103) it is dropped; hi follows d2f_exp2.
+__device__ inline float2 split_ff(double v, int k) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+  const float hi = d2f_exp2(v, k);
+  const int E = (int)((b >> 52) & 0x7ff);
+  const int ef = E + k - 919;                  // exponent field of 2^(E - 1023 + k - 23)
+  float lo = 0.f;
+  if (E != 0 && E != 0x7ff && ef >= 1 && ef <= 254) {
+    lo = __uint2float_rn((unsigned)(b & 0x1fffffffull)) * 0x1p-29f * __int_as_float(ef << 23);
+    if (b >> 63) lo = -lo;
+  }
+  return make_float2(hi, lo);
+}
+
+// The power-of-two exponent k that brings max |v| of a set into [1/2, 1), from the maximum of
+// the upper words of the bit patterns (0 for an all-zero or non-finite set).
+__device__ inline int scale_of_max(unsigned hi_word_max) {
+  const int e = (int)(hi_word_max >> 20);
+  return (e > 0 && e < 0x7ff) ? 1022 - e : 0;
+}
+__device__ inline unsigned abs_hi_word(double v) {
+  return (unsigned)((unsigned long long)__double_as_longlong(v) >> 32) & 0x7fffffffu;
 }
 // MIXED-precision factor with FP32 diagonal blocks and FP32 coupling coefficients.
 cudaError_t launch_factor_f32(int n, int n_r, int n_sys, const float *diag, const float *lower32,

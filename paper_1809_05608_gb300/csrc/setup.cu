@@ -87,7 +87,9 @@ __global__ void k_zone(Prob p, Ws w, const double *__restrict__ ye, const double
 // down-scattering chains and n-1 of the up-scattering chains (no divergent loop lengths).
 // Rows are staged in shared memory with a padded stride (n + 1) and copied out coalesced.
 static inline int phi_threads_per_zone(int n) { return (n + 1) / 2; }
-static inline size_t phi_zone_bytes(int n) { return sizeof(double) * (2 * (size_t)n * (n + 1) + 2 * (size_t)n); }
+static inline size_t phi_zone_bytes(int n) {
+  return sizeof(double) * (2 * (size_t)n * (n + 1) + 2 * (size_t)n) + sizeof(int) * 2 * (size_t)n;
+}
 // Zones per block: zones * threads per zone a multiple of 32 where the staging fits in 113 KB
 // (two blocks per SM), else as many zones as fit.
 static inline int phi_zones_per_block(int n) {
@@ -185,8 +187,25 @@ __global__ void k_phi(Prob p, Ws w, const double *__restrict__ T, int zpb) {
     if (n - 1 - t != t) w.rsum[(size_t)zi * n + (n - 1 - t)] = rsb;
   }
   __syncthreads();
-  // Coalesced copy of the block's zones (contiguous in [ray][zone][k][k'] order).
   const unsigned nzb = (z0 + zpb <= nz) ? (unsigned)zpb : nz - z0;
+  // MIXED: the power-of-two scale of every row of both kernels (its largest entry into [1/2, 1)),
+  // for their FP32-pair form; integer pipe only.
+  int *rsc = reinterpret_cast<int *>(sin_ + (size_t)zpb * n * ld);   // [zpb][2][n]: in, out
+  if (w.nesff) {
+    for (unsigned r = threadIdx.x; r < nzb * 2 * n; r += blockDim.x) {
+      const unsigned zz = r / (2 * n), rem = r - zz * 2 * n, which = rem / n, row = rem - which * n;
+      const double *src = (which ? sout : sin_) + ((size_t)zz * n + row) * ld;
+      unsigned m = 0u;
+      for (int c = 0; c < n; ++c) m = max(m, abs_hi_word(src[c]));
+      rsc[r] = scale_of_max(m);
+    }
+    __syncthreads();
+    for (unsigned r = threadIdx.x; r < nzb * n; r += blockDim.x) {
+      const unsigned zz = r / n, row = r - zz * n;
+      w.nessc[(size_t)z0 * n + r] = make_int2(rsc[zz * 2 * n + row], rsc[zz * 2 * n + n + row]);
+    }
+  }
+  // Coalesced copy of the block's zones (contiguous in [ray][zone][k][k'] order).
   const unsigned cnt = nzb * n * n;
   const size_t base = (size_t)z0 * n * n;
   for (unsigned e = threadIdx.x; e < cnt; e += blockDim.x) {
@@ -200,6 +219,9 @@ __global__ void k_phi(Prob p, Ws w, const double *__restrict__ T, int zpb) {
       const float vf = d2f_exp2(v, 0);
       w.phin32[base + e] = vf;
       w.phd32[base + e] = __fsub_rn(vf, d2f_exp2(o, 0));
+      const unsigned zz = row / (unsigned)n, k = row - zz * n;
+      const float2 a = split_ff(v, rsc[zz * 2 * n + k]), b = split_ff(o, rsc[zz * 2 * n + n + k]);
+      w.nesff[base + e] = make_float4(a.x, a.y, b.x, b.y);
     } else {
       w.phd[base + e] = v - o;
     }

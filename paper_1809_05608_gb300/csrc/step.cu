@@ -37,6 +37,8 @@ Layout make_layout(int n_ray, int n_r, int n, int precision, int pair) {
   L.rsum = take(sizeof(double) * Z * n);
   L.phin32 = take(precision == MGFLD_MIXED ? sizeof(float) * Z * n * n : 0);
   L.phd32 = take(precision == MGFLD_MIXED ? sizeof(float) * Z * n * n : 0);
+  L.nesff = take(precision == MGFLD_MIXED ? sizeof(float4) * Z * n * n : 0);
+  L.nessc = take(precision == MGFLD_MIXED ? sizeof(int2) * Z * n : 0);
   L.lam = take(sizeof(double) * F);
   L.alpha = take(sizeof(double) * F);
   L.ghost = take(sizeof(double) * R * NS * n);
@@ -110,6 +112,8 @@ Ws resolve(void *base, const Layout &L) {
   w.rsum = (double *)(b + L.rsum);
   w.phin32 = L.mixed ? (float *)(b + L.phin32) : nullptr;
   w.phd32 = L.mixed ? (float *)(b + L.phd32) : nullptr;
+  w.nesff = L.mixed ? (float4 *)(b + L.nesff) : nullptr;
+  w.nessc = L.mixed ? (int2 *)(b + L.nessc) : nullptr;
   w.lam = (double *)(b + L.lam);
   w.slam = (double *)(b + L.slam);
   w.g0 = (double *)(b + L.g0);
@@ -298,6 +302,9 @@ __global__ void k_update_ye(Prob p, Ws w, Tol tl, const double *__restrict__ psi
     const double cy = kFourPiHC3 * p.eos.mb / rho;
     const double capT = kExpCap * Ti;
     const double eps0 = w.E[0] * inv_a;
+    // rows of an even number of groups in 16-byte aligned arrays are read in 16-byte pieces
+    const bool vec = (n % 2 == 0) &&
+                     ((((uintptr_t)psi | (uintptr_t)p.kabs | (uintptr_t)w.jbuf) & 15u) == 0);
     double Y = ye[zi];
     double mu, dmu;
     mu_nue_zone(p.eos, z[ZC_MUA], z[ZC_MUB], Ti, Y, mu, dmu);
@@ -308,13 +315,30 @@ __global__ void k_update_ye(Prob p, Ws w, Tol tl, const double *__restrict__ psi
       const size_t g0 = (((size_t)ray * NS + q) * p.n_r + i) * n;
       double a0, a1 = 0.0, c = 0.0;
       if (muq - eps0 < capT) {                    // no group at the cap
-        for (int k = 0; k < n; ++k) {
-          const double wk = w.W[k];
-          const double kap = p.scale ? p.kabs[g0 + k] * p.scale[q * n + k] : p.kabs[g0 + k];
-          const double pk = psi[g0 + k];
-          const double wj = wk * w.jbuf[g0 + k];
-          a1 += fma(-wj, pk, wj);                 // w j (1 - psi)
-          c = fma(wk * kap, pk, c);               // w kappa psi
+        if (vec) {
+          // the same sums in the same order, the rows read 16 bytes at a time
+          for (int k = 0; k < n; k += 2) {
+            const double2 kp2 = *reinterpret_cast<const double2 *>(p.kabs + g0 + k);
+            const double2 ps2 = *reinterpret_cast<const double2 *>(psi + g0 + k);
+            const double2 jb2 = *reinterpret_cast<const double2 *>(w.jbuf + g0 + k);
+            const double w0 = w.W[k], w1 = w.W[k + 1];
+            const double k0 = p.scale ? kp2.x * p.scale[q * n + k] : kp2.x;
+            const double k1 = p.scale ? kp2.y * p.scale[q * n + k + 1] : kp2.y;
+            const double wj0 = w0 * jb2.x, wj1 = w1 * jb2.y;
+            a1 += fma(-wj0, ps2.x, wj0);
+            c = fma(w0 * k0, ps2.x, c);
+            a1 += fma(-wj1, ps2.y, wj1);
+            c = fma(w1 * k1, ps2.y, c);
+          }
+        } else {
+          for (int k = 0; k < n; ++k) {
+            const double wk = w.W[k];
+            const double kap = p.scale ? p.kabs[g0 + k] * p.scale[q * n + k] : p.kabs[g0 + k];
+            const double pk = psi[g0 + k];
+            const double wj = wk * w.jbuf[g0 + k];
+            a1 += fma(-wj, pk, wj);               // w j (1 - psi)
+            c = fma(wk * kap, pk, c);             // w kappa psi
+          }
         }
         a0 = a1 - c;
       } else {
@@ -345,7 +369,17 @@ __global__ void k_update_ye(Prob p, Ws w, Tol tl, const double *__restrict__ psi
       const double ratio = exp((m1 - m0) / Ti);
       const size_t g0 = (((size_t)ray * NS + q) * p.n_r + i) * n;
       if (m0 - eps0 < capT && m1 - eps0 < capT) {
-        for (int k = 0; k < n; ++k) w.jbuf[g0 + k] *= ratio;
+        if (vec) {
+          for (int k = 0; k < n; k += 2) {
+            double2 *jb = reinterpret_cast<double2 *>(w.jbuf + g0 + k);
+            double2 v = *jb;
+            v.x *= ratio;
+            v.y *= ratio;
+            *jb = v;
+          }
+        } else {
+          for (int k = 0; k < n; ++k) w.jbuf[g0 + k] *= ratio;
+        }
       } else {
         for (int k = 0; k < n; ++k) {
           const double eps = w.E[k] * inv_a;
@@ -738,14 +772,18 @@ static cudaError_t enqueue_iteration(const StepCall &c, int it, int n_act, int n
     MGFLD_ENQ(launch_coef_iterate(p, w, c.st.psi, w.list_act, n_act, cnt_act, s));
     if (prof) prof->end(MGFLD_PROF_SETUP, 3);
   }
-  if (prof) prof->begin(MGFLD_PROF_ASSEMBLE);
+  const bool incremental = !pair && it > 0 && tl.mixed && !c.coef_iterate;
+  if (prof) prof->begin(incremental ? MGFLD_PROF_RESIDUAL : MGFLD_PROF_ASSEMBLE);
   if (pair)
     MGFLD_ENQ(launch_assemble_pair(p, w, c.st.psi, w.diag, tl.mixed, w.lower, w.upper, w.rhs, w.list_act, n_act, jac,
                                    s, nullptr, it == 0, cnt_act));
+  else if (incremental)
+    MGFLD_ENQ(launch_resid_ff(p, w, c.st.psi, (float *)w.diag, w.lower, w.upper, w.rhs, w.list_act, n_act, jac,
+                              tl.tolmin, s, cnt_act));
   else
     MGFLD_ENQ(launch_assemble(p, w, c.st.psi, w.diag, tl.mixed, w.lower, w.upper, w.rhs, w.list_act, n_act, jac, s,
                               nullptr, it == 0 || c.coef_iterate, cnt_act));
-  if (prof) prof->end(MGFLD_PROF_ASSEMBLE, 1);
+  if (prof) prof->end(incremental ? MGFLD_PROF_RESIDUAL : MGFLD_PROF_ASSEMBLE, 1);
   const int *flist = tl.chord ? w.list_ref : w.list_act;
   const int nf = tl.chord ? n_ref : n_act;
   if (nf > 0) {

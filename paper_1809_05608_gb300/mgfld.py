@@ -192,13 +192,14 @@ class DeviceProblem:
                        off('u', n_r), off('eta1', N_SPECIES * n_r * n_e), off('pair_coef', n_r), self.pair_chi)
 
 
-PROF_NAMES = ('setup', 'assemble', 'factor', 'solve', 'update', 'finish')
+PROF_NAMES = ('setup', 'assemble', 'factor', 'solve', 'update', 'finish', 'residual')
+PROF_N = len(PROF_NAMES)
 
 
 def step_opts(precision=MGFLD_FP64, tol=1e-10, tolmin_psi=1.0, tol_ye=None, tolmin_ye=0.1, max_iter=40,
               refactor_ratio=None, profile=None, coef_iterate=False):
     """`refactor_ratio`: None gives 0.1 for MIXED and Newton (0) for FP64; a positive value makes
-    FP64 reuse its factors too.  `profile`: optional ctypes (c_double * 12) array accumulating
+    FP64 reuse its factors too.  `profile`: optional ctypes (c_double * (2 * PROF_N)) array accumulating
     per-category (milliseconds, launches) for the categories of PROF_NAMES.  `coef_iterate`: the
     flux coefficients of Eq. a59 at the outer iterate (n+1) instead of at psi^n."""
     if refactor_ratio is None:

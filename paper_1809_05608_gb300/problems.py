@@ -201,6 +201,25 @@ def make_shock_problem(config: int, rays=None, n_ray=None, n_r=None, n_e=None, b
     return out
 
 
+def make_pair_problem(config: int, rays=None, n_ray=None, n_r=None, n_e=None, pair=1.0, chi=True):
+    """Configuration `config` with the synthetic pair process: the pair kernel scale pair_coef =
+    pair x the NES scale (1e-41 rho, cm^3/s) per zone and, with chi, the angular correction on with
+    the flux factor of flux_factor (shared by the species)."""
+    out = make_problem(config, n_ray=n_ray, n_r=n_r, n_e=n_e)
+    prob = dict(out['problem'])
+    prob['pair_coef'] = np.ascontiguousarray(1e-41 * pair * prob['rho'])
+    if chi:
+        r_edge, e_edge = prob['r_edge'], prob['e_edge']
+        rc = 0.5 * (r_edge[:, 1:] + r_edge[:, :-1])
+        eta1 = flux_factor(rc, np.sqrt(e_edge[1:] * e_edge[:-1]))
+        prob['eta1'] = np.ascontiguousarray(np.broadcast_to(eta1[:, None], rc.shape[:1] + (N_SPECIES,) + eta1.shape[1:]))
+        prob['pair_chi'] = True
+    out = dict(out, problem=prob)
+    if rays is not None:
+        out = subset_rays(out, rays)
+    return out
+
+
 def stress_inputs(inp):
     """Matter pressure and inner mass for the neutrino stress and the lapse on a transport
     workload: p = 1.2435e15 (Ye rho)^(4/3) + rho kT / m_B (relativistic degenerate electrons plus

@@ -41,7 +41,9 @@ def test_workspace_query(L):
     b64 = M.mgfld_workspace_bytes(d, M.MGFLD_FP64)
     b32 = M.mgfld_workspace_bytes(d, M.MGFLD_MIXED)
     blocks = 256 * 4 * 512 * 20 * 20
-    assert b64 > 16 * blocks and b32 < b64 and b64 - b32 >= 4 * blocks
+    # FP64 keeps FP64 blocks and inverses (16 B per block entry); MIXED FP32 ones (8 B) plus the
+    # NES kernels as FP32 pairs (16 B per kernel entry and zone: 4 B per block entry)
+    assert b64 > 16 * blocks and b32 < b64 and b64 - b32 >= 2 * blocks
     assert M.mgfld_workspace_bytes(M.Dims(1, 1, 33, 4), 0) == 0
     assert M.mgfld_workspace_bytes(M.Dims(1, 4, 4, 3), 0) == 0
     assert M.mgfld_factor_bytes(M.Dims(2, 3, 5, 4), M.MGFLD_MIXED) == 2 * 4 * 3 * 25 * 4

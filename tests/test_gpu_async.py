@@ -57,7 +57,7 @@ def test_the_call_returns_before_the_step_has_run():
 
 
 def _host_loop_step(st, psi, ye, T):
-    prof = (ctypes.c_double * 12)()
+    prof = (ctypes.c_double * (2 * M.PROF_N))()
     st.opts.profile = ctypes.cast(prof, ctypes.c_void_p)
     rc = st.step(psi, ye, T)
     st.opts.profile = None

@@ -25,7 +25,7 @@ def test_noalloc_rejects_oversize_and_profiling_before_touching_the_gpu():
     L = M.lib()
     assert L.mgfld_step_noalloc(ctypes.byref(big), ctypes.byref(prob), ctypes.byref(st),
                                 ctypes.byref(M.step_opts()), None, None) == M.MGFLD_ENOMEM
-    prof = (ctypes.c_double * 12)()
+    prof = (ctypes.c_double * (2 * M.PROF_N))()
     small = M.Dims(1, 8, 4, 4)
     assert L.mgfld_step_noalloc(ctypes.byref(small), ctypes.byref(prob), ctypes.byref(st),
                                 ctypes.byref(M.step_opts(profile=prof)), None, None) == M.MGFLD_EINVAL
