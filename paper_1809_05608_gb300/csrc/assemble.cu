@@ -328,7 +328,27 @@ __device__ inline void two_sum2(float2 &s, float2 &err, float2 b) {
   err = __fadd2_rn(err, __fadd2_rn(u, v));
 }
 
-__global__ void __launch_bounds__(256)
+// The NES sums of one row at psi in FP64, as k_assemble forms them (a group whose last correction
+// is too large for the FP32-pair increment).  Kept out of line, so that the common path does not
+// carry its registers.
+__device__ __noinline__ void nes_sums_fp64(const double *__restrict__ fin, const double *__restrict__ fout,
+                                           const double *__restrict__ ps, int n, double *gain, double *lp) {
+  double a = 0.0, b = 0.0;
+  for (int kp = 0; kp < n; ++kp) {
+    const double pv = ps[kp];
+    a += fin[kp] * pv;
+    b += fout[kp] * pv;
+  }
+  *gain = a;
+  *lp = b;
+}
+
+// CTAs of 256 threads per SM the residual kernel is compiled for (its register budget).
+#ifndef MGFLD_FF_MINB
+#define MGFLD_FF_MINB 7
+#endif
+
+__global__ void __launch_bounds__(256, MGFLD_FF_MINB)
 k_resid_ff(Prob p, Ws w, const double *__restrict__ psi, float *__restrict__ diag, double *__restrict__ lower,
            double *__restrict__ upper, double *__restrict__ rhs, const int *__restrict__ list, int n_list,
            const int *__restrict__ jac_flag, double tolmin, const int *__restrict__ n_dev) {
@@ -422,14 +442,7 @@ k_resid_ff(Prob p, Ws w, const double *__restrict__ psi, float *__restrict__ dia
     lp = (l0 + f2d_exp2(sum.y, ul)) + f2d_exp2(err.y, ul);
   } else {
     // a large last correction: the sums at the iterate in FP64, as k_assemble forms them
-    const double *fin = w.phin + (zi * n + k) * n, *fout = w.phout + (zi * n + k) * n;
-    gain = 0.0;
-    lp = 0.0;
-    for (int kp = 0; kp < n; ++kp) {
-      const double pv = ps[kp];
-      gain += fin[kp] * pv;
-      lp += fout[kp] * pv;
-    }
+    nes_sums_fp64(w.phin + (zi * n + k) * n, w.phout + (zi * n + k) * n, ps, n, &gain, &lp);
   }
   w.g0[g] = gain;
   w.l0[g] = lp;

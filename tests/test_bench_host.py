@@ -12,7 +12,7 @@ from paper_1809_05608_gb300 import problems
 def test_traffic_records_match_the_current_kernel_sources():
     """bench.py reports roofline traffic only while the sources hash to the digest of the ncu
     capture; the committed records must be those of the committed sources."""
-    for kernel in ('k_assemble', 'k_factor', 'k_factor_row2', 'k_solve_tma'):
+    for kernel in ('k_assemble', 'k_factor', 'k_factor_row2', 'k_solve_tma', 'k_resid_ff'):
         rec = bench.traffic_record(kernel)
         assert rec is not None and rec['bytes'] > 0 and rec['units'] == 256.0, kernel
 
