@@ -17,7 +17,7 @@ namespace mgfld {
 
 // Shared memory of k_pair per zone: e^{-eps/T} and eps^2 d eps of each group, and the flux
 // factor and cone edge (Eqs. d17, d22) of every species and group.
-__host__ __device__ inline size_t pair_zone_doubles(int n) { return (size_t)(2 + 2 * NS) * n; }
+__host__ __device__ inline size_t pair_zone_doubles(int n) { return (size_t)(2 + 3 * NS) * n; }
 static inline int pair_zones_per_block(int n) {
   const int z = 256 / (NS * n);
   return z < 1 ? 1 : z;
@@ -40,7 +40,7 @@ __global__ void k_pair(Prob p, Ws w, const double *__restrict__ T, int zpb) {
   const unsigned zi = blockIdx.x * (unsigned)zpb + zl;
   const bool live = zl < zpb && zi < nz;
   double *ez = sm + (size_t)(live ? zl : 0) * pair_zone_doubles(n);
-  double *wl = ez + n, *eta = wl + n, *mu = eta + NS * n;
+  double *wl = ez + n, *eta = wl + n, *mu = eta + NS * n, *mu1 = mu + NS * n;
   int ray = 0, i = 0;
   if (live) {
     ray = (int)(zi / (unsigned)p.n_r);
@@ -48,7 +48,7 @@ __global__ void k_pair(Prob p, Ws w, const double *__restrict__ T, int zpb) {
     const double inv_a = 1.0 / lapse_at(p, ray, i);
     if (q == 0) {
       ez[k] = exp(-(w.E[k] * inv_a) / T[zi]);
-      wl[k] = w.W[k] * inv_a * inv_a * inv_a;
+      wl[k] = kCNes * p.pair[zi] * (w.W[k] * inv_a * inv_a * inv_a);
     }
     const size_t g = (((size_t)ray * NS + q) * p.n_r + i) * n + k;
     eta[q * n + k] = p.eta1 ? fmin(fmax(p.eta1[g], 0.0), 1.0) : 0.0;
@@ -56,29 +56,32 @@ __global__ void k_pair(Prob p, Ws w, const double *__restrict__ T, int zpb) {
     const double rc = 0.5 * (re[i] + re[i + 1]);
     const double rr = w.rnu[((size_t)ray * NS + q) * n + k] / rc;
     const double x = 1.0 - rr * rr;
-    mu[q * n + k] = fmax(x > 0.0 ? sqrt(x) : (x < 0.0 ? -sqrt(-x) : 0.0), -1.0);
+    const double m = fmax(x > 0.0 ? sqrt(x) : (x < 0.0 ? -sqrt(-x) : 0.0), -1.0);
+    mu[q * n + k] = m;
+    mu1[q * n + k] = 1.0 + m;
   }
   __syncthreads();
   if (!live) return;
-  const double cc = kCNes * p.pair[zi];
   const int qb = q ^ 1;
   double *kill = w.pkill + (((size_t)zi * NS + q) * n + k) * n;
-  const double et = eta[q * n + k], mt = mu[q * n + k];
-  for (int kp = 0; kp < n; ++kp) {
-    double chi = 1.0;
-    if (p.pair_chi) {
-      const double eb = eta[qb * n + kp], mb = mu[qb * n + kp];
-      const double c1 = 1.0 - et * eb / 6.0;
-      const double c2 = (8.0 + (mt * mb - 3.0) * (1.0 + mt) * (1.0 + mb)) / 8.0;
-      chi = fmin(c1, c2);
+  if (p.pair_chi) {
+    // the factors of this row taken out of the loop: chi_1 = 1 - (eta / 6) eta', and
+    // chi_2 = 1 + (mu mu' - 3) ((1 + mu) / 8) (1 + mu') (the 1/8 exact)
+    const double e6 = eta[q * n + k] / 6.0, mt = mu[q * n + k], m8 = 0.125 * mu1[q * n + k];
+    for (int kp = 0; kp < n; ++kp) {
+      const double c1 = fma(-e6, eta[qb * n + kp], 1.0);
+      const double c2 = fma(fma(mt, mu[qb * n + kp], -3.0) * m8, mu1[qb * n + kp], 1.0);
+      kill[kp] = wl[kp] * fmin(c1, c2);
     }
-    kill[kp] = cc * wl[kp] * chi;
+  } else {
+    for (int kp = 0; kp < n; ++kp) kill[kp] = wl[kp];
   }
   if (q == 0) {
     double *make = w.pmake + ((size_t)zi * n + k) * n;
+    const double ek = ez[k];
     double ms = 0.0;
     for (int kp = 0; kp < n; ++kp) {
-      const double v = cc * wl[kp] * (ez[k] * ez[kp]);
+      const double v = wl[kp] * (ek * ez[kp]);
       make[kp] = v;
       ms += v;
     }
