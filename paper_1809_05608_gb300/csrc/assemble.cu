@@ -312,20 +312,20 @@ __host__ __device__ inline int ff_zpb(int n) { return (256 / (NS * n)) > 0 ? 256
 __host__ __device__ inline int ff_ld(int n) { return (n % 2 == 0) ? n + 1 : n; }      // odd row stride in float4
 static inline size_t ff_smem(int n) {
   const int z = ff_zpb(n), rows = z * NS * n;
-  return sizeof(float4) * (size_t)z * n * ff_ld(n) + sizeof(int2) * (size_t)z * n + sizeof(float4) * rows +
+  return sizeof(float4) * (size_t)z * n * ff_ld(n) + sizeof(int2) * (size_t)z * n + sizeof(float2) * rows +
          2 * sizeof(unsigned) * (size_t)z * NS + sizeof(long long) * (size_t)z;
 }
 
-// Knuth's two-sum of the two lanes of a pair, s + b -> s, its rounding error added to err; the
+// Knuth's two-sum of the two lanes of a pair: s + b -> s, returning its rounding error; the
 // differences are FMAs with a -1 multiplier (exact as subtractions, no negations).
-__device__ inline void two_sum2(float2 &s, float2 &err, float2 b) {
+__device__ inline float2 two_sum2(float2 &s, float2 b) {
   const float2 m1 = make_float2(-1.f, -1.f);
   const float2 a = s;
   s = __fadd2_rn(a, b);
-  const float2 bb = __ffma2_rn(a, m1, s);                 // s - a
+  const float2 bb = __ffma2_rn(a, m1, s);                      // s - a
   const float2 u = __ffma2_rn(__ffma2_rn(bb, m1, s), m1, a);   // a - (s - bb)
-  const float2 v = __ffma2_rn(bb, m1, b);                 // b - bb
-  err = __fadd2_rn(err, __fadd2_rn(u, v));
+  const float2 v = __ffma2_rn(bb, m1, b);                      // b - bb
+  return __fadd2_rn(u, v);
 }
 
 // The NES sums of one row at psi in FP64, as k_assemble forms them (a group whose last correction
@@ -357,7 +357,7 @@ k_resid_ff(Prob p, Ws w, const double *__restrict__ psi, float *__restrict__ dia
   const unsigned zrows = (unsigned)(NS * n), bt = (unsigned)zpb * zrows, nn = (unsigned)(n * n);
   // (16-byte pieces first, then 8-byte, then 4-byte: every array aligned to its element)
   float4 *tile = reinterpret_cast<float4 *>(ff_sm);                       // [zpb][n][ld]
-  float4 *dff = tile + (size_t)zpb * n * ld;                               // [bt]: (hi, lo, -hi, 0)
+  float2 *dff = reinterpret_cast<float2 *>(tile + (size_t)zpb * n * ld);   // [bt]: (d, -d)
   int2 *rsc = reinterpret_cast<int2 *>(dff + bt);                          // [zpb][n]
   long long *zoff = reinterpret_cast<long long *>(rsc + (size_t)zpb * n);  // [zpb]: zone index ray n_r + i
   unsigned *gmx = reinterpret_cast<unsigned *>(zoff + zpb);                // [zpb NS]: max |dpsi| (upper words)
@@ -410,8 +410,10 @@ k_resid_ff(Prob p, Ws w, const double *__restrict__ psi, float *__restrict__ dia
   __syncthreads();
   const int sgrp = scale_of_max(gmx[grp]);
   {
-    const float2 d = split_ff(dx, sgrp);
-    dff[threadIdx.x] = make_float4(d.x, d.y, -d.x, 0.f);
+    // the correction of the mixed path comes from the FP32 substitution (an FP32 value times a
+    // power of two), so its scaled FP32 form is exact (the lo part of split_ff is zero)
+    const float d = d2f_exp2(dx, sgrp);
+    dff[threadIdx.x] = make_float2(d, -d);
   }
   __syncthreads();
   if (!in) return;
@@ -423,23 +425,33 @@ k_resid_ff(Prob p, Ws w, const double *__restrict__ psi, float *__restrict__ dia
   // by exponents (the same decision for every row of the group)
   if ((int)(gmx[grp] >> 20) + 6 <= (int)(max(gpx[grp], abs_hi_word(tolmin)) >> 20)) {
     const float4 *fr = tile + ((size_t)zs * n + k) * ld;
-    const float4 *dr = dff + (size_t)grp * n;
-    float2 sum = make_float2(0.f, 0.f), err = make_float2(0.f, 0.f);   // (gain, loss) lanes
-    for (int kp = 0; kp < n; ++kp) {
+    const float2 *dr = dff + (size_t)grp * n;
+    // (gain, loss) lanes; two running sums (even and odd k') for two independent dependency chains
+    float2 s0 = make_float2(0.f, 0.f), s1 = s0, e0 = s0, e1 = s0;
+    auto term = [&](int kp, float2 &sum, float2 &err) {
       const float4 f = fr[kp];                       // (in hi, in lo, out hi, out lo)
-      const float4 d = dr[kp];                       // (hi, lo, -hi, 0)
+      const float2 d = dr[kp];                       // (d, -d)
       const float2 fh = make_float2(f.x, f.z), fl = make_float2(f.y, f.w);
-      const float2 dh = make_float2(d.x, d.x), dl = make_float2(d.y, d.y), nd = make_float2(d.z, d.z);
+      const float2 dh = make_float2(d.x, d.x), nd = make_float2(d.y, d.y);
       const float2 pr = __fmul2_rn(fh, dh);
       const float2 ex = __ffma2_rn(fh, dh, __fmul2_rn(fh, nd));          // exact product error
-      const float2 cr = __ffma2_rn(fh, dl, __fmul2_rn(fl, dh));          // cross terms
-      err = __fadd2_rn(err, __fadd2_rn(ex, cr));
-      two_sum2(sum, err, pr);
+      const float2 cr = __fmul2_rn(fl, dh);                              // the kernels' lo part
+      const float2 e = two_sum2(sum, pr);
+      err = __fadd2_rn(err, __fadd2_rn(__fadd2_rn(ex, cr), e));
+    };
+    int kp = 0;
+    for (; kp + 1 < n; kp += 2) {
+      term(kp, s0, e0);
+      term(kp + 1, s1, e1);
     }
+    if (kp < n) term(kp, s0, e0);
+    const float2 e01 = two_sum2(s0, s1);
+    const float2 er = __fadd2_rn(__fadd2_rn(e0, e1), e01);
+    const float2 sm = s0;
     const int2 sc = rsc[zs * n + k];
     const int ug = -(sc.x + sgrp), ul = -(sc.y + sgrp);
-    gain = (g0 + f2d_exp2(sum.x, ug)) + f2d_exp2(err.x, ug);
-    lp = (l0 + f2d_exp2(sum.y, ul)) + f2d_exp2(err.y, ul);
+    gain = (g0 + f2d_exp2(sm.x, ug)) + f2d_exp2(er.x, ug);
+    lp = (l0 + f2d_exp2(sm.y, ul)) + f2d_exp2(er.y, ul);
   } else {
     // a large last correction: the sums at the iterate in FP64, as k_assemble forms them
     nes_sums_fp64(w.phin + (zi * n + k) * n, w.phout + (zi * n + k) * n, ps, n, &gain, &lp);
