@@ -860,6 +860,8 @@ def profile_step(path, n_rays, config):
         return 0
     if path == 'shock':
         inp = problems.make_shock_problem(config, rays=slice(0, n_rays))
+    elif path == 'pair':
+        inp = problems.make_pair_problem(config, rays=slice(0, n_rays))
     else:
         inp = problems.make_problem(config, rays=slice(0, n_rays))
     prec = M.MGFLD_FP64 if path == 'fp64' else M.MGFLD_MIXED
@@ -896,11 +898,12 @@ def main():
     ap.add_argument('--impl', default='mgfld', choices=['mgfld', 'reference'])
     ap.add_argument('--no-cpu-baseline', action='store_true')
     ap.add_argument('--no-extra', action='store_true',
-                    help='headline and its FP64 comparison only (no 3D-scale, shock, n+1, stress, '
+                    help='headline and its FP64 comparison only (no 3D-scale, shock, n+1, pair, stress, '
                          'energy-advection lines)')
-    ap.add_argument('--profile-step', choices=['mixed', 'fp64', 'shock', 'coef', 'eadv', 'stress'],
+    ap.add_argument('--profile-step', choices=['mixed', 'fp64', 'shock', 'coef', 'pair', 'eadv', 'stress'],
                     help='profiling target: one implicit step of this path (shock: the mixed path with '
-                         'the shock terms; coef: the mixed path with the flux coefficients formed at '
+                         'the shock terms; pair: the mixed path with the pair process and its angular '
+                         'correction; coef: the mixed path with the flux coefficients formed at '
                          'every outer iterate; eadv: two energy-advection steps; stress: two stress-and-lapse '
                          'calls) on --rays rays of --config, no timing')
     ap.add_argument('--rays', type=int, default=64)
