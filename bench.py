@@ -532,64 +532,85 @@ def step_roofline(res, inp, precision):
                        'HBM bytes / HBM peak), algorithmic counts per unit from the formulas')
 
 
-def e2e_run(M, torch, inp, precision, steps):
-    """Same metric through the public API from pinned HOST buffers: every step uploads
-    that step's inputs (matter, opacities, NES scale, grid, state), runs mgfld_step and
-    reads the new state back.  The problem arrays of step s+1 are uploaded on a second
-    stream into a second device copy while step s runs (double buffering); the state goes
-    host -> device -> host on the compute stream, in order."""
-    st = M.Stepper(inp, precision, tol=TOL, max_iter=60)
-    prob = inp['problem']
+def e2e_run(M, torch, inp, precision, steps, parts=2):
+    """Same metric through the public API from pinned HOST buffers: every step uploads that
+    step's inputs (matter, opacities, NES scale, grid, state), runs mgfld_step and reads the new
+    state back.  The rays are processed in `parts` contiguous blocks, each with its own Stepper on
+    its own CUDA stream, where its state goes host -> device -> host around its step in order, so
+    that one block's state copies overlap the other blocks' steps; each block's problem arrays of
+    step s+1 are uploaded on a copy stream into a second device copy while step s runs (double
+    buffering)."""
+    n_ray = inp['psi0'].shape[0]
     names = ('r_edge', 'rho', 'kappa_abs', 'kappa_scat', 'nes_coef')
-    host = {k: torch.from_numpy(np.ascontiguousarray(prob[k], dtype=np.float64)).pin_memory() for k in names}
-    hs = [torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).pin_memory()
-          for a in (inp['psi0'], inp['ye0'], inp['T0'])]
-    dev = [torch.empty_like(h, device='cuda') for h in hs]
-    out = [torch.empty_like(h).pin_memory() for h in hs]
-    bufs = [st.prob, M.DeviceProblem(prob)]
-    h2d = sum(v.numel() * 8 for v in host.values()) + sum(h.numel() * 8 for h in hs)
-    d2h = sum(h.numel() * 8 for h in hs)
-    stream = torch.cuda.current_stream()
-    copy = torch.cuda.Stream()
-    ready = [torch.cuda.Event(), torch.cuda.Event()]     # buffer b uploaded
-    free = [torch.cuda.Event(), torch.cuda.Event()]      # buffer b no longer read by a step
+    main = torch.cuda.current_stream()
+    blocks = []
+    h2d = d2h = 0
+    for c in range(parts):
+        sub = problems.subset_rays(inp, slice(n_ray * c // parts, n_ray * (c + 1) // parts))
+        st = M.Stepper(sub, precision, tol=TOL, max_iter=60)
+        prob = sub['problem']
+        host = {k: torch.from_numpy(np.ascontiguousarray(prob[k], dtype=np.float64)).pin_memory() for k in names}
+        hs = [torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).pin_memory()
+              for a in (sub['psi0'], sub['ye0'], sub['T0'])]
+        blk = dict(st=st, host=host, hs=hs, dev=[torch.empty_like(h, device='cuda') for h in hs],
+                   out=[torch.empty_like(h).pin_memory() for h in hs], bufs=[st.prob, M.DeviceProblem(prob)],
+                   stream=torch.cuda.Stream(), copy=torch.cuda.Stream(),
+                   ready=[torch.cuda.Event(), torch.cuda.Event()], free=[torch.cuda.Event(), torch.cuda.Event()])
+        h2d += sum(v.numel() * 8 for v in host.values()) + sum(h.numel() * 8 for h in hs)
+        d2h += sum(h.numel() * 8 for h in hs)
+        blocks.append(blk)
 
-    def upload(b):
-        with torch.cuda.stream(copy):
+    def upload(blk, b):
+        with torch.cuda.stream(blk['copy']):
             for k in names:
-                bufs[b].t[k].copy_(host[k], non_blocking=True)
-            ready[b].record(copy)
+                blk['bufs'][b].t[k].copy_(blk['host'][k], non_blocking=True)
+            blk['ready'][b].record(blk['copy'])
 
+    def run(n_steps, e0, e1, first):
+        e0.record(main)
+        for blk in blocks:
+            blk['copy'].wait_event(e0)
+            blk['stream'].wait_event(e0)
+            upload(blk, 0)
+        for s in range(n_steps):
+            b = s % 2
+            for blk in blocks:
+                if s + 1 < n_steps:
+                    if s >= 1:
+                        blk['copy'].wait_event(blk['free'][1 - b])
+                    upload(blk, 1 - b)
+                stream = blk['stream']
+                stream.wait_event(blk['ready'][b])
+                blk['st'].prob = blk['bufs'][b]
+                src = blk['hs'] if (first and s == 0) else blk['out']
+                with torch.cuda.stream(stream):
+                    for d, h in zip(blk['dev'], src):
+                        d.copy_(h, non_blocking=True)
+                    rc = blk['st'].step(*blk['dev'], stream=stream, wait=False)
+                    assert rc == M.MGFLD_OK, M.status_str(rc)
+                    blk['free'][b].record(stream)
+                    for o, d in zip(blk['out'], blk['dev']):
+                        o.copy_(d, non_blocking=True)
+        for blk in blocks:
+            main.wait_stream(blk['stream'])
+            main.wait_stream(blk['copy'])
+        e1.record(main)
+        torch.cuda.synchronize()
+
+    # two untimed steps (each block's step graphs for both problem buffers built and cached); the
+    # timed steps continue from their state, read back to the host
     torch.cuda.synchronize()
+    run(2, torch.cuda.Event(), torch.cuda.Event(), True)
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    copy.wait_event(e0)
-    upload(0)
-    for s in range(steps):
-        b = s % 2
-        if s + 1 < steps:
-            if s >= 1:
-                copy.wait_event(free[1 - b])
-            upload(1 - b)
-        stream.wait_event(ready[b])
-        st.prob = bufs[b]
-        src = hs if s == 0 else out
-        for d, h in zip(dev, src):
-            d.copy_(h, non_blocking=True)
-        rc = st.step(*dev, wait=False)            # asynchronous: the next uploads overlap it
-        assert rc == M.MGFLD_OK, M.status_str(rc)
-        free[b].record(stream)
-        for o, d in zip(out, dev):
-            o.copy_(d, non_blocking=True)
-    e1.record(stream)
-    torch.cuda.synchronize()
+    run(steps, e0, e1, False)
     ms = e0.elapsed_time(e1)
-    assert st.worst_status() == M.MGFLD_OK
-    st.prob = bufs[0]
-    del st, bufs, dev
+    for blk in blocks:
+        assert blk['st'].worst_status() == M.MGFLD_OK
+        blk['st'].prob = blk['bufs'][0]
+    del blocks
     torch.cuda.empty_cache()
-    return dict(ms=ms, h2d=h2d, d2h=d2h)
+    return dict(ms=ms, h2d=h2d, d2h=d2h, parts=parts)
 
 
 # ------------------------------------------------------------------------- CPU oracle

@@ -179,11 +179,18 @@ __global__ void k_assemble_pair(Prob p, Ws w, const double *__restrict__ psi, TD
   TD *row = diag + gc * n2;
   const int own = sq * n, part = (1 - sq) * n;
   if (sizeof(TD) == 4 && w.phin32) {
+    // FP32 rows (the preconditioner of the FP64 refinement): operands converted on the integer
+    // pipe (truncated), the partner's columns from FP32 copies of the pair kernels
     const float *fi = w.phin32 + (zi * n + k) * n, *fd = w.phd32 + (zi * n + k) * n;
-    const float pf = (float)pk;
+    const float pf = d2f_exp2(pk, 0);
+    const float dgf = (float)dg;
     for (int kp = 0; kp < n; ++kp) {
       const float e = fmaf(pf, fd[kp], -fi[kp]);
-      row[own + kp] = TD(kp == k ? (float)((double)e + dg) : e);
+      row[own + kp] = TD(kp == k ? e + dgf : e);
+    }
+    for (int kp = 0; kp < n; ++kp) {
+      const float m = d2f_exp2(mk[kp], 0);
+      row[part + kp] = TD(fmaf(pf, d2f_exp2(kl[kp], 0) - m, m));
     }
   } else {
     const double *fd = w.phd + (zi * n + k) * n;
@@ -191,13 +198,14 @@ __global__ void k_assemble_pair(Prob p, Ws w, const double *__restrict__ psi, TD
       const double e = fma(pk, fd[kp], -fin[kp]);
       row[own + kp] = TD(kp == k ? e + dg : e);
     }
+    for (int kp = 0; kp < n; ++kp) row[part + kp] = TD(fma(pk, kl[kp] - mk[kp], mk[kp]));
   }
-  for (int kp = 0; kp < n; ++kp) row[part + kp] = TD(fma(pk, kl[kp] - mk[kp], mk[kp]));
-  lower[gc] = -pre * al_in;
-  upper[gc] = i < last ? -pre * al_out : 0.0;
+  const double c_low = pre * al_in, c_up = i < last ? pre * al_out : 0.0;
+  lower[gc] = -c_low;
+  upper[gc] = -c_up;
   if (w.lower32) {
-    w.lower32[gc] = (float)lower[gc];
-    w.upper32[gc] = (float)upper[gc];
+    w.lower32[gc] = d2f_exp2(-c_low, 0);
+    w.upper32[gc] = d2f_exp2(-c_up, 0);
   }
 }
 
