@@ -886,7 +886,8 @@ template <int NP>
 struct Row2 {
   static constexpr int L = NP / 2;                 // lanes per half-system
   static constexpr int S = 32 / L;                 // half-systems per warp
-  static constexpr int PAD = NP + 4;               // row stride of the shared-memory rows (floats)
+  static constexpr int PAD = (NP / 4) % 2 ? NP : NP + 4;   // pivot-row stride: an odd number of
+                                                           // 16-byte pieces (conflict-free reads)
 };
 
 // CTAs per SM the two-rows-per-lane factor is compiled for (its register budget).
@@ -902,11 +903,14 @@ k_factor_row2(int n_r, int n_sys, const float *__restrict__ diag, const float *_
   using C = Row2<NP>;
   constexpr int L = C::L, S = C::S, PD = C::PAD;
   static_assert(NP % 4 == 0 && L % 2 == 0, "pivot pairs in one lane pair, rows in 16-byte pieces");
-  __shared__ __align__(16) float rows[2][S][NP][PD];       // the next zone's rows, per warp
+  // The next zone's rows and couplings arrive by cp.async, per warp (each lane copies and later
+  // reads only its own two rows: 80-byte rows are conflict-free for its 16-byte reads); after its
+  // last zone the bottom-up warp leaves its last inverse in its row buffer for the middle zone of
+  // the top-down warp.
+  __shared__ __align__(16) float rows[2][S][NP][NP];       // the next zone's rows, per warp
   __shared__ __align__(16) float cpl[2][S][2][NP];         // its couplings (to the previous / next zone)
   __shared__ __align__(16) float prow[2][2][S][2][PD];     // per warp, double-buffered pivot row pairs
   __shared__ __align__(16) float ucol[2][S][NP];           // column scaling of the next zone's Schur term
-  __shared__ __align__(16) float midt[S][NP][PD];          // bottom-up half's last inverse (middle zone)
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int half = wid;                                    // 0: zones 0..m top-down, 1: n_r-1..m+1 bottom-up
   const int g = lane / L, mm = lane % L;                   // half-system of the warp, lane in it
@@ -937,6 +941,7 @@ k_factor_row2(int n_r, int n_sys, const float *__restrict__ diag, const float *_
     }
     cp_async_commit();
   };
+  float (*midt)[NP][NP] = rows[1];                         // the bottom-up warp's last inverse
   float a0[NP], a1[NP];
   issue(0);
   for (int j = 0; j < len; ++j) {
@@ -993,9 +998,9 @@ k_factor_row2(int n_r, int n_sys, const float *__restrict__ diag, const float *_
       if (g < S && (mm == pl || mm == pl + 1)) {          // lanes beyond the S half-systems publish nothing
         float *dst = pb[gs][mm - pl];
 #pragma unroll
-        for (int c = 0; c < NP; c += 2) {
-          if (sl == 0) *reinterpret_cast<float2 *>(dst + c) = make_float2(a0[c], a0[c + 1]);
-          else *reinterpret_cast<float2 *>(dst + c) = make_float2(a1[c], a1[c + 1]);
+        for (int c = 0; c < NP; c += 4) {
+          if (sl == 0) *reinterpret_cast<float4 *>(dst + c) = make_float4(a0[c], a0[c + 1], a0[c + 2], a0[c + 3]);
+          else *reinterpret_cast<float4 *>(dst + c) = make_float4(a1[c], a1[c + 1], a1[c + 2], a1[c + 3]);
         }
       }
       __syncwarp();
