@@ -852,12 +852,13 @@ def reference_arm(args, n_gpus, rank):
 
 # ------------------------------------------------------------------------- main
 
-def profile_step(path, n_rays, config):
+def profile_step(path, n_rays, config, zones=None):
     """One implicit step of the first n_rays rays of a workload (FP64 Newton, the mixed path, the
     mixed path with the shock terms or with the flux coefficients formed at every outer iterate),
     two energy-advection steps, or one stress-and-lapse call, for ncu captures of single launches
     (the step with its outer iteration driven from the host, whose kernels are ordinary launches);
-    exits non-zero on a failed step."""
+    `zones` builds the rays with that many zones over the same radial range (a launch with the
+    workload's systems per SM at a fraction of its memory); exits non-zero on a failed step."""
     import torch
     from paper_1809_05608_gb300 import build as B
     if not os.path.exists(B.LIB):
@@ -880,11 +881,11 @@ def profile_step(path, n_rays, config):
         print(f'profile step stress: {n_rays} rays, {res["ms_per_call"]:.3f} ms', flush=True)
         return 0
     if path == 'shock':
-        inp = problems.make_shock_problem(config, rays=slice(0, n_rays))
+        inp = problems.make_shock_problem(config, rays=slice(0, n_rays), n_r=zones)
     elif path == 'pair':
-        inp = problems.make_pair_problem(config, rays=slice(0, n_rays))
+        inp = problems.make_pair_problem(config, rays=slice(0, n_rays), n_r=zones)
     else:
-        inp = problems.make_problem(config, rays=slice(0, n_rays))
+        inp = problems.make_problem(config, rays=slice(0, n_rays), n_r=zones)
     prec = M.MGFLD_FP64 if path == 'fp64' else M.MGFLD_MIXED
     st = M.Stepper(inp, prec, tol=TOL, max_iter=60, coef_iterate=path == 'coef')
     psi, ye, T = st.state_to_device(inp['psi0'], inp['ye0'], inp['T0'])
@@ -929,9 +930,11 @@ def main():
                          'calls) on --rays rays of --config, no timing')
     ap.add_argument('--rays', type=int, default=64)
     ap.add_argument('--config', type=int, default=CONFIG_ID)
+    ap.add_argument('--zones', type=int, default=None,
+                    help='profiling target: the rays built with ZONES zones over the same radial range')
     args = ap.parse_args()
     if args.profile_step:
-        return profile_step(args.profile_step, args.rays, args.config)
+        return profile_step(args.profile_step, args.rays, args.config, args.zones)
     ws, rank, local = dist_info()
     n_gpus = max(args.gpus, ws)
     if args.impl == 'reference':
