@@ -10,11 +10,14 @@
 // runs over the elements in shared memory between block barriers.  All arithmetic is FP64, and
 // the FP64 pipe bounds the kernel (every FP64 warp instruction occupies it for the same time,
 // however few lanes are active), so the work is arranged to keep FP64 instructions few and
-// warp-wide: the zone's constants are spread over the system's first threads, quotients that
-// share a denominator are formed with one division (slopes, interface values), cube moments and
-// cell averages use the factored form (hi^3 - lo^3)/(hi - lo) = hi^2 + hi lo + lo^2, the grid at
-// infinity (moments, centres) is formed once per block, and the three energy sums of xi are a
-// tree reduction over the system's threads.  Only the occupation limiter, rarely active, is
+// warp-wide: the zone's constants are spread over the system's first threads; quotients are
+// formed from a reciprocal seeded on the integer and FP32 pipes and refined by Newton steps
+// (a few FP64 FMAs instead of a division), the quotients that share a denominator from one of
+// them (slopes, interface values), and a group's slope and interface from one reciprocal of the
+// product of their denominators; the number on a shifted group needs no quotient (Eq. a78 times
+// its moment); cube moments use the factored form (hi^3 - lo^3)/(hi - lo) = hi^2 + hi lo + lo^2;
+// the grid at infinity (moments, centres) is formed once per block; and the two sums of xi are
+// a tree reduction over the system's threads.  Only the occupation limiter, rarely active, is
 // sequential.  The PPM limiters are continuous in their inputs, so these rearrangements move
 // results by rounding only.
 #include "mgfld_internal.cuh"
@@ -23,6 +26,28 @@ namespace mgfld {
 
 constexpr int kEadvThreads = 256;
 constexpr double kThird = 1.0 / 3.0;
+
+// n/d within about an ulp at a third of a division's FP64 instructions: the reciprocal seed of
+// recip (~2^-46, its conversions on the integer pipe) and one Newton correction of the quotient,
+// q = n x + x (n - d n x), whose error is of the order of the square of the seed's.
+__device__ inline double quot(double n, double d) {
+  const double x = recip(d);
+  const double q = n * x;
+  return fma(x, fma(-d, q, n), q);
+}
+
+// 1/d within about an ulp: recip and a second Newton-Raphson step.
+__device__ inline double recip2(double d) {
+  const double x = recip(d);
+  return fma(x, fma(-d, x, 1.0), x);
+}
+
+// eta2 of the Minerbo closure (Eqs. a86-a87): the weighting of the thick (1/3) and thin (1)
+// limits by the closure's factor p, (1 - p)/2 + (3p - 1)/2, is p itself.
+__device__ inline double eddington_p(double eta1) {
+  const double x = fmin(fmax(eta1, 0.0), 1.0);
+  return kThird + 2.0 * x * x / 15.0 * (3.0 - x + 3.0 * x * x);
+}
 
 struct EadvArgs {
   int n_ray, n_r, n, spb, limit;
@@ -74,12 +99,12 @@ __global__ void __launch_bounds__(kEadvThreads) k_energy_advect(EadvArgs g) {
     const double lo = g.e_edge[tid], hi = g.e_edge[tid + 1];
     const double q = hi * hi + hi * lo + lo * lo;
     cmE[tid] = (hi - lo) * q * kThird;
-    icmE[tid] = 1.0 / cmE[tid];
+    icmE[tid] = recip2(cmE[tid]);
     Ec[tid] = sqrt(q * kThird);
   }
   if (live) {
     psi0 = g.psi[el];
-    eta2[k] = g.eta1 ? minerbo_eta2(g.eta1[el]) : kThird;
+    eta2[k] = g.eta1 ? eddington_p(g.eta1[el]) : kThird;
     // quotient j of the zone (every thread of the system takes one or two, same code path):
     // 0 a^{n+1}/a^n, 1 1/a^{n+1}, 2 R^{n+1}/R^n, 3 b^{n+1}/b^n, 4 the number factor
     const double *re0 = g.r_n + ray * (size_t)(g.n_r + 1) + i, *re1 = g.r_np1 + ray * (size_t)(g.n_r + 1) + i;
@@ -89,7 +114,7 @@ __global__ void __launch_bounds__(kEadvThreads) k_energy_advect(EadvArgs g) {
     for (int j = k; j < 5; j += n) {
       const double num = j == 0 ? a1 : j == 1 ? 1.0 : j == 2 ? r1 : j == 3 ? r0 * r0 * rho0 : rho1 * a1 * a1 * a1;
       const double den = j == 0 ? a0 : j == 1 ? a1 : j == 2 ? r0 : j == 3 ? r1 * r1 * rho1 : rho0 * a0 * a0 * a0;
-      zc[j < 2 ? 4 * j : j - 1] = num / den;    // slots 0, 4, 1, 2, 3
+      zc[j < 2 ? 4 * j : j - 1] = quot(num, den);    // slots 0, 4, 1, 2, 3
     }
     if (k == 0) {
       zc[7] = 0.0;
@@ -124,18 +149,22 @@ __global__ void __launch_bounds__(kEadvThreads) k_energy_advect(EadvArgs g) {
   __syncthreads();
   // Phase 3: Eq. a78 (psi on the shifted group), its number nd and the cell average eps^2 psi
   // of the parabolic remap (number per unit comoving energy), with two zero-slope ghost groups at
-  // each end; the shifted group centre (Eq. a01b).
+  // each end; the shifted group centre (Eq. a01b).  psi on the shifted group times that group's
+  // moment is the number of Eq. a78, so nd = (the number factor) E^2 dE psi^n / (a^{n+1})^3 takes
+  // no quotient; the cell average is nd over the comoving width, and 1/(Dh - Dl) serves the
+  // fluxes of phase 7 as well (kept in the reduction scratch, free until phase 8).
+  double *iw = red + 2 * (n + 5);
   if (live) {
     const double ia1 = zc[4];
     const double Dl = E_d[k], Dh = E_d[k + 1];
+    const double dD = Dh - Dl, rw = recip2(dD);
     const double qD = Dh * Dh + Dh * Dl + Dl * Dl;
-    const double psi_d = zc[3] * cmE[k] / ((Dh - Dl) * qD * kThird) * psi0;
-    const double lo = Dl * ia1, hi = Dh * ia1;
-    const double q = hi * hi + hi * lo + lo * lo;
-    const double dx = hi - lo;
-    const double avg = psi_d * q * kThird;
-    nd[k] = avg * dx;
-    epsd_c[k] = sqrt(q * kThird);
+    const double b2 = zc[3] * cmE[k] * psi0 * (ia1 * ia1);
+    iw[k] = rw;
+    const double dx = dD * ia1;
+    const double avg = b2 * rw;
+    nd[k] = b2 * ia1;
+    epsd_c[k] = ia1 * sqrt(qD * kThird);
     A[k + 2] = avg;
     X[k + 2] = dx;
     if (k == 0) {
@@ -151,23 +180,29 @@ __global__ void __launch_bounds__(kEadvThreads) k_energy_advect(EadvArgs g) {
   // Phase 4: average slopes (Eq. h9) monotonised (Eq. h11) at the groups (extended index
   // 2..n+1), the two quotients of Eq. h9 over a common denominator.  The ghost groups copy their
   // neighbour, so one of their two differences is zero and the limiter makes their slopes zero.
-  auto slope = [&](int j) {
-    const double xl = X[j - 1], x0 = X[j], xr = X[j + 1];
-    const double dp = A[j + 1] - A[j], dn = A[j] - A[j - 1];
+  // Thread k takes slope and interface k + 2: one reciprocal of the product of the two
+  // denominators serves both (each is the other times it).
+  double inv5 = 0.0;
+  if (live) {
+    const int j = k + 2;
+    const double xl = X[j - 1], x0 = X[j], xr = X[j + 1], x2 = X[j + 2];
     const double sl_ = xl + x0, sr = xr + x0;
-    const double s = x0 * ((2.0 * xl + x0) * sl_ * dp + (x0 + 2.0 * xr) * sr * dn) / ((xl + x0 + xr) * sr * sl_);
+    const double d4 = (xl + x0 + xr) * sr * sl_;
+    const double d5 = (x0 + xr) * (2.0 * x0 + xr) * (x0 + 2.0 * xr) * (xl + x0 + xr + x2);
+    const double r45 = recip2(d4 * d5);
+    inv5 = d4 * r45;
+    const double dp = A[j + 1] - A[j], dn = A[j] - A[j - 1];
+    const double s = x0 * ((2.0 * xl + x0) * sl_ * dp + (x0 + 2.0 * xr) * sr * dn) * (d5 * r45);
     const double lim = fmin(fabs(s), fmin(2.0 * fabs(dp), 2.0 * fabs(dn)));
     dm[j] = dp * dn > 0.0 ? copysign(lim, s) : 0.0;
-  };
-  if (live) {
-    slope(k + 2);
     if (k < 2) dm[k == 0 ? 1 : n + 2] = 0.0;
   }
   __syncthreads();
   // Phase 5: interface values between extended groups j and j+1, j = 1..n+1 (Eq. h12, the cubic
   // through the group integrals), limited to the range of the two averages (Eqs. h15-h16); the
-  // five quotients over one denominator (x0 + x1)(2 x0 + x1)(x0 + 2 x1)(xl + x0 + x1 + x2).  At
-  // the two end interfaces the ghost's average equals the group's, so the limiter returns it.
+  // five quotients over one denominator (x0 + x1)(2 x0 + x1)(x0 + 2 x1)(xl + x0 + x1 + x2), whose
+  // reciprocal phase 4 formed.  At the two end interfaces the ghost's average equals the group's,
+  // so the limiter returns it.
   auto interface = [&](int j) {
     const double xl = X[j - 1], x0 = X[j], x1 = X[j + 1], x2 = X[j + 2];
     const double d = A[j + 1] - A[j];
@@ -175,7 +210,7 @@ __global__ void __launch_bounds__(kEadvThreads) k_energy_advect(EadvArgs g) {
     const double tot = xl + x0 + x1 + x2;
     const double tn = 2.0 * x0 * x1 * ((xl + x0) * Q - (x2 + x1) * P) * d
                       - s01 * (x0 * (xl + x0) * Q * dm[j + 1] - x1 * (x1 + x2) * P * dm[j]);
-    double f = A[j] + (x0 * d * P * Q * tot + tn) / (s01 * P * Q * tot);
+    double f = A[j] + (x0 * d * P * Q * tot + tn) * inv5;
     f = fmax(f, fmin(A[j], A[j + 1]));
     f = fmin(f, fmax(A[j], A[j + 1]));
     face[j] = f;
@@ -212,27 +247,29 @@ __global__ void __launch_bounds__(kEadvThreads) k_energy_advect(EadvArgs g) {
       F[n] = 0.0;
     } else {
       // d < 0: the top of group k-1 moves up into target group k (slice from its right end);
-      // d > 0: the bottom of group k moves down into target group k-1 (from its left end).
-      const double d = (g.e_edge[k] - E_d[k]) * ia1;
+      // d > 0: the bottom of group k moves down into target group k-1 (from its left end).  The
+      // slice's fraction of its group is |d| / (Dh - Dl) at infinity (the factor 1/a^{n+1} of
+      // both cancels), with 1/(Dh - Dl) from phase 3.
+      const double d = g.e_edge[k] - E_d[k];
       const bool up = d < 0.0;
       const int gsrc = up ? k - 1 : k;
       const double dir = up ? -1.0 : 1.0;
       const double dx = X[gsrc + 2];
-      const double y = fmin(fmax(fabs(d) / dx, 0.0), 1.0);
+      const double y = fmin(fabs(d) * iw[gsrc], 1.0);
       const double end = up ? aR[gsrc] : aL[gsrc];
       const double avg = end + dir * 0.5 * y * ((aR[gsrc] - aL[gsrc]) + dir * (1.0 - 2.0 * kThird * y) * a6[gsrc]);
       F[k] = -dir * avg * y * dx;
     }
   }
   __syncthreads();
-  // Phase 8: the three sums of xi (Eqs. p6-p8) over the system's groups by a tree over its
-  // threads: energy held by the shifted groups, the same numbers at the target centres, and the
-  // flux divergence at the target centres.
-  double *r0 = red, *r1 = red + (n + 5), *r2 = red + 2 * (n + 5);
+  // Phase 8: the sums of xi (Eqs. p6-p8) over the system's groups by a tree over its threads:
+  // the energy the shifted groups' numbers lose when they move to the target centres (the energy
+  // held by the shifted groups minus the same numbers at the target centres, taken per group), and
+  // the flux divergence at the target centres.
+  double *r0 = red, *r2 = red + (n + 5);
   if (live) {
     const double div = F[k] - F[k + 1];
-    r0[k] = nd[k] * epsd_c[k];
-    r1[k] = nd[k] * ct[k];
+    r0[k] = nd[k] * (epsd_c[k] - ct[k]);
     r2[k] = div * ct[k];
   }
   int top = 1;
@@ -241,7 +278,6 @@ __global__ void __launch_bounds__(kEadvThreads) k_energy_advect(EadvArgs g) {
     __syncthreads();
     if (live && k < s && k + s < n) {
       r0[k] += r0[k + s];
-      r1[k] += r1[k + s];
       r2[k] += r2[k + s];
     }
   }
@@ -250,7 +286,7 @@ __global__ void __launch_bounds__(kEadvThreads) k_energy_advect(EadvArgs g) {
   // E^2 dE / (a^{n+1})^3; groups below the top two that end above one flag the limiter.
   if (live) {
     const double s2 = r2[0];
-    const double xi = s2 != 0.0 ? (r0[0] - r1[0]) / s2 : 1.0;
+    const double xi = s2 != 0.0 ? quot(r0[0], s2) : 1.0;
     const double num = nd[k] + xi * (F[k] - F[k + 1]);
     const double v = num * zc[8] * icmE[k];
     nd[k] = v;

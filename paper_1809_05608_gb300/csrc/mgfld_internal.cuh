@@ -327,6 +327,29 @@ __device__ inline int scale_of_max(unsigned hi_word_max) {
 __device__ inline unsigned abs_hi_word(double v) {
   return (unsigned)((unsigned long long)__double_as_longlong(v) >> 32) & 0x7fffffffu;
 }
+// 1/d without FP64-pipe conversions or compares (the pivots of the FP64 Gauss-Jordan steps; the
+// seed of the energy remap's quotients): the mantissa of d, rounded to 24 bits, becomes an FP32
+// value m in [1, 2] by bit manipulation (integer pipe), its reciprocal is taken in FP32, the
+// exponent of 1/d is rebuilt from the two exponents, and one Newton-Raphson step
+// x1 = x0 + x0 (1 - d x0) (two FMAs on the FP64 pipe) takes the ~2^-23 seed to ~2^-46 relative.
+// Zero, subnormal, non-finite and extreme-exponent values take a plain division (rare; a zero
+// pivot means a singular block).  The factors only steer the outer iteration, whose fixed point
+// is set by the FP64 residual.
+__device__ inline double recip(double d) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(d);
+  const int e = (int)((b >> 52) & 0x7ff);
+  const unsigned m23 = (unsigned)((b >> 29) & 0x7fffff);
+  const float up = ((b >> 28) & 1ull) ? 1.1920928955078125e-7f : 0.f;     // round the dropped bits
+  const float m = __uint_as_float(0x3f800000u | m23) + up;                 // exact; may be 2.0
+  const unsigned rb = __float_as_uint(__frcp_rn(m));                      // 1/m in (0.5, 1]
+  const int ed = (int)(rb >> 23) - 127 + 2046 - e;                         // biased exponent of 1/|d|
+  if (e == 0 || e == 0x7ff || ed <= 0 || ed >= 0x7ff) return 1.0 / d;
+  const double x = __longlong_as_double((long long)((b & 0x8000000000000000ull) |
+                                                    ((unsigned long long)ed << 52) |
+                                                    ((unsigned long long)(rb & 0x7fffff) << 29)));
+  return fma(x, fma(-d, x, 1.0), x);
+}
+
 // MIXED-precision factor with FP32 diagonal blocks and FP32 coupling coefficients.
 cudaError_t launch_factor_f32(int n, int n_r, int n_sys, const float *diag, const float *lower32,
                               const float *upper32, float *dinv, const int *ray_list, cudaStream_t s,
