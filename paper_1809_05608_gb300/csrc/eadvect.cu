@@ -180,44 +180,43 @@ __global__ void __launch_bounds__(kEadvThreads) k_energy_advect(EadvArgs g) {
   // Phase 4: average slopes (Eq. h9) monotonised (Eq. h11) at the groups (extended index
   // 2..n+1), the two quotients of Eq. h9 over a common denominator.  The ghost groups copy their
   // neighbour, so one of their two differences is zero and the limiter makes their slopes zero.
-  // Thread k takes slope and interface k + 2: one reciprocal of the product of the two
-  // denominators serves both (each is the other times it).
-  double inv5 = 0.0;
+  // Thread k takes slope and interface k + 2 (phase 5): one reciprocal of the product of the two
+  // denominators serves both (each is the other times it), and the interface's terms that do not
+  // involve the slopes are formed here from the same widths.
+  double fb = 0.0, cR = 0.0, cL = 0.0, flo = 0.0, fhi = 0.0;
   if (live) {
     const int j = k + 2;
-    const double xl = X[j - 1], x0 = X[j], xr = X[j + 1], x2 = X[j + 2];
-    const double sl_ = xl + x0, sr = xr + x0;
-    const double d4 = (xl + x0 + xr) * sr * sl_;
-    const double d5 = (x0 + xr) * (2.0 * x0 + xr) * (x0 + 2.0 * xr) * (xl + x0 + xr + x2);
+    const double xl = X[j - 1], x0 = X[j], x1 = X[j + 1], x2 = X[j + 2];
+    const double sl_ = xl + x0, s01 = x0 + x1, s3 = sl_ + x1;
+    const double P = 2.0 * x0 + x1, Q = x0 + 2.0 * x1, tot = s3 + x2;
+    const double d4 = s3 * s01 * sl_;
+    const double d5 = s01 * P * Q * tot;
     const double r45 = recip2(d4 * d5);
-    inv5 = d4 * r45;
+    const double inv5 = d4 * r45;
     const double dp = A[j + 1] - A[j], dn = A[j] - A[j - 1];
-    const double s = x0 * ((2.0 * xl + x0) * sl_ * dp + (x0 + 2.0 * xr) * sr * dn) * (d5 * r45);
-    const double lim = fmin(fabs(s), fmin(2.0 * fabs(dp), 2.0 * fabs(dn)));
+    const double s = x0 * ((2.0 * xl + x0) * sl_ * dp + (x0 + 2.0 * x1) * s01 * dn) * (d5 * r45);
+    const double lim = fmin(fabs(s), 2.0 * fmin(fabs(dp), fabs(dn)));
     dm[j] = dp * dn > 0.0 ? copysign(lim, s) : 0.0;
     if (k < 2) dm[k == 0 ? 1 : n + 2] = 0.0;
+    // Phase 5's interface j (Eq. h12): f = A_j + [x0 d P Q tot + 2 x0 x1 ((xl + x0) Q - (x2 + x1) P) d
+    //   - s01 (x0 (xl + x0) Q dm_{j+1} - x1 (x1 + x2) P dm_j)] / (s01 P Q tot), d = A_{j+1} - A_j
+    fb = A[j] + (x0 * dp * P * Q * tot + 2.0 * x0 * x1 * (sl_ * Q - (x2 + x1) * P) * dp) * inv5;
+    cR = -(s01 * x0 * sl_ * Q * inv5);
+    cL = s01 * x1 * (x1 + x2) * P * inv5;
+    flo = fmin(A[j], A[j + 1]);
+    fhi = fmax(A[j], A[j + 1]);
   }
   __syncthreads();
   // Phase 5: interface values between extended groups j and j+1, j = 1..n+1 (Eq. h12, the cubic
-  // through the group integrals), limited to the range of the two averages (Eqs. h15-h16); the
-  // five quotients over one denominator (x0 + x1)(2 x0 + x1)(x0 + 2 x1)(xl + x0 + x1 + x2), whose
-  // reciprocal phase 4 formed.  At the two end interfaces the ghost's average equals the group's,
-  // so the limiter returns it.
-  auto interface = [&](int j) {
-    const double xl = X[j - 1], x0 = X[j], x1 = X[j + 1], x2 = X[j + 2];
-    const double d = A[j + 1] - A[j];
-    const double P = 2.0 * x0 + x1, Q = x0 + 2.0 * x1, s01 = x0 + x1;
-    const double tot = xl + x0 + x1 + x2;
-    const double tn = 2.0 * x0 * x1 * ((xl + x0) * Q - (x2 + x1) * P) * d
-                      - s01 * (x0 * (xl + x0) * Q * dm[j + 1] - x1 * (x1 + x2) * P * dm[j]);
-    double f = A[j] + (x0 * d * P * Q * tot + tn) * inv5;
-    f = fmax(f, fmin(A[j], A[j + 1]));
-    f = fmin(f, fmax(A[j], A[j + 1]));
-    face[j] = f;
-  };
+  // through the group integrals), limited to the range of the two averages (Eqs. h15-h16).  At
+  // the two end interfaces the ghost's average equals the group's, so the limiter returns it.
   if (live) {
-    if (k < n - 1) interface(k + 2);
-    else face[1] = A[2];
+    if (k < n - 1) {
+      const int j = k + 2;
+      face[j] = fmin(fmax(fma(cR, dm[j + 1], fma(cL, dm[j], fb)), flo), fhi);
+    } else {
+      face[1] = A[2];
+    }
     if (k == 0) face[n + 1] = A[n + 1];
   }
   __syncthreads();
@@ -267,8 +266,9 @@ __global__ void __launch_bounds__(kEadvThreads) k_energy_advect(EadvArgs g) {
   // held by the shifted groups minus the same numbers at the target centres, taken per group), and
   // the flux divergence at the target centres.
   double *r0 = red, *r2 = red + (n + 5);
+  double div = 0.0;
   if (live) {
-    const double div = F[k] - F[k + 1];
+    div = F[k] - F[k + 1];
     r0[k] = nd[k] * (epsd_c[k] - ct[k]);
     r2[k] = div * ct[k];
   }
@@ -287,7 +287,7 @@ __global__ void __launch_bounds__(kEadvThreads) k_energy_advect(EadvArgs g) {
   if (live) {
     const double s2 = r2[0];
     const double xi = s2 != 0.0 ? quot(r0[0], s2) : 1.0;
-    const double num = nd[k] + xi * (F[k] - F[k + 1]);
+    const double num = nd[k] + xi * div;
     const double v = num * zc[8] * icmE[k];
     nd[k] = v;
     if (k == 0) zc[6] = xi;
