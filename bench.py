@@ -535,14 +535,15 @@ def step_roofline(res, inp, precision):
 def e2e_run(M, torch, inp, precision, steps, parts=2):
     """Same metric through the public API from pinned HOST buffers: every step uploads that
     step's inputs (matter, opacities, NES scale, grid, state), runs mgfld_step and reads the new
-    state back.  The rays are processed in `parts` contiguous blocks, each with its own Stepper on
-    its own CUDA stream, where its state goes host -> device -> host around its step in order, so
-    that one block's state copies overlap the other blocks' steps; each block's problem arrays of
-    step s+1 are uploaded on a copy stream into a second device copy while step s runs (double
-    buffering)."""
+    state back.  The rays are processed in `parts` contiguous blocks, each with its own Stepper;
+    the blocks' steps run one after another on one compute stream, and each block's copies run on
+    its own copy streams while the other blocks compute: its state is read back (device -> host)
+    as soon as its step ends and uploaded again (host -> device) for its next step, and its
+    problem arrays of step s+1 go into a second device copy while step s runs (double buffering)."""
     n_ray = inp['psi0'].shape[0]
     names = ('r_edge', 'rho', 'kappa_abs', 'kappa_scat', 'nes_coef')
     main = torch.cuda.current_stream()
+    comp = torch.cuda.Stream()
     blocks = []
     h2d = d2h = 0
     for c in range(parts):
@@ -554,8 +555,9 @@ def e2e_run(M, torch, inp, precision, steps, parts=2):
               for a in (sub['psi0'], sub['ye0'], sub['T0'])]
         blk = dict(st=st, host=host, hs=hs, dev=[torch.empty_like(h, device='cuda') for h in hs],
                    out=[torch.empty_like(h).pin_memory() for h in hs], bufs=[st.prob, M.DeviceProblem(prob)],
-                   stream=torch.cuda.Stream(), copy=torch.cuda.Stream(),
-                   ready=[torch.cuda.Event(), torch.cuda.Event()], free=[torch.cuda.Event(), torch.cuda.Event()])
+                   copy=torch.cuda.Stream(), back=torch.cuda.Stream(),
+                   ready=[torch.cuda.Event(), torch.cuda.Event()], free=[torch.cuda.Event(), torch.cuda.Event()],
+                   state=torch.cuda.Event(), done=torch.cuda.Event(), read=torch.cuda.Event())
         h2d += sum(v.numel() * 8 for v in host.values()) + sum(h.numel() * 8 for h in hs)
         d2h += sum(h.numel() * 8 for h in hs)
         blocks.append(blk)
@@ -566,12 +568,20 @@ def e2e_run(M, torch, inp, precision, steps, parts=2):
                 blk['bufs'][b].t[k].copy_(blk['host'][k], non_blocking=True)
             blk['ready'][b].record(blk['copy'])
 
+    def upload_state(blk, src):
+        with torch.cuda.stream(blk['copy']):
+            for d, h in zip(blk['dev'], src):
+                d.copy_(h, non_blocking=True)
+            blk['state'].record(blk['copy'])
+
     def run(n_steps, e0, e1, first):
         e0.record(main)
+        comp.wait_event(e0)
         for blk in blocks:
             blk['copy'].wait_event(e0)
-            blk['stream'].wait_event(e0)
+            blk['back'].wait_event(e0)
             upload(blk, 0)
+            upload_state(blk, blk['hs'] if first else blk['out'])
         for s in range(n_steps):
             b = s % 2
             for blk in blocks:
@@ -579,21 +589,27 @@ def e2e_run(M, torch, inp, precision, steps, parts=2):
                     if s >= 1:
                         blk['copy'].wait_event(blk['free'][1 - b])
                     upload(blk, 1 - b)
-                stream = blk['stream']
-                stream.wait_event(blk['ready'][b])
+                comp.wait_event(blk['ready'][b])
+                comp.wait_event(blk['state'])
                 blk['st'].prob = blk['bufs'][b]
-                src = blk['hs'] if (first and s == 0) else blk['out']
-                with torch.cuda.stream(stream):
-                    for d, h in zip(blk['dev'], src):
-                        d.copy_(h, non_blocking=True)
-                    rc = blk['st'].step(*blk['dev'], stream=stream, wait=False)
+                with torch.cuda.stream(comp):
+                    rc = blk['st'].step(*blk['dev'], stream=comp, wait=False)
                     assert rc == M.MGFLD_OK, M.status_str(rc)
-                    blk['free'][b].record(stream)
+                    blk['free'][b].record(comp)
+                    blk['done'].record(comp)
+                # the new state back to the host, then up again for the block's next step
+                blk['back'].wait_event(blk['done'])
+                with torch.cuda.stream(blk['back']):
                     for o, d in zip(blk['out'], blk['dev']):
                         o.copy_(d, non_blocking=True)
+                    blk['read'].record(blk['back'])
+                if s + 1 < n_steps:
+                    blk['copy'].wait_event(blk['read'])
+                    upload_state(blk, blk['out'])
         for blk in blocks:
-            main.wait_stream(blk['stream'])
+            main.wait_stream(blk['back'])
             main.wait_stream(blk['copy'])
+        main.wait_stream(comp)
         e1.record(main)
         torch.cuda.synchronize()
 
