@@ -927,17 +927,14 @@ k_factor_row2(int n_r, int n_sys, const float *__restrict__ diag, const float *_
     __syncwarp();
     // the zone's rows minus the Schur term of the previous zone: row r gets
     // -l_r (row r of the previous inverse, this lane's registers) * u_prev (column scaling)
-    const float l0 = (valid && j > 0) ? cpl[wid][gs][0][r0] : 0.f;
-    const float l1 = (valid && j > 0) ? cpl[wid][gs][0][r1] : 0.f;
-    const float u0 = valid ? cpl[wid][gs][1][r0] : 0.f, u1 = valid ? cpl[wid][gs][1][r1] : 0.f;
+    // (lanes without a system run on whatever their slot holds: they store nothing, and a slot
+    // without a system is read by its own lanes only)
+    const float l0 = cpl[wid][gs][0][r0], l1 = cpl[wid][gs][0][r1];   // used from the second zone on
+    const float u0 = cpl[wid][gs][1][r0], u1 = cpl[wid][gs][1][r1];
 #pragma unroll
     for (int c = 0; c < NP; c += 4) {
-      float4 x0 = valid ? *reinterpret_cast<const float4 *>(&rows[wid][gs][r0][c]) : make_float4(0.f, 0.f, 0.f, 0.f);
-      float4 x1 = valid ? *reinterpret_cast<const float4 *>(&rows[wid][gs][r1][c]) : make_float4(0.f, 0.f, 0.f, 0.f);
-      if (!valid) {                                        // identity blocks for lanes without a system
-        x0 = make_float4(c == r0 ? 1.f : 0.f, c + 1 == r0 ? 1.f : 0.f, c + 2 == r0 ? 1.f : 0.f, c + 3 == r0 ? 1.f : 0.f);
-        x1 = make_float4(c == r1 ? 1.f : 0.f, c + 1 == r1 ? 1.f : 0.f, c + 2 == r1 ? 1.f : 0.f, c + 3 == r1 ? 1.f : 0.f);
-      }
+      float4 x0 = *reinterpret_cast<const float4 *>(&rows[wid][gs][r0][c]);
+      float4 x1 = *reinterpret_cast<const float4 *>(&rows[wid][gs][r1][c]);
       if (j > 0) {
         const float4 u = *reinterpret_cast<const float4 *>(&ucol[wid][gs][c]);
         x0.x = fmaf(-(l0 * a0[c]), u.x, x0.x);
