@@ -27,21 +27,6 @@ namespace mgfld {
 constexpr int kEadvThreads = 256;
 constexpr double kThird = 1.0 / 3.0;
 
-// n/d within about an ulp at a third of a division's FP64 instructions: the reciprocal seed of
-// recip (~2^-46, its conversions on the integer pipe) and one Newton correction of the quotient,
-// q = n x + x (n - d n x), whose error is of the order of the square of the seed's.
-__device__ inline double quot(double n, double d) {
-  const double x = recip(d);
-  const double q = n * x;
-  return fma(x, fma(-d, q, n), q);
-}
-
-// 1/d within about an ulp: recip and a second Newton-Raphson step.
-__device__ inline double recip2(double d) {
-  const double x = recip(d);
-  return fma(x, fma(-d, x, 1.0), x);
-}
-
 // eta2 of the Minerbo closure (Eqs. a86-a87): the weighting of the thick (1/3) and thin (1)
 // limits by the closure's factor p, (1 - p)/2 + (3p - 1)/2, is p itself.
 __device__ inline double eddington_p(double eta1) {
@@ -195,7 +180,11 @@ __global__ void __launch_bounds__(kEadvThreads) k_energy_advect(EadvArgs g) {
     const double inv5 = d4 * r45;
     const double dp = A[j + 1] - A[j], dn = A[j] - A[j - 1];
     const double s = x0 * ((2.0 * xl + x0) * sl_ * dp + (x0 + 2.0 * x1) * s01 * dn) * (d5 * r45);
-    const double lim = fmin(fabs(s), 2.0 * fmin(fabs(dp), fabs(dn)));
+    // (minima of non-negative values by their bit patterns, on the integer pipe: fmin's result,
+    // NaN operands included)
+    const double adp = fabs(dp), adn = fabs(dn), as = fabs(s);
+    const double m2d = 2.0 * (dbits(adp) < dbits(adn) ? adp : adn);
+    const double lim = dbits(as) < dbits(m2d) ? as : m2d;
     dm[j] = dp * dn > 0.0 ? copysign(lim, s) : 0.0;
     if (k < 2) dm[k == 0 ? 1 : n + 2] = 0.0;
     // Phase 5's interface j (Eq. h12): f = A_j + [x0 d P Q tot + 2 x0 x1 ((xl + x0) Q - (x2 + x1) P) d
@@ -226,7 +215,8 @@ __global__ void __launch_bounds__(kEadvThreads) k_energy_advect(EadvArgs g) {
     const double a = A[k + 2];
     double l = face[k + 1], r = face[k + 2];
     const double d = r - l, s6 = 6.0 * (a - 0.5 * (l + r));
-    const bool lm = d * d < d * s6, rm = d * d < -d * s6;
+    const double dd = d * d, ds = d * s6;
+    const bool lm = ord_key(dd) < ord_key(ds), rm = ord_key(dd) < ord_key(-ds);   // integer pipe
     const double l2 = lm ? 3.0 * a - 2.0 * r : l;
     const double r2 = rm ? 3.0 * a - 2.0 * l : r;
     aL[k] = l2;
@@ -250,11 +240,12 @@ __global__ void __launch_bounds__(kEadvThreads) k_energy_advect(EadvArgs g) {
       // slice's fraction of its group is |d| / (Dh - Dl) at infinity (the factor 1/a^{n+1} of
       // both cancels), with 1/(Dh - Dl) from phase 3.
       const double d = g.e_edge[k] - E_d[k];
-      const bool up = d < 0.0;
+      const bool up = ord_key(d) < ord_key(-0.0);     // d < 0, on the integer pipe
       const int gsrc = up ? k - 1 : k;
       const double dir = up ? -1.0 : 1.0;
       const double dx = X[gsrc + 2];
-      const double y = fmin(fabs(d) * iw[gsrc], 1.0);
+      const double yr = fabs(d) * iw[gsrc];
+      const double y = dbits(yr) < dbits(1.0) ? yr : 1.0;
       const double end = up ? aR[gsrc] : aL[gsrc];
       const double avg = end + dir * 0.5 * y * ((aR[gsrc] - aL[gsrc]) + dir * (1.0 - 2.0 * kThird * y) * a6[gsrc]);
       F[k] = -dir * avg * y * dx;
@@ -286,12 +277,12 @@ __global__ void __launch_bounds__(kEadvThreads) k_energy_advect(EadvArgs g) {
   // E^2 dE / (a^{n+1})^3; groups below the top two that end above one flag the limiter.
   if (live) {
     const double s2 = r2[0];
-    const double xi = s2 != 0.0 ? quot(r0[0], s2) : 1.0;
+    const double xi = !is_zero(s2) ? quot(r0[0], s2) : 1.0;
     const double num = nd[k] + xi * div;
     const double v = num * zc[8] * icmE[k];
     nd[k] = v;
     if (k == 0) zc[6] = xi;
-    if (k < n - 2 && v > 1.0) zc[7] = 1.0;     // benign race: every writer stores 1
+    if (k < n - 2 && ord_key(v) > ord_key(1.0)) zc[7] = 1.0;     // benign race: every writer stores 1
   }
   __syncthreads();
   // Phase 10: the occupation limiter (Eqs. a81a-a81d), sequential over groups k = 0..n-3, only

@@ -350,6 +350,30 @@ __device__ inline double recip(double d) {
   return fma(x, fma(-d, x, 1.0), x);
 }
 
+// n/d within about an ulp at a third of a division's FP64 instructions: the reciprocal seed of
+// recip (~2^-46, its conversions on the integer pipe) and one Newton correction of the quotient,
+// q = n x + x (n - d n x), whose error is of the order of the square of the seed's.
+__device__ inline double quot(double n, double d) {
+  const double x = recip(d);
+  const double q = n * x;
+  return fma(x, fma(-d, q, n), q);
+}
+
+// 1/d within about an ulp: recip and a second Newton-Raphson step.
+__device__ inline double recip2(double d) {
+  const double x = recip(d);
+  return fma(x, fma(-d, x, 1.0), x);
+}
+
+// Order keys of doubles for comparisons on the integer pipe: the bit pattern of a non-negative
+// value orders like the value, so two non-negative values compare by their patterns (dbits); ord_key
+// maps every non-NaN value to an integer of the same order (-0 just below +0).
+__device__ inline long long ord_key(double x) {
+  const long long b = __double_as_longlong(x);
+  return b >= 0 ? b : b ^ 0x7fffffffffffffffLL;
+}
+__device__ inline bool is_zero(double x) { return (__double_as_longlong(x) << 1) == 0; }
+
 // MIXED-precision factor with FP32 diagonal blocks and FP32 coupling coefficients.
 cudaError_t launch_factor_f32(int n, int n_r, int n_sys, const float *diag, const float *lower32,
                               const float *upper32, float *dinv, const int *ray_list, cudaStream_t s,

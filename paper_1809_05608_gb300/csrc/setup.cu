@@ -412,9 +412,10 @@ __global__ void k_edges(Prob p, Ws w, const double *__restrict__ psi_src, const 
   // derivatives of Phi = F (psi_r - psi_i) with respect to psi_i and psi_r on the branch the
   // limiter selects (lambda and R_nu held), for the coefficients at the outer iterate
   double dl = 0.0, dr = 0.0;
-  if (psi_e <= 1e-300) {
+  // (the comparisons on the integer pipe, by order keys: the same outcomes as the FP64 ones)
+  if (ord_key(psi_e) <= ord_key(1e-300)) {
     F = 0.0;
-  } else if (dpsi == 0.0) {
+  } else if (is_zero(dpsi)) {
     F = 1.0;
     dl = -1.0;
     dr = 1.0;
@@ -430,10 +431,10 @@ __global__ void k_edges(Prob p, Ws w, const double *__restrict__ psi_src, const 
     bool geom = false;
     double m2 = 1.0;
     const double sp = psi_e + x;
-    if (re[i + 1] > rnu && x > psi_e) {
+    if (dbits(re[i + 1]) > dbits(rnu) && dbits(x) > dbits(psi_e)) {   // all of them >= 0 here
       m2 = fmax(1.0 - rnu * rnu * z[ZC_EIR2], 0.0);
       const double df = x - psi_e;
-      geom = m2 * (sp * sp) < df * df;
+      geom = dbits(m2 * (sp * sp)) < dbits(df * df);
     }
     // one quotient for both branches: numerator and denominator selected first
     double num = psi_e, den = sp, h = 1.0;
@@ -442,16 +443,18 @@ __global__ void k_edges(Prob p, Ws w, const double *__restrict__ psi_src, const 
       num = h * psi_e;
       den = x;
     }
+    // MIXED (the coefficients steer an iteration converged to 1e-10): the quotient from the
+    // integer-pipe reciprocal seed and one Newton correction, within an ulp; the FP64 path divides
     if (!w.jl) {
-      F = num / den;
+      F = w.phin32 ? quot(num, den) : num / den;
     } else {
-      // the derivatives need 1/den as well: one division for F and both of them
-      const double r = 1.0 / den;
+      // the derivatives need 1/den as well: one reciprocal for F and both of them
+      const double r = w.phin32 ? recip2(den) : 1.0 / den;
       F = num * r;
       if (geom) {                       // Phi = (h / b) psi_e s with 1/b = |d| / x
         dl = dr = 0.5 * h * dpsi * r;
       } else {                          // Phi = psi_e d / (psi_e + b |d|) = F d
-        const double s = dpsi > 0.0 ? 1.0 : -1.0;
+        const double s = __double_as_longlong(dpsi) >= 0 ? 1.0 : -1.0;     // dpsi != 0 here
         const double phi = F * dpsi;
         dl = ((0.5 * dpsi - psi_e) - phi * (0.5 - b * s)) * r;
         dr = ((0.5 * dpsi + psi_e) - phi * (0.5 + b * s)) * r;
