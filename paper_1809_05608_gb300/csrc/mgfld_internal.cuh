@@ -374,6 +374,19 @@ __device__ inline long long ord_key(double x) {
 }
 __device__ inline bool is_zero(double x) { return (__double_as_longlong(x) << 1) == 0; }
 
+// mu_nue_zone with its three quotients (ye / yn, and the two terms of dmu over ye and yn) from one
+// reciprocal of ye yn (recip2, within about an ulp): the mixed path's Ye update, whose iteration
+// converges to 1e-10.
+__device__ inline void mu_nue_zone_q(const Eos &e, double A, double B, double T, double ye, double &mu,
+                                     double &dmu) {
+  const double yn = 1.0 - ye;
+  const double r = recip2(ye * yn);
+  const double mu_e = A * (e.g1_is_4_3 ? cbrt(ye) : pow(ye, e.g1 - 1.0));
+  const double mu_nn = B * (e.g2_is_5_2 ? yn * sqrt(yn) : pow(yn, e.g2 - 1.0));
+  mu = mu_e - mu_nn + T * (log(ye * (ye * r)) + e.log_gn_gp);
+  dmu = ((e.g1 - 1.0) * mu_e + T) * (yn * r) + ((e.g2 - 1.0) * mu_nn + T) * (ye * r);
+}
+
 // MIXED-precision factor with FP32 diagonal blocks and FP32 coupling coefficients.
 cudaError_t launch_factor_f32(int n, int n_r, int n_sys, const float *diag, const float *lower32,
                               const float *upper32, float *dinv, const int *ray_list, cudaStream_t s,

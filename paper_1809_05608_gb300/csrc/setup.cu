@@ -345,7 +345,7 @@ __global__ void k_nusphere(Prob p, Ws w, const int *__restrict__ list, int n_lis
   for (int j = 0; j < cnt; ++j) {
     const int i = top - j;
     const double dtau = (re[i + 1] - re[i]) * kt[(size_t)i * n];
-    if (tau_out + dtau >= kTauNu) {
+    if (dbits(tau_out + dtau) >= dbits(kTauNu)) {          // depths >= 0: compared on the integer pipe
       rnu = re[i + 1] - (kTauNu - tau_out) * w.lam[off + (size_t)i * n];
       hit = true;
       break;

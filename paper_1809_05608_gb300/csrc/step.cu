@@ -335,7 +335,12 @@ __global__ void k_update_ye(Prob p, Ws w, Tol tl, const double *__restrict__ psi
     const double inv_a3 = inv_a * inv_a * inv_a;
     const double inv_acdt = z[ZC_INV_ACDT];
     const double Ti = T[zi], rho = p.rho[zi];
-    const double cy = kFourPiHC3 * p.eos.mb / rho;
+    // MIXED: the quotients by T^n as products with the zone's 1/T^n, the others from a reciprocal
+    // seed with a Newton correction (within an ulp; the iteration converges to 1e-10); the FP64 path
+    // divides
+    const bool fast = w.phin32 != nullptr;
+    const double iT = z[ZC_INV_T];
+    const double cy = fast ? quot(kFourPiHC3 * p.eos.mb, rho) : kFourPiHC3 * p.eos.mb / rho;
     const double capT = kExpCap * Ti;
     const double eps0 = w.E[0] * inv_a;
     // rows of an even number of groups in 16-byte aligned arrays are read in 16-byte pieces
@@ -343,11 +348,12 @@ __global__ void k_update_ye(Prob p, Ws w, Tol tl, const double *__restrict__ psi
                      ((((uintptr_t)psi | (uintptr_t)p.kabs | (uintptr_t)w.jbuf) & 15u) == 0);
     double Y = ye[zi];
     double mu, dmu;
-    mu_nue_zone(p.eos, z[ZC_MUA], z[ZC_MUB], Ti, Y, mu, dmu);
+    if (fast) mu_nue_zone_q(p.eos, z[ZC_MUA], z[ZC_MUB], Ti, Y, mu, dmu);
+    else mu_nue_zone(p.eos, z[ZC_MUA], z[ZC_MUB], Ti, Y, mu, dmu);
     double sG = 0.0, sdG = 0.0;
     for (int q = 0; q < 2; ++q) {
       const double sg = lepton_sign(q);
-      const double muq = species_mu(q, mu), dmuq_T = sg * dmu / Ti;
+      const double muq = species_mu(q, mu), dmuq_T = fast ? sg * dmu * iT : sg * dmu / Ti;
       const size_t g0 = (((size_t)ray * NS + q) * p.n_r + i) * n;
       double a0, a1 = 0.0, c = 0.0;
       if (muq - eps0 < capT) {                    // no group at the cap
@@ -394,15 +400,16 @@ __global__ void k_update_ye(Prob p, Ws w, Tol tl, const double *__restrict__ psi
     }
     const double GY = (Y - w.ye_n[zi]) * inv_acdt + cy * sG;
     const double dGY = inv_acdt + cy * sdG;
-    const double dY = -GY / dGY;
+    const double dY = fast ? -quot(GY, dGY) : -GY / dGY;
     Y += dY;
     ye[zi] = Y;
     viol = tol_ratio(fabs(dY), fmax(fabs(Y), tl.tolmin_ye), tl.tolm_ye, tl.tole_ye);
     double mu1, dmu1;
-    mu_nue_zone(p.eos, z[ZC_MUA], z[ZC_MUB], Ti, Y, mu1, dmu1);
+    if (fast) mu_nue_zone_q(p.eos, z[ZC_MUA], z[ZC_MUB], Ti, Y, mu1, dmu1);
+    else mu_nue_zone(p.eos, z[ZC_MUA], z[ZC_MUB], Ti, Y, mu1, dmu1);
     for (int q = 0; q < 2; ++q) {
       const double m0 = species_mu(q, mu), m1 = species_mu(q, mu1);
-      const double ratio = exp((m1 - m0) / Ti);
+      const double ratio = exp(fast ? (m1 - m0) * iT : (m1 - m0) / Ti);
       const size_t g0 = (((size_t)ray * NS + q) * p.n_r + i) * n;
       if (m0 - eps0 < capT && m1 - eps0 < capT) {
         if (vec) {
