@@ -85,38 +85,45 @@ __global__ void k_zone(Prob p, Ws w, const double *__restrict__ ye, const double
 // (coef e^{-2(eps_k' - eps_k)/T}) and Phi_in(eps_k, eps_k') = Phi_out(eps_k', eps_k).
 // Rows k and n-1-k share a thread, so that every thread runs the same n-1 steps of the
 // down-scattering chains and n-1 of the up-scattering chains (no divergent loop lengths).
-// Rows are staged in shared memory with a padded stride (n + 1) and copied out coalesced.
+// The running products (P along a row's down-scattering entries, Q along its up-scattering ones,
+// 1 on the diagonal) are staged in shared memory with a padded stride (n + 1), and the copy-out
+// forms each entry pair from its product with the chain's own two multiplications (a = cw_k' P,
+// then a P: down-scattering (out, in) = (a, a P), up-scattering (in, out) = (a, a P)), so the
+// values are those of the chains, bit for bit, from one staged FP64 per entry.
 static inline int phi_threads_per_zone(int n) { return (n + 1) / 2; }
 static inline size_t phi_zone_bytes(int n) {
-  return sizeof(double) * (2 * (size_t)n * (n + 1) + 2 * (size_t)n) + sizeof(int) * 2 * (size_t)n;
+  return sizeof(double) * ((size_t)n * (n + 1) + 2 * (size_t)n) + sizeof(int) * 2 * (size_t)n;
 }
-// Zones per block: zones * threads per zone a multiple of 32 where the staging fits in 113 KB
-// (two blocks per SM), else as many zones as fit.
+// Zones per block: zones * threads per zone a multiple of 32 where the staging fits in 75 KB
+// (three blocks per SM), else as many zones as fit.
 static inline int phi_zones_per_block(int n) {
   const int h = phi_threads_per_zone(n);
   int g = h, b = 32;
   while (b) { const int t = g % b; g = b; b = t; }
   const int full = 32 / g;
-  const int fit = (int)((size_t)113 * 1024 / phi_zone_bytes(n));
+  const int fit = (int)((size_t)75 * 1024 / phi_zone_bytes(n));
   return full <= fit ? full : (fit < 1 ? 1 : fit);
 }
 static inline size_t phi_smem_bytes(int n) { return (size_t)phi_zones_per_block(n) * phi_zone_bytes(n); }
 
-// Rows ka = t and kb = n-1-t of one zone's kernels into the staged tiles so (out) and si (in)
-// (row stride ld), from the zone's consecutive-group ratios gap[m] and weights cw[m]; returns
-// the two rows' sums of the out-kernel (equal rows of odd n: the middle row, both chains).
+// Rows ka = t and kb = n-1-t of one zone's kernels: their running products into the staged tile
+// sp (row stride ld), from the zone's consecutive-group ratios gap[m] and weights cw[m]; returns
+// the two rows' sums of the out-kernel (equal rows of odd n: the middle row, both chains) and,
+// with want_max, the largest upper words of |in| and |out| of each row (for the FP32-pair scales).
 // Down-scattering entries run along a row as P = prod gap (one multiply per step) with the
 // up-scattering partner o P = cw P^2; up-scattering entries likewise from Q = prod gap.
-__device__ inline void phi_chains(int n, int t, const double *gap, const double *cw, double *so, double *si, int ld,
-                                  double &rs_a, double &rs_b) {
+struct PhiRowMax {
+  unsigned in_a, out_a, in_b, out_b;
+};
+__device__ inline void phi_chains(int n, int t, const double *gap, const double *cw, double *sp, int ld, bool want_max,
+                                  double &rs_a, double &rs_b, PhiRowMax &mx) {
   const int ka = t, kb = n - 1 - t;                     // ka <= kb; equal for the middle row of odd n
-  double *oa = so + (size_t)ka * ld, *ia = si + (size_t)ka * ld;
-  double *ob = so + (size_t)kb * ld, *ib = si + (size_t)kb * ld;
+  double *pa = sp + (size_t)ka * ld, *pb = sp + (size_t)kb * ld;
   double rsa = cw[ka], rsb = (ka == kb) ? 0.0 : cw[kb];
-  oa[ka] = cw[ka];
-  ia[ka] = cw[ka];
-  ob[kb] = cw[kb];
-  ib[kb] = cw[kb];
+  pa[ka] = 1.0;
+  pb[kb] = 1.0;
+  mx.in_a = mx.out_a = abs_hi_word(cw[ka]);
+  mx.in_b = mx.out_b = abs_hi_word(cw[kb]);
   // Down-scattering (k' < k): row ka's ka entries, then row kb's kb entries (n - 1 steps).
   double P = 1.0;
   for (int j = 0; j < n - 1; ++j) {
@@ -126,8 +133,12 @@ __device__ inline void phi_chains(int n, int t, const double *gap, const double 
     if (j == ka) P = 1.0;
     P *= gap[kp + 1];                                   // e^{-(eps_k - eps_kp)/T}
     const double o = cw[kp] * P;                        // down-scattering k -> kp
-    const double v = o * P;                             // up-scattering kp -> k: cw e^{-2(eps_k - eps_kp)/T}
-    if (first) { oa[kp] = o; ia[kp] = v; rsa += o; } else { ob[kp] = o; ib[kp] = v; rsb += o; }
+    if (first) { pa[kp] = P; rsa += o; } else { pb[kp] = P; rsb += o; }
+    if (want_max) {
+      const unsigned ho = abs_hi_word(o), hv = abs_hi_word(o * P);   // in: cw e^{-2(eps_k - eps_kp)/T}
+      if (first) { mx.out_a = max(mx.out_a, ho); mx.in_a = max(mx.in_a, hv); }
+      else { mx.out_b = max(mx.out_b, ho); mx.in_b = max(mx.in_b, hv); }
+    }
   }
   // Up-scattering (k' > k): row kb's n-1-kb entries, then row ka's n-1-ka entries.
   const int nb = n - 1 - kb;
@@ -140,13 +151,20 @@ __device__ inline void phi_chains(int n, int t, const double *gap, const double 
     Q *= gap[kp];                                       // e^{-(eps_kp - eps_k)/T}
     const double v = cw[kp] * Q;                        // down-scattering kp -> k
     const double o = v * Q;                             // up-scattering k -> kp
-    if (first) { ob[kp] = o; ib[kp] = v; rsb += o; } else { oa[kp] = o; ia[kp] = v; rsa += o; }
+    if (first) { pb[kp] = Q; rsb += o; } else { pa[kp] = Q; rsa += o; }
+    if (want_max) {
+      const unsigned ho = abs_hi_word(o), hv = abs_hi_word(v);
+      if (first) { mx.out_b = max(mx.out_b, ho); mx.in_b = max(mx.in_b, hv); }
+      else { mx.out_a = max(mx.out_a, ho); mx.in_a = max(mx.in_a, hv); }
+    }
   }
   if (kb != ka) {
     rs_a = rsa;
     rs_b = rsb;
   } else {
     rs_a = rs_b = rsa + rsb;
+    mx.in_a = mx.in_b = max(mx.in_a, mx.in_b);
+    mx.out_a = mx.out_b = max(mx.out_a, mx.out_b);
   }
 }
 
@@ -166,8 +184,8 @@ __global__ void k_phi(Prob p, Ws w, const double *__restrict__ T, int zpb) {
   const int n = p.n, H = (n + 1) / 2, ld = n + 1;
   double *gapm = smem;                                   // [zpb][n]  e^{-(eps_m - eps_{m-1})/T}
   double *cwm = gapm + (size_t)zpb * n;                   // [zpb][n]  C w_m = C W_m / a^3
-  double *sout = cwm + (size_t)zpb * n;                   // [zpb][n][n + 1]
-  double *sin_ = sout + (size_t)zpb * n * ld;             // [zpb][n][n + 1]
+  double *sp = cwm + (size_t)zpb * n;                     // [zpb][n][n + 1]  running products
+  int *rsc = reinterpret_cast<int *>(sp + (size_t)zpb * n * ld);   // [zpb][2][n]: in, out scales
   const int zl = threadIdx.x / H, t = threadIdx.x % H;
   const unsigned nz = (unsigned)(p.n_ray * p.n_r);
   const unsigned z0 = blockIdx.x * (unsigned)zpb;
@@ -180,26 +198,26 @@ __global__ void k_phi(Prob p, Ws w, const double *__restrict__ T, int zpb) {
     phi_zone_consts(w, n, t, H, 1.0 / lapse_at(p, ray, i), T[zi], p.nes ? p.nes[zi] : 0.0, gap, cw);
   }
   __syncthreads();
+  const bool mixed = w.nesff != nullptr;
   if (live) {
     double rsa, rsb;
-    phi_chains(n, t, gap, cw, sout + (size_t)zl * n * ld, sin_ + (size_t)zl * n * ld, ld, rsa, rsb);
+    PhiRowMax mx;
+    phi_chains(n, t, gap, cw, sp + (size_t)zl * n * ld, ld, mixed, rsa, rsb, mx);
     w.rsum[(size_t)zi * n + t] = rsa;
     if (n - 1 - t != t) w.rsum[(size_t)zi * n + (n - 1 - t)] = rsb;
+    if (mixed) {
+      // MIXED: the power-of-two scale of every row of both kernels (its largest entry into
+      // [1/2, 1)), for their FP32-pair form
+      int *rz = rsc + (size_t)zl * 2 * n;
+      rz[t] = scale_of_max(mx.in_a);
+      rz[n + t] = scale_of_max(mx.out_a);
+      rz[n - 1 - t] = scale_of_max(mx.in_b);
+      rz[2 * n - 1 - t] = scale_of_max(mx.out_b);
+    }
   }
   __syncthreads();
   const unsigned nzb = (z0 + zpb <= nz) ? (unsigned)zpb : nz - z0;
-  // MIXED: the power-of-two scale of every row of both kernels (its largest entry into [1/2, 1)),
-  // for their FP32-pair form; integer pipe only.
-  int *rsc = reinterpret_cast<int *>(sin_ + (size_t)zpb * n * ld);   // [zpb][2][n]: in, out
-  if (w.nesff) {
-    for (unsigned r = threadIdx.x; r < nzb * 2 * n; r += blockDim.x) {
-      const unsigned zz = r / (2 * n), rem = r - zz * 2 * n, which = rem / n, row = rem - which * n;
-      const double *src = (which ? sout : sin_) + ((size_t)zz * n + row) * ld;
-      unsigned m = 0u;
-      for (int c = 0; c < n; ++c) m = max(m, abs_hi_word(src[c]));
-      rsc[r] = scale_of_max(m);
-    }
-    __syncthreads();
+  if (mixed) {
     for (unsigned r = threadIdx.x; r < nzb * n; r += blockDim.x) {
       const unsigned zz = r / n, row = r - zz * n;
       w.nessc[(size_t)z0 * n + r] = make_int2(rsc[zz * 2 * n + row], rsc[zz * 2 * n + n + row]);
@@ -210,7 +228,11 @@ __global__ void k_phi(Prob p, Ws w, const double *__restrict__ T, int zpb) {
   const size_t base = (size_t)z0 * n * n;
   for (unsigned e = threadIdx.x; e < cnt; e += blockDim.x) {
     const unsigned row = e / (unsigned)n, col = e - row * n;
-    const double o = sout[row * ld + col], v = sin_[row * ld + col];
+    const unsigned zz = row / (unsigned)n, k = row - zz * n;
+    const double P = sp[row * ld + col];
+    const double a = cwm[zz * n + col] * P, b = a * P;
+    const bool down = col <= k;                       // the diagonal: P = 1, a = b = cw_k
+    const double o = down ? a : b, v = down ? b : a;
     w.phout[base + e] = o;
     w.phin[base + e] = v;
     if (w.phin32) {
@@ -219,9 +241,8 @@ __global__ void k_phi(Prob p, Ws w, const double *__restrict__ T, int zpb) {
       const float vf = d2f_exp2(v, 0);
       w.phin32[base + e] = vf;
       w.phd32[base + e] = __fsub_rn(vf, d2f_exp2(o, 0));
-      const unsigned zz = row / (unsigned)n, k = row - zz * n;
-      const float2 a = split_ff(v, rsc[zz * 2 * n + k]), b = split_ff(o, rsc[zz * 2 * n + n + k]);
-      w.nesff[base + e] = make_float4(a.x, a.y, b.x, b.y);
+      const float2 fa = split_ff(v, rsc[zz * 2 * n + k]), fb = split_ff(o, rsc[zz * 2 * n + n + k]);
+      w.nesff[base + e] = make_float4(fa.x, fa.y, fb.x, fb.y);
     } else {
       w.phd[base + e] = v - o;
     }
