@@ -249,9 +249,7 @@ k_src_mixed(Prob p, Ws w, const double *__restrict__ psi, double *__restrict__ s
     const unsigned gq = gq0 + j / (unsigned)n, kk = j % (unsigned)n;
     const unsigned ray = gq / (unsigned)(NS * p.n_r), rem = gq - ray * (unsigned)(NS * p.n_r);
     const unsigned i = rem / NS, q = rem - i * NS;
-    // (the correction is an FP32 value times a power of two: its FP32 form by bit arithmetic on
-    // the integer pipe is exact)
-    xs[j] = d2f_exp2(w.x[(((size_t)ray * NS + q) * p.n_r + i) * n + kk], 0);
+    xs[j] = (float)w.x[(((size_t)ray * NS + q) * p.n_r + i) * n + kk];
   }
   __syncthreads();
   const unsigned t = b0 + threadIdx.x;
@@ -279,7 +277,7 @@ k_src_mixed(Prob p, Ws w, const double *__restrict__ psi, double *__restrict__ s
   const float corr = fmaf(1.f - pf, dg, pf * dl);
   const double kap = scaled(p, p.kabs, g, q, k);
   const double loss0 = w.rsum[zi * n + k] - w.l0[g];
-  double S = fma(q1, w.g0[g], fma(-pk, loss0, f2d_exp2(corr, 0)));
+  double S = fma(q1, w.g0[g], fma(-pk, loss0, (double)corr));
   S = fma(w.jbuf[g], q1, fma(-kap, pk, S));
   src[g] = S;
 }
