@@ -422,6 +422,19 @@ mgfld_status mgfld_stress_lapse(const mgfld_dims *dims, const mgfld_problem *pro
 /* Human-readable name of a status code (static string). */
 const char *mgfld_status_str(mgfld_status s);
 
+/*
+ * mgfld_arith_check -- self-check of the FP64 arithmetic the kernels use in place of FP64
+ * divisions and comparisons (no paper counterpart; a diagnostic).  For i < count, with x = a[i],
+ * y = b[i], writes out[8 i + 0..7] = the library's quotient x / y (a reciprocal seeded on the
+ * integer and FP32 pipes with one Newton correction of the quotient), CUDA's x / y, the library's
+ * reciprocal of y with two Newton steps, CUDA's 1 / y, the one-step reciprocal seed (~2^-46
+ * relative), the integer-pipe comparison x < y by order keys (1 or 0), CUDA's x < y (1 or 0), and
+ * the integer-pipe test x == 0 (1 or 0).  a, b: count device doubles; out: 8 count device doubles;
+ * all caller-owned.  Asynchronous on `stream`.  Returns OK, EINVAL (count < 0 or a NULL pointer
+ * with count > 0) or ECUDA.
+ */
+mgfld_status mgfld_arith_check(const double *a, const double *b, int count, double *out, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -18,7 +18,7 @@ BUILD = os.path.join(HERE, '_build')
 LIB = os.path.join(BUILD, 'libmgfld.so')
 
 SOURCES = ['setup.cu', 'assemble.cu', 'blocktri.cu', 'step.cu', 'noalloc.cu', 'adjoint.cu', 'eadvect.cu',
-           'stress.cu', 'pair.cu']
+           'stress.cu', 'pair.cu', 'check.cu']
 ARCH = ['-gencode', 'arch=compute_103a,code=sm_103a']
 NVCC_FLAGS = ARCH + ['-O3', '-lineinfo', '-std=c++17', '-Xcompiler', '-fPIC,-O2',
                      '-I', INCLUDE, '-I', CSRC]

@@ -352,15 +352,23 @@ __device__ inline double recip(double d) {
 
 // n/d within about an ulp at a third of a division's FP64 instructions: the reciprocal seed of
 // recip (~2^-46, its conversions on the integer pipe) and one Newton correction of the quotient,
-// q = n x + x (n - d n x), whose error is of the order of the square of the seed's.
+// q = n x + x (n - d n x), whose error is of the order of the square of the seed's.  Zero,
+// subnormal and non-finite divisors, and quotients that overflow, take the plain division (the
+// tests on the integer pipe).
 __device__ inline double quot(double n, double d) {
+  const int ed = (int)((__double_as_longlong(d) >> 52) & 0x7ff);
   const double x = recip(d);
   const double q = n * x;
+  const int eq = (int)((__double_as_longlong(q) >> 52) & 0x7ff);
+  if (ed == 0 || ed == 0x7ff || eq == 0x7ff) return n / d;
   return fma(x, fma(-d, q, n), q);
 }
 
-// 1/d within about an ulp: recip and a second Newton-Raphson step.
+// 1/d within about an ulp: recip and a second Newton-Raphson step (zero, subnormal and non-finite
+// d: the plain division).
 __device__ inline double recip2(double d) {
+  const int ed = (int)((__double_as_longlong(d) >> 52) & 0x7ff);
+  if (ed == 0 || ed == 0x7ff) return 1.0 / d;
   const double x = recip(d);
   return fma(x, fma(-d, x, 1.0), x);
 }

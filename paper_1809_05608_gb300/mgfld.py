@@ -22,7 +22,8 @@ N_SPECIES = 4
 
 EXPORTED = ('mgfld_eos_default', 'mgfld_workspace_bytes', 'mgfld_workspace_bytes_pair', 'mgfld_step', 'mgfld_assemble',
             'mgfld_factor_bytes', 'mgfld_factor', 'mgfld_solve', 'mgfld_status_str', 'mgfld_step_noalloc',
-            'mgfld_adjoint_workspace_bytes', 'mgfld_adjoint', 'mgfld_energy_advect', 'mgfld_stress_lapse')
+            'mgfld_adjoint_workspace_bytes', 'mgfld_adjoint', 'mgfld_energy_advect', 'mgfld_stress_lapse',
+            'mgfld_arith_check')
 NOALLOC_SCRATCH_BYTES = 64 << 20
 
 
@@ -129,12 +130,28 @@ def lib():
     L.mgfld_energy_advect.argtypes = [P(Dims), P(EadvProblem), ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
     L.mgfld_status_str.restype = ctypes.c_char_p
     L.mgfld_status_str.argtypes = [ctypes.c_int]
+    L.mgfld_arith_check.restype = ctypes.c_int
+    L.mgfld_arith_check.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]
     _lib = L
     return L
 
 
 def status_str(code: int) -> str:
     return lib().mgfld_status_str(int(code)).decode()
+
+
+def arith_check(a, b, stream=None):
+    """mgfld_arith_check on two equal-length FP64 device tensors: returns a [count, 8] device tensor
+    (library quotient, CUDA quotient, library reciprocal, CUDA reciprocal, reciprocal seed,
+    integer-pipe x < y, CUDA x < y, integer-pipe x == 0)."""
+    import torch
+    a = a.contiguous()
+    b = b.contiguous()
+    out = torch.empty((a.numel(), 8), dtype=torch.float64, device=a.device)
+    rc = lib().mgfld_arith_check(_ptr(a), _ptr(b), a.numel(), _ptr(out), _stream(stream))
+    if rc != MGFLD_OK:
+        raise MgfldError(rc, 'mgfld_arith_check')
+    return out
 
 
 class MgfldError(RuntimeError):
